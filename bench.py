@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput of the hybrid LBM / FENE-P step on GB300 (one JSON line).
+
+Workload: the D3Q19 two-component Shan-Chen FENE-P confined droplet,
+128 x 128 x 64 with the 64 axis wall-normal (NX = 128, NY = 64, NZ = 128),
+droplet R = 16 at the box centre, G = 1.5, rho 2.0 / 0.1, interface width 5,
+phi noise 1e-3 (SplitMix64 seed 1), viscoelastic droplet (f_+ feedback),
+L^2 = 100, De = 1, Ca = 0.1 (sigma = 0.09), tau_B = 1 at rho = 2.1,
+eta_A = 0.6 eta_B, eta_P = 0.4 eta_B, kappa = 1e-3.  FP32 populations and C.
+
+One bench step = one time step of the whole hot path over the lattice.
+`value` is MLUPS (1e6 node updates per second) summed over ranks, timed with
+CUDA events on the library's stream over exactly --steps steps after
+--warmup untimed steps.  The populations (152 MB per buffer) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the only other place this file
+runs oracle code) on a bounded slab of the same workload.
+Multi-GPU (torchrun): every rank runs its own replica (weak scaling, no
+collective on the data path); the max time over ranks is reported.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX, NY, NZ, RADIUS = 128, 64, 128, 16.0
+ETA_B = 2.1 / 3.0 * 0.5
+ETA_A, ETA_P, SIGMA = 0.6 * ETA_B, 0.4 * ETA_B, 0.09
+GDOT = 0.1 * SIGMA / (RADIUS * ETA_B)
+U_WALL = GDOT * NY / 2.0
+TAU_P = 1.0 * RADIUS * ETA_B / SIGMA * ETA_B / ETA_P
+WORKLOAD = ("D3Q19 two-component Shan-Chen FENE-P confined droplet R=16, 128x128x64 "
+            "(NX=128, NY=64 wall-normal, NZ=128), G=1.5, L2=100, De=1, Ca=0.1, FP32 populations and C")
+# algorithmic bytes per node update (each value read and written once per step)
+STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2 + 6 * 4 * 2 + 6 * 4 * 2   # 400
+KERNEL_NAMES = ["moments", "lattice_collide_stream", "fenep_fd"]
+# algorithmic bytes per node of each kernel class of the current three-kernel step
+KERNEL_ALGO_BYTES = {
+    "moments": 0,                                   # re-read of the populations: overhead, not algorithmic
+    "lattice_collide_stream": 2 * 19 * 4 * 2,       # populations read + written
+    "fenep_fd": 6 * 4 * 2 + 6 * 4 * 2,              # C and AB2 history read + written
+}
+MLUPS = "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1406_2686_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = []
+        smax = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_lattice():
+    from paper_1406_2686_gb300 import vefd
+    lat = vefd.Lattice(lattice=vefd.D3Q19, nx=NX, ny=NY, nz=NZ, ncomp=2, walls=1, G=1.5, eta_A=ETA_A,
+                       eta_B=ETA_B, delta=0.1)
+    lat.set_wall_shear(U_WALL)
+    lat.set_fenep(TAU_P, ETA_P, 100.0, 1e-3, 1, 1)
+    return lat
+
+
+def droplet_host_fields(torch):
+    from paper_1406_2686_gb300 import inputs
+    rA, rB = inputs.droplet_fields(NX, NY, NZ, R=RADIUS, seed=1, noise=1e-3)
+    a = torch.from_numpy(rA.astype("float32")).pin_memory()
+    b = torch.from_numpy(rB.astype("float32")).pin_memory()
+    return a, b
+
+
+def run_e2e(lat, torch, steps):
+    """End to end through the C-ABI with pinned host buffers: upload the initial
+    densities, run `steps` steps, read phi, u and C back to the host and take
+    the FP64 diagnostics; wall-clock time around all of it."""
+    import ctypes
+
+    from paper_1406_2686_gb300 import vefd
+    rA, rB = droplet_host_fields(torch)
+    outs = {f: torch.empty(vefd.vefd_field_bytes(lat.ctx, f) // 4, dtype=torch.float32).pin_memory()
+            for f in (vefd.PHI, vefd.U, vefd.C)}
+    h2d = rA.numel() * 4 + rB.numel() * 4
+    d2h = sum(t.numel() * 4 for t in outs.values()) + 16 * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vefd.vefd_init_fields(lat.ctx, ctypes.c_void_p(rA.data_ptr()), ctypes.c_void_p(rB.data_ptr()), None, None, 0)
+    lat.step(steps)
+    for f, t in outs.items():
+        vefd.vefd_read_field(lat.ctx, f, t.data_ptr(), t.numel() * 4, 0)
+    lat.diagnostics()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dt, h2d, d2h
+
+
+def cpu_baseline(budget_s=15.0):
+    """The FP64 oracle as it stands, on the host cores, on the same droplet
+    lattice: as many steps as fit in the budget (at least two)."""
+    import oracle
+    from paper_1406_2686_gb300 import inputs
+    cores = oracle.set_threads(0)
+    rA, rB = inputs.droplet_fields(NX, NY, NZ, R=RADIUS, seed=1, noise=1e-3)
+    o = oracle.Oracle(lattice=1, nx=NX, ny=NY, nz=NZ, ncomp=2, walls=1, G=1.5, eta_A=ETA_A, eta_B=ETA_B,
+                      delta=0.1, u_wall=U_WALL, tau_p=TAU_P, eta_p=ETA_P, L2=100.0, kappa=1e-3, phase=1)
+    o.init_fields(inputs.to_f32_exact(rA), inputs.to_f32_exact(rB))
+    o.step(1)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if n >= 2 and dt > budget_s:
+            break
+    N = NX * NY * NZ
+    return {"value": N * n / dt / 1e6, "unit": MLUPS, "cores": cores, "kind": "oracle",
+            "sample": "%d steps of the full %dx%dx%d droplet lattice (FP64, OpenMP over nodes)" % (n, NX, NY, NZ)}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1406_2686_gb300 import vefd
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    vefd.load(build_if_missing=True)
+    lat = make_lattice()
+    lat.init_droplet((NX - 1) / 2.0, (NY - 1) / 2.0, (NZ - 1) / 2.0, RADIUS, 2.0, 0.1, 5.0, 1, 1e-3)
+    stream = lat.stream
+    K, W = args.steps, args.warmup
+    with torch.cuda.stream(stream):
+        lat.step(W)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    lat.profile_kernels(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kms, klaunch = lat.kernel_times()
+    lat.profile_kernels(False)
+    status = lat.status()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    N = NX * NY * NZ
+    value = N * K * world / (ms / 1e3) / 1e6
+    peak, peak_kind = measured_peak()
+    # dominant kernel and its roofline
+    dom = max(range(3), key=lambda k: kms[k])
+    dname = KERNEL_NAMES[dom]
+    avg_s = kms[dom] / max(klaunch[dom], 1) / 1e3
+    algo = KERNEL_ALGO_BYTES[dname] * N
+    achieved = algo / avg_s / 1e9
+    traffic = recorded_traffic(dname)
+    roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes_per_launch": algo,
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    step_achieved = STEP_BYTES_PER_NODE * N / (ms / K / 1e3) / 1e9
+    kernels = {KERNEL_NAMES[k]: {"launches": klaunch[k], "ms_total": round(kms[k], 3),
+                                 "share": round(kms[k] / max(sum(kms), 1e-12), 4)} for k in range(3)}
+    e2e = None
+    if not args.no_e2e:
+        dt, h2d, d2h = run_e2e(lat, torch, K)
+        e2e_val = N * K / dt / 1e6
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = N * K * world / float(t.item()) / 1e6
+        e2e = {"value": round(e2e_val, 1), "unit": MLUPS, "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": d2h / K,
+               "what": "init from pinned host densities + %d steps + phi/u/C read to pinned host + diagnostics" % K}
+    line = {
+        "metric": "MLUPS & % HBM roofline", "value": round(value, 1), "unit": MLUPS, "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": round(ms / K, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "global_nodes": N * world,
+                   "l2": "inputs larger than L2 (152 MB per population buffer > 129 MB), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "step_roofline": {"achieved": round(step_achieved, 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(step_achieved / peak, 4),
+                          "algorithmic_bytes_per_node": STEP_BYTES_PER_NODE},
+        "kernels": kernels, "gpu_launches": int(sum(klaunch)), "clocks": clk, "e2e": e2e,
+        "status_bits": status, "source_sha": source_hash(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1406_2686_gb300 import inputs
+    cores = oracle.set_threads(0)
+    K, W = args.steps, args.warmup
+
+    def make(nz_s):
+        rA, rB = inputs.droplet_fields(NX, NY, nz_s, R=RADIUS, seed=1, noise=1e-3,
+                                       center=((NX - 1) / 2.0, (NY - 1) / 2.0, (nz_s - 1) / 2.0))
+        o = oracle.Oracle(lattice=1, nx=NX, ny=NY, nz=nz_s, ncomp=2, walls=1, G=1.5, eta_A=ETA_A, eta_B=ETA_B,
+                          delta=0.1, u_wall=U_WALL, tau_p=TAU_P, eta_p=ETA_P, L2=100.0, kappa=1e-3, phase=1)
+        o.init_fields(inputs.to_f32_exact(rA), inputs.to_f32_exact(rB))
+        return o
+
+    probe = make(4)
+    t0 = time.perf_counter()
+    probe.step(2)
+    per_node = (time.perf_counter() - t0) / (2 * NX * NY * 4)
+    budget = 150.0
+    nz_s = int(budget / max(K + W, 1) / per_node / (NX * NY))
+    nz_s = max(2, min(NZ, nz_s))
+    o = make(nz_s)
+    o.step(W)
+    t0 = time.perf_counter()
+    o.step(K)
+    dt = time.perf_counter() - t0
+    n = NX * NY * nz_s
+    value = n * K / dt / 1e6
+    sample = "each step: one FP64 oracle time step of a %dx%dx%d slab of the droplet workload" % (NX, NY, nz_s)
+    line = {
+        "metric": "MLUPS & % HBM roofline", "value": round(value, 3), "unit": MLUPS, "impl": "reference",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": round(dt / K * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": NX * NY * NZ, "sample_nodes": n},
+        "cpu_baseline": {"value": round(value, 3), "unit": MLUPS, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": MLUPS, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

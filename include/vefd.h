@@ -1,0 +1,173 @@
+/*
+ * vefd - GB300 (sm_103a) library for the hybrid lattice-Boltzmann / finite-
+ * difference step of viscoelastic two-component flows (A. Gupta,
+ * M. Sbragaglia, A. Scagliarini, "Hybrid Lattice Boltzmann/Finite Difference
+ * simulations of viscoelastic multicomponent flows in confined geometries",
+ * arXiv:1406.2686).
+ *
+ * One step advances, on one GPU:
+ *   - a two-component Shan-Chen lattice-Boltzmann fluid (D2Q9 or D3Q19):
+ *     moments, pseudo-potential force (Eq. SCforce), forced BGK collision
+ *     (Eq. LB with Lambda = 1/tau, equilibrium and source of Sec. 2, velocity
+ *     of Eq. equilibrium:vel), phase-dependent viscosity (Eq. smoothingvisco),
+ *     streaming with periodic x, z and half-way bounce-back on moving walls at
+ *     y = -1/2 and y = NY - 1/2 (Sec. 3.1);
+ *   - the FENE-P conformation tensor C (Eq. FENE, f(r_P) of Sec. 2) by
+ *     second-order central finite differences with an artificial diffusivity
+ *     and Adams-Bashforth 2 in time, linear extrapolation at the walls (Sec. 2);
+ *   - the polymer feedback (eta_P/tau_P) div[(f C - I) m(phi)] as a body force
+ *     shared between components by rho_sigma/rho, m = 1, f_+ or f_- (Sec. 2).
+ *
+ * Conventions for every entry point:
+ *   - every function returns a vefd_status and never aborts; on error the
+ *     context (when there is one) keeps a message for vefd_last_error;
+ *   - fields are FP32, x fastest: index = ((comp*NZ + z)*NY + y)*NX + x;
+ *     tensor components are xx xy xz yy yz zz (D3Q19) or xx xy yy zz (D2Q9);
+ *     velocities have 3 (D3Q19) or 2 (D2Q9) components;
+ *   - pointers marked "host or device" are interpreted by the on_device flag;
+ *     buffers passed in stay owned by the caller;
+ *   - work is enqueued on the context's CUDA stream; calls that return data
+ *     to the host synchronise that stream;
+ *   - a context is not thread-safe.
+ */
+#ifndef VEFD_H
+#define VEFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vefd_ctx vefd_ctx;
+
+typedef enum {
+    VEFD_OK = 0,
+    VEFD_ERR_ARG = -1,       /* bad argument or size; nothing was changed */
+    VEFD_ERR_CUDA = -2,      /* a CUDA call failed; see vefd_last_error */
+    VEFD_ERR_UNSTABLE = -3,  /* the device guard word is set (NaN, tr C >= L^2, |u| > 0.3, rho <= 0) */
+    VEFD_ERR_TIMEOUT = -4,   /* reserved for bounded device waits */
+    VEFD_ERR_STATE = -5      /* call out of order (e.g. memory not bound, fields not initialised) */
+} vefd_status;
+
+typedef enum { VEFD_D2Q9 = 0, VEFD_D3Q19 = 1 } vefd_lattice;
+
+typedef enum {
+    VEFD_RHO_A = 0,    /* 1 comp: density of component A of the current state */
+    VEFD_RHO_B = 1,    /* 1 comp: density of component B (zero for one component) */
+    VEFD_PHI = 2,      /* 1 comp: order parameter (rho_A - rho_B)/(rho_A + rho_B) (Sec. 2) */
+    VEFD_U = 3,        /* 2|3 comps: velocity of Eq. (equilibrium:vel) of the current state */
+    VEFD_C = 4,        /* 4|6 comps: conformation tensor C */
+    VEFD_SIGMA_P = 5,  /* 4|6 comps: polymer stress f(r_P) C (Eq. fluidstress) */
+    VEFD_POPS = 6,     /* ncomp*Q comps: populations f_a^sigma, order [sigma][a] */
+    VEFD_RPREV = 7,    /* 4|6 comps: right-hand side of the previous FD step (AB2 history) */
+    VEFD_G_A = 8,      /* 2|3 comps: Shan-Chen force on A of the current state (Eq. SCforce) */
+    VEFD_G_B = 9,      /* 2|3 comps: Shan-Chen force on B */
+    VEFD_F_P = 10,     /* 2|3 comps: polymer feedback force (eta_P/tau_P) div[(f C - I) m(phi)] */
+    VEFD_TAU = 11      /* 1 comp: local relaxation time (Eq. smoothingvisco) */
+} vefd_field;
+
+/* Guard bits of the device status word (sticky until vefd_clear_status). */
+enum { VEFD_ST_NAN = 1, VEFD_ST_TRACE = 2, VEFD_ST_MACH = 4, VEFD_ST_RHO = 8 };
+
+/* Lattice and two-component fluid (Sec. 2). */
+typedef struct {
+    int lattice;         /* vefd_lattice */
+    int nx, ny, nz;      /* nodes; D2Q9 needs nz == 1; walls need ny >= 3 */
+    int ncomp;           /* 1 or 2 components */
+    int walls;           /* 1: walls at y = -1/2 and NY - 1/2; 0: periodic in y */
+    double G;            /* Shan-Chen coupling (Eq. SCforce); ignored for one component */
+    double eta_A;        /* shear viscosity of the A-rich phase (Eq. smoothingvisco) */
+    double eta_B;        /* shear viscosity of the B-rich phase */
+    double delta;        /* smoothing width of f_+-(phi), Eq. (smoothingvisco); paper: 0.1 */
+    int external_memory; /* 1: the caller binds device memory with vefd_bind_device_memory */
+} vefd_config;
+
+/* Creates a context on the current CUDA device; `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Validates cfg; allocates device buffers
+ * unless cfg->external_memory.  Errors: VEFD_ERR_ARG, VEFD_ERR_CUDA. */
+vefd_status vefd_create(const vefd_config *cfg, void *stream, vefd_ctx **out);
+/* Bytes of device memory a context with this config needs. */
+vefd_status vefd_required_bytes(const vefd_config *cfg, size_t *bytes);
+/* Binds caller-owned device memory (>= vefd_required_bytes, 256-byte
+ * aligned) to a context created with external_memory = 1.  The memory must
+ * outlive the context.  Errors: VEFD_ERR_ARG, VEFD_ERR_STATE (already bound). */
+vefd_status vefd_bind_device_memory(vefd_ctx *ctx, void *dev_ptr, size_t bytes);
+/* Frees owned buffers (not bound ones) after synchronising the stream. */
+void vefd_destroy(vefd_ctx *ctx);
+vefd_status vefd_set_stream(vefd_ctx *ctx, void *stream);
+
+/* Wall speed U: +U at y = -1/2, -U at y = NY - 1/2, moving-wall bounce-back
+ * (Sec. 3.1: u_x(y=0) = -u_x(y=H) = U_w).  |U| < 0.1. */
+vefd_status vefd_set_wall_shear(vefd_ctx *ctx, double u_wall);
+/* External body-force density, shared between components by rho_sigma/rho. */
+vefd_status vefd_set_body_force(vefd_ctx *ctx, double fx, double fy, double fz);
+/* FENE-P parameters (Sec. 2): relaxation time tau_P > 0, viscosity eta_P >= 0,
+ * maximum extension squared L2 > 3, artificial diffusivity kappa in
+ * [0, 1/(2 dim)), feedback modulation phase: 0 -> 1, +1 -> f_+(phi),
+ * -1 -> f_-(phi), and fd_on: 0 freezes C (pure lattice-Boltzmann runs). */
+vefd_status vefd_set_fenep(vefd_ctx *ctx, double tau_p, double eta_p, double L2, double kappa, int phase,
+                           int fd_on);
+
+/* Initial state: populations at equilibrium E(rho_sigma, u), C = C0 (or I
+ * when C0 is NULL), AB2 history cleared (the next step is forward Euler).
+ * rho_A (N), rho_B (N, ignored for one component), u (dim*N or NULL for
+ * rest), C0 (nc*N or NULL); host or device FP32 per on_device.
+ * Also resets the step counter and the status word. */
+vefd_status vefd_init_fields(vefd_ctx *ctx, const float *rho_A, const float *rho_B, const float *u,
+                             const float *C0, int on_device);
+/* Convenience droplet initialisation computed on the host: rho_A = rho_out +
+ * (rho_in - rho_out)(1 + tanh(2 (R - r)/width))/2 about (cx, cy, cz), rho_B =
+ * rho_in + rho_out - rho_A, order-parameter noise phi_amp * U[-1, 1) from
+ * SplitMix64(seed) at node counter i, u = 0, C = I. */
+vefd_status vefd_init_droplet(vefd_ctx *ctx, double cx, double cy, double cz, double R, double rho_in,
+                              double rho_out, double width, uint64_t seed, double phi_amp);
+
+/* Overwrites a stored field: VEFD_POPS (absolute populations), VEFD_C, or
+ * VEFD_RPREV (also marks the history valid).  bytes must equal the field size. */
+vefd_status vefd_write_field(vefd_ctx *ctx, vefd_field field, const void *src, size_t bytes, int src_on_device);
+/* Enqueues nsteps >= 0 time steps on the context stream (asynchronous). */
+vefd_status vefd_step(vefd_ctx *ctx, int64_t nsteps);
+/* Copies a field of the current state to dst (host or device); derived
+ * fields (rho, phi, u, sigma_P, forces, tau) are computed on the device
+ * first.  Host destinations synchronise the stream. */
+vefd_status vefd_read_field(vefd_ctx *ctx, vefd_field field, void *dst, size_t bytes, int dst_on_device);
+/* Field size in bytes. */
+vefd_status vefd_field_bytes(const vefd_ctx *ctx, vefd_field field, size_t *bytes);
+
+/* FP64 reductions of the current state (synchronises), out[16]:
+ *  0 mass_A  1 mass_B  2..4 total momentum sum rho u  5 <sigma_P,xy>
+ *  6 <sigma_P,xx - sigma_P,yy>  7 max tr C / L^2  8 max |u|
+ *  9 droplet area (phi > 0) in the plane z = NZ/2  10 deformation D = (a-b)/(a+b)
+ *  11 orientation angle theta of the major axis from +x (Sec. 4.1)
+ *  12, 13 droplet centroid x, y in that plane  14 droplet volume (phi > 0)
+ *  15 <tr sigma_P> - 3 */
+vefd_status vefd_diagnostics(vefd_ctx *ctx, double out[16]);
+/* Reads the guard word (synchronises); returns VEFD_ERR_UNSTABLE when any bit is set. */
+vefd_status vefd_get_status(vefd_ctx *ctx, uint32_t *bits);
+vefd_status vefd_clear_status(vefd_ctx *ctx);
+vefd_status vefd_steps_done(const vefd_ctx *ctx, int64_t *n);
+/* Raw binary checkpoint of populations, C, AB2 history, counters and
+ * parameters; restoring into a context of the same config continues
+ * bit-identically. */
+vefd_status vefd_checkpoint(vefd_ctx *ctx, const char *path);
+vefd_status vefd_restore(vefd_ctx *ctx, const char *path);
+/* Message of the last error of this context ("" when none). */
+const char *vefd_last_error(const vefd_ctx *ctx);
+/* Device kernels one time step enqueues. */
+vefd_status vefd_kernels_per_step(const vefd_ctx *ctx, int *n);
+/* Per-kernel timing of vefd_step: when on, every launch of a step is
+ * bracketed by CUDA events on the context stream (turning it on clears the
+ * record).  Tracing aid, not a hot-path requirement. */
+vefd_status vefd_profile_kernels(vefd_ctx *ctx, int on);
+/* Synchronises and returns, per kernel class (0 moments, 1 lattice
+ * collide-stream, 2 FENE-P finite differences), the summed device time in
+ * milliseconds and the number of timed launches since profiling was turned
+ * on or last read; then clears the record. */
+vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,155 @@
+// Finite-difference FENE-P update of the conformation tensor (Eq. FENE of
+// Gupta, Sbragaglia & Scagliarini, with the artificial diffusivity and the
+// time integration described at the end of Sec. 2):
+//   R = -(u.grad)C + C.grad u + (grad u)^T.C - (f(r_P) C - I)/tau_P + kappa lap C,
+//   (grad u)_ij = d_i u_j, f(r_P) = (L^2 - 3)/(L^2 - tr C),
+//   C^{n+1} = C^n + 3/2 R^n - 1/2 R^{n-1}   (forward Euler without history).
+// Second-order central differences, periodic in x and z; at walls the ghost
+// row is the linear extrapolation v(-1) = 2 v(0) - v(1), which makes the
+// first derivative one-sided and the second derivative vanish.
+// Stored variable: Ct = C - I, so (f C - I) = f Ct + (f - 1) I with
+// f - 1 = tr Ct / (L^2 - 3 - tr Ct), evaluated without cancellation.
+#include "vefd_internal.cuh"
+
+namespace vefd {
+
+namespace {
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+template <int NC>
+__device__ __forceinline__ constexpr int tidx(int i, int j) {
+    // stored component of (i, j), -1 when identically zero (D2Q9 xz, yz)
+    if (NC == 6) {
+        return (i == 0) ? j : (i == 1 ? (j == 0 ? 1 : (j == 1 ? 3 : 4)) : (j == 0 ? 2 : (j == 1 ? 4 : 5)));
+    } else {
+        return (i == 0) ? (j == 0 ? 0 : (j == 1 ? 1 : -1))
+             : (i == 1 ? (j == 0 ? 1 : (j == 1 ? 2 : -1)) : (j == 2 ? 3 : -1));
+    }
+}
+
+template <int NC>
+__device__ __forceinline__ constexpr bool is_diag(int k) {
+    return NC == 6 ? (k == 0 || k == 3 || k == 5) : (k == 0 || k == 2 || k == 3);
+}
+
+template <int NC>
+__device__ __forceinline__ constexpr int row_of(int k) {
+    return NC == 6 ? (k <= 2 ? 0 : (k <= 4 ? 1 : 2)) : (k <= 1 ? 0 : (k == 2 ? 1 : 2));
+}
+
+template <int NC>
+__device__ __forceinline__ constexpr int col_of(int k) {
+    return NC == 6 ? (k == 0 ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : (k == 3 ? 1 : 2)))) : (k == 0 ? 0 : (k <= 2 ? 1 : 2));
+}
+
+template <int D, int NC>
+__global__ void __launch_bounds__(128) k_fenep(const float* __restrict__ Ct, float* __restrict__ Cout,
+                                               float* __restrict__ R, const float* __restrict__ u,
+                                               unsigned* __restrict__ status, StepParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const long long N = p.N;
+    const long long i = ((long long)z * ny + y) * nx + x;
+    const long long ixm = i - x + wrap1(x - 1, nx), ixp = i - x + wrap1(x + 1, nx);
+    // y neighbours and the stencil weights of the first and second derivative
+    long long iym, iyp;
+    float hy1 = 0.5f, hy2 = 1.0f;  // d_y v = hy1 (v+ - v-); d_yy v = hy2 (v+ - 2 v + v-)
+    if (p.walls && y == 0) {
+        iym = i;
+        iyp = i + nx;
+        hy1 = 1.0f;
+        hy2 = 0.0f;
+    } else if (p.walls && y == ny - 1) {
+        iym = i - nx;
+        iyp = i;
+        hy1 = 1.0f;
+        hy2 = 0.0f;
+    } else {
+        iym = ((long long)z * ny + wrap1(y - 1, ny)) * nx + x;
+        iyp = ((long long)z * ny + wrap1(y + 1, ny)) * nx + x;
+    }
+    long long izm = i, izp = i;
+    if (D == 3) {
+        izm = ((long long)wrap1(z - 1, nz) * ny + y) * nx + x;
+        izp = ((long long)wrap1(z + 1, nz) * ny + y) * nx + x;
+    }
+
+    // velocity gradient Gu[a][b] = d_a u_b and the local velocity
+    float Gu[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float uu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        const float* ub = u + b * N;
+        uu[b] = __ldg(ub + i);
+        Gu[0][b] = 0.5f * (__ldg(ub + ixp) - __ldg(ub + ixm));
+        Gu[1][b] = hy1 * (__ldg(ub + iyp) - __ldg(ub + iym));
+        if (D == 3) Gu[2][b] = 0.5f * (__ldg(ub + izp) - __ldg(ub + izm));
+    }
+
+    float c[NC], adv[NC], lap[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const float* ck = Ct + k * N;
+        const float c0 = __ldg(ck + i);
+        const float cxm = __ldg(ck + ixm), cxp = __ldg(ck + ixp);
+        const float cym = __ldg(ck + iym), cyp = __ldg(ck + iyp);
+        c[k] = c0;
+        float a = uu[0] * 0.5f * (cxp - cxm) + uu[1] * hy1 * (cyp - cym);
+        float l = (cxp - 2.0f * c0 + cxm) + hy2 * (cyp - 2.0f * c0 + cym);
+        if (D == 3) {
+            const float czm = __ldg(ck + izm), czp = __ldg(ck + izp);
+            a += uu[2] * 0.5f * (czp - czm);
+            l += czp - 2.0f * c0 + czm;
+        }
+        adv[k] = a;
+        lap[k] = l;
+    }
+    float tr = NC == 6 ? c[0] + c[3] + c[5] : c[0] + c[2] + c[3];
+    const float fm1 = tr / (p.L2m3 - tr);
+    const float f = 1.0f + fm1;
+
+    // full C = Ct + I as a 3x3 matrix
+    float Cm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int k = tidx<NC>(a, b);
+            Cm[a][b] = (k < 0 ? 0.0f : c[k]) + (a == b ? 1.0f : 0.0f);
+        }
+
+    float trn = 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int a = row_of<NC>(k), b = col_of<NC>(k);
+        float up = 0.0f;
+#pragma unroll
+        for (int e = 0; e < D; ++e) up += Cm[a][e] * Gu[e][b] + Gu[e][a] * Cm[e][b];
+        const float relax = (f * c[k] + (is_diag<NC>(k) ? fm1 : 0.0f)) * p.inv_tau_p;
+        const float Rk = -adv[k] + up - relax + p.kappa * lap[k];
+        const float inc = p.have_prev ? 1.5f * Rk - 0.5f * R[k * N + i] : Rk;
+        const float cn = c[k] + inc;
+        Cout[k * N + i] = cn;
+        R[k * N + i] = Rk;
+        if (is_diag<NC>(k)) trn += cn;
+        bad |= isnan(cn);
+    }
+    if (bad || isnan(tr)) atomicOr(status, kStNan);
+    else if (trn + 3.0f >= p.L2m3 + 3.0f || tr + 3.0f >= p.L2m3 + 3.0f) atomicOr(status, kStTrace);
+}
+
+}  // namespace
+
+cudaError_t launch_fenep(int lattice, const StepParams& p, const StepBufs& b, cudaStream_t s) {
+    dim3 blk(32, 4, 1), grd((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz);
+    if (lattice == 1) k_fenep<3, 6><<<grd, blk, 0, s>>>(b.Cin, b.Cout, b.R, b.u, b.status, p);
+    else k_fenep<2, 4><<<grd, blk, 0, s>>>(b.Cin, b.Cout, b.R, b.u, b.status, p);
+    return cudaGetLastError();
+}
+
+}  // namespace vefd

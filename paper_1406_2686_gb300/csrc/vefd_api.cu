@@ -1,0 +1,751 @@
+// C-ABI of libvefd (declared in include/vefd.h): context, memory, parameters,
+// field I/O, time stepping, diagnostics and checkpoints of the hybrid
+// lattice-Boltzmann / finite-difference viscoelastic step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vefd.h"
+#include "vefd_internal.cuh"
+
+using namespace vefd;
+
+struct vefd_ctx {
+    vefd_config cfg;
+    int Q = 0, D = 0, NC = 0;
+    long long N = 0;
+    cudaStream_t stream = nullptr;
+    // physical parameters
+    double u_wall = 0.0, fext[3] = {0.0, 0.0, 0.0};
+    double tau_p = 1.0, eta_p = 0.0, L2 = 100.0, kappa = 0.0;
+    int phase = 0, fd_on = 1;
+    double rho_ref[2] = {1.0, 1.0};
+    // time-level state
+    int have_prev = 0;
+    int64_t steps = 0;
+    int initialised = 0;
+    int cur = 0, ccur = 0;
+    // memory
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    bool owned = false;
+    float* f[2] = {nullptr, nullptr};
+    float* drho = nullptr;
+    float* u = nullptr;
+    float* C[2] = {nullptr, nullptr};
+    float* R = nullptr;
+    float* dbg = nullptr;
+    unsigned* status = nullptr;
+    double* diag_part = nullptr;
+    double* diag_out = nullptr;
+    std::string err;
+    // optional per-kernel timing of vefd_step (events on the context stream)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_used = 0;
+};
+
+namespace {
+
+vefd_status fail(vefd_ctx* c, vefd_status st, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+#define VEFD_CUDA(ctx, call)                                                                      \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail((ctx), VEFD_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                      \
+    } while (0)
+
+int lattice_Q(int lat) { return lat == VEFD_D3Q19 ? 19 : 9; }
+int lattice_D(int lat) { return lat == VEFD_D3Q19 ? 3 : 2; }
+int lattice_NC(int lat) { return lat == VEFD_D3Q19 ? 6 : 4; }
+
+bool config_ok(const vefd_config* c, const char** why) {
+    if (!c) return *why = "config is NULL", false;
+    if (c->lattice != VEFD_D2Q9 && c->lattice != VEFD_D3Q19) return *why = "unknown lattice", false;
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) return *why = "sizes must be >= 1", false;
+    if (c->lattice == VEFD_D2Q9 && c->nz != 1) return *why = "D2Q9 needs nz == 1", false;
+    if (c->walls && c->ny < 3) return *why = "walls need ny >= 3", false;
+    if (c->ncomp != 1 && c->ncomp != 2) return *why = "ncomp must be 1 or 2", false;
+    if (!(c->eta_A > 0.0) || !(c->eta_B > 0.0) || !std::isfinite(c->eta_A) || !std::isfinite(c->eta_B))
+        return *why = "viscosities must be positive", false;
+    if (!(c->delta > 0.0) || !std::isfinite(c->delta)) return *why = "delta must be positive", false;
+    if (!(c->G >= 0.0) || !std::isfinite(c->G)) return *why = "G must be finite and >= 0", false;
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    if (N > (1LL << 31) / 40) return *why = "lattice too large for 32-bit plane offsets", false;
+    return true;
+}
+
+struct Layout {
+    size_t f0, f1, drho, u, c0, c1, r, dbg, status, dpart, dout, total;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout layout_of(const vefd_config* c) {
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    const size_t Q = lattice_Q(c->lattice), NC = lattice_NC(c->lattice);
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.f0 = take(sizeof(float) * c->ncomp * Q * N);
+    L.f1 = take(sizeof(float) * c->ncomp * Q * N);
+    L.drho = take(sizeof(float) * 2 * N);
+    L.u = take(sizeof(float) * 3 * N);
+    L.c0 = take(sizeof(float) * NC * N);
+    L.c1 = take(sizeof(float) * NC * N);
+    L.r = take(sizeof(float) * NC * N);
+    L.dbg = take(sizeof(float) * 10 * N);
+    L.status = take(256);
+    L.dpart = take(sizeof(double) * kDiagBlocks * kDiagVals);
+    L.dout = take(sizeof(double) * kDiagVals);
+    L.total = o;
+    return L;
+}
+
+void carve(vefd_ctx* c) {
+    const Layout L = layout_of(&c->cfg);
+    char* b = (char*)c->mem;
+    c->f[0] = (float*)(b + L.f0);
+    c->f[1] = (float*)(b + L.f1);
+    c->drho = (float*)(b + L.drho);
+    c->u = (float*)(b + L.u);
+    c->C[0] = (float*)(b + L.c0);
+    c->C[1] = (float*)(b + L.c1);
+    c->R = (float*)(b + L.r);
+    c->dbg = (float*)(b + L.dbg);
+    c->status = (unsigned*)(b + L.status);
+    c->diag_part = (double*)(b + L.dpart);
+    c->diag_out = (double*)(b + L.dout);
+}
+
+StepParams params_of(const vefd_ctx* c) {
+    StepParams p;
+    p.nx = c->cfg.nx;
+    p.ny = c->cfg.ny;
+    p.nz = c->cfg.nz;
+    p.walls = c->cfg.walls;
+    p.N = c->N;
+    p.G = (float)c->cfg.G;
+    p.eta_A = (float)c->cfg.eta_A;
+    p.eta_B = (float)c->cfg.eta_B;
+    p.inv_delta = (float)(1.0 / c->cfg.delta);
+    p.u_wall = (float)c->u_wall;
+    for (int k = 0; k < 3; ++k) p.fext[k] = (float)c->fext[k];
+    if (c->D == 2) p.fext[2] = 0.0f;
+    p.inv_tau_p = (float)(1.0 / c->tau_p);
+    p.feedback = (float)(c->eta_p / c->tau_p);
+    p.L2m3 = (float)(c->L2 - 3.0);
+    p.kappa = (float)c->kappa;
+    p.phase = c->phase;
+    p.have_prev = c->have_prev;
+    p.rho_ref[0] = (float)c->rho_ref[0];
+    p.rho_ref[1] = (float)c->rho_ref[1];
+    return p;
+}
+
+StepBufs bufs_of(vefd_ctx* c) {
+    StepBufs b;
+    b.fin = c->f[c->cur];
+    b.fout = c->f[1 - c->cur];
+    b.drho = c->drho;
+    b.u = c->u;
+    b.Cin = c->C[c->ccur];
+    b.Cout = c->C[1 - c->ccur];
+    b.R = c->R;
+    b.status = c->status;
+    b.dbg = nullptr;
+    return b;
+}
+
+vefd_status need_ready(vefd_ctx* c) {
+    if (!c) return VEFD_ERR_ARG;
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    if (!c->initialised) return fail(c, VEFD_ERR_STATE, "fields are not initialised");
+    return VEFD_OK;
+}
+
+size_t field_planes(const vefd_ctx* c, int field) {
+    switch (field) {
+    case VEFD_RHO_A: case VEFD_RHO_B: case VEFD_PHI: case VEFD_TAU: return 1;
+    case VEFD_U: case VEFD_G_A: case VEFD_G_B: case VEFD_F_P: return (size_t)c->D;
+    case VEFD_C: case VEFD_SIGMA_P: case VEFD_RPREV: return (size_t)c->NC;
+    case VEFD_POPS: return (size_t)c->cfg.ncomp * c->Q;
+    default: return 0;
+    }
+}
+
+// moments and the macroscopic pass (velocity, optionally forces and tau) of the current state
+vefd_status macro_pass(vefd_ctx* c, bool with_dbg) {
+    StepParams p = params_of(c);
+    StepBufs b = bufs_of(c);
+    b.dbg = with_dbg ? c->dbg : nullptr;
+    VEFD_CUDA(c, launch_moments(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+    VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, false, p, b, c->stream));
+    return VEFD_OK;
+}
+
+vefd_status copy_out(vefd_ctx* c, void* dst, const void* src, size_t bytes, int dst_on_device) {
+    VEFD_CUDA(c, cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+    if (!dst_on_device) VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VEFD_OK;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): output for counter i of stream seed
+uint64_t splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Records an event pair around one launch when kernel timing is on.
+struct ProfScope {
+    vefd_ctx* c;
+    size_t slot;
+    bool ok;
+    ProfScope(vefd_ctx* ctx, int kind) : c(ctx), slot(0), ok(false) {
+        if (!c->prof_on) return;
+        if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
+            for (int k = 0; k < 256; ++k) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                c->prof_ev.push_back(e);
+            }
+        }
+        slot = c->prof_used++;
+        if (c->prof_kind.size() < c->prof_used) c->prof_kind.resize(c->prof_used);
+        c->prof_kind[slot] = kind;
+        ok = cudaEventRecord(c->prof_ev[2 * slot], c->stream) == cudaSuccess;
+    }
+    ~ProfScope() {
+        if (ok) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+vefd_status vefd_required_bytes(const vefd_config* cfg, size_t* bytes) {
+    const char* why = nullptr;
+    if (!bytes || !config_ok(cfg, &why)) return VEFD_ERR_ARG;
+    *bytes = layout_of(cfg).total;
+    return VEFD_OK;
+}
+
+vefd_status vefd_create(const vefd_config* cfg, void* stream, vefd_ctx** out) {
+    const char* why = nullptr;
+    if (!out) return VEFD_ERR_ARG;
+    *out = nullptr;
+    if (!config_ok(cfg, &why)) return VEFD_ERR_ARG;
+    vefd_ctx* c = new (std::nothrow) vefd_ctx();
+    if (!c) return VEFD_ERR_ARG;
+    c->cfg = *cfg;
+    c->Q = lattice_Q(cfg->lattice);
+    c->D = lattice_D(cfg->lattice);
+    c->NC = lattice_NC(cfg->lattice);
+    c->N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    c->stream = (cudaStream_t)stream;
+    if (!cfg->external_memory) {
+        const size_t bytes = layout_of(cfg).total;
+        cudaError_t e = cudaMalloc(&c->mem, bytes);
+        if (e != cudaSuccess) {
+            delete c;
+            return VEFD_ERR_CUDA;
+        }
+        c->mem_bytes = bytes;
+        c->owned = true;
+        carve(c);
+        if (cudaMemsetAsync(c->mem, 0, bytes, c->stream) != cudaSuccess) {
+            cudaFree(c->mem);
+            delete c;
+            return VEFD_ERR_CUDA;
+        }
+    }
+    *out = c;
+    return VEFD_OK;
+}
+
+vefd_status vefd_bind_device_memory(vefd_ctx* c, void* dev_ptr, size_t bytes) {
+    if (!c || !dev_ptr) return fail(c, VEFD_ERR_ARG, "NULL argument");
+    if (c->mem) return fail(c, VEFD_ERR_STATE, "memory already bound");
+    if (((uintptr_t)dev_ptr & 255u) != 0) return fail(c, VEFD_ERR_ARG, "device memory must be 256-byte aligned");
+    const size_t need = layout_of(&c->cfg).total;
+    if (bytes < need) return fail(c, VEFD_ERR_ARG, "need %zu bytes, got %zu", need, bytes);
+    c->mem = dev_ptr;
+    c->mem_bytes = bytes;
+    c->owned = false;
+    carve(c);
+    VEFD_CUDA(c, cudaMemsetAsync(c->mem, 0, need, c->stream));
+    return VEFD_OK;
+}
+
+void vefd_destroy(vefd_ctx* c) {
+    if (!c) return;
+    if (c->stream || c->mem) cudaStreamSynchronize(c->stream);
+    if (c->owned && c->mem) cudaFree(c->mem);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    delete c;
+}
+
+vefd_status vefd_set_stream(vefd_ctx* c, void* stream) {
+    if (!c) return VEFD_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return VEFD_OK;
+}
+
+vefd_status vefd_set_wall_shear(vefd_ctx* c, double u_wall) {
+    if (!c) return VEFD_ERR_ARG;
+    if (!(std::fabs(u_wall) < 0.1)) return fail(c, VEFD_ERR_ARG, "|u_wall| must be < 0.1 (lattice Mach limit)");
+    c->u_wall = u_wall;
+    return VEFD_OK;
+}
+
+vefd_status vefd_set_body_force(vefd_ctx* c, double fx, double fy, double fz) {
+    if (!c) return VEFD_ERR_ARG;
+    if (!std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(fz))
+        return fail(c, VEFD_ERR_ARG, "body force must be finite");
+    c->fext[0] = fx;
+    c->fext[1] = fy;
+    c->fext[2] = fz;
+    return VEFD_OK;
+}
+
+vefd_status vefd_set_fenep(vefd_ctx* c, double tau_p, double eta_p, double L2, double kappa, int phase, int fd_on) {
+    if (!c) return VEFD_ERR_ARG;
+    if (!(tau_p > 0.0) || !std::isfinite(tau_p)) return fail(c, VEFD_ERR_ARG, "tau_p must be > 0");
+    if (!(eta_p >= 0.0) || !std::isfinite(eta_p)) return fail(c, VEFD_ERR_ARG, "eta_p must be >= 0");
+    if (!(L2 > 3.0)) return fail(c, VEFD_ERR_ARG, "L2 must be > 3");
+    if (!(kappa >= 0.0) || !(kappa < 0.5 / c->D)) return fail(c, VEFD_ERR_ARG, "kappa must be in [0, 1/(2 dim))");
+    if (phase < -1 || phase > 1) return fail(c, VEFD_ERR_ARG, "phase must be -1, 0 or 1");
+    c->tau_p = tau_p;
+    c->eta_p = eta_p;
+    c->L2 = L2;
+    c->kappa = kappa;
+    c->phase = phase;
+    c->fd_on = fd_on ? 1 : 0;
+    return VEFD_OK;
+}
+
+vefd_status vefd_field_bytes(const vefd_ctx* c, vefd_field field, size_t* bytes) {
+    if (!c || !bytes) return VEFD_ERR_ARG;
+    const size_t planes = field_planes(c, field);
+    if (!planes) return VEFD_ERR_ARG;
+    *bytes = planes * (size_t)c->N * sizeof(float);
+    return VEFD_OK;
+}
+
+vefd_status vefd_init_fields(vefd_ctx* c, const float* rho_A, const float* rho_B, const float* u, const float* C0,
+                             int on_device) {
+    if (!c || !rho_A || (c->cfg.ncomp == 2 && !rho_B)) return fail(c, VEFD_ERR_ARG, "density fields missing");
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    const long long N = c->N;
+    const size_t plane = sizeof(float) * (size_t)N;
+    // reference densities: domain means, so that the stored deviations are small
+    std::vector<float> host;
+    for (int s = 0; s < c->cfg.ncomp; ++s) {
+        const float* src = s == 0 ? rho_A : rho_B;
+        const float* h = src;
+        if (on_device) {
+            host.resize((size_t)N);
+            VEFD_CUDA(c, cudaMemcpyAsync(host.data(), src, plane, cudaMemcpyDeviceToHost, c->stream));
+            VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+            h = host.data();
+        }
+        double sum = 0.0;
+        for (long long i = 0; i < N; ++i) {
+            if (!std::isfinite(h[i]) || h[i] < 0.0f) return fail(c, VEFD_ERR_ARG, "densities must be finite and >= 0");
+            sum += h[i];
+        }
+        c->rho_ref[s] = (double)(float)(sum / (double)N);
+    }
+    if (c->cfg.ncomp == 1) c->rho_ref[1] = 0.0;
+    // stage the inputs in the second population buffer
+    c->cur = 0;
+    c->ccur = 0;
+    float* st = c->f[1];
+    float* sA = st;
+    float* sB = st + N;
+    float* sU = st + 2 * N;
+    float* sC = st + 5 * N;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    VEFD_CUDA(c, cudaMemcpyAsync(sA, rho_A, plane, kind, c->stream));
+    if (c->cfg.ncomp == 2) VEFD_CUDA(c, cudaMemcpyAsync(sB, rho_B, plane, kind, c->stream));
+    if (u) VEFD_CUDA(c, cudaMemcpyAsync(sU, u, plane * c->D, kind, c->stream));
+    if (C0) VEFD_CUDA(c, cudaMemcpyAsync(sC, C0, plane * c->NC, kind, c->stream));
+    StepParams p = params_of(c);
+    VEFD_CUDA(c, launch_init_equilibrium(c->cfg.lattice, c->cfg.ncomp, p, sA, sB, u ? sU : nullptr, c->f[0],
+                                         c->stream));
+    if (C0) VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, sC, c->C[0], N, -1.0f, c->stream));
+    else VEFD_CUDA(c, cudaMemsetAsync(c->C[0], 0, plane * c->NC, c->stream));
+    VEFD_CUDA(c, cudaMemsetAsync(c->R, 0, plane * c->NC, c->stream));
+    VEFD_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_prev = 0;
+    c->steps = 0;
+    c->initialised = 1;
+    return VEFD_OK;
+}
+
+vefd_status vefd_init_droplet(vefd_ctx* c, double cx, double cy, double cz, double R, double rho_in, double rho_out,
+                              double width, uint64_t seed, double phi_amp) {
+    if (!c) return VEFD_ERR_ARG;
+    if (c->cfg.ncomp != 2) return fail(c, VEFD_ERR_ARG, "a droplet needs two components");
+    if (!(R > 0.0) || !(width > 0.0) || !(rho_in >= 0.0) || !(rho_out >= 0.0))
+        return fail(c, VEFD_ERR_ARG, "bad droplet parameters");
+    const long long N = c->N;
+    std::vector<float> rA((size_t)N), rB((size_t)N);
+    const double tot = rho_in + rho_out;
+    long long i = 0;
+    for (int z = 0; z < c->cfg.nz; ++z)
+        for (int y = 0; y < c->cfg.ny; ++y)
+            for (int x = 0; x < c->cfg.nx; ++x, ++i) {
+                const double dx = x - cx, dy = y - cy, dz = z - cz;
+                const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+                double a = rho_out + (rho_in - rho_out) * 0.5 * (1.0 + std::tanh(2.0 * (R - r) / width));
+                double b = tot - a;
+                if (phi_amp != 0.0) {
+                    const double uni = (double)(splitmix64(seed, (uint64_t)i) >> 11) * (1.0 / 4503599627370496.0) - 1.0;
+                    const double dphi = phi_amp * uni;
+                    a += 0.5 * tot * dphi;
+                    b -= 0.5 * tot * dphi;
+                }
+                rA[(size_t)i] = (float)a;
+                rB[(size_t)i] = (float)b;
+            }
+    return vefd_init_fields(c, rA.data(), rB.data(), nullptr, nullptr, 0);
+}
+
+vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, size_t bytes, int src_on_device) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (!src) return fail(c, VEFD_ERR_ARG, "NULL source");
+    size_t need = 0;
+    if (vefd_field_bytes(c, field, &need) != VEFD_OK) return fail(c, VEFD_ERR_ARG, "unknown field");
+    if (bytes != need) return fail(c, VEFD_ERR_ARG, "field needs %zu bytes, got %zu", need, bytes);
+    const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    float* stg = c->f[1 - c->cur];
+    StepParams p = params_of(c);
+    switch (field) {
+    case VEFD_POPS:
+        VEFD_CUDA(c, cudaMemcpyAsync(stg, src, bytes, kind, c->stream));
+        VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, stg, c->f[c->cur], 0, c->stream));
+        break;
+    case VEFD_C:
+        VEFD_CUDA(c, cudaMemcpyAsync(stg, src, bytes, kind, c->stream));
+        VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, stg, c->C[c->ccur], c->N, -1.0f, c->stream));
+        break;
+    case VEFD_RPREV:
+        VEFD_CUDA(c, cudaMemcpyAsync(c->R, src, bytes, kind, c->stream));
+        c->have_prev = 1;
+        break;
+    default:
+        return fail(c, VEFD_ERR_ARG, "field %d cannot be written", (int)field);
+    }
+    if (!src_on_device) VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VEFD_OK;
+}
+
+vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (nsteps < 0) return fail(c, VEFD_ERR_ARG, "nsteps must be >= 0");
+    for (int64_t n = 0; n < nsteps; ++n) {
+        StepParams p = params_of(c);
+        StepBufs b = bufs_of(c);
+        {
+            ProfScope ps(c, 0);
+            VEFD_CUDA(c, launch_moments(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+        }
+        {
+            ProfScope ps(c, 1);
+            VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, true, p, b, c->stream));
+        }
+        if (c->fd_on) {
+            {
+                ProfScope ps(c, 2);
+                VEFD_CUDA(c, launch_fenep(c->cfg.lattice, p, b, c->stream));
+            }
+            c->ccur ^= 1;
+            c->have_prev = 1;
+        }
+        c->cur ^= 1;
+        c->steps++;
+    }
+    return VEFD_OK;
+}
+
+vefd_status vefd_read_field(vefd_ctx* c, vefd_field field, void* dst, size_t bytes, int dst_on_device) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (!dst) return fail(c, VEFD_ERR_ARG, "NULL destination");
+    size_t need = 0;
+    if (vefd_field_bytes(c, field, &need) != VEFD_OK) return fail(c, VEFD_ERR_ARG, "unknown field");
+    if (bytes != need) return fail(c, VEFD_ERR_ARG, "field needs %zu bytes, got %zu", need, bytes);
+    float* stg = c->f[1 - c->cur];
+    const long long N = c->N;
+    StepParams p = params_of(c);
+    switch (field) {
+    case VEFD_POPS:
+        VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], stg, 1, c->stream));
+        return copy_out(c, dst, stg, bytes, dst_on_device);
+    case VEFD_C:
+        VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, c->C[c->ccur], stg, N, 1.0f, c->stream));
+        return copy_out(c, dst, stg, bytes, dst_on_device);
+    case VEFD_RPREV:
+        return copy_out(c, dst, c->R, bytes, dst_on_device);
+    case VEFD_SIGMA_P:
+        VEFD_CUDA(c, launch_derived(c->cfg.lattice, c->cfg.ncomp, 5, p, c->drho, c->C[c->ccur], stg, c->stream));
+        return copy_out(c, dst, stg, bytes, dst_on_device);
+    case VEFD_RHO_A:
+    case VEFD_RHO_B:
+    case VEFD_PHI: {
+        StepBufs b = bufs_of(c);
+        VEFD_CUDA(c, launch_moments(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+        VEFD_CUDA(c, launch_derived(c->cfg.lattice, c->cfg.ncomp, (int)field, p, c->drho, c->C[c->ccur], stg,
+                                    c->stream));
+        return copy_out(c, dst, stg, bytes, dst_on_device);
+    }
+    case VEFD_U:
+        st = macro_pass(c, false);
+        if (st != VEFD_OK) return st;
+        return copy_out(c, dst, c->u, bytes, dst_on_device);
+    case VEFD_G_A:
+    case VEFD_G_B:
+    case VEFD_F_P:
+    case VEFD_TAU: {
+        st = macro_pass(c, true);
+        if (st != VEFD_OK) return st;
+        const int plane0 = field == VEFD_G_A ? 0 : (field == VEFD_G_B ? 3 : (field == VEFD_F_P ? 6 : 9));
+        return copy_out(c, dst, c->dbg + (size_t)plane0 * N, bytes, dst_on_device);
+    }
+    default:
+        return fail(c, VEFD_ERR_ARG, "unknown field");
+    }
+}
+
+vefd_status vefd_diagnostics(vefd_ctx* c, double out[16]) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (!out) return fail(c, VEFD_ERR_ARG, "NULL output");
+    st = macro_pass(c, false);
+    if (st != VEFD_OK) return st;
+    StepParams p = params_of(c);
+    VEFD_CUDA(c, launch_diagnostics(c->cfg.lattice, c->cfg.ncomp, p, c->drho, c->u, c->C[c->ccur], c->diag_part,
+                                    c->diag_out, c->stream));
+    double v[kDiagVals];
+    VEFD_CUDA(c, cudaMemcpyAsync(v, c->diag_out, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double N = (double)c->N;
+    for (int k = 0; k < 16; ++k) out[k] = 0.0;
+    out[0] = N * (double)(float)c->rho_ref[0] + v[0];
+    out[1] = c->cfg.ncomp == 2 ? N * (double)(float)c->rho_ref[1] + v[1] : 0.0;
+    out[2] = v[2];
+    out[3] = v[3];
+    out[4] = c->D == 3 ? v[4] : 0.0;
+    out[5] = v[5] / N;
+    out[6] = v[6] / N;
+    out[7] = v[15];
+    out[8] = v[16];
+    const double m0 = v[9];
+    out[9] = m0;
+    if (m0 > 0.0) {
+        const double cx = v[10] / m0, cy = v[11] / m0;
+        const double ixx = v[12] / m0 - cx * cx, ixy = v[13] / m0 - cx * cy, iyy = v[14] / m0 - cy * cy;
+        const double tr = ixx + iyy, det = ixx * iyy - ixy * ixy;
+        const double disc = std::sqrt(std::fmax(0.25 * tr * tr - det, 0.0));
+        const double l1 = 0.5 * tr + disc, l2 = std::fmax(0.5 * tr - disc, 0.0);
+        const double a = std::sqrt(l1), b = std::sqrt(l2);
+        out[10] = (a + b) > 0.0 ? (a - b) / (a + b) : 0.0;
+        out[11] = 0.5 * std::atan2(2.0 * ixy, ixx - iyy);
+        out[12] = cx;
+        out[13] = cy;
+    }
+    out[14] = v[8];
+    out[15] = v[7] / N;
+    return VEFD_OK;
+}
+
+vefd_status vefd_get_status(vefd_ctx* c, uint32_t* bits) {
+    if (!c || !bits) return VEFD_ERR_ARG;
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    unsigned v = 0;
+    VEFD_CUDA(c, cudaMemcpyAsync(&v, c->status, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    *bits = v;
+    return v ? VEFD_ERR_UNSTABLE : VEFD_OK;
+}
+
+vefd_status vefd_clear_status(vefd_ctx* c) {
+    if (!c) return VEFD_ERR_ARG;
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    VEFD_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    return VEFD_OK;
+}
+
+vefd_status vefd_steps_done(const vefd_ctx* c, int64_t* n) {
+    if (!c || !n) return VEFD_ERR_ARG;
+    *n = c->steps;
+    return VEFD_OK;
+}
+
+vefd_status vefd_kernels_per_step(const vefd_ctx* c, int* n) {
+    if (!c || !n) return VEFD_ERR_ARG;
+    *n = 2 + c->fd_on;
+    return VEFD_OK;
+}
+
+const char* vefd_last_error(const vefd_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+vefd_status vefd_profile_kernels(vefd_ctx* c, int on) {
+    if (!c) return VEFD_ERR_ARG;
+    c->prof_on = on != 0;
+    c->prof_used = 0;
+    return VEFD_OK;
+}
+
+vefd_status vefd_kernel_times(vefd_ctx* c, double ms[3], int64_t launches[3]) {
+    if (!c || !ms || !launches) return fail(c, VEFD_ERR_ARG, "NULL output");
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (size_t i = 0; i < c->prof_used; ++i) {
+        float t = 0.0f;
+        VEFD_CUDA(c, cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]));
+        const int k = c->prof_kind[i];
+        ms[k] += t;
+        launches[k] += 1;
+    }
+    c->prof_used = 0;
+    return VEFD_OK;
+}
+
+// ---- checkpoints ------------------------------------------------------------
+
+namespace {
+const char kMagic[8] = {'V', 'E', 'F', 'D', 'C', 'K', 'P', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version;
+    int32_t lattice, nx, ny, nz, ncomp, walls;
+    double G, eta_A, eta_B, delta;
+    double u_wall, fext[3], tau_p, eta_p, L2, kappa;
+    int32_t phase, fd_on, have_prev, pad;
+    double rho_ref[2];
+    int64_t steps;
+    uint32_t status, pad2;
+};
+}  // namespace
+
+vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (!path) return fail(c, VEFD_ERR_ARG, "NULL path");
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.lattice = c->cfg.lattice;
+    h.nx = c->cfg.nx;
+    h.ny = c->cfg.ny;
+    h.nz = c->cfg.nz;
+    h.ncomp = c->cfg.ncomp;
+    h.walls = c->cfg.walls;
+    h.G = c->cfg.G;
+    h.eta_A = c->cfg.eta_A;
+    h.eta_B = c->cfg.eta_B;
+    h.delta = c->cfg.delta;
+    h.u_wall = c->u_wall;
+    for (int k = 0; k < 3; ++k) h.fext[k] = c->fext[k];
+    h.tau_p = c->tau_p;
+    h.eta_p = c->eta_p;
+    h.L2 = c->L2;
+    h.kappa = c->kappa;
+    h.phase = c->phase;
+    h.fd_on = c->fd_on;
+    h.have_prev = c->have_prev;
+    h.rho_ref[0] = c->rho_ref[0];
+    h.rho_ref[1] = c->rho_ref[1];
+    h.steps = c->steps;
+    VEFD_CUDA(c, cudaMemcpyAsync(&h.status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    const size_t np = (size_t)c->cfg.ncomp * c->Q * c->N, nc = (size_t)c->NC * c->N;
+    std::vector<float> buf(np + 2 * nc);
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data(), c->f[c->cur], np * 4, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + np, c->C[c->ccur], nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + np + nc, c->R, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    FILE* fh = fopen(path, "wb");
+    if (!fh) return fail(c, VEFD_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = fwrite(&h, sizeof h, 1, fh) == 1 && fwrite(buf.data(), 4, buf.size(), fh) == buf.size();
+    ok = (fclose(fh) == 0) && ok;
+    return ok ? VEFD_OK : fail(c, VEFD_ERR_ARG, "short write to %s", path);
+}
+
+vefd_status vefd_restore(vefd_ctx* c, const char* path) {
+    if (!c || !path) return fail(c, VEFD_ERR_ARG, "NULL argument");
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    FILE* fh = fopen(path, "rb");
+    if (!fh) return fail(c, VEFD_ERR_ARG, "cannot open %s", path);
+    CkptHeader h;
+    const size_t np = (size_t)c->cfg.ncomp * c->Q * c->N, nc = (size_t)c->NC * c->N;
+    std::vector<float> buf(np + 2 * nc);
+    bool ok = fread(&h, sizeof h, 1, fh) == 1;
+    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 1;
+    ok = ok && h.lattice == c->cfg.lattice && h.nx == c->cfg.nx && h.ny == c->cfg.ny && h.nz == c->cfg.nz &&
+         h.ncomp == c->cfg.ncomp && h.walls == c->cfg.walls;
+    ok = ok && fread(buf.data(), 4, buf.size(), fh) == buf.size();
+    fclose(fh);
+    if (!ok) return fail(c, VEFD_ERR_ARG, "%s is not a checkpoint of this lattice", path);
+    c->cfg.G = h.G;
+    c->cfg.eta_A = h.eta_A;
+    c->cfg.eta_B = h.eta_B;
+    c->cfg.delta = h.delta;
+    c->u_wall = h.u_wall;
+    for (int k = 0; k < 3; ++k) c->fext[k] = h.fext[k];
+    c->tau_p = h.tau_p;
+    c->eta_p = h.eta_p;
+    c->L2 = h.L2;
+    c->kappa = h.kappa;
+    c->phase = h.phase;
+    c->fd_on = h.fd_on;
+    c->have_prev = h.have_prev;
+    c->rho_ref[0] = h.rho_ref[0];
+    c->rho_ref[1] = h.rho_ref[1];
+    c->steps = h.steps;
+    c->cur = 0;
+    c->ccur = 0;
+    VEFD_CUDA(c, cudaMemcpyAsync(c->f[0], buf.data(), np * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->C[0], buf.data() + np, nc * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->R, buf.data() + np + nc, nc * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->status, &h.status, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->initialised = 1;
+    return VEFD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Internal declarations shared by the CUDA translation units of libvefd.
+//
+// Storage (all FP32, x fastest, node i = (z*NY + y)*NX + x):
+//   populations  fd[(s*Q + a)*N + i] = f_a^s - w_a rho_ref_s   (deviation form)
+//   densities    drho[s*N + i] = rho_s - rho_ref_s            (sum of deviations)
+//   velocity     u[k*N + i], k < D                             (Eq. equilibrium:vel)
+//   conformation Ct[k*N + i] = C_k - delta_k                   (k < NC)
+//   AB2 history  R[k*N + i]                                    (right-hand side of the last FD step)
+// Storing deviations keeps FP32 rounding relative to the small departures
+// from a uniform rest state instead of to the full populations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vefd {
+
+constexpr float kCs2 = 1.0f / 3.0f;
+
+// D2Q9: rest, +-x, +-y, diagonals as opposite pairs; weights 4/9, 1/9, 1/36.
+struct D2Q9 {
+    static constexpr int Q = 9, D = 2, NC = 4;
+    __host__ __device__ static constexpr int cx(int a) {
+        return a == 1 || a == 5 || a == 7 ? 1 : (a == 2 || a == 6 || a == 8 ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cy(int a) {
+        return a == 3 || a == 5 || a == 8 ? 1 : (a == 4 || a == 6 || a == 7 ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr float w(int a) {
+        return a == 0 ? 4.0f / 9.0f : (a <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+    }
+};
+
+// D3Q19: rest, +-x, +-y, +-z, then the twelve face diagonals as opposite
+// pairs; weights 1/3, 1/18, 1/36 (Sec. 2).
+struct D3Q19 {
+    static constexpr int Q = 19, D = 3, NC = 6;
+    __host__ __device__ static constexpr int cx(int a) {
+        return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+             : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int cy(int a) {
+        return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+             : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int cz(int a) {
+        return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+             : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr float w(int a) {
+        return a == 0 ? 1.0f / 3.0f : (a <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+};
+
+__host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+// Scalars every kernel needs, passed by value.
+struct StepParams {
+    int nx, ny, nz;
+    int walls;             // 1: walls in y; 0: periodic
+    long long N;
+    float G;               // Shan-Chen coupling
+    float eta_A, eta_B;    // phase viscosities
+    float inv_delta;       // 1 / smoothing width
+    float u_wall;          // +u_wall at the lower wall
+    float fext[3];         // body force density
+    float inv_tau_p;       // 1 / tau_P
+    float feedback;        // eta_P / tau_P
+    float L2m3;            // L^2 - 3
+    float kappa;           // artificial diffusivity
+    int phase;             // 0: m = 1, +1: f_+, -1: f_-
+    int have_prev;         // AB2 history valid
+    float rho_ref[2];      // deviation reference densities
+};
+
+// Device guard bits (mirror VEFD_ST_*).
+constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u;
+
+// Pointers of one step.
+struct StepBufs {
+    const float* fin;      // populations at time n (deviation form)
+    float* fout;           // populations at time n+1
+    float* drho;           // densities of time n
+    float* u;              // velocity of time n (written by the lattice kernel)
+    const float* Cin;      // C - I at time n
+    float* Cout;           // C - I at time n+1
+    float* R;              // AB2 history (in: n-1, out: n)
+    unsigned* status;
+    float* dbg;            // optional: g_A(3), g_B(3), F_p(3), tau(1) planes of N
+};
+
+// Launchers (return cudaGetLastError of the launch).
+cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s);
+cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
+                           cudaStream_t s);
+cudaError_t launch_fenep(int lattice, const StepParams& p, const StepBufs& b, cudaStream_t s);
+
+// Field conversions.
+cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
+                                    const float* rhoB, const float* u, float* fd, cudaStream_t s);
+cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, const float* src, float* dst,
+                                int to_absolute, cudaStream_t s);
+cudaError_t launch_tensor_shift(int lattice, const float* src, float* dst, long long N, float sign,
+                                cudaStream_t s);
+// which: 0 rho_A, 1 rho_B, 2 phi, 4 C, 5 sigma_P = f(r_P) C
+cudaError_t launch_derived(int lattice, int ncomp, int which, const StepParams& p, const float* drho,
+                           const float* Ct, float* dst, cudaStream_t s);
+
+// Diagnostics: per-block FP64 partials then a fixed-order final reduction.
+constexpr int kDiagSums = 15, kDiagMax = 2, kDiagVals = kDiagSums + kDiagMax;
+constexpr int kDiagBlocks = 608;  // 4 x 152 SMs
+cudaError_t launch_diagnostics(int lattice, int ncomp, const StepParams& p, const float* drho, const float* u,
+                               const float* Ct, double* partial, double* out, cudaStream_t s);
+
+}  // namespace vefd

@@ -1,0 +1,99 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point
+declared in include/vefd.h, and validates arguments on the host (no GPU
+calls are made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1406_2686_gb300 import build_lib, vefd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "vefd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vefd_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return vefd.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(vefd.EXPORTS) == names
+
+
+def test_build_targets_sm_103a():
+    assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _cfg(**kw):
+    d = dict(lattice=vefd.D3Q19, nx=8, ny=6, nz=4, ncomp=2, walls=1, G=1.5, eta_A=0.2, eta_B=0.3, delta=0.1,
+             external_memory=1)
+    d.update(kw)
+    return vefd.vefd_config(**d)
+
+
+def test_required_bytes_matches_layout(lib):
+    cfg = _cfg()
+    n = vefd.vefd_required_bytes(cfg)
+    N = 8 * 6 * 4
+    # two population buffers, densities, velocity, C twice, AB2 history, debug planes
+    assert n >= 4 * N * (2 * 2 * 19 + 2 + 3 + 3 * 6 + 10)
+    assert n % 256 == 0
+
+
+@pytest.mark.parametrize("bad", [dict(lattice=7), dict(nx=0), dict(lattice=vefd.D2Q9, nz=2), dict(ny=2),
+                                 dict(ncomp=3), dict(eta_A=0.0), dict(delta=-1.0), dict(G=float("nan"))])
+def test_create_rejects_bad_config(lib, bad):
+    cfg = _cfg(**bad)
+    h = ctypes.c_void_p()
+    st = lib.vefd_create(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert st == vefd.ERR_ARG and not h.value
+
+
+def test_parameter_validation_on_host(lib):
+    cfg = _cfg()
+    ctx = vefd.vefd_create(cfg, 0)
+    try:
+        assert lib.vefd_set_wall_shear(ctx, 0.2) == vefd.ERR_ARG
+        assert "Mach" in vefd.vefd_last_error(ctx)
+        assert lib.vefd_set_wall_shear(ctx, 0.05) == vefd.OK
+        assert lib.vefd_set_fenep(ctx, -1.0, 0.1, 100.0, 0.0, 0, 1) == vefd.ERR_ARG
+        assert lib.vefd_set_fenep(ctx, 10.0, 0.1, 2.0, 0.0, 0, 1) == vefd.ERR_ARG
+        assert lib.vefd_set_fenep(ctx, 10.0, 0.1, 100.0, 0.2, 0, 1) == vefd.ERR_ARG  # kappa >= 1/6 in 3D
+        assert lib.vefd_set_fenep(ctx, 10.0, 0.1, 100.0, 0.0, 2, 1) == vefd.ERR_ARG
+        assert lib.vefd_set_fenep(ctx, 10.0, 0.1, 100.0, 1e-3, 1, 1) == vefd.OK
+        assert lib.vefd_set_body_force(ctx, float("inf"), 0.0, 0.0) == vefd.ERR_ARG
+        # nothing is bound yet: stepping and reading are refused, not attempted
+        assert lib.vefd_step(ctx, 1) == vefd.ERR_STATE
+        assert lib.vefd_bind_device_memory(ctx, ctypes.c_void_p(0x1001), 1 << 30) == vefd.ERR_ARG  # misaligned
+        assert lib.vefd_bind_device_memory(ctx, ctypes.c_void_p(0x1000), 16) == vefd.ERR_ARG  # too small
+        sz = ctypes.c_size_t()
+        assert lib.vefd_field_bytes(ctx, vefd.POPS, ctypes.byref(sz)) == vefd.OK and sz.value == 4 * 2 * 19 * 192
+        assert lib.vefd_field_bytes(ctx, vefd.C, ctypes.byref(sz)) == vefd.OK and sz.value == 4 * 6 * 192
+        assert lib.vefd_field_bytes(ctx, 99, ctypes.byref(sz)) == vefd.ERR_ARG
+        n = ctypes.c_int()
+        assert lib.vefd_kernels_per_step(ctx, ctypes.byref(n)) == vefd.OK and n.value == 3
+    finally:
+        vefd.vefd_destroy(ctx)
+
+
+def test_d2q9_field_sizes(lib):
+    cfg = _cfg(lattice=vefd.D2Q9, nz=1, ncomp=1)
+    ctx = vefd.vefd_create(cfg, 0)
+    try:
+        assert vefd.vefd_field_bytes(ctx, vefd.POPS) == 4 * 9 * 48
+        assert vefd.vefd_field_bytes(ctx, vefd.U) == 4 * 2 * 48
+        assert vefd.vefd_field_bytes(ctx, vefd.C) == 4 * 4 * 48
+    finally:
+        vefd.vefd_destroy(ctx)

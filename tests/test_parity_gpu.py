@@ -1,0 +1,263 @@
+"""Parity of the CUDA library with the FP64 oracle (GPU required).
+
+Tolerances follow from FP32 storage: one step moves populations and C by
+rounding of ~6e-8 relative, so stage-wise comparisons use 1e-5 relative L2;
+after 2000 steps the contract is 1e-5 relative L2 in u and C and 1e-6
+relative total-mass drift.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from paper_1406_2686_gb300 import inputs
+
+from pairs import Pair, max_abs, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = {
+    "d2q9_1c_walls": dict(lattice=0, nx=37, ny=13, ncomp=1, walls=1, u_wall=0.03, fext=(2e-5, -1e-5, 0.0),
+                          eta_p=0.05, tau_p=40.0, L2=50.0, kappa=0.02, phase=0),
+    "d2q9_2c_periodic": dict(lattice=0, nx=33, ny=20, ncomp=2, walls=0, G=1.5, eta_p=0.1, tau_p=30.0, L2=40.0,
+                             kappa=0.01, phase=1),
+    "d2q9_2c_walls_matrix": dict(lattice=0, nx=24, ny=17, ncomp=2, walls=1, G=1.2, u_wall=-0.02, eta_p=0.08,
+                                 tau_p=25.0, L2=60.0, kappa=0.0, phase=-1),
+    "d3q19_2c_walls": dict(lattice=1, nx=35, ny=7, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.04, eta_p=0.12,
+                           tau_p=50.0, L2=100.0, kappa=1e-3, phase=1, fext=(1e-5, 0.0, 2e-6)),
+    "d3q19_1c_periodic": dict(lattice=1, nx=9, ny=10, nz=11, ncomp=1, walls=0, fext=(3e-5, 1e-5, -2e-5),
+                              eta_p=0.2, tau_p=20.0, L2=30.0, kappa=0.03),
+    "d3q19_2c_nx1": dict(lattice=1, nx=1, ny=5, nz=3, ncomp=2, walls=1, G=1.4, u_wall=0.02, eta_p=0.1,
+                         tau_p=15.0, L2=40.0, phase=1),
+    "d3q19_2c_nz1": dict(lattice=1, nx=40, ny=9, nz=1, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1,
+                         tau_p=15.0, L2=40.0, phase=-1, kappa=0.01),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(0)
+
+
+@pytest.mark.parametrize("name", sorted(VARIANTS))
+def test_stagewise_derived_fields(name):
+    """Moments, Shan-Chen force, polymer force, velocity and relaxation time
+    of one seeded state agree with the oracle before any step."""
+    P = Pair(**VARIANTS[name])
+    P.init_random(seed=3)
+    for fld, tol in (("rhoA", 1e-6), ("phi", 1e-6), ("u", 1e-5), ("tau", 1e-6), ("gA", 1e-5), ("gB", 1e-5),
+                     ("Fp", 1e-5), ("sigma", 1e-6), ("C", 1e-6)):
+        if fld in ("gA", "gB", "phi") and P.p["ncomp"] == 1:
+            continue
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < tol, (fld, rel_l2(g, o))
+
+
+@pytest.mark.parametrize("name", sorted(VARIANTS))
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_steps_match_oracle(name, nsteps):
+    """Populations, u, C and the AB2 history after 1 and 3 full steps
+    (the first is forward Euler, the rest AB2)."""
+    P = Pair(**VARIANTS[name])
+    P.init_random(seed=5)
+    P.step(nsteps)
+    for fld, tol in (("pops", 1e-6), ("u", 1e-5), ("C", 1e-6), ("R", 1e-5)):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < tol, (fld, rel_l2(g, o))
+    assert P.g.status() == 0 and P.o.status == 0
+
+
+def test_config1_couette_2000_steps():
+    """D2Q9 single-component FENE-P Couette, 64 x 32, walls +-0.01, tau = 1,
+    lambda = 1000 steps, eta_P/(eta_s + eta_P) = 0.4, L^2 = 100, C = I:
+    after 2000 steps, relative L2 of u and C within 1e-5 of the oracle and
+    total mass drift within 1e-6."""
+    eta_s = 1.0 / 6.0
+    P = Pair(lattice=0, nx=64, ny=32, ncomp=1, walls=1, eta_A=eta_s, eta_B=eta_s, u_wall=0.01, tau_p=1000.0,
+             eta_p=eta_s * 0.4 / 0.6, L2=100.0, kappa=0.0)
+    P.init(np.ones((1, 32, 64)))
+    m0 = P.g.diagnostics()[0]
+    P.step(2000)
+    for fld in ("u", "C"):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    assert abs(P.g.diagnostics()[0] / m0 - 1) < 1e-6
+
+
+def _droplet_pair(nx, ny, nz, R, seed=1, **kw):
+    """Confined droplet set-up (D3Q19, 2 components, G = 1.5, rho 2.0 / 0.1,
+    width 5, phi noise 1e-3, viscoelastic droplet, L^2 = 100) scaled to the
+    box: tau_B = 1 at rho = 2.1, eta_A = 0.6 eta_B, eta_P = 0.4 eta_B,
+    Ca = 0.1 and De = 1 with sigma = 0.09."""
+    etaB = 2.1 / 3.0 * 0.5
+    etaA, etaP, sigma = 0.6 * etaB, 0.4 * etaB, 0.09
+    gdot = 0.1 * sigma / (R * etaB)
+    taup = 1.0 * R * etaB / sigma * etaB / etaP
+    p = dict(lattice=1, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=etaA, eta_B=etaB, u_wall=gdot * ny / 2,
+             tau_p=taup, eta_p=etaP, L2=100.0, kappa=1e-3, phase=1)
+    p.update(kw)
+    P = Pair(**p)
+    rA, rB = inputs.droplet_fields(nx, ny, nz, R=R, seed=seed, noise=1e-3)
+    P.init(rA, rB)
+    return P
+
+
+def test_droplet_2000_steps():
+    """Scaled confined viscoelastic droplet (40 x 24 x 40, R = 6, 2R/H = 0.5):
+    after 2000 steps the relative L2 error of u and C is within 1e-5 and the
+    per-component mass drift within 1e-6."""
+    P = _droplet_pair(40, 24, 40, 6.0)
+    m0 = P.g.diagnostics()[:2]
+    P.step(2000)
+    for fld in ("u", "C"):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    m1 = P.g.diagnostics()[:2]
+    assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
+    assert P.g.status() == 0
+
+
+def test_full_size_droplet_sampled_step():
+    """Full 128 x 64 x 128 confined droplet in the benchmark's launch
+    configuration: after 50 GPU steps the state is loaded into the oracle and
+    both take one more step; every node agrees (one FP32 step), mass is
+    conserved over the run, and the diagnostics agree."""
+    P = _droplet_pair(128, 64, 128, 16.0)
+    m0 = P.g.diagnostics()[:2]
+    P.g.step(50)
+    m1 = P.g.diagnostics()[:2]
+    assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
+    from paper_1406_2686_gb300 import vefd
+    P.o.write(oracle.F_POPS, P.g.read(vefd.POPS).astype(np.float64))
+    P.o.write(oracle.F_C, P.g.read(vefd.C).astype(np.float64))
+    P.o.write(oracle.F_RPREV, P.g.read(vefd.RPREV).astype(np.float64))
+    dg, do = P.g.diagnostics(), P.o.diagnostics()
+    assert abs(dg[0] / do[0] - 1) < 1e-6 and abs(dg[1] / do[1] - 1) < 1e-6
+    assert np.allclose(dg[2:5], do[2:5], rtol=1e-4, atol=1e-6 * abs(do[0]) * 1e-3)
+    assert abs(dg[10] - do[10]) < 2e-3 and abs(dg[9] - do[9]) <= 4
+    P.step(1)
+    for fld, tol in (("pops", 1e-6), ("u", 1e-5), ("C", 1e-6)):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < tol, (fld, rel_l2(g, o))
+
+
+def test_config1_closed_form_20000_steps():
+    """The GPU path alone reaches the steady-shear closed form of Sec. 3.1
+    (Lambda = -0.625, L^2 = 100) after 20000 steps = 20 tau_P.  The bound is
+    the FP32 stagnation limit of the AB2 update: increments below half an
+    ulp of C - I are lost, so C can stop within (tau_P / f) * ulp of steady
+    state; the profile stays the exact Couette line."""
+    from paper_1406_2686_gb300 import vefd
+    eta_s = 1.0 / 6.0
+    g = vefd.Lattice(lattice=0, nx=64, ny=32, nz=1, ncomp=1, walls=1, eta_A=eta_s, eta_B=eta_s)
+    g.set_wall_shear(0.01)
+    g.set_fenep(1000.0, eta_s * 0.4 / 0.6, 100.0, 0.0, 0, 1)
+    g.init_fields(np.ones((1, 32, 64), np.float32))
+    g.step(20000)
+    C = g.read(vefd.C).astype(np.float64)
+    Cex, Z = cf.shear_conformation(-0.625, 100.0)
+    for k, kk in enumerate((0, 1, 3, 5)):
+        dev = abs(Cex[kk] - (1.0 if kk in (0, 3, 5) else 0.0))
+        ulp = np.spacing(np.float32(max(dev, 1e-3)))
+        tol = 1000.0 / Z * float(ulp) + 1e-6
+        assert np.max(np.abs(C[k] - Cex[kk])) < tol, (k, np.max(np.abs(C[k] - Cex[kk])), tol)
+    u = g.read(vefd.U)[0].astype(np.float64)
+    assert np.max(np.abs(u - cf.couette_profile(32, 0.01)[None, :, None])) < 2e-7
+    sig = g.read(vefd.SIGMA_P).astype(np.float64)
+    assert abs(np.mean(sig[1]) - (-cf.shear_S(0.625, 100.0))) < 1e-4
+    assert abs(np.mean(sig[0] - sig[2]) - cf.shear_N(0.625, 100.0)) < 2e-4
+
+
+def test_guards_flag_instability():
+    """The device guard word reports a NaN and tr C >= L^2 written into C, and
+    |u| above the Mach limit (the failure is made on the host side, through
+    the field interface; no kernel faults)."""
+    from paper_1406_2686_gb300 import vefd
+    P = Pair(lattice=1, nx=8, ny=6, nz=4, ncomp=1, walls=1, eta_p=0.1, tau_p=10.0, L2=20.0)
+    P.init(np.ones((4, 6, 8)))
+    P.g.step(2)
+    assert P.g.status() == 0
+    C = P.g.read(vefd.C)
+    C[0, 1, 2, 3] = np.nan
+    P.g.write(vefd.C, C)
+    P.g.step(1)
+    assert P.g.status() & vefd.ST_NAN
+    P.g.init_fields(np.ones((4, 6, 8), np.float32))
+    C = P.g.read(vefd.C)
+    C[0, 2, 2, 2] = 19.0  # tr C = 21 > L^2 = 20
+    P.g.write(vefd.C, C)
+    P.g.step(1)
+    assert P.g.status() & vefd.ST_TRACE
+    with pytest.raises(vefd.VefdError) as ei:
+        vefd._check(P.g.ctx, vefd.load().vefd_diagnostics(P.g.ctx, None))
+    assert ei.value.status == vefd.ERR_ARG
+    u = np.zeros((3, 4, 6, 8), np.float32)
+    u[0, 1, 1, 1] = 0.35
+    P.g.init_fields(np.ones((4, 6, 8), np.float32), None, u)
+    P.g.step(1)
+    assert P.g.status() & vefd.ST_MACH
+    P.g.clear_status()
+    assert P.g.status() == 0
+
+
+def test_checkpoint_restore_bit_identical(tmp_path):
+    """A restored context continues bit-identically."""
+    from paper_1406_2686_gb300 import vefd
+    P = _droplet_pair(24, 16, 20, 4.0)
+    P.g.step(7)
+    path = str(tmp_path / "ck.bin")
+    P.g.checkpoint(path)
+    P.g.step(9)
+    a_pops, a_C, a_R = P.g.read(vefd.POPS), P.g.read(vefd.C), P.g.read(vefd.RPREV)
+    g2 = vefd.Lattice(lattice=1, nx=24, ny=16, nz=20, ncomp=2, walls=1, G=0.0, eta_A=1.0, eta_B=1.0)
+    g2.restore(path)
+    assert g2.steps_done == 7
+    g2.step(9)
+    assert np.array_equal(g2.read(vefd.POPS), a_pops)
+    assert np.array_equal(g2.read(vefd.C), a_C)
+    assert np.array_equal(g2.read(vefd.RPREV), a_R)
+
+
+def test_init_droplet_matches_generator():
+    """The library's droplet initialiser reproduces the seeded generator
+    (same profile and the same SplitMix64 counter stream)."""
+    from paper_1406_2686_gb300 import vefd
+    nx, ny, nz = 30, 20, 26
+    g = vefd.Lattice(lattice=1, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=0.2, eta_B=0.3)
+    g.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, 6.0, 2.0, 0.1, 5.0, 11, 1e-3)
+    rA, rB = inputs.droplet_fields(nx, ny, nz, R=6.0, seed=11, noise=1e-3)
+    assert np.max(np.abs(g.read(vefd.RHO_A) - rA)) < 2e-6
+    assert np.max(np.abs(g.read(vefd.RHO_B) - rB)) < 2e-6
+
+
+def test_device_pointer_io_roundtrip():
+    """Fields read to and written from device memory (torch tensors) match the
+    host path."""
+    import torch
+    from paper_1406_2686_gb300 import vefd
+    P = Pair(lattice=1, nx=10, ny=6, nz=4, ncomp=2, walls=1)
+    P.init_random(seed=9)
+    P.g.step(2)
+    for f in (vefd.POPS, vefd.C, vefd.U, vefd.PHI):
+        assert np.array_equal(P.g.read(f, device=True).cpu().numpy(), P.g.read(f))
+    C = P.g.read(vefd.C, device=True) * 1.0
+    C[0] += 0.01
+    P.g.write(vefd.C, C)
+    assert np.allclose(P.g.read(vefd.C), C.cpu().numpy())
+    torch.cuda.synchronize()
+
+
+def test_empty_step_and_errors():
+    from paper_1406_2686_gb300 import vefd
+    P = Pair(lattice=0, nx=8, ny=5, ncomp=1)
+    P.init_random(seed=2)
+    before = P.g.read(vefd.POPS)
+    P.g.step(0)
+    assert np.array_equal(before, P.g.read(vefd.POPS))
+    with pytest.raises(vefd.VefdError):
+        P.g.step(-1)
+    with pytest.raises(ValueError):
+        P.g.write(vefd.C, np.zeros(3, np.float32))
