@@ -245,7 +245,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    lat.profile_kernels(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -257,6 +256,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    # per-kernel durations: the same K steps again with an event pair around
+    # every launch (on the library's stream), kept out of the headline timing
+    lat.profile_kernels(True)
+    lat.step(K)
     kms, klaunch = lat.kernel_times()
     lat.profile_kernels(False)
     status = lat.status()
@@ -302,7 +305,7 @@ def run_ours(args):
         "step_roofline": {"achieved": round(step_achieved, 1), "peak": peak, "unit": "GB/s",
                           "frac": round(step_achieved / peak, 4),
                           "algorithmic_bytes_per_node": STEP_BYTES_PER_NODE},
-        "kernels": kernels, "gpu_launches": int(sum(klaunch)), "clocks": clk, "e2e": e2e,
+        "kernels": kernels, "gpu_launches": int(K * lat.kernels_per_step()), "clocks": clk, "e2e": e2e,
         "status_bits": status, "source_sha": source_hash(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -298,27 +298,39 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p) {
         const float uF = ux * Fx + uy * Fy + uz * Fz;
         const float rsv = rs[s];
         const float drs = dr[s];
+        // The collision conserves mass exactly: sum_a f*_a = sum_a f_a.  The rest
+        // population is therefore taken as that remainder after the moving ones,
+        // so that the FP32 lattice weights (whose sum is 1 + 1.5e-8) leave no
+        // systematic mass bias; what remains is unbiased rounding.
+        float moved = 0.0f;
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) {
-            const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-            const float wa = L::w(a);
+        for (int a = 1; a <= L::Q; ++a) {
+            const int ai = a == L::Q ? 0 : a;  // rest population last
+            const int cx = L::cx(ai), cy = L::cy(ai), cz = L::cz(ai);
+            const float wa = L::w(ai);
             const float cu = cx * ux + cy * uy + cz * uz;
             const float cF = cx * Fx + cy * Fy + cz * Fz;
             // deviation equilibrium: E_a - w_a rho_ref = w_a [drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)]
             const float Ed = wa * (drs + rsv * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
             const float S = wa * (3.0f * (cF - uF) + 9.0f * cu * cF);
-            const float fpost = f[s][a] + omega * (Ed - f[s][a]) + src_w * S;
+            float fpost;
+            if (ai == 0) {
+                fpost = drs - moved;
+            } else {
+                fpost = f[s][ai] + omega * (Ed - f[s][ai]) + src_w * S;
+                moved += fpost;
+            }
             int yt = y + cy;
             if (p.walls && (yt < 0 || yt >= ny)) {
                 // half-way bounce-back into the opposite direction at this node,
                 // moving wall +U (lower) / -U (upper): -2 w rho_s (c.U)/c_s^2
                 const float Uw = yt < 0 ? uw3 : -uw3;
-                b.fout[(s * L::Q + opposite(a)) * N + i] = fpost - 2.0f * wa * rsv * (float)cx * Uw;
+                b.fout[(s * L::Q + opposite(ai)) * N + i] = fpost - 2.0f * wa * rsv * (float)cx * Uw;
             } else {
                 yt = wrap1(yt, ny);
                 const int xt = cx < 0 ? xm : (cx > 0 ? xp : x);
                 const int zt = cz < 0 ? zm : (cz > 0 ? zp : z);
-                b.fout[(s * L::Q + a) * N + ((long long)zt * ny + yt) * nx + xt] = fpost;
+                b.fout[(s * L::Q + ai) * N + ((long long)zt * ny + yt) * nx + xt] = fpost;
             }
         }
     }
@@ -336,11 +348,17 @@ __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restric
         for (int s = 0; s < NCOMP; ++s) {
             const float r = s == 0 ? rhoA[i] : rhoB[i];
             const float d = r - p.rho_ref[s];
+            // moving populations first; the rest population carries the remainder
+            // so that the stored deviations sum to rho - rho_ref
+            float moved = 0.0f;
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
+            for (int a = 1; a < L::Q; ++a) {
                 const float cu = L::cx(a) * ux + L::cy(a) * uy + L::cz(a) * uz;
-                fd[(s * L::Q + a) * N + i] = L::w(a) * (d + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+                const float e = L::w(a) * (d + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+                fd[(s * L::Q + a) * N + i] = e;
+                moved += e;
             }
+            fd[(s * L::Q) * N + i] = d - moved;
         }
     }
 }
