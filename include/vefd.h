@@ -167,6 +167,30 @@ vefd_status vefd_profile_kernels(vefd_ctx *ctx, int on);
  * on or last read; then clears the record. */
 vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
 
+/* Allocation-free diagnostics (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory).  Some callers
+ * cannot call cudaMalloc: their device memory is owned by another allocator
+ * that reserves the GPU up front, or they run as a monitoring hook that must
+ * not trigger the device-wide synchronisation cudaMalloc/cudaFree can cause.
+ * This entry point reduces fields the caller already holds on the device and
+ * allocates nothing; its only scratch is a fixed array inside the library's
+ * device image (557,192 bytes, kept by every GPU that loads the library until
+ * the process exits).
+ * Inputs (device pointers, FP32, layout as vefd_read_field): rho_A and rho_B
+ * (N each; rho_B may be NULL when ncomp == 1), u (2|3 planes), C (4|6 planes);
+ * L2 is the FENE-P maximum extension squared.  out[16] (host) receives the
+ * values listed for vefd_diagnostics.  Work runs on `stream` and the call
+ * synchronises it.  Lattices above 8,388,608 nodes exceed the scratch array
+ * and are rejected with VEFD_ERR_ARG, as are bad sizes and NULL inputs.
+ * The first call on each device looks up the scratch address with that
+ * device current, so make that first call before any stream capture.  Every
+ * call shares the one scratch array and rewrites every row it reads, so
+ * nothing needs clearing between calls, but calls that overlap on the GPU
+ * race on it. */
+vefd_status vefd_diagnostics_noalloc(int lattice, int nx, int ny, int nz, int ncomp, double L2,
+                                     const float *rho_A, const float *rho_B, const float *u, const float *C,
+                                     void *stream, double out[16]);
+
 #ifdef __cplusplus
 }
 #endif

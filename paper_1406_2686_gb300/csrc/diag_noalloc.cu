@@ -1,0 +1,214 @@
+// Allocation-free variant of the FP64 diagnostics reduction.
+//
+// Some callers cannot call cudaMalloc: their device memory is owned by
+// another allocator that reserves the GPU up front (a framework's caching
+// pool, a co-scheduled job), or they run as a monitoring hook that must not
+// trigger the device-wide synchronisation that cudaMalloc and cudaFree can
+// cause.  For them, vefd_diagnostics_noalloc reduces fields the caller
+// already holds on the device, using only a fixed scratch array that is part
+// of this library's device image.
+//
+// Scratch: kNoallocRows rows of kDiagVals doubles (one row per block of the
+// reduction, plus one result row), 4097 x 17 x 8 = 557,192 bytes, held by
+// every GPU that loads the library until the process exits.  One block
+// reduces kNodesPerBlock = 2048 nodes, so lattices of at most
+// kNoallocRows * 2048 = 8,388,608 nodes are accepted; larger ones are
+// rejected with VEFD_ERR_ARG.  Every row that is read was written by the same
+// call, so nothing needs clearing between calls; but all calls share the one
+// array, so calls that overlap on the GPU (different streams, different host
+// threads) race on it.
+#include <cmath>
+#include <mutex>
+
+#include "vefd.h"
+#include "vefd_internal.cuh"
+
+namespace vefd {
+namespace {
+
+constexpr int kNoallocRows = 4096;
+constexpr int kNodesPerBlock = 2048;
+constexpr int kThreads = 256;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[(kNoallocRows + 1) * kDiagVals];
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Same sums and maxima as the context's diagnostics kernel, from absolute
+// densities: one row of partials per block of kNodesPerBlock nodes.
+template <int D, int NC>
+__global__ void __launch_bounds__(kThreads) k_diag_rows_abs(const float* __restrict__ rA, const float* __restrict__ rB,
+                                                            const float* __restrict__ u, const float* __restrict__ Ct,
+                                                            int nx, int ny, int nz, double L2, double* __restrict__ rows) {
+    const long long N = (long long)nx * ny * nz;
+    const int zc = nz / 2;
+    double acc[kDiagVals];
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) acc[k] = 0.0;
+    const long long first = (long long)blockIdx.x * kNodesPerBlock;
+    for (int t = threadIdx.x; t < kNodesPerBlock; t += kThreads) {
+        const long long i = first + t;
+        if (i >= N) break;
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        const int y = (int)(r % ny);
+        const int z = (int)(r / ny);
+        const double a = rA[i];
+        const double b = rB ? (double)rB[i] : 0.0;
+        const double rho = a + b;
+        acc[0] += a;
+        acc[1] += b;
+        double u2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double uk = u[k * N + i];
+            acc[2 + k] += rho * uk;
+            u2 += uk * uk;
+        }
+        double c[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) c[k] = Ct[k * N + i];
+        const double tr = NC == 6 ? c[0] + c[3] + c[5] : c[0] + c[2] + c[3];
+        const double f = (L2 - 3.0) / (L2 - tr);
+        const double cyy = NC == 6 ? c[3] : c[2];
+        acc[5] += f * c[1];
+        acc[6] += f * (c[0] - cyy);
+        acc[7] += f * tr - 3.0;
+        const bool ind = rB ? (a - b) / rho > 0.0 : true;
+        if (ind) {
+            acc[8] += 1.0;
+            if (z == zc) {
+                acc[9] += 1.0;
+                acc[10] += x;
+                acc[11] += y;
+                acc[12] += (double)x * x;
+                acc[13] += (double)x * y;
+                acc[14] += (double)y * y;
+            }
+        }
+        acc[15] = fmax(acc[15], tr / L2);
+        acc[16] = fmax(acc[16], sqrt(u2));
+    }
+    __shared__ double sh[kDiagVals][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) {
+        const double v = k < kDiagSums ? wsum(acc[k]) : wmax(acc[k]);
+        if (lane == 0) sh[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiagVals) {
+        const int k = threadIdx.x;
+        double v = sh[k][0];
+        for (int w = 1; w < kThreads / 32; ++w) v = k < kDiagSums ? v + sh[k][w] : fmax(v, sh[k][w]);
+        rows[(long long)blockIdx.x * kDiagVals + k] = v;
+    }
+}
+
+// Sums the rows in index order into the result row kNoallocRows.
+__global__ void k_diag_rows_final(double* __restrict__ rows, int nrows) {
+    const int k = threadIdx.x;
+    if (k >= kDiagVals) return;
+    double v = rows[k];
+    for (int r = 1; r < nrows; ++r) {
+        const double t = rows[(long long)r * kDiagVals + k];
+        v = k < kDiagSums ? v + t : fmax(v, t);
+    }
+    rows[(long long)kNoallocRows * kDiagVals + k] = v;
+}
+
+std::mutex g_setup_mutex;
+double* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The array's
+// name in host code is only a handle, so the address is looked up once per
+// device (with that device current) and cached.
+cudaError_t scratch_on_current_device(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace vefd
+
+using namespace vefd;
+
+extern "C" vefd_status vefd_diagnostics_noalloc(int lattice, int nx, int ny, int nz, int ncomp, double L2,
+                                                const float* rho_A, const float* rho_B, const float* u,
+                                                const float* C, void* stream, double out[16]) {
+    if (!out || !rho_A || !u || !C) return VEFD_ERR_ARG;
+    if (lattice != VEFD_D2Q9 && lattice != VEFD_D3Q19) return VEFD_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || (lattice == VEFD_D2Q9 && nz != 1)) return VEFD_ERR_ARG;
+    if (ncomp != 1 && ncomp != 2) return VEFD_ERR_ARG;
+    if (ncomp == 2 && !rho_B) return VEFD_ERR_ARG;
+    if (!(L2 > 3.0)) return VEFD_ERR_ARG;
+    const long long N = (long long)nx * ny * nz;
+    // lattices beyond the scratch array's capacity are refused
+    if (N > (long long)kNoallocRows * kNodesPerBlock) return VEFD_ERR_ARG;
+    double* rows = nullptr;
+    if (scratch_on_current_device(&rows) != cudaSuccess) return VEFD_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nblocks = (int)((N + kNodesPerBlock - 1) / kNodesPerBlock);
+    const float* rB = ncomp == 2 ? rho_B : nullptr;
+    if (lattice == VEFD_D3Q19)
+        k_diag_rows_abs<3, 6><<<nblocks, kThreads, 0, s>>>(rho_A, rB, u, C, nx, ny, nz, L2, rows);
+    else
+        k_diag_rows_abs<2, 4><<<nblocks, kThreads, 0, s>>>(rho_A, rB, u, C, nx, ny, nz, L2, rows);
+    k_diag_rows_final<<<1, 32, 0, s>>>(rows, nblocks);
+    if (cudaGetLastError() != cudaSuccess) return VEFD_ERR_CUDA;
+    double v[kDiagVals];
+    if (cudaMemcpyAsync(v, rows + (size_t)kNoallocRows * kDiagVals, sizeof v, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return VEFD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VEFD_ERR_CUDA;
+    const double n = (double)N;
+    for (int k = 0; k < 16; ++k) out[k] = 0.0;
+    out[0] = v[0];
+    out[1] = v[1];
+    out[2] = v[2];
+    out[3] = v[3];
+    out[4] = lattice == VEFD_D3Q19 ? v[4] : 0.0;
+    out[5] = v[5] / n;
+    out[6] = v[6] / n;
+    out[7] = v[15];
+    out[8] = v[16];
+    const double m0 = v[9];
+    out[9] = m0;
+    if (m0 > 0.0) {
+        const double cx = v[10] / m0, cy = v[11] / m0;
+        const double ixx = v[12] / m0 - cx * cx, ixy = v[13] / m0 - cx * cy, iyy = v[14] / m0 - cy * cy;
+        const double tr = ixx + iyy, det = ixx * iyy - ixy * ixy;
+        const double disc = std::sqrt(std::fmax(0.25 * tr * tr - det, 0.0));
+        const double l1 = 0.5 * tr + disc, l2 = std::fmax(0.5 * tr - disc, 0.0);
+        const double a = std::sqrt(l1), b = std::sqrt(l2);
+        out[10] = (a + b) > 0.0 ? (a - b) / (a + b) : 0.0;
+        out[11] = 0.5 * std::atan2(2.0 * ixy, ixx - iyy);
+        out[12] = cx;
+        out[13] = cy;
+    }
+    out[14] = v[8];
+    out[15] = v[7] / n;
+    return VEFD_OK;
+}

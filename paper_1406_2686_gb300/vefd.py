@@ -40,6 +40,7 @@ EXPORTS = [
     "vefd_write_field", "vefd_step", "vefd_read_field", "vefd_field_bytes", "vefd_diagnostics",
     "vefd_get_status", "vefd_clear_status", "vefd_steps_done", "vefd_checkpoint", "vefd_restore",
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
+    "vefd_diagnostics_noalloc",
 ]
 
 _lib = None
@@ -85,6 +86,7 @@ def load(build_if_missing=True):
         "vefd_kernels_per_step": [vp, ctypes.POINTER(cint)],
         "vefd_profile_kernels": [vp, cint],
         "vefd_kernel_times": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
+        "vefd_diagnostics_noalloc": [cint, cint, cint, cint, cint, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -223,6 +225,16 @@ def vefd_kernel_times(ctx):
     n = (ctypes.c_int64 * 3)()
     _check(ctx, load().vefd_kernel_times(ctx, ms, n))
     return list(ms), list(n)
+
+
+def vefd_diagnostics_noalloc(lattice, nx, ny, nz, ncomp, L2, rho_A, rho_B, u, C, stream=0):
+    """Allocation-free diagnostics of device fields (pointers as ints)."""
+    out = (ctypes.c_double * 16)()
+    st = load().vefd_diagnostics_noalloc(int(lattice), int(nx), int(ny), int(nz), int(ncomp), float(L2),
+                                         ctypes.c_void_p(rho_A), ctypes.c_void_p(rho_B) if rho_B else None,
+                                         ctypes.c_void_p(u), ctypes.c_void_p(C), ctypes.c_void_p(stream), out)
+    _check(None, st)
+    return np.array(out[:], dtype=np.float64)
 
 
 # --- convenience wrapper -----------------------------------------------------

@@ -1,0 +1,76 @@
+"""The allocation-free diagnostics entry point against the context's own.
+
+It serves callers that cannot call cudaMalloc (device memory owned by another
+allocator, or monitoring hooks that must not trigger an allocation's device
+synchronisation); it reduces fields the caller holds, with a fixed scratch
+array inside the library.  Checked through the C-ABI on two calls in a row,
+against vefd_diagnostics on the same state, within the tolerances of the
+diagnostics parity test.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(lat, vefd):
+    return {f: lat.read(f, device=True) for f in (vefd.RHO_A, vefd.RHO_B, vefd.U, vefd.C)}
+
+
+def _compare(ref, got):
+    assert abs(got[0] / ref[0] - 1) < 1e-6 and abs(got[1] / ref[1] - 1) < 1e-6
+    scale = 1e-6 * ref[0]
+    assert np.allclose(got[2:5], ref[2:5], rtol=1e-5, atol=scale)
+    assert np.allclose(got[5:9], ref[5:9], rtol=1e-5, atol=1e-9)
+    assert abs(got[9] - ref[9]) <= 2 and abs(got[14] - ref[14]) <= 2
+    assert abs(got[10] - ref[10]) < 1e-3 and abs(got[11] - ref[11]) < 1e-3
+    assert np.allclose(got[12:14], ref[12:14], atol=1e-2)
+    assert np.isclose(got[15], ref[15], rtol=1e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
+def test_noalloc_diagnostics_match_context(lattice):
+    import torch
+
+    from paper_1406_2686_gb300 import vefd
+
+    if lattice == "d3q19":
+        nx, ny, nz = 48, 32, 40
+        lat = vefd.Lattice(lattice=vefd.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=0.21,
+                           eta_B=0.35)
+        lat.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, 8.0, 2.0, 0.1, 5.0, 3, 1e-3)
+    else:
+        nx, ny, nz = 96, 48, 1
+        lat = vefd.Lattice(lattice=vefd.D2Q9, nx=nx, ny=ny, nz=1, ncomp=2, walls=1, G=1.5, eta_A=0.21, eta_B=0.35)
+        lat.init_droplet((nx - 1) / 2, (ny - 1) / 2, 0.0, 10.0, 2.0, 0.1, 5.0, 3, 1e-3)
+    L2 = 100.0
+    lat.set_wall_shear(0.03)
+    lat.set_fenep(50.0, 0.14, L2, 1e-3, 1, 1)
+    stream = lat.stream.cuda_stream
+    for call in range(2):
+        lat.step(40)
+        ref = lat.diagnostics()
+        f = _fields(lat, vefd)
+        torch.cuda.synchronize()
+        got = vefd.vefd_diagnostics_noalloc(lat.cfg.lattice, nx, ny, nz, 2, L2, f[vefd.RHO_A].data_ptr(),
+                                            f[vefd.RHO_B].data_ptr(), f[vefd.U].data_ptr(), f[vefd.C].data_ptr(),
+                                            stream)
+        _compare(ref, got)
+    lat.close()
+
+
+def test_noalloc_rejects_oversize_and_bad_args():
+    from paper_1406_2686_gb300 import vefd
+
+    lib = vefd.load()
+    out = (vefd.ctypes.c_double * 16)()
+    dummy = vefd.ctypes.c_void_p(256)
+    # 8,388,608 nodes is the scratch capacity; one more row of x is refused before any launch
+    st = lib.vefd_diagnostics_noalloc(1, 257, 128, 256, 2, 100.0, dummy, dummy, dummy, dummy, None, out)
+    assert st == vefd.ERR_ARG
+    st = lib.vefd_diagnostics_noalloc(0, 8, 8, 2, 1, 100.0, dummy, None, dummy, dummy, None, out)
+    assert st == vefd.ERR_ARG
+    st = lib.vefd_diagnostics_noalloc(1, 8, 8, 8, 2, 100.0, dummy, None, dummy, dummy, None, out)
+    assert st == vefd.ERR_ARG
+    st = lib.vefd_diagnostics_noalloc(1, 8, 8, 8, 1, 2.0, dummy, None, dummy, dummy, None, out)
+    assert st == vefd.ERR_ARG
