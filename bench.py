@@ -43,12 +43,13 @@ WORKLOAD = ("D3Q19 two-component Shan-Chen FENE-P confined droplet R=16, 128x128
             "(NX=128, NY=64 wall-normal, NZ=128), G=1.5, L2=100, De=1, Ca=0.1, FP32 populations and C")
 # algorithmic bytes per node update (each value read and written once per step)
 STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2 + 6 * 4 * 2 + 6 * 4 * 2   # 400
-KERNEL_NAMES = ["moments", "lattice_collide_stream", "fenep_fd"]
-# algorithmic bytes per node of each kernel class of the current three-kernel step
+KERNEL_NAMES = ["moments", "lattice_collide_stream", "densities_fenep_fd"]
+# algorithmic bytes per node of each kernel class of the two-kernel step
 KERNEL_ALGO_BYTES = {
-    "moments": 0,                                   # re-read of the populations: overhead, not algorithmic
+    "moments": 0,                                   # only before the first step
     "lattice_collide_stream": 2 * 19 * 4 * 2,       # populations read + written
-    "fenep_fd": 6 * 4 * 2 + 6 * 4 * 2,              # C and AB2 history read + written
+    "densities_fenep_fd": 6 * 4 * 2 + 6 * 4 * 2,    # C and AB2 history read + written (the population
+                                                    # re-read for the densities is overhead)
 }
 MLUPS = "MLUPS"
 

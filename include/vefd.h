@@ -46,7 +46,7 @@ typedef enum {
     VEFD_OK = 0,
     VEFD_ERR_ARG = -1,       /* bad argument or size; nothing was changed */
     VEFD_ERR_CUDA = -2,      /* a CUDA call failed; see vefd_last_error */
-    VEFD_ERR_UNSTABLE = -3,  /* the device guard word is set (NaN, tr C >= L^2, |u| > 0.3, rho <= 0) */
+    VEFD_ERR_UNSTABLE = -3,  /* the device guard word is set (NaN, tr C >= L^2, |u| > 0.3, rho <= 0, wait timeout) */
     VEFD_ERR_TIMEOUT = -4,   /* reserved for bounded device waits */
     VEFD_ERR_STATE = -5      /* call out of order (e.g. memory not bound, fields not initialised) */
 } vefd_status;
@@ -69,7 +69,7 @@ typedef enum {
 } vefd_field;
 
 /* Guard bits of the device status word (sticky until vefd_clear_status). */
-enum { VEFD_ST_NAN = 1, VEFD_ST_TRACE = 2, VEFD_ST_MACH = 4, VEFD_ST_RHO = 8 };
+enum { VEFD_ST_NAN = 1, VEFD_ST_TRACE = 2, VEFD_ST_MACH = 4, VEFD_ST_RHO = 8, VEFD_ST_TIMEOUT = 16 };
 
 /* Lattice and two-component fluid (Sec. 2). */
 typedef struct {
@@ -161,8 +161,9 @@ vefd_status vefd_kernels_per_step(const vefd_ctx *ctx, int *n);
  * bracketed by CUDA events on the context stream (turning it on clears the
  * record).  Tracing aid, not a hot-path requirement. */
 vefd_status vefd_profile_kernels(vefd_ctx *ctx, int on);
-/* Synchronises and returns, per kernel class (0 moments, 1 lattice
- * collide-stream, 2 FENE-P finite differences), the summed device time in
+/* Synchronises and returns, per kernel class (0 densities of the initial
+ * populations, 1 lattice collide-stream, 2 densities of the new populations
+ * fused with the FENE-P finite-difference update), the summed device time in
  * milliseconds and the number of timed launches since profiling was turned
  * on or last read; then clears the record. */
 vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);

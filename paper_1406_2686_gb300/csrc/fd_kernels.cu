@@ -9,6 +9,8 @@
 // first derivative one-sided and the second derivative vanish.
 // Stored variable: Ct = C - I, so (f C - I) = f Ct + (f - 1) I with
 // f - 1 = tr Ct / (L^2 - 3 - tr Ct), evaluated without cancellation.
+// The update runs in the same pass as the densities of the new populations
+// (k_post), since both only wait for the lattice kernel.
 #include "vefd_internal.cuh"
 
 namespace vefd {
@@ -43,14 +45,14 @@ __device__ __forceinline__ constexpr int col_of(int k) {
     return NC == 6 ? (k == 0 ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : (k == 3 ? 1 : 2)))) : (k == 0 ? 0 : (k <= 2 ? 1 : 2));
 }
 
+// One FENE-P update at node (x, y, z): reads C - I and u with their stencil
+// neighbours and the AB2 history, writes C - I of the next time level and the
+// new history, and sets the guard bits.
 template <int D, int NC>
-__global__ void __launch_bounds__(128) k_fenep(const float* __restrict__ Ct, float* __restrict__ Cout,
-                                               float* __restrict__ R, const float* __restrict__ u,
-                                               unsigned* __restrict__ status, StepParams p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
+__device__ __forceinline__ void fenep_node(const float* __restrict__ Ct, float* __restrict__ Cout,
+                                           float* __restrict__ R, const float* __restrict__ u,
+                                           unsigned* __restrict__ status, const StepParams& p, int x, int y, int z,
+                                           float cnew[NC]) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const long long N = p.N;
     const long long i = ((long long)z * ny + y) * nx + x;
@@ -134,21 +136,140 @@ __global__ void __launch_bounds__(128) k_fenep(const float* __restrict__ Ct, flo
         const float Rk = -adv[k] + up - relax + p.kappa * lap[k];
         const float inc = p.have_prev ? 1.5f * Rk - 0.5f * R[k * N + i] : Rk;
         const float cn = c[k] + inc;
+        cnew[k] = cn;
         Cout[k * N + i] = cn;
         R[k * N + i] = Rk;
         if (is_diag<NC>(k)) trn += cn;
         bad |= isnan(cn);
     }
     if (bad || isnan(tr)) atomicOr(status, kStNan);
-    else if (trn + 3.0f >= p.L2m3 + 3.0f || tr + 3.0f >= p.L2m3 + 3.0f) atomicOr(status, kStTrace);
+    else if (trn >= p.L2m3 || tr >= p.L2m3) atomicOr(status, kStTrace);
+}
+
+// Feedback stress at one node, Q = (f C - I) m(phi) = (f Ct + (f - 1) I) m(phi)
+// with f - 1 = tr Ct / (L^2 - 3 - tr Ct) and m = 1, f_+(phi) or f_-(phi)
+// (Eq. NS and the last equation of Sec. 2); stored as the NQ components
+// xx xy xz yy yz zz (3D) or xx xy yy (2D) that the divergence needs.
+template <class L, int NCOMP>
+__device__ __forceinline__ void store_feedback(const float c[L::NC], const float d[NCOMP], const StepParams& p,
+                                               float* __restrict__ Q, long long N, long long i) {
+    const float tr = L::NC == 6 ? c[0] + c[3] + c[5] : c[0] + c[2] + c[3];
+    const float fm1 = tr / (p.L2m3 - tr);
+    const float f = 1.0f + fm1;
+    float m = 1.0f;
+    if (p.phase != 0) {
+        float phi = 1.0f;  // one component: phi = 1 everywhere
+        if (NCOMP == 2) {
+            const float ra = p.rho_ref[0] + d[0], rb = p.rho_ref[1] + d[NCOMP - 1];
+            phi = (ra - rb) / (ra + rb);
+        }
+        const float t = tanhf(phi * p.inv_delta);
+        m = p.phase > 0 ? 0.5f * (1.0f + t) : 0.5f * (1.0f - t);
+    }
+    if (L::NC == 6) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Q[k * N + i] = (f * c[k] + (is_diag<6>(k) ? fm1 : 0.0f)) * m;
+    } else {
+        Q[i] = (f * c[0] + fm1) * m;          // xx
+        Q[N + i] = (f * c[1]) * m;            // xy
+        Q[2 * N + i] = (f * c[2] + fm1) * m;  // yy
+    }
+}
+
+// After the lattice kernel of step n: densities of the new populations
+// (same summation order as the moments kernel), the FENE-P update of C from
+// time n to n+1 when the polymer is evolved, and the feedback stress of time
+// n+1 for the next lattice step.  All of it only reads data the lattice kernel
+// has finished writing, so one pass over the lattice does it.
+template <class L, int NCOMP, bool FD>
+__global__ void __launch_bounds__(128) k_post(const float* __restrict__ fnew, float* __restrict__ drho,
+                                              const float* __restrict__ Ct, float* __restrict__ Cout,
+                                              float* __restrict__ R, const float* __restrict__ u,
+                                              float* __restrict__ Q, unsigned* __restrict__ status, StepParams p,
+                                              int rev) {
+    const int bxi = rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int byi = rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+    const int x = bxi * blockDim.x + threadIdx.x;
+    const int y = byi * blockDim.y + threadIdx.y;
+    const int z = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long N = p.N;
+    const long long i = ((long long)z * p.ny + y) * p.nx + x;
+    float d[NCOMP];
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) {
+        d[s] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) d[s] += __ldg(fnew + (s * L::Q + a) * N + i);
+    }
+    float c[L::NC];
+    if (FD) {
+        fenep_node<L::D, L::NC>(Ct, Cout, R, u, status, p, x, y, z, c);
+    } else {
+#pragma unroll
+        for (int k = 0; k < L::NC; ++k) c[k] = __ldg(Ct + k * N + i);
+    }
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) drho[s * N + i] = d[s];
+    if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
+}
+
+// Densities and feedback stress of a given state (no time step).
+template <class L, int NCOMP>
+__global__ void __launch_bounds__(128) k_pre(const float* __restrict__ f, float* __restrict__ drho,
+                                             const float* __restrict__ Ct, float* __restrict__ Q, StepParams p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const long long N = p.N;
+    const long long i = ((long long)z * p.ny + y) * p.nx + x;
+    float d[NCOMP];
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) {
+        d[s] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) d[s] += __ldg(f + (s * L::Q + a) * N + i);
+        drho[s * N + i] = d[s];
+    }
+    float c[L::NC];
+#pragma unroll
+    for (int k = 0; k < L::NC; ++k) c[k] = __ldg(Ct + k * N + i);
+    if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
 }
 
 }  // namespace
 
-cudaError_t launch_fenep(int lattice, const StepParams& p, const StepBufs& b, cudaStream_t s) {
+cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
+                        const float* fnew, cudaStream_t s, int rev) {
     dim3 blk(32, 4, 1), grd((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz);
-    if (lattice == 1) k_fenep<3, 6><<<grd, blk, 0, s>>>(b.Cin, b.Cout, b.R, b.u, b.status, p);
-    else k_fenep<2, 4><<<grd, blk, 0, s>>>(b.Cin, b.Cout, b.R, b.u, b.status, p);
+#define VEFD_POST(LT, NCP)                                                                                        \
+    do {                                                                                                          \
+        if (fd)                                                                                                   \
+            k_post<LT, NCP, true><<<grd, blk, 0, s>>>(fnew, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, rev);  \
+        else                                                                                                      \
+            k_post<LT, NCP, false><<<grd, blk, 0, s>>>(fnew, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, rev); \
+    } while (0)
+    if (lattice == 1) {
+        if (ncomp == 2) VEFD_POST(D3Q19, 2);
+        else VEFD_POST(D3Q19, 1);
+    } else {
+        if (ncomp == 2) VEFD_POST(D2Q9, 2);
+        else VEFD_POST(D2Q9, 1);
+    }
+#undef VEFD_POST
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s) {
+    dim3 blk(32, 4, 1), grd((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz);
+    if (lattice == 1) {
+        if (ncomp == 2) k_pre<D3Q19, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
+        else k_pre<D3Q19, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
+    } else {
+        if (ncomp == 2) k_pre<D2Q9, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
+        else k_pre<D2Q9, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
+    }
     return cudaGetLastError();
 }
 

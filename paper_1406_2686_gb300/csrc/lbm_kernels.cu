@@ -1,14 +1,25 @@
 // Lattice-Boltzmann kernels of the hybrid step (Sec. 2 of Gupta,
 // Sbragaglia & Scagliarini):
-//   k_moments  : rho_s - rho_ref_s = sum_a fd_a^s                     (Sec. 2, moments)
-//   k_lattice  : per node, in registers: moments, Shan-Chen force (Eq. SCforce),
-//                polymer feedback (eta_P/tau_P) div[(f C - I) m(phi)] (Eq. NS,
-//                last equation of Sec. 2), velocity (Eq. equilibrium:vel),
-//                viscosity (Eq. smoothingvisco), forced BGK collision (Eq. LB)
-//                and push streaming with half-way bounce-back on moving walls.
+//   k_moments     rho_s - rho_ref_s = sum_a fd_a^s                    (Sec. 2, moments)
+//   k_lattice     per node: moments, Shan-Chen force (Eq. SCforce), polymer
+//                 feedback (eta_P/tau_P) div[(f C - I) m(phi)] (Eq. NS and the
+//                 last equation of Sec. 2) from the per-node stress written by
+//                 the densities/FD pass, velocity (Eq. equilibrium:vel),
+//                 viscosity (Eq. smoothingvisco), forced BGK collision (Eq. LB)
+//                 and push streaming with half-way bounce-back on moving walls.
+//                 Populations held in registers; used for any lattice size and
+//                 for the macroscopic (non-streaming) passes.
+//   k_lattice_tma the same step for lattices whose rows are 16-byte multiples:
+//                 one TMA copy stages the block's populations (all components
+//                 and directions of a 32 x BY x BZ tile) in shared memory while
+//                 the threads gather the neighbour densities and the feedback
+//                 stress; the collision then reads its populations from shared
+//                 memory, which keeps register use low and the memory system busy.
 // One thread per node; a warp covers 32 consecutive x, so every population
 // plane is read and written as contiguous 128-byte rows (writes of moving
 // populations are shifted by one element in x).
+#include <cuda.h>
+
 #include "vefd_internal.cuh"
 
 namespace vefd {
@@ -24,12 +35,15 @@ __device__ __forceinline__ int y_clamped(int y, int ny, int walls) {
     return wrap1(y, ny);
 }
 
+// Tile coordinate along one grid axis, optionally traversed backwards.
+__device__ __forceinline__ int tile_index(unsigned b, unsigned n, int rev) { return rev ? (int)(n - 1 - b) : (int)b; }
+
 template <class L, int NCOMP>
 __global__ void __launch_bounds__(128) k_moments(const float* __restrict__ fd, float* __restrict__ drho,
-                                                 StepParams p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
+                                                 StepParams p, int rev) {
+    const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
+    const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
+    const int z = tile_index(blockIdx.z, gridDim.z, rev);
     if (x >= p.nx || y >= p.ny) return;
     const long long N = p.N;
     const long long i = ((long long)z * p.ny + y) * p.nx + x;
@@ -40,44 +54,6 @@ __global__ void __launch_bounds__(128) k_moments(const float* __restrict__ fd, f
         for (int a = 0; a < L::Q; ++a) d += __ldg(fd + (s * L::Q + a) * N + i);
         drho[s * N + i] = d;
     }
-}
-
-// Feedback stress components needed for the divergence at one neighbour:
-// Q = (f C - I) m(phi) = (f Ct + (f - 1) I) m(phi), with f - 1 = tr Ct / (L^2 - 3 - tr Ct).
-template <class L>
-struct QTensor {
-    float q[L::NC];
-};
-
-template <class L, int NCOMP>
-__device__ __forceinline__ QTensor<L> feedback_stress(const float* __restrict__ Ct, long long N, long long j,
-                                                      float drA, float drB, const StepParams& p) {
-    QTensor<L> r;
-    float c[L::NC];
-#pragma unroll
-    for (int k = 0; k < L::NC; ++k) c[k] = __ldg(Ct + k * N + j);
-    float tr;
-    if (L::NC == 6) tr = c[0] + c[3] + c[5];
-    else tr = c[0] + c[2] + c[3];
-    const float fm1 = tr / (p.L2m3 - tr);
-    const float f = 1.0f + fm1;
-    float m = 1.0f;
-    if (p.phase != 0) {
-        // one component: phi = 1 everywhere
-        float phi = 1.0f;
-        if (NCOMP == 2) {
-            const float ra = p.rho_ref[0] + drA, rb = p.rho_ref[1] + drB;
-            phi = (ra - rb) / (ra + rb);
-        }
-        const float t = tanhf(phi * p.inv_delta);
-        m = p.phase > 0 ? 0.5f * (1.0f + t) : 0.5f * (1.0f - t);
-    }
-#pragma unroll
-    for (int k = 0; k < L::NC; ++k) {
-        bool diag = (L::NC == 6) ? (k == 0 || k == 3 || k == 5) : (k == 0 || k == 2 || k == 3);
-        r.q[k] = (f * c[k] + (diag ? fm1 : 0.0f)) * m;
-    }
-    return r;
 }
 
 // index of tensor component (i, j) in the stored order
@@ -91,17 +67,255 @@ __device__ __forceinline__ constexpr int sym(int i, int j) {
     }
 }
 
-template <class L, int NCOMP, bool STREAM>
-__global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const long long N = p.N;
-    const long long i = ((long long)z * ny + y) * nx + x;
+// index of feedback-stress component (i, j), i, j < D, in the stored order
+template <class L>
+__device__ __forceinline__ constexpr int qidx(int i, int j) {
+    return L::D == 3 ? sym<L>(i, j) : (i + j);  // 2D: xx 0, xy 1, yy 2
+}
 
-    // --- moments (same summation order as k_moments) -----------------------
+// Neighbour coordinates of one node.
+struct Nbr {
+    int x, y, z, xm, xp, ymc, ypc, zm, zp, nx, ny;
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
+        const int xx = dx < 0 ? xm : (dx > 0 ? xp : x);
+        const int yy = dy < 0 ? ymc : (dy > 0 ? ypc : y);
+        const int zz = dz < 0 ? zm : (dz > 0 ? zp : z);
+        return ((long long)zz * ny + yy) * nx + xx;
+    }
+};
+
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p) {
+    Nbr n;
+    n.x = x;
+    n.y = y;
+    n.z = z;
+    n.nx = p.nx;
+    n.ny = p.ny;
+    n.xm = wrap1(x - 1, p.nx);
+    n.xp = wrap1(x + 1, p.nx);
+    n.zm = wrap1(z - 1, p.nz);
+    n.zp = wrap1(z + 1, p.nz);
+    n.ymc = y_clamped(y - 1, p.ny, p.walls);
+    n.ypc = y_clamped(y + 1, p.ny, p.walls);
+    return n;
+}
+
+// Neighbour part of the forces at one node:
+//   acc[s] = sum_{a>0} w_a (rho_s(x + c_a) - rho_ref_s) c_a   (Shan-Chen lattice sum;
+//            sum_a w_a c_a rho_ref = 0 so deviations suffice)
+//   Fp     = (eta_P / tau_P) div Q, Q = (f C - I) m(phi) precomputed per node,
+//            central differences, one-sided at walls (the linear-extrapolation
+//            ghost row v(-1) = 2 v(0) - v(1)).
+template <class L, int NCOMP>
+__device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepParams& p, const Nbr& nb, long long i,
+                                                 float acc[2][3], float Fp[3]) {
+    const long long N = p.N;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) acc[s][0] = acc[s][1] = acc[s][2] = 0.0f;
+    if (NCOMP == 2) {
+#pragma unroll
+        for (int a = 1; a < L::Q; ++a) {
+            const long long j = nb.at(L::cx(a), L::cy(a), L::cz(a));
+            const float wa = L::w(a);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float t = wa * __ldg(b.drho + s * N + j);
+                if (L::cx(a)) acc[s][0] += L::cx(a) * t;
+                if (L::cy(a)) acc[s][1] += L::cy(a) * t;
+                if (L::cz(a)) acc[s][2] += L::cz(a) * t;
+            }
+        }
+    }
+    Fp[0] = Fp[1] = Fp[2] = 0.0f;
+    if (p.feedback == 0.0f) return;
+    const float* Q = b.Q;
+    float div[3] = {0.f, 0.f, 0.f};
+    {
+        const long long jm = nb.at(-1, 0, 0), jp = nb.at(1, 0, 0);
+#pragma unroll
+        for (int jj = 0; jj < L::D; ++jj) {
+            const int k = qidx<L>(0, jj);
+            div[jj] += 0.5f * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
+        }
+    }
+    {
+        long long jm = nb.at(0, -1, 0), jp = nb.at(0, 1, 0);
+        float h = 0.5f;
+        if (p.walls && nb.y == 0) {
+            jm = i;
+            h = 1.0f;
+        } else if (p.walls && nb.y == nb.ny - 1) {
+            jp = i;
+            h = 1.0f;
+        }
+#pragma unroll
+        for (int jj = 0; jj < L::D; ++jj) {
+            const int k = qidx<L>(1, jj);
+            div[jj] += h * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
+        }
+    }
+    if (L::D == 3) {
+        const long long jm = nb.at(0, 0, -1), jp = nb.at(0, 0, 1);
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const int k = qidx<L>(2, jj);
+            div[jj] += 0.5f * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fp[k] = p.feedback * div[k];
+}
+
+// Local state after the forces: velocity, relaxation and per-component force.
+template <int NCOMP>
+struct Local {
+    float rs[NCOMP], dr[NCOMP];
+    float inv_rho, ux, uy, uz, usq, omega, src_w;
+    float F[NCOMP][3];
+};
+
+template <class L, int NCOMP>
+__device__ __forceinline__ void local_state(const StepParams& p, const float dr[NCOMP], float jx, float jy, float jz,
+                                            const float acc[2][3], const float Fp[3], Local<NCOMP>& st,
+                                            unsigned* status) {
+    float rho = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) {
+        st.dr[s] = dr[s];
+        st.rs[s] = p.rho_ref[s] + dr[s];
+        rho += st.rs[s];
+    }
+    st.inv_rho = 1.0f / rho;
+    // Shan-Chen: force on A from B's neighbourhood and on B from A's
+    float g[NCOMP][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (NCOMP == 2) {
+            g[0][k] = -p.G * st.rs[0] * acc[1][k];
+            g[NCOMP - 1][k] = -p.G * st.rs[NCOMP - 1] * acc[0][k];
+        } else {
+            g[0][k] = 0.0f;
+        }
+    }
+    float Fb[3], Ftot[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Fb[k] = Fp[k] + p.fext[k];
+        Ftot[k] = Fb[k];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) Ftot[k] += g[s][k];
+    }
+    // velocity with half the total force (Eq. equilibrium:vel)
+    st.ux = (jx + 0.5f * Ftot[0]) * st.inv_rho;
+    st.uy = (jy + 0.5f * Ftot[1]) * st.inv_rho;
+    st.uz = L::D == 3 ? (jz + 0.5f * Ftot[2]) * st.inv_rho : 0.0f;
+    st.usq = st.ux * st.ux + st.uy * st.uy + st.uz * st.uz;
+    // rho c_s^2 (tau - 1/2) = eta_A f_+(phi) + eta_B f_-(phi); one component: phi = 1
+    const float phi = NCOMP == 2 ? (st.rs[0] - st.rs[NCOMP - 1]) * st.inv_rho : 1.0f;
+    const float t = tanhf(phi * p.inv_delta);
+    const float eta = p.eta_A * 0.5f * (1.0f + t) + p.eta_B * 0.5f * (1.0f - t);
+    const float tau = 0.5f + eta * 3.0f * st.inv_rho;
+    st.omega = 1.0f / tau;
+    st.src_w = 1.0f - 0.5f * st.omega;
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) {
+        const float share = st.rs[s] * st.inv_rho;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) st.F[s][k] = g[s][k] + share * Fb[k];
+    }
+    unsigned bits = 0;
+    if (isnan(st.usq) || isnan(rho)) bits |= kStNan;
+    else if (st.usq > 0.09f) bits |= kStMach;
+    if (!(rho > 0.0f) && !isnan(rho)) bits |= kStRho;
+    if (bits) atomicOr(status, bits);
+}
+
+// Collision of every population of every component and push streaming.
+// fget(s, a) returns the stored deviation f_a^s of this node.
+//
+// Opposite directions a and a' (c_a' = -c_a) share c.u and c.F up to sign, so
+// each pair is relaxed together: with E_a = E_even + E_odd, E_a' = E_even -
+// E_odd and likewise for the source,
+//   f*_a  = (1 - omega) f_a  + (omega E_even + (1 - omega/2) S_even) + (omega E_odd + (1 - omega/2) S_odd)
+//   f*_a' = (1 - omega) f_a' + (omega E_even + (1 - omega/2) S_even) - (omega E_odd + (1 - omega/2) S_odd)
+// where, for the deviation equilibrium and the source of Sec. 2,
+//   E_even = w [drho + rho (4.5 (c.u)^2 - 1.5 u.u)],  E_odd = 3 w rho c.u,
+//   S_even = w [9 (c.u)(c.F) - 3 u.F],                  S_odd = 3 w c.F.
+template <class L, int NCOMP, class FGet>
+__device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb, long long i,
+                                               const Local<NCOMP>& st, FGet fget) {
+    const int N = (int)p.N;
+    const int node = (int)i;
+    const int nx = nb.nx, plane = nb.nx * nb.ny;
+    // offsets of the neighbour rows/planes (periodic images included)
+    const int ox[3] = {nb.xm - nb.x, 0, nb.xp - nb.x};
+    const int oz[3] = {(nb.zm - nb.z) * plane, 0, (nb.zp - nb.z) * plane};
+    int oy[3];
+    const bool wall_lo = p.walls && nb.y == 0, wall_hi = p.walls && nb.y == nb.ny - 1;
+    oy[0] = (nb.y == 0 ? nb.ny - 1 : -1) * nx;
+    oy[1] = 0;
+    oy[2] = (nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
+    const float uw6 = 6.0f * p.u_wall;  // 2 (c.U) / c_s^2 with U = +-u_wall along x
+    const float keep = 1.0f - st.omega;
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) {
+        const float Fx = st.F[s][0], Fy = st.F[s][1], Fz = st.F[s][2];
+        const float uF = st.ux * Fx + st.uy * Fy + st.uz * Fz;
+        const float rsv = st.rs[s], drs = st.dr[s];
+        const float base = drs - 1.5f * rsv * st.usq;
+        float* out = b.fout + (long long)s * L::Q * N;
+        // The collision conserves mass exactly (the source has no zeroth
+        // moment), so the rest population is taken as the remainder after the
+        // moving ones; the FP32 weights (sum 1 + 1.5e-8) then leave no
+        // systematic mass bias, only unbiased rounding.
+        float moved = 0.0f;
+#pragma unroll
+        for (int a = 1; a < L::Q; a += 2) {
+            const int ab = a + 1;  // opposite of a
+            const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+            const float wa = L::w(a);
+            const float cu = cx * st.ux + cy * st.uy + cz * st.uz;
+            const float cF = cx * Fx + cy * Fy + cz * Fz;
+            const float e_even = wa * (base + 4.5f * rsv * cu * cu);
+            const float e_odd = 3.0f * wa * rsv * cu;
+            const float s_even = wa * (9.0f * cu * cF - 3.0f * uF);
+            const float s_odd = 3.0f * wa * cF;
+            const float A = st.omega * e_even + st.src_w * s_even;
+            const float B = st.omega * e_odd + st.src_w * s_odd;
+            const float fa = keep * fget(s, a) + (A + B);
+            const float fb = keep * fget(s, ab) + (A - B);
+            moved += fa;
+            moved += fb;
+            // a streams to x + c, its opposite to x - c; a population leaving
+            // through a wall returns to this node in the opposite direction with
+            // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
+            if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
+                const float Uw = cy < 0 ? uw6 : -uw6;
+                out[ab * N + node] = fa - wa * rsv * (float)cx * Uw;
+            } else {
+                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = fa;
+            }
+            if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
+                const float Uw = cy > 0 ? uw6 : -uw6;
+                out[a * N + node] = fb + wa * rsv * (float)cx * Uw;
+            } else {
+                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = fb;
+            }
+        }
+        out[node] = drs - moved;
+    }
+}
+
+template <class L, int NCOMP, bool STREAM>
+__global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int rev) {
+    const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
+    const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
+    const int z = tile_index(blockIdx.z, gridDim.z, rev);
+    if (x >= p.nx || y >= p.ny) return;
+    const long long N = p.N;
+    const long long i = ((long long)z * p.ny + y) * p.nx + x;
+
+    // moments (same summation order as k_moments)
     float f[NCOMP][L::Q];
     float dr[NCOMP];
     float jx = 0.0f, jy = 0.0f, jz = 0.0f;
@@ -122,218 +336,112 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p) {
             if (L::cy(a)) jy += L::cy(a) * f[s][a];
             if (L::cz(a)) jz += L::cz(a) * f[s][a];
         }
-    float rs[NCOMP];
-    float rho = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        rs[s] = p.rho_ref[s] + dr[s];
-        rho += rs[s];
-    }
-    const float inv_rho = 1.0f / rho;
-
-    // neighbour coordinates
-    const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
-    const int zm = wrap1(z - 1, nz), zp = wrap1(z + 1, nz);
-    const int ymc = y_clamped(y - 1, ny, p.walls), ypc = y_clamped(y + 1, ny, p.walls);
-    auto nbr = [&](int dx, int dy, int dz) -> long long {
-        const int xx = dx < 0 ? xm : (dx > 0 ? xp : x);
-        const int yy = dy < 0 ? ymc : (dy > 0 ? ypc : y);
-        const int zz = dz < 0 ? zm : (dz > 0 ? zp : z);
-        return ((long long)zz * ny + yy) * nx + xx;
-    };
-
-    // --- Shan-Chen force: g_s = -G rho_s sum_a w_a rho_s'(x + c_a) c_a ---------
-    // The sum uses density deviations: sum_a w_a c_a rho_ref = 0.
-    float g[NCOMP][3];
-    float axis_dr[NCOMP][6];  // deviations at -x +x -y +y -z +z (for phi of the feedback)
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) g[s][0] = g[s][1] = g[s][2] = 0.0f;
-    if (NCOMP == 2) {
-        float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int a = 1; a < L::Q; ++a) {
-            const long long j = nbr(L::cx(a), L::cy(a), L::cz(a));
-            const float wa = L::w(a);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float dn = __ldg(b.drho + s * N + j);
-                // axis neighbours are remembered for the order parameter
-                if (L::cy(a) == 0 && L::cz(a) == 0) axis_dr[s][L::cx(a) < 0 ? 0 : 1] = dn;
-                if (L::cx(a) == 0 && L::cz(a) == 0) axis_dr[s][L::cy(a) < 0 ? 2 : 3] = dn;
-                if (L::cx(a) == 0 && L::cy(a) == 0) axis_dr[s][L::cz(a) < 0 ? 4 : 5] = dn;
-                const float t = wa * dn;
-                if (L::cx(a)) acc[s][0] += L::cx(a) * t;
-                if (L::cy(a)) acc[s][1] += L::cy(a) * t;
-                if (L::cz(a)) acc[s][2] += L::cz(a) * t;
-            }
-        }
-        // force on A from B's neighbourhood and on B from A's
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            g[0][k] = -p.G * rs[0] * acc[1][k];
-            g[1 % NCOMP][k] = -p.G * rs[NCOMP - 1] * acc[0][k];
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 6; ++q) axis_dr[0][q] = 0.0f;
-    }
-
-    // --- polymer feedback force F_p = (eta_P/tau_P) div Q ----------------------
-    float Fp[3] = {0.0f, 0.0f, 0.0f};
-    if (p.feedback != 0.0f) {
-        const float drA0 = dr[0], drB0 = NCOMP == 2 ? dr[NCOMP - 1] : 0.0f;
-        auto q_at = [&](long long j, int axis_slot) -> QTensor<L> {
-            float dA = 0.f, dB = 0.f;
-            if (NCOMP == 2) {
-                if (axis_slot < 0) {
-                    dA = drA0;
-                    dB = drB0;
-                } else {
-                    dA = axis_dr[0][axis_slot];
-                    dB = axis_dr[NCOMP - 1][axis_slot];
-                }
-            }
-            return feedback_stress<L, NCOMP>(b.Cin, N, j, dA, dB, p);
-        };
-        float div[3] = {0.f, 0.f, 0.f};
-        // x: periodic central difference of Q_x.
-        {
-            QTensor<L> qm = q_at(nbr(-1, 0, 0), 0), qp = q_at(nbr(1, 0, 0), 1);
-#pragma unroll
-            for (int jj = 0; jj < L::D; ++jj) div[jj] += 0.5f * (qp.q[sym<L>(0, jj)] - qm.q[sym<L>(0, jj)]);
-        }
-        // y: central difference, or one-sided at walls (linear-extrapolation ghost).
-        {
-            QTensor<L> qm, qp;
-            float h = 0.5f;
-            if (p.walls && y == 0) {
-                qm = q_at(i, -1);
-                qp = q_at(nbr(0, 1, 0), 3);
-                h = 1.0f;
-            } else if (p.walls && y == ny - 1) {
-                qm = q_at(nbr(0, -1, 0), 2);
-                qp = q_at(i, -1);
-                h = 1.0f;
-            } else {
-                qm = q_at(nbr(0, -1, 0), 2);
-                qp = q_at(nbr(0, 1, 0), 3);
-            }
-#pragma unroll
-            for (int jj = 0; jj < L::D; ++jj) div[jj] += h * (qp.q[sym<L>(1, jj)] - qm.q[sym<L>(1, jj)]);
-        }
-        if (L::D == 3) {
-            QTensor<L> qm = q_at(nbr(0, 0, -1), 4), qp = q_at(nbr(0, 0, 1), 5);
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj) div[jj] += 0.5f * (qp.q[sym<L>(2, jj)] - qm.q[sym<L>(2, jj)]);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Fp[k] = p.feedback * div[k];
-    }
-
-    // --- velocity with half the total force (Eq. equilibrium:vel) --------------
-    float Fb[3];  // polymer + external, shared by rho_s / rho
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Fb[k] = Fp[k] + p.fext[k];
-    float Ftot[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        Ftot[k] = Fb[k];
-#pragma unroll
-        for (int s = 0; s < NCOMP; ++s) Ftot[k] += g[s][k];
-    }
-    const float ux = (jx + 0.5f * Ftot[0]) * inv_rho;
-    const float uy = (jy + 0.5f * Ftot[1]) * inv_rho;
-    const float uz = L::D == 3 ? (jz + 0.5f * Ftot[2]) * inv_rho : 0.0f;
-    const float usq = ux * ux + uy * uy + uz * uz;
-
-    // --- relaxation time: rho c_s^2 (tau - 1/2) = eta_A f_+ + eta_B f_- --------
-    float eta;
-    if (NCOMP == 2) {
-        const float phi = (rs[0] - rs[NCOMP - 1]) * inv_rho;
-        const float t = tanhf(phi * p.inv_delta);
-        eta = p.eta_A * 0.5f * (1.0f + t) + p.eta_B * 0.5f * (1.0f - t);
-    } else {
-        eta = p.eta_A * 0.5f * (1.0f + tanhf(p.inv_delta));
-        eta += p.eta_B * 0.5f * (1.0f - tanhf(p.inv_delta));
-    }
-    const float tau = 0.5f + eta * 3.0f * inv_rho;
-    const float omega = 1.0f / tau;
-    const float src_w = 1.0f - 0.5f * omega;
-
-    // --- guards -----------------------------------------------------------------
-    {
-        unsigned bits = 0;
-        if (isnan(usq) || isnan(rho)) bits |= kStNan;
-        else if (usq > 0.09f) bits |= kStMach;
-        if (!(rho > 0.0f) && !isnan(rho)) bits |= kStRho;
-        if (bits) atomicOr(b.status, bits);
-    }
-
+    const Nbr nb = make_nbr(x, y, z, p);
+    float acc[2][3], Fp[3];
+    neighbour_forces<L, NCOMP>(b, p, nb, i, acc, Fp);
+    Local<NCOMP> st;
+    local_state<L, NCOMP>(p, dr, jx, jy, jz, acc, Fp, st, b.status);
+    b.u[i] = st.ux;
+    b.u[N + i] = st.uy;
+    if (L::D == 3) b.u[2 * N + i] = st.uz;
     if (!STREAM) {
-        b.u[i] = ux;
-        b.u[N + i] = uy;
-        if (L::D == 3) b.u[2 * N + i] = uz;
         if (b.dbg) {
+            // g_s from the lattice sums; F_p; tau
             for (int k = 0; k < 3; ++k) {
-                b.dbg[k * N + i] = g[0][k];
-                b.dbg[(3 + k) * N + i] = NCOMP == 2 ? g[NCOMP - 1][k] : 0.0f;
+                b.dbg[k * N + i] = NCOMP == 2 ? -p.G * st.rs[0] * acc[1][k] : 0.0f;
+                b.dbg[(3 + k) * N + i] = NCOMP == 2 ? -p.G * st.rs[NCOMP - 1] * acc[0][k] : 0.0f;
                 b.dbg[(6 + k) * N + i] = Fp[k];
             }
-            b.dbg[9 * N + i] = tau;
+            b.dbg[9 * N + i] = 1.0f / st.omega;
         }
         return;
     }
-    b.u[i] = ux;
-    b.u[N + i] = uy;
-    if (L::D == 3) b.u[2 * N + i] = uz;
+    collide_stream<L, NCOMP>(b, p, nb, i, st, [&](int s, int a) { return f[s][a]; });
+}
 
-    // --- collision and streaming per component --------------------------------
-    const float uw3 = 3.0f * p.u_wall;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        const float share = rs[s] * inv_rho;
-        const float Fx = g[s][0] + share * Fb[0];
-        const float Fy = g[s][1] + share * Fb[1];
-        const float Fz = g[s][2] + share * Fb[2];
-        const float uF = ux * Fx + uy * Fy + uz * Fz;
-        const float rsv = rs[s];
-        const float drs = dr[s];
-        // The collision conserves mass exactly: sum_a f*_a = sum_a f_a.  The rest
-        // population is therefore taken as that remainder after the moving ones,
-        // so that the FP32 lattice weights (whose sum is 1 + 1.5e-8) leave no
-        // systematic mass bias; what remains is unbiased rounding.
-        float moved = 0.0f;
-#pragma unroll
-        for (int a = 1; a <= L::Q; ++a) {
-            const int ai = a == L::Q ? 0 : a;  // rest population last
-            const int cx = L::cx(ai), cy = L::cy(ai), cz = L::cz(ai);
-            const float wa = L::w(ai);
-            const float cu = cx * ux + cy * uy + cz * uz;
-            const float cF = cx * Fx + cy * Fy + cz * Fz;
-            // deviation equilibrium: E_a - w_a rho_ref = w_a [drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)]
-            const float Ed = wa * (drs + rsv * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-            const float S = wa * (3.0f * (cF - uF) + 9.0f * cu * cF);
-            float fpost;
-            if (ai == 0) {
-                fpost = drs - moved;
-            } else {
-                fpost = f[s][ai] + omega * (Ed - f[s][ai]) + src_w * S;
-                moved += fpost;
-            }
-            int yt = y + cy;
-            if (p.walls && (yt < 0 || yt >= ny)) {
-                // half-way bounce-back into the opposite direction at this node,
-                // moving wall +U (lower) / -U (upper): -2 w rho_s (c.U)/c_s^2
-                const float Uw = yt < 0 ? uw3 : -uw3;
-                b.fout[(s * L::Q + opposite(ai)) * N + i] = fpost - 2.0f * wa * rsv * (float)cx * Uw;
-            } else {
-                yt = wrap1(yt, ny);
-                const int xt = cx < 0 ? xm : (cx > 0 ? xp : x);
-                const int zt = cz < 0 ? zm : (cz > 0 ? zp : z);
-                b.fout[(s * L::Q + ai) * N + ((long long)zt * ny + yt) * nx + xt] = fpost;
-            }
-        }
+// --- TMA-staged variant --------------------------------------------------------
+
+__device__ __forceinline__ unsigned smem_addr(const void* ptr) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
+}
+
+template <class L, int NCOMP, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
+                                                              StepParams p, int rev) {
+    constexpr int P = NCOMP * L::Q;
+    constexpr int T = BX * BY * BZ;
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(float));
+    extern __shared__ __align__(128) float sf[];  // [P][BZ][BY][BX], the TMA box layout
+    __shared__ __align__(8) unsigned long long bar;
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int x0 = tile_index(blockIdx.x, gridDim.x, rev) * BX;
+    const int y0 = tile_index(blockIdx.y, gridDim.y, rev) * BY;
+    const int z0 = tile_index(blockIdx.z, gridDim.z, rev) * BZ;
+    const bool leader = (tx | ty | tz) == 0;
+    const unsigned bar_a = smem_addr(&bar);
+    if (leader) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    if (leader) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(kBytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+            "[%6];" ::"r"(smem_addr(sf)),
+            "l"(reinterpret_cast<unsigned long long>(&tm_fin)), "r"(x0), "r"(y0), "r"(z0), "r"(0), "r"(bar_a)
+            : "memory");
+    }
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    const bool active = x < p.nx && y < p.ny && z < p.nz;
+    const long long N = p.N;
+    const long long i = active ? ((long long)z * p.ny + y) * p.nx + x : 0;
+
+    // neighbour work overlaps the copy; the node's own deviations come from the
+    // density buffer (bit-identical to the sum of the staged populations)
+    float dr[NCOMP];
+    float acc[2][3], Fp[3];
+    Nbr nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
+    if (active) {
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) dr[s] = __ldg(b.drho + s * N + i);
+        neighbour_forces<L, NCOMP>(b, p, nb, i, acc, Fp);
+    }
+
+    // bounded wait for the staged populations; on timeout report and leave
+    unsigned done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar_a), "r"(0u)
+            : "memory");
+    }
+    if (!done) {
+        if (leader) atomicOr(b.status, kStTimeout);
+        return;
+    }
+    if (!active) return;
+
+    const int t = (tz * BY + ty) * BX + tx;
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s)
+#pragma unroll
+        for (int a = 1; a < L::Q; ++a) {
+            const float fa = sf[(s * L::Q + a) * T + t];
+            if (L::cx(a)) jx += L::cx(a) * fa;
+            if (L::cy(a)) jy += L::cy(a) * fa;
+            if (L::cz(a)) jz += L::cz(a) * fa;
+        }
+    Local<NCOMP> st;
+    local_state<L, NCOMP>(p, dr, jx, jy, jz, acc, Fp, st, b.status);
+    b.u[i] = st.ux;
+    b.u[N + i] = st.uy;
+    if (L::D == 3) b.u[2 * N + i] = st.uz;
+    // volatile reads keep the populations in shared memory instead of registers
+    const volatile float* sv = sf;
+    collide_stream<L, NCOMP>(b, p, nb, i, st, [&](int s, int a) { return sv[(s * L::Q + a) * T + t]; });
 }
 
 template <class L, int NCOMP>
@@ -386,27 +494,86 @@ int grid_1d(long long n) {
 
 dim3 node_grid(const StepParams& p) { return dim3((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz); }
 
+// Tile of the TMA variant per lattice.
+template <class L>
+struct Tile;
+template <>
+struct Tile<D3Q19> {
+    static constexpr int BX = 32, BY = 4, BZ = 2;
+};
+template <>
+struct Tile<D2Q9> {
+    static constexpr int BX = 32, BY = 8, BZ = 1;
+};
+
+template <class L, int NCOMP>
+cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
+    constexpr int BX = Tile<L>::BX, BY = Tile<L>::BY, BZ = Tile<L>::BZ;
+    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(float);
+    static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
+    dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
+    k_lattice_tma<L, NCOMP, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b, p, rev);
+    return cudaGetLastError();
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
 }  // namespace
 
-cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s) {
+bool pop_tile_eligible(int lattice, int nx, int ny, int nz) {
+    const int bx = 32, by = lattice == 1 ? 4 : 8, bz = lattice == 1 ? 2 : 1;
+    return nx % 4 == 0 && nx >= bx && ny >= by && nz >= bz;
+}
+
+bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out) {
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    const int Q = lattice == 1 ? 19 : 9;
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(ncomp * Q)};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+    const cuuint32_t box[4] = {32u, lattice == 1 ? 4u : 8u, lattice == 1 ? 2u : 1u, (cuuint32_t)(ncomp * Q)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
     dim3 blk(32, 4, 1), grd = node_grid(p);
     if (lattice == 1) {
-        if (ncomp == 2) k_moments<D3Q19, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, p);
-        else k_moments<D3Q19, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, p);
+        if (ncomp == 2) k_moments<D3Q19, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
+        else k_moments<D3Q19, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
     } else {
-        if (ncomp == 2) k_moments<D2Q9, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, p);
-        else k_moments<D2Q9, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, p);
+        if (ncomp == 2) k_moments<D2Q9, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
+        else k_moments<D2Q9, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
-                           cudaStream_t s) {
+                           cudaStream_t s, const void* tensor_map, int rev) {
+    if (stream_pops && tensor_map) {
+        const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map);
+        if (lattice == 1)
+            return ncomp == 2 ? launch_tma<D3Q19, 2>(tm, p, b, rev, s) : launch_tma<D3Q19, 1>(tm, p, b, rev, s);
+        return ncomp == 2 ? launch_tma<D2Q9, 2>(tm, p, b, rev, s) : launch_tma<D2Q9, 1>(tm, p, b, rev, s);
+    }
     dim3 blk(32, 4, 1), grd = node_grid(p);
-#define VEFD_LAT(LT, NCP)                                                         \
-    do {                                                                          \
-        if (stream_pops) k_lattice<LT, NCP, true><<<grd, blk, 0, s>>>(b, p);      \
-        else k_lattice<LT, NCP, false><<<grd, blk, 0, s>>>(b, p);                 \
+#define VEFD_LAT(LT, NCP)                                                          \
+    do {                                                                           \
+        if (stream_pops) k_lattice<LT, NCP, true><<<grd, blk, 0, s>>>(b, p, rev);  \
+        else k_lattice<LT, NCP, false><<<grd, blk, 0, s>>>(b, p, rev);             \
     } while (0)
     if (lattice == 1) {
         if (ncomp == 2) VEFD_LAT(D3Q19, 2);

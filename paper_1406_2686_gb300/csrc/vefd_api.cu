@@ -4,10 +4,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <cuda.h>
 
 #include "vefd.h"
 #include "vefd_internal.cuh"
@@ -39,10 +42,19 @@ struct vefd_ctx {
     float* C[2] = {nullptr, nullptr};
     float* R = nullptr;
     float* dbg = nullptr;
+    float* qbuf = nullptr;  // feedback stress Q
     unsigned* status = nullptr;
     double* diag_part = nullptr;
     double* diag_out = nullptr;
     std::string err;
+    // TMA descriptors of the two population buffers (when the shape allows)
+    alignas(64) CUtensorMap tmap[2];
+    bool tma_ok = false;
+    // densities and feedback stress of the current state are in drho and Q
+    bool drho_valid = false;
+    // tile traversal: bit0 lattice kernel backwards, bit1 densities/FD kernel
+    // backwards (the default starts it on the tiles the lattice kernel wrote last)
+    int sched = 2;
     // optional per-kernel timing of vefd_step (events on the context stream)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -93,7 +105,7 @@ bool config_ok(const vefd_config* c, const char** why) {
 }
 
 struct Layout {
-    size_t f0, f1, drho, u, c0, c1, r, dbg, status, dpart, dout, total;
+    size_t f0, f1, drho, u, c0, c1, r, dbg, q, status, dpart, dout, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -116,6 +128,7 @@ Layout layout_of(const vefd_config* c) {
     L.c1 = take(sizeof(float) * NC * N);
     L.r = take(sizeof(float) * NC * N);
     L.dbg = take(sizeof(float) * 10 * N);
+    L.q = take(sizeof(float) * 6 * N);
     L.status = take(256);
     L.dpart = take(sizeof(double) * kDiagBlocks * kDiagVals);
     L.dout = take(sizeof(double) * kDiagVals);
@@ -134,9 +147,18 @@ void carve(vefd_ctx* c) {
     c->C[1] = (float*)(b + L.c1);
     c->R = (float*)(b + L.r);
     c->dbg = (float*)(b + L.dbg);
+    c->qbuf = (float*)(b + L.q);
     c->status = (unsigned*)(b + L.status);
     c->diag_part = (double*)(b + L.dpart);
     c->diag_out = (double*)(b + L.dout);
+    c->tma_ok = false;
+    if (!getenv("VEFD_NO_TMA") && pop_tile_eligible(c->cfg.lattice, c->cfg.nx, c->cfg.ny, c->cfg.nz)) {
+        c->tma_ok = make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[0],
+                                        &c->tmap[0]) &&
+                    make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1],
+                                        &c->tmap[1]);
+    }
+    if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
 }
 
 StepParams params_of(const vefd_ctx* c) {
@@ -175,6 +197,7 @@ StepBufs bufs_of(vefd_ctx* c) {
     b.R = c->R;
     b.status = c->status;
     b.dbg = nullptr;
+    b.Q = c->qbuf;
     return b;
 }
 
@@ -200,8 +223,9 @@ vefd_status macro_pass(vefd_ctx* c, bool with_dbg) {
     StepParams p = params_of(c);
     StepBufs b = bufs_of(c);
     b.dbg = with_dbg ? c->dbg : nullptr;
-    VEFD_CUDA(c, launch_moments(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
-    VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, false, p, b, c->stream));
+    VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+    VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, false, p, b, c->stream, nullptr, 0));
+    c->drho_valid = true;
     return VEFD_OK;
 }
 
@@ -346,6 +370,7 @@ vefd_status vefd_set_fenep(vefd_ctx* c, double tau_p, double eta_p, double L2, d
     c->kappa = kappa;
     c->phase = phase;
     c->fd_on = fd_on ? 1 : 0;
+    c->drho_valid = false;  // the feedback stress depends on these parameters
     return VEFD_OK;
 }
 
@@ -406,6 +431,7 @@ vefd_status vefd_init_fields(vefd_ctx* c, const float* rho_A, const float* rho_B
     c->have_prev = 0;
     c->steps = 0;
     c->initialised = 1;
+    c->drho_valid = false;
     return VEFD_OK;
 }
 
@@ -452,10 +478,12 @@ vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, siz
     case VEFD_POPS:
         VEFD_CUDA(c, cudaMemcpyAsync(stg, src, bytes, kind, c->stream));
         VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, stg, c->f[c->cur], 0, c->stream));
+        c->drho_valid = false;
         break;
     case VEFD_C:
         VEFD_CUDA(c, cudaMemcpyAsync(stg, src, bytes, kind, c->stream));
         VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, stg, c->C[c->ccur], c->N, -1.0f, c->stream));
+        c->drho_valid = false;
         break;
     case VEFD_RPREV:
         VEFD_CUDA(c, cudaMemcpyAsync(c->R, src, bytes, kind, c->stream));
@@ -472,25 +500,32 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
     vefd_status st = need_ready(c);
     if (st != VEFD_OK) return st;
     if (nsteps < 0) return fail(c, VEFD_ERR_ARG, "nsteps must be >= 0");
+    const int lat_rev = c->sched & 1, post_rev = (c->sched >> 1) & 1;
     for (int64_t n = 0; n < nsteps; ++n) {
         StepParams p = params_of(c);
         StepBufs b = bufs_of(c);
-        {
+        if (!c->drho_valid) {
             ProfScope ps(c, 0);
-            VEFD_CUDA(c, launch_moments(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+            VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
         }
         {
+            // populations n -> n+1, velocity of time n
             ProfScope ps(c, 1);
-            VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, true, p, b, c->stream));
+            VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, true, p, b, c->stream,
+                                        c->tma_ok ? (const void*)&c->tmap[c->cur] : nullptr, lat_rev));
+        }
+        {
+            // densities of time n+1 (they only depend on the new populations)
+            // and the conformation update n -> n+1 (it only needs u^n and C^n)
+            ProfScope ps(c, 2);
+            VEFD_CUDA(c, launch_post(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, c->f[1 - c->cur], c->stream,
+                                     post_rev));
         }
         if (c->fd_on) {
-            {
-                ProfScope ps(c, 2);
-                VEFD_CUDA(c, launch_fenep(c->cfg.lattice, p, b, c->stream));
-            }
             c->ccur ^= 1;
             c->have_prev = 1;
         }
+        c->drho_valid = true;
         c->cur ^= 1;
         c->steps++;
     }
@@ -523,7 +558,8 @@ vefd_status vefd_read_field(vefd_ctx* c, vefd_field field, void* dst, size_t byt
     case VEFD_RHO_B:
     case VEFD_PHI: {
         StepBufs b = bufs_of(c);
-        VEFD_CUDA(c, launch_moments(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+        VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+        c->drho_valid = true;
         VEFD_CUDA(c, launch_derived(c->cfg.lattice, c->cfg.ncomp, (int)field, p, c->drho, c->C[c->ccur], stg,
                                     c->stream));
         return copy_out(c, dst, stg, bytes, dst_on_device);
@@ -613,7 +649,9 @@ vefd_status vefd_steps_done(const vefd_ctx* c, int64_t* n) {
 
 vefd_status vefd_kernels_per_step(const vefd_ctx* c, int* n) {
     if (!c || !n) return VEFD_ERR_ARG;
-    *n = 2 + c->fd_on;
+    // lattice + (densities of the new populations with the FD update); the
+    // first step after initialisation adds one densities pass
+    *n = 2;
     return VEFD_OK;
 }
 
@@ -745,6 +783,7 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     VEFD_CUDA(c, cudaMemcpyAsync(c->status, &h.status, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
     VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = 1;
+    c->drho_valid = false;
     return VEFD_OK;
 }
 

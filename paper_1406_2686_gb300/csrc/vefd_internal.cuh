@@ -6,6 +6,8 @@
 //   velocity     u[k*N + i], k < D                             (Eq. equilibrium:vel)
 //   conformation Ct[k*N + i] = C_k - delta_k                   (k < NC)
 //   AB2 history  R[k*N + i]                                    (right-hand side of the last FD step)
+//   feedback     Q[k*N + i] = (f(r_P) C - I) m(phi), k < NQ    (the stress whose divergence is the
+//                polymer force; derived from C and the densities of the same time level)
 // Storing deviations keeps FP32 rounding relative to the small departures
 // from a uniform rest state instead of to the full populations.
 #pragma once
@@ -19,7 +21,7 @@ constexpr float kCs2 = 1.0f / 3.0f;
 
 // D2Q9: rest, +-x, +-y, diagonals as opposite pairs; weights 4/9, 1/9, 1/36.
 struct D2Q9 {
-    static constexpr int Q = 9, D = 2, NC = 4;
+    static constexpr int Q = 9, D = 2, NC = 4, NQ = 3;  // NQ: xx xy yy of the feedback stress
     __host__ __device__ static constexpr int cx(int a) {
         return a == 1 || a == 5 || a == 7 ? 1 : (a == 2 || a == 6 || a == 8 ? -1 : 0);
     }
@@ -35,7 +37,7 @@ struct D2Q9 {
 // D3Q19: rest, +-x, +-y, +-z, then the twelve face diagonals as opposite
 // pairs; weights 1/3, 1/18, 1/36 (Sec. 2).
 struct D3Q19 {
-    static constexpr int Q = 19, D = 3, NC = 6;
+    static constexpr int Q = 19, D = 3, NC = 6, NQ = 6;
     __host__ __device__ static constexpr int cx(int a) {
         return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
              : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
@@ -75,7 +77,7 @@ struct StepParams {
 };
 
 // Device guard bits (mirror VEFD_ST_*).
-constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u;
+constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTimeout = 16u;
 
 // Pointers of one step.
 struct StepBufs {
@@ -88,13 +90,33 @@ struct StepBufs {
     float* R;              // AB2 history (in: n-1, out: n)
     unsigned* status;
     float* dbg;            // optional: g_A(3), g_B(3), F_p(3), tau(1) planes of N
+    float* Q;              // feedback stress of time n (read by the lattice kernel; the
+                           // densities/FD pass overwrites it with time n+1)
 };
 
-// Launchers (return cudaGetLastError of the launch).
-cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s);
+// Launchers (return cudaGetLastError of the launch).  `rev` walks the tiles in
+// reverse order, so that a kernel starts on the data its predecessor touched
+// last (still in L2).
+cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev);
+// tensor_map: a CUtensorMap of b.fin for the TMA-staged kernel (streaming
+// steps only), or nullptr for the register-only kernel.
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
-                           cudaStream_t s);
-cudaError_t launch_fenep(int lattice, const StepParams& p, const StepBufs& b, cudaStream_t s);
+                           cudaStream_t s, const void* tensor_map, int rev);
+// Densities of the populations `fnew` into b.drho, when fd the FENE-P update
+// b.Cin -> b.Cout with the AB2 history b.R and velocity b.u, and the feedback
+// stress of the new time level into b.Q.
+cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
+                        const float* fnew, cudaStream_t s, int rev);
+// Densities of b.fin and the feedback stress of (b.fin, b.Cin): the derived
+// state the lattice kernel needs, for the initial state and after writes.
+cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s);
+
+// TMA staging of populations: lattice shapes it applies to, and the tensor
+// map over one population buffer ([ncomp*Q][NZ][NY][NX] FP32) written to `out`
+// (a 64-byte aligned CUtensorMap).  Returns false when the driver entry point
+// is unavailable or the encoding is refused.
+bool pop_tile_eligible(int lattice, int nx, int ny, int nz);
+bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out);
 
 // Field conversions.
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,

@@ -83,7 +83,7 @@ def test_parameter_validation_on_host(lib):
         assert lib.vefd_field_bytes(ctx, vefd.C, ctypes.byref(sz)) == vefd.OK and sz.value == 4 * 6 * 192
         assert lib.vefd_field_bytes(ctx, 99, ctypes.byref(sz)) == vefd.ERR_ARG
         n = ctypes.c_int()
-        assert lib.vefd_kernels_per_step(ctx, ctypes.byref(n)) == vefd.OK and n.value == 3
+        assert lib.vefd_kernels_per_step(ctx, ctypes.byref(n)) == vefd.OK and n.value == 2
     finally:
         vefd.vefd_destroy(ctx)
 

@@ -34,6 +34,16 @@ VARIANTS = {
                          tau_p=15.0, L2=40.0, phase=1),
     "d3q19_2c_nz1": dict(lattice=1, nx=40, ny=9, nz=1, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1,
                          tau_p=15.0, L2=40.0, phase=-1, kappa=0.01),
+    # shapes taken by the TMA-staged lattice kernel (rows of 16-byte multiples),
+    # with ragged last tiles in y and z
+    "d3q19_2c_tma_ragged": dict(lattice=1, nx=36, ny=10, nz=7, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1,
+                                tau_p=20.0, L2=50.0, kappa=0.01, phase=1, fext=(0.0, 0.0, 1e-5)),
+    "d3q19_1c_tma_one_tile": dict(lattice=1, nx=32, ny=4, nz=2, ncomp=1, walls=0, eta_p=0.1, tau_p=20.0, L2=50.0,
+                                  fext=(1e-5, 0.0, 0.0)),
+    "d2q9_2c_tma_periodic": dict(lattice=0, nx=64, ny=13, ncomp=2, walls=0, G=1.5, eta_p=0.1, tau_p=30.0, L2=40.0,
+                                 kappa=0.01, phase=-1),
+    "d2q9_1c_tma_walls": dict(lattice=0, nx=44, ny=9, ncomp=1, walls=1, u_wall=0.02, eta_p=0.05, tau_p=40.0,
+                              L2=50.0, kappa=0.02, fext=(1e-5, 0.0, 0.0)),
 }
 
 
@@ -68,6 +78,24 @@ def test_steps_match_oracle(name, nsteps):
         g, o = P.both(fld)
         assert rel_l2(g, o) < tol, (fld, rel_l2(g, o))
     assert P.g.status() == 0 and P.o.status == 0
+
+
+@pytest.mark.parametrize("name", ["d3q19_2c_tma_ragged", "d2q9_2c_tma_periodic", "d2q9_1c_tma_walls"])
+def test_tma_and_register_kernels_agree(name, monkeypatch):
+    """The TMA-staged lattice kernel and the register-only kernel run the same
+    arithmetic in the same order: populations agree bit for bit."""
+    from paper_1406_2686_gb300 import vefd
+    from pairs import Pair
+    P = Pair(**VARIANTS[name])
+    P.init_random(seed=8)
+    monkeypatch.setenv("VEFD_NO_TMA", "1")
+    Q = Pair(**VARIANTS[name])
+    monkeypatch.delenv("VEFD_NO_TMA")
+    Q.init_random(seed=8)
+    P.g.step(4)
+    Q.g.step(4)
+    assert np.array_equal(P.g.read(vefd.POPS), Q.g.read(vefd.POPS))
+    assert np.array_equal(P.g.read(vefd.C), Q.g.read(vefd.C))
 
 
 def test_config1_couette_2000_steps():
