@@ -11,6 +11,8 @@
 // f - 1 = tr Ct / (L^2 - 3 - tr Ct), evaluated without cancellation.
 // The update runs in the same pass as the densities of the new populations
 // (k_post), since both only wait for the lattice kernel.
+#include <cuda.h>
+
 #include "vefd_internal.cuh"
 
 namespace vefd {
@@ -214,6 +216,60 @@ __global__ void __launch_bounds__(128) k_post(const float* __restrict__ fnew, fl
     if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
 }
 
+// The same pass with the tile's new populations staged in shared memory by
+// one bulk tensor copy, issued before the stencil loads so that both are in
+// flight together; the densities are summed from shared memory afterwards in
+// the same order.
+template <class L, int NCOMP, bool FD, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant__ CUtensorMap tm_fnew,
+                                                           float* __restrict__ drho, const float* __restrict__ Ct,
+                                                           float* __restrict__ Cout, float* __restrict__ R,
+                                                           const float* __restrict__ u, float* __restrict__ Q,
+                                                           unsigned* __restrict__ status, StepParams p, int rev) {
+    constexpr int P = NCOMP * L::Q;
+    constexpr int T = BX * BY * BZ;
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(float));
+    extern __shared__ __align__(128) float sf[];  // [P][BZ][BY][BX]
+    __shared__ __align__(8) unsigned long long bar;
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * BX;
+    const int y0 = (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * BY;
+    const int z0 = (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z) * BZ;
+    const bool leader = (tx | ty | tz) == 0;
+    const unsigned bar_a = smem_u32(&bar);
+    if (leader) mbar_init(bar_a);
+    __syncthreads();
+    if (leader) tma_load_4d(smem_u32(sf), &tm_fnew, x0, y0, z0, 0, bar_a, kBytes);
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    const bool active = x < p.nx && y < p.ny && z < p.nz;
+    const long long N = p.N;
+    const long long i = active ? ((long long)z * p.ny + y) * p.nx + x : 0;
+    float c[L::NC];
+    if (active) {
+        if (FD) {
+            fenep_node<L::D, L::NC>(Ct, Cout, R, u, status, p, x, y, z, c);
+        } else {
+#pragma unroll
+            for (int k = 0; k < L::NC; ++k) c[k] = __ldg(Ct + k * N + i);
+        }
+    }
+    if (!mbar_wait_bounded(bar_a)) {
+        if (leader) atomicOr(status, kStTimeout);
+        return;
+    }
+    if (!active) return;
+    const int t = (tz * BY + ty) * BX + tx;
+    float d[NCOMP];
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) {
+        d[s] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) d[s] += sf[(s * L::Q + a) * T + t];
+        drho[s * N + i] = d[s];
+    }
+    if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
+}
+
 // Densities and feedback stress of a given state (no time step).
 template <class L, int NCOMP>
 __global__ void __launch_bounds__(128) k_pre(const float* __restrict__ f, float* __restrict__ drho,
@@ -259,6 +315,29 @@ cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, co
     }
 #undef VEFD_POST
     return cudaGetLastError();
+}
+
+namespace {
+template <class L, int NCOMP, int BX, int BY, int BZ>
+cudaError_t post_tma(bool fd, const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
+    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(float);
+    dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
+    if (fd)
+        k_post_tma<L, NCOMP, true, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
+                                                                       b.status, p, rev);
+    else
+        k_post_tma<L, NCOMP, false, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
+                                                                        b.status, p, rev);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
+                            const void* tensor_map_fnew, cudaStream_t s, int rev) {
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map_fnew);
+    if (lattice == 1)
+        return ncomp == 2 ? post_tma<D3Q19, 2, 32, 4, 2>(fd, tm, p, b, s, rev) : post_tma<D3Q19, 1, 32, 4, 2>(fd, tm, p, b, s, rev);
+    return ncomp == 2 ? post_tma<D2Q9, 2, 32, 8, 1>(fd, tm, p, b, s, rev) : post_tma<D2Q9, 1, 32, 8, 1>(fd, tm, p, b, s, rev);
 }
 
 cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s) {

@@ -73,15 +73,13 @@ __device__ __forceinline__ constexpr int qidx(int i, int j) {
     return L::D == 3 ? sym<L>(i, j) : (i + j);  // 2D: xx 0, xy 1, yy 2
 }
 
-// Neighbour coordinates of one node.
+// Neighbour offsets of one node (periodic images and wall clamping folded in),
+// as 32-bit node-index differences: lattices are limited to fewer than 2^31
+// population entries, so every plane offset fits.
 struct Nbr {
-    int x, y, z, xm, xp, ymc, ypc, zm, zp, nx, ny;
-    __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
-        const int xx = dx < 0 ? xm : (dx > 0 ? xp : x);
-        const int yy = dy < 0 ? ymc : (dy > 0 ? ypc : y);
-        const int zz = dz < 0 ? zm : (dz > 0 ? zp : z);
-        return ((long long)zz * ny + yy) * nx + xx;
-    }
+    int x, y, z, ny, i;
+    int ox[3], oy[3], oz[3];  // for d = -1, 0, +1 along x, y (clamped at walls), z
+    __device__ __forceinline__ int at(int dx, int dy, int dz) const { return i + ox[dx + 1] + oy[dy + 1] + oz[dz + 1]; }
 };
 
 __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p) {
@@ -89,14 +87,18 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p
     n.x = x;
     n.y = y;
     n.z = z;
-    n.nx = p.nx;
     n.ny = p.ny;
-    n.xm = wrap1(x - 1, p.nx);
-    n.xp = wrap1(x + 1, p.nx);
-    n.zm = wrap1(z - 1, p.nz);
-    n.zp = wrap1(z + 1, p.nz);
-    n.ymc = y_clamped(y - 1, p.ny, p.walls);
-    n.ypc = y_clamped(y + 1, p.ny, p.walls);
+    const int nx = p.nx, plane = p.nx * p.ny;
+    n.i = (z * p.ny + y) * nx + x;
+    n.ox[0] = wrap1(x - 1, nx) - x;
+    n.ox[1] = 0;
+    n.ox[2] = wrap1(x + 1, nx) - x;
+    n.oy[0] = (y_clamped(y - 1, p.ny, p.walls) - y) * nx;
+    n.oy[1] = 0;
+    n.oy[2] = (y_clamped(y + 1, p.ny, p.walls) - y) * nx;
+    n.oz[0] = (wrap1(z - 1, p.nz) - z) * plane;
+    n.oz[1] = 0;
+    n.oz[2] = (wrap1(z + 1, p.nz) - z) * plane;
     return n;
 }
 
@@ -107,15 +109,16 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p
 //            central differences, one-sided at walls (the linear-extrapolation
 //            ghost row v(-1) = 2 v(0) - v(1)).
 template <class L, int NCOMP>
-__device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepParams& p, const Nbr& nb, long long i,
+__device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepParams& p, const Nbr& nb,
                                                  float acc[2][3], float Fp[3]) {
-    const long long N = p.N;
+    const int N = (int)p.N;
+    const int i = nb.i;
 #pragma unroll
     for (int s = 0; s < 2; ++s) acc[s][0] = acc[s][1] = acc[s][2] = 0.0f;
     if (NCOMP == 2) {
 #pragma unroll
         for (int a = 1; a < L::Q; ++a) {
-            const long long j = nb.at(L::cx(a), L::cy(a), L::cz(a));
+            const int j = nb.at(L::cx(a), L::cy(a), L::cz(a));
             const float wa = L::w(a);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -131,7 +134,7 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
     const float* Q = b.Q;
     float div[3] = {0.f, 0.f, 0.f};
     {
-        const long long jm = nb.at(-1, 0, 0), jp = nb.at(1, 0, 0);
+        const int jm = nb.at(-1, 0, 0), jp = nb.at(1, 0, 0);
 #pragma unroll
         for (int jj = 0; jj < L::D; ++jj) {
             const int k = qidx<L>(0, jj);
@@ -139,7 +142,7 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
         }
     }
     {
-        long long jm = nb.at(0, -1, 0), jp = nb.at(0, 1, 0);
+        int jm = nb.at(0, -1, 0), jp = nb.at(0, 1, 0);
         float h = 0.5f;
         if (p.walls && nb.y == 0) {
             jm = i;
@@ -155,7 +158,7 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
         }
     }
     if (L::D == 3) {
-        const long long jm = nb.at(0, 0, -1), jp = nb.at(0, 0, 1);
+        const int jm = nb.at(0, 0, -1), jp = nb.at(0, 0, 1);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             const int k = qidx<L>(2, jj);
@@ -242,14 +245,14 @@ __device__ __forceinline__ void local_state(const StepParams& p, const float dr[
 //   E_even = w [drho + rho (4.5 (c.u)^2 - 1.5 u.u)],  E_odd = 3 w rho c.u,
 //   S_even = w [9 (c.u)(c.F) - 3 u.F],                  S_odd = 3 w c.F.
 template <class L, int NCOMP, class FGet>
-__device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb, long long i,
+__device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
                                                const Local<NCOMP>& st, FGet fget) {
     const int N = (int)p.N;
-    const int node = (int)i;
-    const int nx = nb.nx, plane = nb.nx * nb.ny;
-    // offsets of the neighbour rows/planes (periodic images included)
-    const int ox[3] = {nb.xm - nb.x, 0, nb.xp - nb.x};
-    const int oz[3] = {(nb.zm - nb.z) * plane, 0, (nb.zp - nb.z) * plane};
+    const int node = nb.i;
+    const int* ox = nb.ox;
+    const int* oz = nb.oz;
+    // streaming offsets in y are periodic (walls are handled by bounce-back)
+    const int nx = p.nx;
     int oy[3];
     const bool wall_lo = p.walls && nb.y == 0, wall_hi = p.walls && nb.y == nb.ny - 1;
     oy[0] = (nb.y == 0 ? nb.ny - 1 : -1) * nx;
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
         }
     const Nbr nb = make_nbr(x, y, z, p);
     float acc[2][3], Fp[3];
-    neighbour_forces<L, NCOMP>(b, p, nb, i, acc, Fp);
+    neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp);
     Local<NCOMP> st;
     local_state<L, NCOMP>(p, dr, jx, jy, jz, acc, Fp, st, b.status);
     b.u[i] = st.ux;
@@ -356,14 +359,10 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
         }
         return;
     }
-    collide_stream<L, NCOMP>(b, p, nb, i, st, [&](int s, int a) { return f[s][a]; });
+    collide_stream<L, NCOMP>(b, p, nb, st, [&](int s, int a) { return f[s][a]; });
 }
 
 // --- TMA-staged variant --------------------------------------------------------
-
-__device__ __forceinline__ unsigned smem_addr(const void* ptr) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
-}
 
 template <class L, int NCOMP, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
@@ -378,20 +377,10 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     const int y0 = tile_index(blockIdx.y, gridDim.y, rev) * BY;
     const int z0 = tile_index(blockIdx.z, gridDim.z, rev) * BZ;
     const bool leader = (tx | ty | tz) == 0;
-    const unsigned bar_a = smem_addr(&bar);
-    if (leader) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    const unsigned bar_a = smem_u32(&bar);
+    if (leader) mbar_init(bar_a);
     __syncthreads();
-    if (leader) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(kBytes) : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-            "[%6];" ::"r"(smem_addr(sf)),
-            "l"(reinterpret_cast<unsigned long long>(&tm_fin)), "r"(x0), "r"(y0), "r"(z0), "r"(0), "r"(bar_a)
-            : "memory");
-    }
+    if (leader) tma_load_4d(smem_u32(sf), &tm_fin, x0, y0, z0, 0, bar_a, kBytes);
     const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
     const bool active = x < p.nx && y < p.ny && z < p.nz;
     const long long N = p.N;
@@ -405,19 +394,11 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     if (active) {
 #pragma unroll
         for (int s = 0; s < NCOMP; ++s) dr[s] = __ldg(b.drho + s * N + i);
-        neighbour_forces<L, NCOMP>(b, p, nb, i, acc, Fp);
+        neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp);
     }
 
     // bounded wait for the staged populations; on timeout report and leave
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar_a), "r"(0u)
-            : "memory");
-    }
-    if (!done) {
+    if (!mbar_wait_bounded(bar_a)) {
         if (leader) atomicOr(b.status, kStTimeout);
         return;
     }
@@ -441,7 +422,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     if (L::D == 3) b.u[2 * N + i] = st.uz;
     // volatile reads keep the populations in shared memory instead of registers
     const volatile float* sv = sf;
-    collide_stream<L, NCOMP>(b, p, nb, i, st, [&](int s, int a) { return sv[(s * L::Q + a) * T + t]; });
+    collide_stream<L, NCOMP>(b, p, nb, st, [&](int s, int a) { return sv[(s * L::Q + a) * T + t]; });
 }
 
 template <class L, int NCOMP>

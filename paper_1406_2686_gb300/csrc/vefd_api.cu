@@ -518,8 +518,12 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
             // densities of time n+1 (they only depend on the new populations)
             // and the conformation update n -> n+1 (it only needs u^n and C^n)
             ProfScope ps(c, 2);
-            VEFD_CUDA(c, launch_post(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, c->f[1 - c->cur], c->stream,
-                                     post_rev));
+            if (c->tma_ok)
+                VEFD_CUDA(c, launch_post_tma(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap[1 - c->cur],
+                                             c->stream, post_rev));
+            else
+                VEFD_CUDA(c, launch_post(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, c->f[1 - c->cur],
+                                         c->stream, post_rev));
         }
         if (c->fd_on) {
             c->ccur ^= 1;

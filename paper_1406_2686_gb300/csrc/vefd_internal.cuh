@@ -76,6 +76,45 @@ struct StepParams {
     float rho_ref[2];      // deviation reference densities
 };
 
+// --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(ptr));
+}
+
+// One-shot transaction barrier: init for one arrival, made visible to the
+// asynchronous proxy before any copy is issued against it.
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive once, announcing `bytes` of incoming copies, and issue a 4-D tiled
+// bulk tensor copy of the box at (c0, c1, c2, c3) into shared memory.
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                            unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Waits for phase 0 of the barrier for a bounded number of polls; returns
+// false when the copy has not landed (the caller reports a timeout).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar) {
+    unsigned done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(0u)
+            : "memory");
+    }
+    return done != 0;
+}
+
 // Device guard bits (mirror VEFD_ST_*).
 constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTimeout = 16u;
 
@@ -107,6 +146,10 @@ cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepP
 // stress of the new time level into b.Q.
 cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
                         const float* fnew, cudaStream_t s, int rev);
+// With a tensor map of `fnew` (TMA-eligible shapes), the same pass stages the
+// tile's populations with one bulk copy while the stencil loads are in flight.
+cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
+                            const void* tensor_map_fnew, cudaStream_t s, int rev);
 // Densities of b.fin and the feedback stress of (b.fin, b.Cin): the derived
 // state the lattice kernel needs, for the initial state and after writes.
 cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s);
