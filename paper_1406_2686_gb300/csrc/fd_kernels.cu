@@ -47,75 +47,44 @@ __device__ __forceinline__ constexpr int col_of(int k) {
     return NC == 6 ? (k == 0 ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : (k == 3 ? 1 : 2)))) : (k == 0 ? 0 : (k <= 2 ? 1 : 2));
 }
 
-// One FENE-P update at node (x, y, z): reads C - I and u with their stencil
-// neighbours and the AB2 history, writes C - I of the next time level and the
-// new history, and sets the guard bits.
-template <int D, int NC>
-__device__ __forceinline__ void fenep_node(const float* __restrict__ Ct, float* __restrict__ Cout,
-                                           float* __restrict__ R, const float* __restrict__ u,
-                                           unsigned* __restrict__ status, const StepParams& p, int x, int y, int z,
-                                           float cnew[NC]) {
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const long long N = p.N;
-    const long long i = ((long long)z * ny + y) * nx + x;
-    const long long ixm = i - x + wrap1(x - 1, nx), ixp = i - x + wrap1(x + 1, nx);
-    // y neighbours and the stencil weights of the first and second derivative
-    long long iym, iyp;
-    float hy1 = 0.5f, hy2 = 1.0f;  // d_y v = hy1 (v+ - v-); d_yy v = hy2 (v+ - 2 v + v-)
-    if (p.walls && y == 0) {
-        iym = i;
-        iyp = i + nx;
-        hy1 = 1.0f;
-        hy2 = 0.0f;
-    } else if (p.walls && y == ny - 1) {
-        iym = i - nx;
-        iyp = i;
-        hy1 = 1.0f;
-        hy2 = 0.0f;
-    } else {
-        iym = ((long long)z * ny + wrap1(y - 1, ny)) * nx + x;
-        iyp = ((long long)z * ny + wrap1(y + 1, ny)) * nx + x;
-    }
-    long long izm = i, izp = i;
-    if (D == 3) {
-        izm = ((long long)wrap1(z - 1, nz) * ny + y) * nx + x;
-        izp = ((long long)wrap1(z + 1, nz) * ny + y) * nx + x;
-    }
-
+// FENE-P update at one node from its gathered stencil.  v(k, d) returns field
+// k (0..NC-1: C - I components, NC..NC+D-1: velocity components) at stencil
+// point d (0 centre, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z); hy1 and hy2 are the
+// y weights of the first and second differences (1/2 and 1 inside, 1 and 0
+// at a wall row, where the -y or +y point is the node itself).  Writes the new
+// C - I to cnew, the right-hand side to Rnew, and returns the guard bits.
+template <int D, int NC, class V>
+__device__ __forceinline__ unsigned fenep_compute(V v, float hy1, float hy2, const float Rprev[NC], const StepParams& p,
+                                                  float cnew[NC], float Rnew[NC]) {
     // velocity gradient Gu[a][b] = d_a u_b and the local velocity
     float Gu[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float uu[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-        const float* ub = u + b * N;
-        uu[b] = __ldg(ub + i);
-        Gu[0][b] = 0.5f * (__ldg(ub + ixp) - __ldg(ub + ixm));
-        Gu[1][b] = hy1 * (__ldg(ub + iyp) - __ldg(ub + iym));
-        if (D == 3) Gu[2][b] = 0.5f * (__ldg(ub + izp) - __ldg(ub + izm));
+        uu[b] = v(NC + b, 0);
+        Gu[0][b] = 0.5f * (v(NC + b, 2) - v(NC + b, 1));
+        Gu[1][b] = hy1 * (v(NC + b, 4) - v(NC + b, 3));
+        if (D == 3) Gu[2][b] = 0.5f * (v(NC + b, 6) - v(NC + b, 5));
     }
-
     float c[NC], adv[NC], lap[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        const float* ck = Ct + k * N;
-        const float c0 = __ldg(ck + i);
-        const float cxm = __ldg(ck + ixm), cxp = __ldg(ck + ixp);
-        const float cym = __ldg(ck + iym), cyp = __ldg(ck + iyp);
+        const float c0 = v(k, 0);
+        const float cxm = v(k, 1), cxp = v(k, 2), cym = v(k, 3), cyp = v(k, 4);
         c[k] = c0;
         float a = uu[0] * 0.5f * (cxp - cxm) + uu[1] * hy1 * (cyp - cym);
         float l = (cxp - 2.0f * c0 + cxm) + hy2 * (cyp - 2.0f * c0 + cym);
         if (D == 3) {
-            const float czm = __ldg(ck + izm), czp = __ldg(ck + izp);
+            const float czm = v(k, 5), czp = v(k, 6);
             a += uu[2] * 0.5f * (czp - czm);
             l += czp - 2.0f * c0 + czm;
         }
         adv[k] = a;
         lap[k] = l;
     }
-    float tr = NC == 6 ? c[0] + c[3] + c[5] : c[0] + c[2] + c[3];
+    const float tr = NC == 6 ? c[0] + c[3] + c[5] : c[0] + c[2] + c[3];
     const float fm1 = tr / (p.L2m3 - tr);
     const float f = 1.0f + fm1;
-
     // full C = Ct + I as a 3x3 matrix
     float Cm[3][3];
 #pragma unroll
@@ -125,7 +94,6 @@ __device__ __forceinline__ void fenep_node(const float* __restrict__ Ct, float* 
             const int k = tidx<NC>(a, b);
             Cm[a][b] = (k < 0 ? 0.0f : c[k]) + (a == b ? 1.0f : 0.0f);
         }
-
     float trn = 0.0f;
     bool bad = false;
 #pragma unroll
@@ -136,16 +104,66 @@ __device__ __forceinline__ void fenep_node(const float* __restrict__ Ct, float* 
         for (int e = 0; e < D; ++e) up += Cm[a][e] * Gu[e][b] + Gu[e][a] * Cm[e][b];
         const float relax = (f * c[k] + (is_diag<NC>(k) ? fm1 : 0.0f)) * p.inv_tau_p;
         const float Rk = -adv[k] + up - relax + p.kappa * lap[k];
-        const float inc = p.have_prev ? 1.5f * Rk - 0.5f * R[k * N + i] : Rk;
+        const float inc = p.have_prev ? 1.5f * Rk - 0.5f * Rprev[k] : Rk;
         const float cn = c[k] + inc;
         cnew[k] = cn;
-        Cout[k * N + i] = cn;
-        R[k * N + i] = Rk;
+        Rnew[k] = Rk;
         if (is_diag<NC>(k)) trn += cn;
         bad |= isnan(cn);
     }
-    if (bad || isnan(tr)) atomicOr(status, kStNan);
-    else if (trn >= p.L2m3 || tr >= p.L2m3) atomicOr(status, kStTrace);
+    if (bad || isnan(tr)) return kStNan;
+    if (trn >= p.L2m3 || tr >= p.L2m3) return kStTrace;
+    return 0u;
+}
+
+// One FENE-P update at node (x, y, z) with its stencil read from global
+// memory; writes C - I of the next time level and the new history.
+template <int D, int NC>
+__device__ __forceinline__ void fenep_node(const float* __restrict__ Ct, float* __restrict__ Cout,
+                                           float* __restrict__ R, const float* __restrict__ u,
+                                           unsigned* __restrict__ status, const StepParams& p, int x, int y, int z,
+                                           float cnew[NC]) {
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const long long N = p.N;
+    const long long i = ((long long)z * ny + y) * nx + x;
+    long long idx[7];
+    idx[0] = i;
+    idx[1] = i - x + wrap1(x - 1, nx);
+    idx[2] = i - x + wrap1(x + 1, nx);
+    float hy1 = 0.5f, hy2 = 1.0f;
+    if (p.walls && y == 0) {
+        idx[3] = i;
+        idx[4] = i + nx;
+        hy1 = 1.0f;
+        hy2 = 0.0f;
+    } else if (p.walls && y == ny - 1) {
+        idx[3] = i - nx;
+        idx[4] = i;
+        hy1 = 1.0f;
+        hy2 = 0.0f;
+    } else {
+        idx[3] = ((long long)z * ny + wrap1(y - 1, ny)) * nx + x;
+        idx[4] = ((long long)z * ny + wrap1(y + 1, ny)) * nx + x;
+    }
+    idx[5] = idx[6] = i;
+    if (D == 3) {
+        idx[5] = ((long long)wrap1(z - 1, nz) * ny + y) * nx + x;
+        idx[6] = ((long long)wrap1(z + 1, nz) * ny + y) * nx + x;
+    }
+    auto v = [&](int k, int d) -> float {
+        const float* base = k < NC ? Ct + k * N : u + (k - NC) * N;
+        return __ldg(base + idx[d]);
+    };
+    float Rprev[NC], Rnew[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) Rprev[k] = p.have_prev ? R[k * N + i] : 0.0f;
+    const unsigned bits = fenep_compute<D, NC>(v, hy1, hy2, Rprev, p, cnew, Rnew);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        Cout[k * N + i] = cnew[k];
+        R[k * N + i] = Rnew[k];
+    }
+    if (bits) atomicOr(status, bits);
 }
 
 // Feedback stress at one node, Q = (f C - I) m(phi) = (f Ct + (f - 1) I) m(phi)
@@ -270,6 +288,171 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
     if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
 }
 
+// D3Q19 variant of the pass that marches along z through a column of
+// 32 x 8 nodes.  C - I and u of four consecutive planes (with a one-node halo
+// in x and y) live in a shared-memory ring, so every stencil value is read
+// from global memory about 1.3 times instead of 7; each plane's new
+// populations arrive by one bulk tensor copy (box 32 x 8 x 1 x P) that
+// overlaps the stencil arithmetic.  Needs NX % 32 == 0 and NY % 8 == 0.
+constexpr int kZmBX = 32, kZmBY = 8, kZmHX = kZmBX + 2, kZmHY = kZmBY + 2, kZmNF = 9;
+constexpr int kZmPlane = kZmNF * kZmHY * kZmHX;  // floats per ring plane
+
+template <int NCOMP>
+constexpr int zm_smem_bytes() {
+    return (NCOMP * 19 * kZmBX * kZmBY + 4 * kZmPlane) * (int)sizeof(float);
+}
+
+template <int NCOMP, bool FD>
+__global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
+                                                               float* __restrict__ drho, const float* __restrict__ Ct,
+                                                               float* __restrict__ Cout, float* __restrict__ R,
+                                                               const float* __restrict__ u, float* __restrict__ Q,
+                                                               unsigned* __restrict__ status, StepParams p, int zs,
+                                                               int rev) {
+    using L = D3Q19;
+    constexpr int P = NCOMP * L::Q;
+    constexpr int T = kZmBX * kZmBY;
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(float));
+    extern __shared__ __align__(128) float sm[];
+    float* sP = sm;            // [P][BY][BX] populations of the current plane
+    float* ring = sm + P * T;  // [4][NF][HY][HX]
+    __shared__ __align__(8) unsigned long long bar;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int N = (int)p.N, plane = nx * ny;
+    const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * kZmBX;
+    const int y0 = (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kZmBY;
+    const int z0 = (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z) * zs;
+    const int z1 = min(z0 + zs, nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool leader = (tx | ty) == 0;
+    const unsigned bar_a = smem_u32(&bar);
+    if (leader) mbar_init(bar_a);
+
+    // which ring cells this thread stages: its own (interior) cell and, for
+    // some warps, one halo cell (rows y0-1 / y0+8, columns x0-1 / x0+32)
+    int hr = -1, hc = -1;
+    if (ty == 0) {
+        hr = 0;
+        hc = tx + 1;
+    } else if (ty == kZmBY - 1) {
+        hr = kZmHY - 1;
+        hc = tx + 1;
+    } else if (ty == 1 && tx < 2 * kZmHY) {
+        hr = tx % kZmHY;
+        hc = tx < kZmHY ? 0 : kZmHX - 1;
+    }
+    int hx = 0, hyg = 0;
+    bool hvalid = false;
+    if (hr >= 0) {
+        hx = wrap1(x0 - 1 + hc, nx);
+        const int yy = y0 - 1 + hr;
+        if (p.walls) {
+            hvalid = yy >= 0 && yy < ny;  // ghost rows beyond walls are never read
+            hyg = yy;
+        } else {
+            hvalid = true;
+            hyg = wrap1(yy, ny);
+        }
+    }
+    auto load_plane = [&](int zp, float v_in[kZmNF], float v_h[kZmNF]) {
+        const int zz = wrap1(zp, nz);
+        const int gi = zz * plane + y * nx + x;
+        const int gh = zz * plane + hyg * nx + hx;
+#pragma unroll
+        for (int k = 0; k < kZmNF; ++k) {
+            const float* base = k < 6 ? Ct + k * N : u + (k - 6) * N;
+            v_in[k] = __ldg(base + gi);
+            if (hvalid) v_h[k] = __ldg(base + gh);
+        }
+    };
+    auto store_plane = [&](int slot, const float v_in[kZmNF], const float v_h[kZmNF]) {
+        float* rp = ring + slot * kZmPlane;
+#pragma unroll
+        for (int k = 0; k < kZmNF; ++k) {
+            rp[(k * kZmHY + ty + 1) * kZmHX + tx + 1] = v_in[k];
+            if (hvalid) rp[(k * kZmHY + hr) * kZmHX + hc] = v_h[k];
+        }
+    };
+    float vi[kZmNF], vh[kZmNF];
+    // prologue: planes z0-1, z0, z0+1 into slots 0, 1, 2
+    for (int q = 0; q < 3; ++q) {
+        load_plane(z0 - 1 + q, vi, vh);
+        store_plane(q, vi, vh);
+    }
+    __syncthreads();
+
+    const bool wall_lo = p.walls && y == 0, wall_hi = p.walls && y == ny - 1;
+    const float hy1 = (wall_lo || wall_hi) ? 1.0f : 0.5f;
+    const float hy2 = (wall_lo || wall_hi) ? 0.0f : 1.0f;
+    const int ry = ty + 1, rc = tx + 1;
+    const int rym = wall_lo ? ry : ry - 1, ryp = wall_hi ? ry : ry + 1;
+    const int t = ty * kZmBX + tx;
+
+    for (int k = 0; k < z1 - z0; ++k) {
+        const int z = z0 + k;
+        // new populations of this plane: one bulk copy (the buffer was released
+        // by every thread at the barrier ending the previous iteration)
+        if (leader) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_load_4d(smem_u32(sP), &tm_fnew, x0, y0, z, 0, bar_a, kBytes);
+        }
+        // stage plane z+2 while this plane is computed
+        const bool more = z + 2 <= z1;
+        if (more) load_plane(z + 2, vi, vh);
+        const int i = z * plane + y * nx + x;
+        float c[6];
+        if (FD) {
+            const float* pm = ring + (k % 4) * kZmPlane;
+            const float* pc = ring + ((k + 1) % 4) * kZmPlane;
+            const float* pp = ring + ((k + 2) % 4) * kZmPlane;
+            auto v = [&](int f, int d) -> float {
+                const int o = f * kZmHY * kZmHX;
+                switch (d) {
+                case 0: return pc[o + ry * kZmHX + rc];
+                case 1: return pc[o + ry * kZmHX + rc - 1];
+                case 2: return pc[o + ry * kZmHX + rc + 1];
+                case 3: return pc[o + rym * kZmHX + rc];
+                case 4: return pc[o + ryp * kZmHX + rc];
+                case 5: return pm[o + ry * kZmHX + rc];
+                default: return pp[o + ry * kZmHX + rc];
+                }
+            };
+            float Rprev[6], Rnew[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) Rprev[q] = p.have_prev ? R[q * N + i] : 0.0f;
+            const unsigned bits = fenep_compute<3, 6>(v, hy1, hy2, Rprev, p, c, Rnew);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                Cout[q * N + i] = c[q];
+                R[q * N + i] = Rnew[q];
+            }
+            if (bits) atomicOr(status, bits);
+        } else {
+            const float* pc = ring + ((k + 1) % 4) * kZmPlane;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) c[q] = pc[(q * kZmHY + ry) * kZmHX + rc];
+        }
+        // densities of the new populations (same summation order as elsewhere)
+        const bool ok = mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));
+        if (__syncthreads_or(!ok)) {
+            if (leader) atomicOr(status, kStTimeout);
+            return;
+        }
+        float d[NCOMP];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) {
+            d[s] = 0.0f;
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) d[s] += sP[(s * L::Q + a) * T + t];
+            drho[s * N + i] = d[s];
+        }
+        if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
+        if (more) store_plane((k + 3) % 4, vi, vh);
+        __syncthreads();
+    }
+}
+
 // Densities and feedback stress of a given state (no time step).
 template <class L, int NCOMP>
 __global__ void __launch_bounds__(128) k_pre(const float* __restrict__ f, float* __restrict__ drho,
@@ -338,6 +521,45 @@ cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p
     if (lattice == 1)
         return ncomp == 2 ? post_tma<D3Q19, 2, 32, 4, 2>(fd, tm, p, b, s, rev) : post_tma<D3Q19, 1, 32, 4, 2>(fd, tm, p, b, s, rev);
     return ncomp == 2 ? post_tma<D2Q9, 2, 32, 8, 1>(fd, tm, p, b, s, rev) : post_tma<D2Q9, 1, 32, 8, 1>(fd, tm, p, b, s, rev);
+}
+
+bool post_zm_eligible(int lattice, int nx, int ny) { return lattice == 1 && nx % kZmBX == 0 && ny % kZmBY == 0; }
+
+namespace {
+int g_sm_count = 0;
+
+template <int NCOMP, bool FD>
+cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
+    constexpr int smem = zm_smem_bytes<NCOMP>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_post_zm<NCOMP, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_sm_count = 152;
+    }
+    // one wave: split z so that the columns x z-segments fill two blocks per SM
+    const int bxy = (p.nx / kZmBX) * (p.ny / kZmBY);
+    int nzb = (2 * g_sm_count) / bxy;
+    if (nzb < 1) nzb = 1;
+    if (nzb > p.nz) nzb = p.nz;
+    const int zs = (p.nz + nzb - 1) / nzb;
+    nzb = (p.nz + zs - 1) / zs;
+    dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, p.ny / kZmBY, nzb);
+    k_post_zm<NCOMP, FD><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, zs, rev);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBufs& b, const void* tensor_map_fnew,
+                           cudaStream_t s, int rev) {
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map_fnew);
+    if (ncomp == 2) return fd ? post_zm<2, true>(tm, p, b, s, rev) : post_zm<2, false>(tm, p, b, s, rev);
+    return fd ? post_zm<1, true>(tm, p, b, s, rev) : post_zm<1, false>(tm, p, b, s, rev);
 }
 
 cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s) {

@@ -508,7 +508,8 @@ bool pop_tile_eligible(int lattice, int nx, int ny, int nz) {
     return nx % 4 == 0 && nx >= bx && ny >= by && nz >= bz;
 }
 
-bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out) {
+bool make_pop_tensor_map_box(int lattice, int ncomp, int nx, int ny, int nz, const float* base, int bx, int by, int bz,
+                             void* out) {
     static EncodeTiled encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -522,12 +523,17 @@ bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const f
     const int Q = lattice == 1 ? 19 : 9;
     const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(ncomp * Q)};
     const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
-    const cuuint32_t box[4] = {32u, lattice == 1 ? 4u : 8u, lattice == 1 ? 2u : 1u, (cuuint32_t)(ncomp * Q)};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)(ncomp * Q)};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out) {
+    return make_pop_tensor_map_box(lattice, ncomp, nx, ny, nz, base, 32, lattice == 1 ? 4 : 8, lattice == 1 ? 2 : 1,
+                                   out);
 }
 
 cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {

@@ -50,11 +50,15 @@ struct vefd_ctx {
     // TMA descriptors of the two population buffers (when the shape allows)
     alignas(64) CUtensorMap tmap[2];
     bool tma_ok = false;
+    // tensor maps with a 32 x 8 x 1 box for the z-marching densities/FD pass
+    alignas(64) CUtensorMap tmap_zm[2];
+    bool zm_ok = false;
     // densities and feedback stress of the current state are in drho and Q
     bool drho_valid = false;
     // tile traversal: bit0 lattice kernel backwards, bit1 densities/FD kernel
-    // backwards (the default starts it on the tiles the lattice kernel wrote last)
-    int sched = 2;
+    // backwards; opposite orders make each kernel start on the tiles the other
+    // touched last (still in L2)
+    int sched = 1;
     // optional per-kernel timing of vefd_step (events on the context stream)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -157,6 +161,13 @@ void carve(vefd_ctx* c) {
                                         &c->tmap[0]) &&
                     make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1],
                                         &c->tmap[1]);
+    }
+    c->zm_ok = false;
+    if (c->tma_ok && !getenv("VEFD_NO_ZMARCH") && post_zm_eligible(c->cfg.lattice, c->cfg.nx, c->cfg.ny)) {
+        c->zm_ok = make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[0], 32,
+                                           8, 1, &c->tmap_zm[0]) &&
+                   make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1], 32,
+                                           8, 1, &c->tmap_zm[1]);
     }
     if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
 }
@@ -518,7 +529,10 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
             // densities of time n+1 (they only depend on the new populations)
             // and the conformation update n -> n+1 (it only needs u^n and C^n)
             ProfScope ps(c, 2);
-            if (c->tma_ok)
+            if (c->zm_ok)
+                VEFD_CUDA(c, launch_post_zm(c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_zm[1 - c->cur], c->stream,
+                                            post_rev));
+            else if (c->tma_ok)
                 VEFD_CUDA(c, launch_post_tma(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap[1 - c->cur],
                                              c->stream, post_rev));
             else

@@ -101,19 +101,22 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const void* tmap, int 
         : "memory");
 }
 
-// Waits for phase 0 of the barrier for a bounded number of polls; returns
-// false when the copy has not landed (the caller reports a timeout).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar) {
+// Waits for the given phase parity of the barrier for a bounded number of
+// polls; returns false when the copy has not landed (the caller reports a
+// timeout).
+__device__ __forceinline__ bool mbar_wait_bounded_parity(unsigned bar, unsigned parity) {
     unsigned done = 0;
     for (int it = 0; it < (1 << 22) && !done; ++it) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(bar), "r"(0u)
+            : "r"(bar), "r"(parity)
             : "memory");
     }
     return done != 0;
 }
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar) { return mbar_wait_bounded_parity(bar, 0u); }
 
 // Device guard bits (mirror VEFD_ST_*).
 constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTimeout = 16u;
@@ -150,6 +153,11 @@ cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, co
 // tile's populations with one bulk copy while the stencil loads are in flight.
 cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
                             const void* tensor_map_fnew, cudaStream_t s, int rev);
+// D3Q19 z-marching variant of the pass (needs NX % 32 == 0 and NY % 8 == 0 and a
+// tensor map of `fnew` with box 32 x 8 x 1 x P).
+bool post_zm_eligible(int lattice, int nx, int ny);
+cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBufs& b, const void* tensor_map_fnew,
+                           cudaStream_t s, int rev);
 // Densities of b.fin and the feedback stress of (b.fin, b.Cin): the derived
 // state the lattice kernel needs, for the initial state and after writes.
 cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s);
@@ -160,6 +168,9 @@ cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBu
 // is unavailable or the encoding is refused.
 bool pop_tile_eligible(int lattice, int nx, int ny, int nz);
 bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out);
+// Tensor map over one population buffer with an explicit box (bx, by, bz, all planes).
+bool make_pop_tensor_map_box(int lattice, int ncomp, int nx, int ny, int nz, const float* base, int bx, int by, int bz,
+                             void* out);
 
 // Field conversions.
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,

@@ -44,6 +44,14 @@ VARIANTS = {
                                  kappa=0.01, phase=-1),
     "d2q9_1c_tma_walls": dict(lattice=0, nx=44, ny=9, ncomp=1, walls=1, u_wall=0.02, eta_p=0.05, tau_p=40.0,
                               L2=50.0, kappa=0.02, fext=(1e-5, 0.0, 0.0)),
+    # shapes taken by the z-marching densities/FD pass (NX % 32 == 0, NY % 8 == 0);
+    # the last one splits z into segments of two planes
+    "d3q19_2c_zm_walls": dict(lattice=1, nx=64, ny=16, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1,
+                              tau_p=20.0, L2=50.0, kappa=0.01, phase=1),
+    "d3q19_1c_zm_periodic": dict(lattice=1, nx=32, ny=8, nz=5, ncomp=1, walls=0, eta_p=0.1, tau_p=20.0, L2=50.0,
+                                 kappa=0.02, fext=(1e-5, -1e-5, 0.0)),
+    "d3q19_2c_zm_segments": dict(lattice=1, nx=256, ny=40, nz=8, ncomp=2, walls=1, G=1.5, u_wall=0.02, eta_p=0.1,
+                                 tau_p=20.0, L2=50.0, kappa=0.01, phase=-1),
 }
 
 
@@ -80,10 +88,12 @@ def test_steps_match_oracle(name, nsteps):
     assert P.g.status() == 0 and P.o.status == 0
 
 
-@pytest.mark.parametrize("name", ["d3q19_2c_tma_ragged", "d2q9_2c_tma_periodic", "d2q9_1c_tma_walls"])
+@pytest.mark.parametrize("name", ["d3q19_2c_tma_ragged", "d2q9_2c_tma_periodic", "d2q9_1c_tma_walls",
+                                  "d3q19_2c_zm_walls", "d3q19_1c_zm_periodic", "d3q19_2c_zm_segments"])
 def test_tma_and_register_kernels_agree(name, monkeypatch):
-    """The TMA-staged lattice kernel and the register-only kernel run the same
-    arithmetic in the same order: populations agree bit for bit."""
+    """The TMA-staged kernels (lattice; densities/FD pass, z-marching where the
+    shape allows) and the register-only kernels run the same arithmetic in the
+    same order: populations and C agree bit for bit."""
     from paper_1406_2686_gb300 import vefd
     from pairs import Pair
     P = Pair(**VARIANTS[name])
