@@ -82,6 +82,8 @@ typedef struct {
     double eta_B;        /* shear viscosity of the B-rich phase */
     double delta;        /* smoothing width of f_+-(phi), Eq. (smoothingvisco); paper: 0.1 */
     int external_memory; /* 1: the caller binds device memory with vefd_bind_device_memory */
+    int precision;       /* storage of the population deviations f - w rho_ref: 0 FP32, 1 FP16,
+                            2 BF16 (arithmetic is FP32 and C is FP32 in every case) */
 } vefd_config;
 
 /* Creates a context on the current CUDA device; `stream` is a cudaStream_t

@@ -201,8 +201,8 @@ __device__ __forceinline__ void store_feedback(const float c[L::NC], const float
 // time n to n+1 when the polymer is evolved, and the feedback stress of time
 // n+1 for the next lattice step.  All of it only reads data the lattice kernel
 // has finished writing, so one pass over the lattice does it.
-template <class L, int NCOMP, bool FD>
-__global__ void __launch_bounds__(128) k_post(const float* __restrict__ fnew, float* __restrict__ drho,
+template <class PT, class L, int NCOMP, bool FD>
+__global__ void __launch_bounds__(128) k_post(const PT* __restrict__ fnew, float* __restrict__ drho,
                                               const float* __restrict__ Ct, float* __restrict__ Cout,
                                               float* __restrict__ R, const float* __restrict__ u,
                                               float* __restrict__ Q, unsigned* __restrict__ status, StepParams p,
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(128) k_post(const float* __restrict__ fnew, fl
     for (int s = 0; s < NCOMP; ++s) {
         d[s] = 0.0f;
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d[s] += __ldg(fnew + (s * L::Q + a) * N + i);
+        for (int a = 0; a < L::Q; ++a) d[s] += pop_load(fnew + (s * L::Q + a) * N + i);
     }
     float c[L::NC];
     if (FD) {
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128) k_post(const float* __restrict__ fnew, fl
 // one bulk tensor copy, issued before the stencil loads so that both are in
 // flight together; the densities are summed from shared memory afterwards in
 // the same order.
-template <class L, int NCOMP, bool FD, int BX, int BY, int BZ>
+template <class PT, class L, int NCOMP, bool FD, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant__ CUtensorMap tm_fnew,
                                                            float* __restrict__ drho, const float* __restrict__ Ct,
                                                            float* __restrict__ Cout, float* __restrict__ R,
@@ -246,8 +246,9 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
                                                            unsigned* __restrict__ status, StepParams p, int rev) {
     constexpr int P = NCOMP * L::Q;
     constexpr int T = BX * BY * BZ;
-    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(float));
-    extern __shared__ __align__(128) float sf[];  // [P][BZ][BY][BX]
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
+    extern __shared__ __align__(128) unsigned char sraw[];
+    PT* sf = reinterpret_cast<PT*>(sraw);  // [P][BZ][BY][BX]
     __shared__ __align__(8) unsigned long long bar;
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
     const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * BX;
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
     for (int s = 0; s < NCOMP; ++s) {
         d[s] = 0.0f;
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d[s] += sf[(s * L::Q + a) * T + t];
+        for (int a = 0; a < L::Q; ++a) d[s] += pop_get(sf[(s * L::Q + a) * T + t]);
         drho[s * N + i] = d[s];
     }
     if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
@@ -297,12 +298,12 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
 constexpr int kZmBX = 32, kZmBY = 8, kZmHX = kZmBX + 2, kZmHY = kZmBY + 2, kZmNF = 9;
 constexpr int kZmPlane = kZmNF * kZmHY * kZmHX;  // floats per ring plane
 
-template <int NCOMP>
+template <class PT, int NCOMP>
 constexpr int zm_smem_bytes() {
-    return (NCOMP * 19 * kZmBX * kZmBY + 4 * kZmPlane) * (int)sizeof(float);
+    return NCOMP * 19 * kZmBX * kZmBY * (int)sizeof(PT) + 4 * kZmPlane * (int)sizeof(float);
 }
 
-template <int NCOMP, bool FD>
+template <class PT, int NCOMP, bool FD>
 __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
                                                                float* __restrict__ drho, const float* __restrict__ Ct,
                                                                float* __restrict__ Cout, float* __restrict__ R,
@@ -312,10 +313,10 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
     using L = D3Q19;
     constexpr int P = NCOMP * L::Q;
     constexpr int T = kZmBX * kZmBY;
-    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(float));
-    extern __shared__ __align__(128) float sm[];
-    float* sP = sm;            // [P][BY][BX] populations of the current plane
-    float* ring = sm + P * T;  // [4][NF][HY][HX]
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
+    extern __shared__ __align__(128) unsigned char sraw[];
+    PT* sP = reinterpret_cast<PT*>(sraw);                           // [P][BY][BX] populations of the current plane
+    float* ring = reinterpret_cast<float*>(sraw + P * T * sizeof(PT));  // [4][NF][HY][HX]
     __shared__ __align__(8) unsigned long long bar;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
         for (int s = 0; s < NCOMP; ++s) {
             d[s] = 0.0f;
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) d[s] += sP[(s * L::Q + a) * T + t];
+            for (int a = 0; a < L::Q; ++a) d[s] += pop_get(sP[(s * L::Q + a) * T + t]);
             drho[s * N + i] = d[s];
         }
         if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
@@ -454,8 +455,8 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
 }
 
 // Densities and feedback stress of a given state (no time step).
-template <class L, int NCOMP>
-__global__ void __launch_bounds__(128) k_pre(const float* __restrict__ f, float* __restrict__ drho,
+template <class PT, class L, int NCOMP>
+__global__ void __launch_bounds__(128) k_pre(const PT* __restrict__ f, float* __restrict__ drho,
                                              const float* __restrict__ Ct, float* __restrict__ Q, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(128) k_pre(const float* __restrict__ f, float*
     for (int s = 0; s < NCOMP; ++s) {
         d[s] = 0.0f;
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d[s] += __ldg(f + (s * L::Q + a) * N + i);
+        for (int a = 0; a < L::Q; ++a) d[s] += pop_load(f + (s * L::Q + a) * N + i);
         drho[s * N + i] = d[s];
     }
     float c[L::NC];
@@ -480,37 +481,42 @@ __global__ void __launch_bounds__(128) k_pre(const float* __restrict__ f, float*
 }  // namespace
 
 cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
-                        const float* fnew, cudaStream_t s, int rev) {
+                        const void* fnew, cudaStream_t s, int rev) {
     dim3 blk(32, 4, 1), grd((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz);
-#define VEFD_POST(LT, NCP)                                                                                        \
-    do {                                                                                                          \
-        if (fd)                                                                                                   \
-            k_post<LT, NCP, true><<<grd, blk, 0, s>>>(fnew, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, rev);  \
-        else                                                                                                      \
-            k_post<LT, NCP, false><<<grd, blk, 0, s>>>(fnew, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, rev); \
+#define VEFD_POST(LT, NCP)                                                                                  \
+    do {                                                                                                    \
+        const PT* fn = static_cast<const PT*>(fnew);                                                        \
+        if (fd)                                                                                             \
+            k_post<PT, LT, NCP, true><<<grd, blk, 0, s>>>(fn, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p,  \
+                                                          rev);                                             \
+        else                                                                                                \
+            k_post<PT, LT, NCP, false><<<grd, blk, 0, s>>>(fn, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, \
+                                                           rev);                                            \
     } while (0)
-    if (lattice == 1) {
-        if (ncomp == 2) VEFD_POST(D3Q19, 2);
-        else VEFD_POST(D3Q19, 1);
-    } else {
-        if (ncomp == 2) VEFD_POST(D2Q9, 2);
-        else VEFD_POST(D2Q9, 1);
-    }
+    VEFD_WITH_PT(p.prec, {
+        if (lattice == 1) {
+            if (ncomp == 2) VEFD_POST(D3Q19, 2);
+            else VEFD_POST(D3Q19, 1);
+        } else {
+            if (ncomp == 2) VEFD_POST(D2Q9, 2);
+            else VEFD_POST(D2Q9, 1);
+        }
+    });
 #undef VEFD_POST
     return cudaGetLastError();
 }
 
 namespace {
-template <class L, int NCOMP, int BX, int BY, int BZ>
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
 cudaError_t post_tma(bool fd, const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
-    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(float);
+    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(PT);
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     if (fd)
-        k_post_tma<L, NCOMP, true, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
-                                                                       b.status, p, rev);
+        k_post_tma<PT, L, NCOMP, true, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
+                                                                           b.status, p, rev);
     else
-        k_post_tma<L, NCOMP, false, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
-                                                                        b.status, p, rev);
+        k_post_tma<PT, L, NCOMP, false, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
+                                                                            b.status, p, rev);
     return cudaGetLastError();
 }
 }  // namespace
@@ -518,9 +524,16 @@ cudaError_t post_tma(bool fd, const CUtensorMap* tm, const StepParams& p, const 
 cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
                             const void* tensor_map_fnew, cudaStream_t s, int rev) {
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map_fnew);
-    if (lattice == 1)
-        return ncomp == 2 ? post_tma<D3Q19, 2, 32, 4, 2>(fd, tm, p, b, s, rev) : post_tma<D3Q19, 1, 32, 4, 2>(fd, tm, p, b, s, rev);
-    return ncomp == 2 ? post_tma<D2Q9, 2, 32, 8, 1>(fd, tm, p, b, s, rev) : post_tma<D2Q9, 1, 32, 8, 1>(fd, tm, p, b, s, rev);
+    cudaError_t e = cudaSuccess;
+    VEFD_WITH_PT(p.prec, {
+        if (lattice == 1)
+            e = ncomp == 2 ? post_tma<PT, D3Q19, 2, 32, 4, 2>(fd, tm, p, b, s, rev)
+                           : post_tma<PT, D3Q19, 1, 32, 4, 2>(fd, tm, p, b, s, rev);
+        else
+            e = ncomp == 2 ? post_tma<PT, D2Q9, 2, 32, 8, 1>(fd, tm, p, b, s, rev)
+                           : post_tma<PT, D2Q9, 1, 32, 8, 1>(fd, tm, p, b, s, rev);
+    });
+    return e;
 }
 
 bool post_zm_eligible(int lattice, int nx, int ny) { return lattice == 1 && nx % kZmBX == 0 && ny % kZmBY == 0; }
@@ -528,12 +541,13 @@ bool post_zm_eligible(int lattice, int nx, int ny) { return lattice == 1 && nx %
 namespace {
 int g_sm_count = 0;
 
-template <int NCOMP, bool FD>
+template <class PT, int NCOMP, bool FD>
 cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
-    constexpr int smem = zm_smem_bytes<NCOMP>();
+    constexpr int smem = zm_smem_bytes<PT, NCOMP>();
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_post_zm<NCOMP, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_post_zm<PT, NCOMP, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -550,7 +564,7 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     const int zs = (p.nz + nzb - 1) / nzb;
     nzb = (p.nz + zs - 1) / zs;
     dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, p.ny / kZmBY, nzb);
-    k_post_zm<NCOMP, FD><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, zs, rev);
+    k_post_zm<PT, NCOMP, FD><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, zs, rev);
     return cudaGetLastError();
 }
 }  // namespace
@@ -558,19 +572,26 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
 cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBufs& b, const void* tensor_map_fnew,
                            cudaStream_t s, int rev) {
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map_fnew);
-    if (ncomp == 2) return fd ? post_zm<2, true>(tm, p, b, s, rev) : post_zm<2, false>(tm, p, b, s, rev);
-    return fd ? post_zm<1, true>(tm, p, b, s, rev) : post_zm<1, false>(tm, p, b, s, rev);
+    cudaError_t e = cudaSuccess;
+    VEFD_WITH_PT(p.prec, {
+        if (ncomp == 2) e = fd ? post_zm<PT, 2, true>(tm, p, b, s, rev) : post_zm<PT, 2, false>(tm, p, b, s, rev);
+        else e = fd ? post_zm<PT, 1, true>(tm, p, b, s, rev) : post_zm<PT, 1, false>(tm, p, b, s, rev);
+    });
+    return e;
 }
 
 cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s) {
     dim3 blk(32, 4, 1), grd((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz);
-    if (lattice == 1) {
-        if (ncomp == 2) k_pre<D3Q19, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
-        else k_pre<D3Q19, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
-    } else {
-        if (ncomp == 2) k_pre<D2Q9, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
-        else k_pre<D2Q9, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, b.Cin, b.Q, p);
-    }
+    VEFD_WITH_PT(p.prec, {
+        const PT* f = static_cast<const PT*>(b.fin);
+        if (lattice == 1) {
+            if (ncomp == 2) k_pre<PT, D3Q19, 2><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
+            else k_pre<PT, D3Q19, 1><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
+        } else {
+            if (ncomp == 2) k_pre<PT, D2Q9, 2><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
+            else k_pre<PT, D2Q9, 1><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
+        }
+    });
     return cudaGetLastError();
 }
 

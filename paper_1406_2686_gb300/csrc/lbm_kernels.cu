@@ -38,8 +38,8 @@ __device__ __forceinline__ int y_clamped(int y, int ny, int walls) {
 // Tile coordinate along one grid axis, optionally traversed backwards.
 __device__ __forceinline__ int tile_index(unsigned b, unsigned n, int rev) { return rev ? (int)(n - 1 - b) : (int)b; }
 
-template <class L, int NCOMP>
-__global__ void __launch_bounds__(128) k_moments(const float* __restrict__ fd, float* __restrict__ drho,
+template <class PT, class L, int NCOMP>
+__global__ void __launch_bounds__(128) k_moments(const PT* __restrict__ fd, float* __restrict__ drho,
                                                  StepParams p, int rev) {
     const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
     const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(128) k_moments(const float* __restrict__ fd, f
     for (int s = 0; s < NCOMP; ++s) {
         float d = 0.0f;
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d += __ldg(fd + (s * L::Q + a) * N + i);
+        for (int a = 0; a < L::Q; ++a) d += pop_load(fd + (s * L::Q + a) * N + i);
         drho[s * N + i] = d;
     }
 }
@@ -244,7 +244,7 @@ __device__ __forceinline__ void local_state(const StepParams& p, const float dr[
 // where, for the deviation equilibrium and the source of Sec. 2,
 //   E_even = w [drho + rho (4.5 (c.u)^2 - 1.5 u.u)],  E_odd = 3 w rho c.u,
 //   S_even = w [9 (c.u)(c.F) - 3 u.F],                  S_odd = 3 w c.F.
-template <class L, int NCOMP, class FGet>
+template <class PT, class L, int NCOMP, class FGet>
 __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
                                                const Local<NCOMP>& st, FGet fget) {
     const int N = (int)p.N;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
         const float uF = st.ux * Fx + st.uy * Fy + st.uz * Fz;
         const float rsv = st.rs[s], drs = st.dr[s];
         const float base = drs - 1.5f * rsv * st.usq;
-        float* out = b.fout + (long long)s * L::Q * N;
+        PT* out = static_cast<PT*>(b.fout) + (long long)s * L::Q * N;
         // The collision conserves mass exactly (the source has no zeroth
         // moment), so the rest population is taken as the remainder after the
         // moving ones; the FP32 weights (sum 1 + 1.5e-8) then leave no
@@ -294,22 +294,22 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
             // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
             if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
                 const float Uw = cy < 0 ? uw6 : -uw6;
-                out[ab * N + node] = fa - wa * rsv * (float)cx * Uw;
+                out[ab * N + node] = pop_put<PT>(fa - wa * rsv * (float)cx * Uw);
             } else {
-                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = fa;
+                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = pop_put<PT>(fa);
             }
             if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
                 const float Uw = cy > 0 ? uw6 : -uw6;
-                out[a * N + node] = fb + wa * rsv * (float)cx * Uw;
+                out[a * N + node] = pop_put<PT>(fb + wa * rsv * (float)cx * Uw);
             } else {
-                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = fb;
+                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = pop_put<PT>(fb);
             }
         }
-        out[node] = drs - moved;
+        out[node] = pop_put<PT>(drs - moved);
     }
 }
 
-template <class L, int NCOMP, bool STREAM>
+template <class PT, class L, int NCOMP, bool STREAM>
 __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int rev) {
     const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
     const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
         dr[s] = 0.0f;
 #pragma unroll
         for (int a = 0; a < L::Q; ++a) {
-            f[s][a] = __ldg(b.fin + (s * L::Q + a) * N + i);
+            f[s][a] = pop_load(static_cast<const PT*>(b.fin) + (s * L::Q + a) * N + i);
             dr[s] += f[s][a];
         }
     }
@@ -359,18 +359,19 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
         }
         return;
     }
-    collide_stream<L, NCOMP>(b, p, nb, st, [&](int s, int a) { return f[s][a]; });
+    collide_stream<PT, L, NCOMP>(b, p, nb, st, [&](int s, int a) { return f[s][a]; });
 }
 
 // --- TMA-staged variant --------------------------------------------------------
 
-template <class L, int NCOMP, int BX, int BY, int BZ>
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
                                                               StepParams p, int rev) {
     constexpr int P = NCOMP * L::Q;
     constexpr int T = BX * BY * BZ;
-    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(float));
-    extern __shared__ __align__(128) float sf[];  // [P][BZ][BY][BX], the TMA box layout
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
+    extern __shared__ __align__(128) unsigned char sraw[];
+    PT* sf = reinterpret_cast<PT*>(sraw);  // [P][BZ][BY][BX], the TMA box layout
     __shared__ __align__(8) unsigned long long bar;
     const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
     const int x0 = tile_index(blockIdx.x, gridDim.x, rev) * BX;
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     for (int s = 0; s < NCOMP; ++s)
 #pragma unroll
         for (int a = 1; a < L::Q; ++a) {
-            const float fa = sf[(s * L::Q + a) * T + t];
+            const float fa = pop_get(sf[(s * L::Q + a) * T + t]);
             if (L::cx(a)) jx += L::cx(a) * fa;
             if (L::cy(a)) jy += L::cy(a) * fa;
             if (L::cz(a)) jz += L::cz(a) * fa;
@@ -421,13 +422,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     b.u[N + i] = st.uy;
     if (L::D == 3) b.u[2 * N + i] = st.uz;
     // volatile reads keep the populations in shared memory instead of registers
-    const volatile float* sv = sf;
-    collide_stream<L, NCOMP>(b, p, nb, st, [&](int s, int a) { return sv[(s * L::Q + a) * T + t]; });
+    collide_stream<PT, L, NCOMP>(b, p, nb, st, [&](int s, int a) { return pop_smem(sf, (s * L::Q + a) * T + t); });
 }
 
-template <class L, int NCOMP>
+template <class PT, class L, int NCOMP>
 __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restrict__ rhoB,
-                          const float* __restrict__ u, float* __restrict__ fd, StepParams p) {
+                          const float* __restrict__ u, PT* __restrict__ fd, StepParams p) {
     const long long N = p.N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const float ux = u ? u[i] : 0.0f, uy = u ? u[N + i] : 0.0f;
@@ -444,26 +444,30 @@ __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restric
             for (int a = 1; a < L::Q; ++a) {
                 const float cu = L::cx(a) * ux + L::cy(a) * uy + L::cz(a) * uz;
                 const float e = L::w(a) * (d + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-                fd[(s * L::Q + a) * N + i] = e;
+                fd[(s * L::Q + a) * N + i] = pop_put<PT>(e);
                 moved += e;
             }
-            fd[(s * L::Q) * N + i] = d - moved;
+            fd[(s * L::Q) * N + i] = pop_put<PT>(d - moved);
         }
     }
 }
 
-template <class L, int NCOMP>
-__global__ void k_pops_convert(const float* __restrict__ src, float* __restrict__ dst, int to_abs, StepParams p) {
+// Planes [plane0, plane0 + nplanes) of the population buffer (plane = s*Q + a):
+// stored deviations <-> absolute FP32 populations f = deviation + w_a rho_ref_s.
+template <class PT, class L>
+__global__ void k_pops_convert(PT* __restrict__ pops, float* __restrict__ absf, int plane0, int nplanes, int to_abs,
+                               StepParams p) {
     const long long N = p.N;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int s = 0; s < NCOMP; ++s)
-#pragma unroll
-            for (int a = 0; a < L::Q; ++a) {
-                const float sh = L::w(a) * p.rho_ref[s];
-                const long long k = (s * L::Q + a) * N + i;
-                dst[k] = to_abs ? src[k] + sh : src[k] - sh;
-            }
+    const long long total = N * nplanes;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int pl = plane0 + (int)(e / N);
+        const long long i = e % N;
+        const int s = pl / L::Q, a = pl % L::Q;
+        const float sh = L::w(a) * p.rho_ref[s];
+        const long long k = (long long)pl * N + i;
+        if (to_abs) absf[e] = pop_get(pops[k]) + sh;
+        else pops[k] = pop_put<PT>(absf[e] - sh);
     }
 }
 
@@ -487,13 +491,13 @@ struct Tile<D2Q9> {
     static constexpr int BX = 32, BY = 8, BZ = 1;
 };
 
-template <class L, int NCOMP>
+template <class PT, class L, int NCOMP>
 cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
     constexpr int BX = Tile<L>::BX, BY = Tile<L>::BY, BZ = Tile<L>::BZ;
-    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(float);
+    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(PT);
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
-    k_lattice_tma<L, NCOMP, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b, p, rev);
+    k_lattice_tma<PT, L, NCOMP, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b, p, rev);
     return cudaGetLastError();
 }
 
@@ -503,13 +507,14 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 
 }  // namespace
 
-bool pop_tile_eligible(int lattice, int nx, int ny, int nz) {
+bool pop_tile_eligible(int lattice, int prec, int nx, int ny, int nz) {
     const int bx = 32, by = lattice == 1 ? 4 : 8, bz = lattice == 1 ? 2 : 1;
-    return nx % 4 == 0 && nx >= bx && ny >= by && nz >= bz;
+    const int align = prec == kPrecFp32 ? 4 : 8;  // rows must be 16-byte multiples
+    return nx % align == 0 && nx >= bx && ny >= by && nz >= bz;
 }
 
-bool make_pop_tensor_map_box(int lattice, int ncomp, int nx, int ny, int nz, const float* base, int bx, int by, int bz,
-                             void* out) {
+bool make_pop_tensor_map_box(int lattice, int ncomp, int prec, int nx, int ny, int nz, const void* base, int bx,
+                             int by, int bz, void* out) {
     static EncodeTiled encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -522,29 +527,36 @@ bool make_pop_tensor_map_box(int lattice, int ncomp, int nx, int ny, int nz, con
     }
     const int Q = lattice == 1 ? 19 : 9;
     const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(ncomp * Q)};
-    const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+    const cuuint64_t es = prec == kPrecFp32 ? 4 : 2;
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)(ncomp * Q)};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUtensorMapDataType dt = prec == kPrecFp16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : prec == kPrecBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = encode(static_cast<CUtensorMap*>(out), dt, 4, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out) {
-    return make_pop_tensor_map_box(lattice, ncomp, nx, ny, nz, base, 32, lattice == 1 ? 4 : 8, lattice == 1 ? 2 : 1,
-                                   out);
+bool make_pop_tensor_map(int lattice, int ncomp, int prec, int nx, int ny, int nz, const void* base, void* out) {
+    return make_pop_tensor_map_box(lattice, ncomp, prec, nx, ny, nz, base, 32, lattice == 1 ? 4 : 8,
+                                   lattice == 1 ? 2 : 1, out);
 }
 
 cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
     dim3 blk(32, 4, 1), grd = node_grid(p);
-    if (lattice == 1) {
-        if (ncomp == 2) k_moments<D3Q19, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
-        else k_moments<D3Q19, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
-    } else {
-        if (ncomp == 2) k_moments<D2Q9, 2><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
-        else k_moments<D2Q9, 1><<<grd, blk, 0, s>>>(b.fin, b.drho, p, rev);
-    }
+    VEFD_WITH_PT(p.prec, {
+        const PT* fin = static_cast<const PT*>(b.fin);
+        if (lattice == 1) {
+            if (ncomp == 2) k_moments<PT, D3Q19, 2><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
+            else k_moments<PT, D3Q19, 1><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
+        } else {
+            if (ncomp == 2) k_moments<PT, D2Q9, 2><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
+            else k_moments<PT, D2Q9, 1><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
+        }
+    });
     return cudaGetLastError();
 }
 
@@ -552,50 +564,59 @@ cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepP
                            cudaStream_t s, const void* tensor_map, int rev) {
     if (stream_pops && tensor_map) {
         const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map);
-        if (lattice == 1)
-            return ncomp == 2 ? launch_tma<D3Q19, 2>(tm, p, b, rev, s) : launch_tma<D3Q19, 1>(tm, p, b, rev, s);
-        return ncomp == 2 ? launch_tma<D2Q9, 2>(tm, p, b, rev, s) : launch_tma<D2Q9, 1>(tm, p, b, rev, s);
+        cudaError_t e = cudaSuccess;
+        VEFD_WITH_PT(p.prec, {
+            if (lattice == 1)
+                e = ncomp == 2 ? launch_tma<PT, D3Q19, 2>(tm, p, b, rev, s) : launch_tma<PT, D3Q19, 1>(tm, p, b, rev, s);
+            else
+                e = ncomp == 2 ? launch_tma<PT, D2Q9, 2>(tm, p, b, rev, s) : launch_tma<PT, D2Q9, 1>(tm, p, b, rev, s);
+        });
+        return e;
     }
     dim3 blk(32, 4, 1), grd = node_grid(p);
-#define VEFD_LAT(LT, NCP)                                                          \
-    do {                                                                           \
-        if (stream_pops) k_lattice<LT, NCP, true><<<grd, blk, 0, s>>>(b, p, rev);  \
-        else k_lattice<LT, NCP, false><<<grd, blk, 0, s>>>(b, p, rev);             \
+#define VEFD_LAT(LT, NCP)                                                              \
+    do {                                                                               \
+        if (stream_pops) k_lattice<PT, LT, NCP, true><<<grd, blk, 0, s>>>(b, p, rev);  \
+        else k_lattice<PT, LT, NCP, false><<<grd, blk, 0, s>>>(b, p, rev);             \
     } while (0)
-    if (lattice == 1) {
-        if (ncomp == 2) VEFD_LAT(D3Q19, 2);
-        else VEFD_LAT(D3Q19, 1);
-    } else {
-        if (ncomp == 2) VEFD_LAT(D2Q9, 2);
-        else VEFD_LAT(D2Q9, 1);
-    }
+    VEFD_WITH_PT(p.prec, {
+        if (lattice == 1) {
+            if (ncomp == 2) VEFD_LAT(D3Q19, 2);
+            else VEFD_LAT(D3Q19, 1);
+        } else {
+            if (ncomp == 2) VEFD_LAT(D2Q9, 2);
+            else VEFD_LAT(D2Q9, 1);
+        }
+    });
 #undef VEFD_LAT
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
-                                    const float* rhoB, const float* u, float* fd, cudaStream_t s) {
+                                    const float* rhoB, const float* u, void* fd, cudaStream_t s) {
     const int g = grid_1d(p.N);
-    if (lattice == 1) {
-        if (ncomp == 2) k_init_eq<D3Q19, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, fd, p);
-        else k_init_eq<D3Q19, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, fd, p);
-    } else {
-        if (ncomp == 2) k_init_eq<D2Q9, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, fd, p);
-        else k_init_eq<D2Q9, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, fd, p);
-    }
+    VEFD_WITH_PT(p.prec, {
+        PT* out = static_cast<PT*>(fd);
+        if (lattice == 1) {
+            if (ncomp == 2) k_init_eq<PT, D3Q19, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
+            else k_init_eq<PT, D3Q19, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
+        } else {
+            if (ncomp == 2) k_init_eq<PT, D2Q9, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
+            else k_init_eq<PT, D2Q9, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
+        }
+    });
     return cudaGetLastError();
 }
 
-cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, const float* src, float* dst,
-                                int to_absolute, cudaStream_t s) {
-    const int g = grid_1d(p.N);
-    if (lattice == 1) {
-        if (ncomp == 2) k_pops_convert<D3Q19, 2><<<g, 256, 0, s>>>(src, dst, to_absolute, p);
-        else k_pops_convert<D3Q19, 1><<<g, 256, 0, s>>>(src, dst, to_absolute, p);
-    } else {
-        if (ncomp == 2) k_pops_convert<D2Q9, 2><<<g, 256, 0, s>>>(src, dst, to_absolute, p);
-        else k_pops_convert<D2Q9, 1><<<g, 256, 0, s>>>(src, dst, to_absolute, p);
-    }
+cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, void* pops, float* absf, int plane0,
+                                int nplanes, int to_absolute, cudaStream_t s) {
+    (void)ncomp;
+    const int g = grid_1d(p.N * nplanes);
+    VEFD_WITH_PT(p.prec, {
+        PT* pp = static_cast<PT*>(pops);
+        if (lattice == 1) k_pops_convert<PT, D3Q19><<<g, 256, 0, s>>>(pp, absf, plane0, nplanes, to_absolute, p);
+        else k_pops_convert<PT, D2Q9><<<g, 256, 0, s>>>(pp, absf, plane0, nplanes, to_absolute, p);
+    });
     return cudaGetLastError();
 }
 

@@ -36,7 +36,8 @@ struct vefd_ctx {
     void* mem = nullptr;
     size_t mem_bytes = 0;
     bool owned = false;
-    float* f[2] = {nullptr, nullptr};
+    void* f[2] = {nullptr, nullptr};  // population deviations, storage type of cfg.precision
+    size_t psize = 4;                 // bytes per stored population value
     float* drho = nullptr;
     float* u = nullptr;
     float* C[2] = {nullptr, nullptr};
@@ -103,10 +104,15 @@ bool config_ok(const vefd_config* c, const char** why) {
         return *why = "viscosities must be positive", false;
     if (!(c->delta > 0.0) || !std::isfinite(c->delta)) return *why = "delta must be positive", false;
     if (!(c->G >= 0.0) || !std::isfinite(c->G)) return *why = "G must be finite and >= 0", false;
+    if (c->precision < 0 || c->precision > 2) return *why = "precision must be 0 (FP32), 1 (FP16) or 2 (BF16)", false;
     const long long N = (long long)c->nx * c->ny * c->nz;
     if (N > (1LL << 31) / 40) return *why = "lattice too large for 32-bit plane offsets", false;
     return true;
 }
+
+// staging planes (FP32): the initial fields (rho_A, rho_B, 3 velocity, 6 C) and
+// the derived fields of reads and writes go through this buffer
+constexpr int kStagePlanes = 11;
 
 struct Layout {
     size_t f0, f1, drho, u, c0, c1, r, dbg, q, status, dpart, dout, total;
@@ -124,14 +130,15 @@ Layout layout_of(const vefd_config* c) {
         o = align256(o + bytes);
         return at;
     };
-    L.f0 = take(sizeof(float) * c->ncomp * Q * N);
-    L.f1 = take(sizeof(float) * c->ncomp * Q * N);
+    const size_t ps = c->precision == 0 ? 4 : 2;
+    L.f0 = take(ps * c->ncomp * Q * N);
+    L.f1 = take(ps * c->ncomp * Q * N);
     L.drho = take(sizeof(float) * 2 * N);
     L.u = take(sizeof(float) * 3 * N);
     L.c0 = take(sizeof(float) * NC * N);
     L.c1 = take(sizeof(float) * NC * N);
     L.r = take(sizeof(float) * NC * N);
-    L.dbg = take(sizeof(float) * 10 * N);
+    L.dbg = take(sizeof(float) * kStagePlanes * N);
     L.q = take(sizeof(float) * 6 * N);
     L.status = take(256);
     L.dpart = take(sizeof(double) * kDiagBlocks * kDiagVals);
@@ -143,8 +150,8 @@ Layout layout_of(const vefd_config* c) {
 void carve(vefd_ctx* c) {
     const Layout L = layout_of(&c->cfg);
     char* b = (char*)c->mem;
-    c->f[0] = (float*)(b + L.f0);
-    c->f[1] = (float*)(b + L.f1);
+    c->f[0] = b + L.f0;
+    c->f[1] = b + L.f1;
     c->drho = (float*)(b + L.drho);
     c->u = (float*)(b + L.u);
     c->C[0] = (float*)(b + L.c0);
@@ -156,18 +163,19 @@ void carve(vefd_ctx* c) {
     c->diag_part = (double*)(b + L.dpart);
     c->diag_out = (double*)(b + L.dout);
     c->tma_ok = false;
-    if (!getenv("VEFD_NO_TMA") && pop_tile_eligible(c->cfg.lattice, c->cfg.nx, c->cfg.ny, c->cfg.nz)) {
-        c->tma_ok = make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[0],
+    const int prec = c->cfg.precision;
+    if (!getenv("VEFD_NO_TMA") && pop_tile_eligible(c->cfg.lattice, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz)) {
+        c->tma_ok = make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[0],
                                         &c->tmap[0]) &&
-                    make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1],
+                    make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1],
                                         &c->tmap[1]);
     }
     c->zm_ok = false;
     if (c->tma_ok && !getenv("VEFD_NO_ZMARCH") && post_zm_eligible(c->cfg.lattice, c->cfg.nx, c->cfg.ny)) {
-        c->zm_ok = make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[0], 32,
-                                           8, 1, &c->tmap_zm[0]) &&
-                   make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1], 32,
-                                           8, 1, &c->tmap_zm[1]);
+        c->zm_ok = make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
+                                           c->f[0], 32, 8, 1, &c->tmap_zm[0]) &&
+                   make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
+                                           c->f[1], 32, 8, 1, &c->tmap_zm[1]);
     }
     if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
 }
@@ -194,6 +202,7 @@ StepParams params_of(const vefd_ctx* c) {
     p.have_prev = c->have_prev;
     p.rho_ref[0] = (float)c->rho_ref[0];
     p.rho_ref[1] = (float)c->rho_ref[1];
+    p.prec = c->cfg.precision;
     return p;
 }
 
@@ -302,6 +311,7 @@ vefd_status vefd_create(const vefd_config* cfg, void* stream, vefd_ctx** out) {
     c->D = lattice_D(cfg->lattice);
     c->NC = lattice_NC(cfg->lattice);
     c->N = (long long)cfg->nx * cfg->ny * cfg->nz;
+    c->psize = cfg->precision == 0 ? 4 : 2;
     c->stream = (cudaStream_t)stream;
     if (!cfg->external_memory) {
         const size_t bytes = layout_of(cfg).total;
@@ -421,7 +431,7 @@ vefd_status vefd_init_fields(vefd_ctx* c, const float* rho_A, const float* rho_B
     // stage the inputs in the second population buffer
     c->cur = 0;
     c->ccur = 0;
-    float* st = c->f[1];
+    float* st = c->dbg;
     float* sA = st;
     float* sB = st + N;
     float* sU = st + 2 * N;
@@ -483,14 +493,21 @@ vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, siz
     if (vefd_field_bytes(c, field, &need) != VEFD_OK) return fail(c, VEFD_ERR_ARG, "unknown field");
     if (bytes != need) return fail(c, VEFD_ERR_ARG, "field needs %zu bytes, got %zu", need, bytes);
     const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    float* stg = c->f[1 - c->cur];
+    float* stg = c->dbg;
     StepParams p = params_of(c);
     switch (field) {
-    case VEFD_POPS:
-        VEFD_CUDA(c, cudaMemcpyAsync(stg, src, bytes, kind, c->stream));
-        VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, stg, c->f[c->cur], 0, c->stream));
+    case VEFD_POPS: {
+        // absolute FP32 populations -> stored deviations, a few planes at a time
+        const int planes = c->cfg.ncomp * c->Q;
+        const size_t plane = sizeof(float) * (size_t)c->N;
+        for (int p0 = 0; p0 < planes; p0 += kStagePlanes) {
+            const int k = planes - p0 < kStagePlanes ? planes - p0 : kStagePlanes;
+            VEFD_CUDA(c, cudaMemcpyAsync(stg, (const char*)src + p0 * plane, k * plane, kind, c->stream));
+            VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], stg, p0, k, 0, c->stream));
+        }
         c->drho_valid = false;
         break;
+    }
     case VEFD_C:
         VEFD_CUDA(c, cudaMemcpyAsync(stg, src, bytes, kind, c->stream));
         VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, stg, c->C[c->ccur], c->N, -1.0f, c->stream));
@@ -557,13 +574,23 @@ vefd_status vefd_read_field(vefd_ctx* c, vefd_field field, void* dst, size_t byt
     size_t need = 0;
     if (vefd_field_bytes(c, field, &need) != VEFD_OK) return fail(c, VEFD_ERR_ARG, "unknown field");
     if (bytes != need) return fail(c, VEFD_ERR_ARG, "field needs %zu bytes, got %zu", need, bytes);
-    float* stg = c->f[1 - c->cur];
+    float* stg = c->dbg;
     const long long N = c->N;
     StepParams p = params_of(c);
     switch (field) {
-    case VEFD_POPS:
-        VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], stg, 1, c->stream));
-        return copy_out(c, dst, stg, bytes, dst_on_device);
+    case VEFD_POPS: {
+        // stored deviations -> absolute FP32 populations, a few planes at a time
+        const int planes = c->cfg.ncomp * c->Q;
+        const size_t plane = sizeof(float) * (size_t)N;
+        for (int p0 = 0; p0 < planes; p0 += kStagePlanes) {
+            const int k = planes - p0 < kStagePlanes ? planes - p0 : kStagePlanes;
+            VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], stg, p0, k, 1, c->stream));
+            VEFD_CUDA(c, cudaMemcpyAsync((char*)dst + p0 * plane, stg, k * plane,
+                                         dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (!dst_on_device) VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+        return VEFD_OK;
+    }
     case VEFD_C:
         VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, c->C[c->ccur], stg, N, 1.0f, c->stream));
         return copy_out(c, dst, stg, bytes, dst_on_device);
@@ -711,7 +738,7 @@ struct CkptHeader {
     int32_t lattice, nx, ny, nz, ncomp, walls;
     double G, eta_A, eta_B, delta;
     double u_wall, fext[3], tau_p, eta_p, L2, kappa;
-    int32_t phase, fd_on, have_prev, pad;
+    int32_t phase, fd_on, have_prev, precision;
     double rho_ref[2];
     int64_t steps;
     uint32_t status, pad2;
@@ -725,7 +752,7 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.lattice = c->cfg.lattice;
     h.nx = c->cfg.nx;
     h.ny = c->cfg.ny;
@@ -745,19 +772,20 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     h.phase = c->phase;
     h.fd_on = c->fd_on;
     h.have_prev = c->have_prev;
+    h.precision = c->cfg.precision;
     h.rho_ref[0] = c->rho_ref[0];
     h.rho_ref[1] = c->rho_ref[1];
     h.steps = c->steps;
     VEFD_CUDA(c, cudaMemcpyAsync(&h.status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    const size_t np = (size_t)c->cfg.ncomp * c->Q * c->N, nc = (size_t)c->NC * c->N;
-    std::vector<float> buf(np + 2 * nc);
-    VEFD_CUDA(c, cudaMemcpyAsync(buf.data(), c->f[c->cur], np * 4, cudaMemcpyDeviceToHost, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + np, c->C[c->ccur], nc * 4, cudaMemcpyDeviceToHost, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + np + nc, c->R, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    const size_t npb = (size_t)c->cfg.ncomp * c->Q * c->N * c->psize, nc = (size_t)c->NC * c->N;
+    std::vector<char> buf(npb + 2 * nc * 4);
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data(), c->f[c->cur], npb, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb, c->C[c->ccur], nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb + nc * 4, c->R, nc * 4, cudaMemcpyDeviceToHost, c->stream));
     VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
     FILE* fh = fopen(path, "wb");
     if (!fh) return fail(c, VEFD_ERR_ARG, "cannot open %s for writing", path);
-    bool ok = fwrite(&h, sizeof h, 1, fh) == 1 && fwrite(buf.data(), 4, buf.size(), fh) == buf.size();
+    bool ok = fwrite(&h, sizeof h, 1, fh) == 1 && fwrite(buf.data(), 1, buf.size(), fh) == buf.size();
     ok = (fclose(fh) == 0) && ok;
     return ok ? VEFD_OK : fail(c, VEFD_ERR_ARG, "short write to %s", path);
 }
@@ -768,13 +796,13 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     FILE* fh = fopen(path, "rb");
     if (!fh) return fail(c, VEFD_ERR_ARG, "cannot open %s", path);
     CkptHeader h;
-    const size_t np = (size_t)c->cfg.ncomp * c->Q * c->N, nc = (size_t)c->NC * c->N;
-    std::vector<float> buf(np + 2 * nc);
+    const size_t npb = (size_t)c->cfg.ncomp * c->Q * c->N * c->psize, nc = (size_t)c->NC * c->N;
+    std::vector<char> buf(npb + 2 * nc * 4);
     bool ok = fread(&h, sizeof h, 1, fh) == 1;
-    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 1;
+    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 2 && h.precision == c->cfg.precision;
     ok = ok && h.lattice == c->cfg.lattice && h.nx == c->cfg.nx && h.ny == c->cfg.ny && h.nz == c->cfg.nz &&
          h.ncomp == c->cfg.ncomp && h.walls == c->cfg.walls;
-    ok = ok && fread(buf.data(), 4, buf.size(), fh) == buf.size();
+    ok = ok && fread(buf.data(), 1, buf.size(), fh) == buf.size();
     fclose(fh);
     if (!ok) return fail(c, VEFD_ERR_ARG, "%s is not a checkpoint of this lattice", path);
     c->cfg.G = h.G;
@@ -795,9 +823,9 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     c->steps = h.steps;
     c->cur = 0;
     c->ccur = 0;
-    VEFD_CUDA(c, cudaMemcpyAsync(c->f[0], buf.data(), np * 4, cudaMemcpyHostToDevice, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(c->C[0], buf.data() + np, nc * 4, cudaMemcpyHostToDevice, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(c->R, buf.data() + np + nc, nc * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->f[0], buf.data(), npb, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->C[0], buf.data() + npb, nc * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->R, buf.data() + npb + nc * 4, nc * 4, cudaMemcpyHostToDevice, c->stream));
     VEFD_CUDA(c, cudaMemcpyAsync(c->status, &h.status, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
     VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = 1;

@@ -9,9 +9,13 @@
 //   feedback     Q[k*N + i] = (f(r_P) C - I) m(phi), k < NQ    (the stress whose divergence is the
 //                polymer force; derived from C and the densities of the same time level)
 // Storing deviations keeps FP32 rounding relative to the small departures
-// from a uniform rest state instead of to the full populations.
+// from a uniform rest state instead of to the full populations.  The
+// population deviations may also be stored in 16 bits (FP16 or BF16, type PT
+// below); all arithmetic stays FP32 and C stays FP32.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +61,55 @@ struct D3Q19 {
 
 __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 
+// --- population storage types: FP32, FP16 or BF16 deviations ------------------
+
+enum { kPrecFp32 = 0, kPrecFp16 = 1, kPrecBf16 = 2 };
+
+__device__ __forceinline__ float pop_load(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float pop_load(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float pop_load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+// plain (non read-only-path) loads, for buffers the same kernel also writes
+__device__ __forceinline__ float pop_get(float v) { return v; }
+__device__ __forceinline__ float pop_get(__half v) { return __half2float(v); }
+__device__ __forceinline__ float pop_get(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <class PT>
+__device__ __forceinline__ PT pop_put(float v);
+template <>
+__device__ __forceinline__ float pop_put<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half pop_put<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 pop_put<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// volatile shared-memory read of a staged population (keeps it out of registers)
+__device__ __forceinline__ float pop_smem(const float* base, int idx) {
+    return static_cast<const volatile float*>(base)[idx];
+}
+__device__ __forceinline__ float pop_smem(const __half* base, int idx) {
+    return __half2float(__ushort_as_half(reinterpret_cast<const volatile unsigned short*>(base)[idx]));
+}
+__device__ __forceinline__ float pop_smem(const __nv_bfloat16* base, int idx) {
+    return __bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const volatile unsigned short*>(base)[idx]));
+}
+
+// Runs the statements that follow `prec` with PT bound to the population
+// storage type of `prec`.
+#define VEFD_WITH_PT(prec, ...)             \
+    do {                                    \
+        if ((prec) == kPrecFp16) {          \
+            using PT = __half;              \
+            __VA_ARGS__;                    \
+        } else if ((prec) == kPrecBf16) {   \
+            using PT = __nv_bfloat16;       \
+            __VA_ARGS__;                    \
+        } else {                            \
+            using PT = float;               \
+            __VA_ARGS__;                    \
+        }                                   \
+    } while (0)
+
 // Scalars every kernel needs, passed by value.
 struct StepParams {
     int nx, ny, nz;
@@ -74,6 +127,7 @@ struct StepParams {
     int phase;             // 0: m = 1, +1: f_+, -1: f_-
     int have_prev;         // AB2 history valid
     float rho_ref[2];      // deviation reference densities
+    int prec;              // population storage: kPrecFp32, kPrecFp16, kPrecBf16
 };
 
 // --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------
@@ -123,8 +177,8 @@ constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTim
 
 // Pointers of one step.
 struct StepBufs {
-    const float* fin;      // populations at time n (deviation form)
-    float* fout;           // populations at time n+1
+    const void* fin;       // populations at time n (deviation form, storage type of p.prec)
+    void* fout;            // populations at time n+1
     float* drho;           // densities of time n
     float* u;              // velocity of time n (written by the lattice kernel)
     const float* Cin;      // C - I at time n
@@ -148,7 +202,7 @@ cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepP
 // b.Cin -> b.Cout with the AB2 history b.R and velocity b.u, and the feedback
 // stress of the new time level into b.Q.
 cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
-                        const float* fnew, cudaStream_t s, int rev);
+                        const void* fnew, cudaStream_t s, int rev);
 // With a tensor map of `fnew` (TMA-eligible shapes), the same pass stages the
 // tile's populations with one bulk copy while the stencil loads are in flight.
 cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p, const StepBufs& b,
@@ -166,17 +220,19 @@ cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBu
 // map over one population buffer ([ncomp*Q][NZ][NY][NX] FP32) written to `out`
 // (a 64-byte aligned CUtensorMap).  Returns false when the driver entry point
 // is unavailable or the encoding is refused.
-bool pop_tile_eligible(int lattice, int nx, int ny, int nz);
-bool make_pop_tensor_map(int lattice, int ncomp, int nx, int ny, int nz, const float* base, void* out);
+bool pop_tile_eligible(int lattice, int prec, int nx, int ny, int nz);
+bool make_pop_tensor_map(int lattice, int ncomp, int prec, int nx, int ny, int nz, const void* base, void* out);
 // Tensor map over one population buffer with an explicit box (bx, by, bz, all planes).
-bool make_pop_tensor_map_box(int lattice, int ncomp, int nx, int ny, int nz, const float* base, int bx, int by, int bz,
-                             void* out);
+bool make_pop_tensor_map_box(int lattice, int ncomp, int prec, int nx, int ny, int nz, const void* base, int bx,
+                             int by, int bz, void* out);
 
 // Field conversions.
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
-                                    const float* rhoB, const float* u, float* fd, cudaStream_t s);
-cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, const float* src, float* dst,
-                                int to_absolute, cudaStream_t s);
+                                    const float* rhoB, const float* u, void* fd, cudaStream_t s);
+// Planes [plane0, plane0 + nplanes) of the population buffer: stored deviations
+// `pops` -> absolute FP32 `absf` (to_absolute) or back.
+cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, void* pops, float* absf, int plane0,
+                                int nplanes, int to_absolute, cudaStream_t s);
 cudaError_t launch_tensor_shift(int lattice, const float* src, float* dst, long long N, float sign,
                                 cudaStream_t s);
 // which: 0 rho_A, 1 rho_B, 2 phi, 4 C, 5 sigma_P = f(r_P) C

@@ -14,6 +14,7 @@ import numpy as np
 from . import build_lib
 
 D2Q9, D3Q19 = 0, 1
+FP32, FP16, BF16 = 0, 1, 2
 RHO_A, RHO_B, PHI, U, C, SIGMA_P, POPS, RPREV, G_A, G_B, F_P, TAU = range(12)
 OK, ERR_ARG, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5
 ST_NAN, ST_TRACE, ST_MACH, ST_RHO = 1, 2, 4, 8
@@ -30,7 +31,7 @@ class vefd_config(ctypes.Structure):
         ("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("ncomp", ctypes.c_int), ("walls", ctypes.c_int),
         ("G", ctypes.c_double), ("eta_A", ctypes.c_double), ("eta_B", ctypes.c_double),
-        ("delta", ctypes.c_double), ("external_memory", ctypes.c_int),
+        ("delta", ctypes.c_double), ("external_memory", ctypes.c_int), ("precision", ctypes.c_int),
     ]
 
 
@@ -251,13 +252,13 @@ class Lattice:
     """
 
     def __init__(self, lattice=D3Q19, nx=16, ny=16, nz=16, ncomp=2, walls=1, G=0.0, eta_A=1.0 / 6.0,
-                 eta_B=1.0 / 6.0, delta=0.1, device="cuda", stream=None):
+                 eta_B=1.0 / 6.0, delta=0.1, device="cuda", stream=None, precision=FP32):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("vefd needs a CUDA device")
         load()
         self.torch = torch
-        self.cfg = vefd_config(lattice, nx, ny, nz, ncomp, walls, G, eta_A, eta_B, delta, 1)
+        self.cfg = vefd_config(lattice, nx, ny, nz, ncomp, walls, G, eta_A, eta_B, delta, 1, precision)
         self.nx, self.ny, self.nz, self.ncomp = nx, ny, nz, ncomp
         self.N = nx * ny * nz
         self.D = 3 if lattice == D3Q19 else 2
