@@ -202,7 +202,8 @@ __device__ __forceinline__ void store_feedback(const float c[L::NC], const float
 // n+1 for the next lattice step.  All of it only reads data the lattice kernel
 // has finished writing, so one pass over the lattice does it.
 template <class PT, class L, int NCOMP, bool FD>
-__global__ void __launch_bounds__(128) k_post(const PT* __restrict__ fnew, float* __restrict__ drho,
+__global__ void __launch_bounds__(128) k_post(const PT* __restrict__ fnew, const float* __restrict__ frest,
+                                              float* __restrict__ drho,
                                               const float* __restrict__ Ct, float* __restrict__ Cout,
                                               float* __restrict__ R, const float* __restrict__ u,
                                               float* __restrict__ Q, unsigned* __restrict__ status, StepParams p,
@@ -218,9 +219,9 @@ __global__ void __launch_bounds__(128) k_post(const PT* __restrict__ fnew, float
     float d[NCOMP];
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
-        d[s] = 0.0f;
+        d[s] = __ldg(frest + s * N + i);
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d[s] += pop_load(fnew + (s * L::Q + a) * N + i);
+        for (int a = 1; a < L::Q; ++a) d[s] += pop_load(fnew + (s * (L::Q - 1) + a - 1) * N + i);
     }
     float c[L::NC];
     if (FD) {
@@ -240,11 +241,12 @@ __global__ void __launch_bounds__(128) k_post(const PT* __restrict__ fnew, float
 // the same order.
 template <class PT, class L, int NCOMP, bool FD, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant__ CUtensorMap tm_fnew,
+                                                           const float* __restrict__ frest,
                                                            float* __restrict__ drho, const float* __restrict__ Ct,
                                                            float* __restrict__ Cout, float* __restrict__ R,
                                                            const float* __restrict__ u, float* __restrict__ Q,
                                                            unsigned* __restrict__ status, StepParams p, int rev) {
-    constexpr int P = NCOMP * L::Q;
+    constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = BX * BY * BZ;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
     extern __shared__ __align__(128) unsigned char sraw[];
@@ -264,7 +266,10 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
     const long long N = p.N;
     const long long i = active ? ((long long)z * p.ny + y) * p.nx + x : 0;
     float c[L::NC];
+    float rest[NCOMP];
     if (active) {
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) rest[s] = __ldg(frest + s * N + i);
         if (FD) {
             fenep_node<L::D, L::NC>(Ct, Cout, R, u, status, p, x, y, z, c);
         } else {
@@ -281,9 +286,9 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
     float d[NCOMP];
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
-        d[s] = 0.0f;
+        d[s] = rest[s];
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d[s] += pop_get(sf[(s * L::Q + a) * T + t]);
+        for (int a = 1; a < L::Q; ++a) d[s] += pop_get(sf[(s * (L::Q - 1) + a - 1) * T + t]);
         drho[s * N + i] = d[s];
     }
     if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
@@ -300,18 +305,19 @@ constexpr int kZmPlane = kZmNF * kZmHY * kZmHX;  // floats per ring plane
 
 template <class PT, int NCOMP>
 constexpr int zm_smem_bytes() {
-    return NCOMP * 19 * kZmBX * kZmBY * (int)sizeof(PT) + 4 * kZmPlane * (int)sizeof(float);
+    return NCOMP * 18 * kZmBX * kZmBY * (int)sizeof(PT) + 4 * kZmPlane * (int)sizeof(float);
 }
 
 template <class PT, int NCOMP, bool FD>
 __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
+                                                               const float* __restrict__ frest,
                                                                float* __restrict__ drho, const float* __restrict__ Ct,
                                                                float* __restrict__ Cout, float* __restrict__ R,
                                                                const float* __restrict__ u, float* __restrict__ Q,
                                                                unsigned* __restrict__ status, StepParams p, int zs,
                                                                int rev) {
     using L = D3Q19;
-    constexpr int P = NCOMP * L::Q;
+    constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = kZmBX * kZmBY;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
     extern __shared__ __align__(128) unsigned char sraw[];
@@ -402,6 +408,9 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
         const bool more = z + 2 <= z1;
         if (more) load_plane(z + 2, vi, vh);
         const int i = z * plane + y * nx + x;
+        float rest[NCOMP];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) rest[s] = __ldg(frest + s * N + i);
         float c[6];
         if (FD) {
             const float* pm = ring + (k % 4) * kZmPlane;
@@ -443,9 +452,9 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
         float d[NCOMP];
 #pragma unroll
         for (int s = 0; s < NCOMP; ++s) {
-            d[s] = 0.0f;
+            d[s] = rest[s];
 #pragma unroll
-            for (int a = 0; a < L::Q; ++a) d[s] += pop_get(sP[(s * L::Q + a) * T + t]);
+            for (int a = 1; a < L::Q; ++a) d[s] += pop_get(sP[(s * (L::Q - 1) + a - 1) * T + t]);
             drho[s * N + i] = d[s];
         }
         if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
@@ -456,7 +465,8 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
 
 // Densities and feedback stress of a given state (no time step).
 template <class PT, class L, int NCOMP>
-__global__ void __launch_bounds__(128) k_pre(const PT* __restrict__ f, float* __restrict__ drho,
+__global__ void __launch_bounds__(128) k_pre(const PT* __restrict__ f, const float* __restrict__ frest,
+                                             float* __restrict__ drho,
                                              const float* __restrict__ Ct, float* __restrict__ Q, StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -467,9 +477,9 @@ __global__ void __launch_bounds__(128) k_pre(const PT* __restrict__ f, float* __
     float d[NCOMP];
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
-        d[s] = 0.0f;
+        d[s] = __ldg(frest + s * N + i);
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d[s] += pop_load(f + (s * L::Q + a) * N + i);
+        for (int a = 1; a < L::Q; ++a) d[s] += pop_load(f + (s * (L::Q - 1) + a - 1) * N + i);
         drho[s * N + i] = d[s];
     }
     float c[L::NC];
@@ -487,10 +497,10 @@ cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, co
     do {                                                                                                    \
         const PT* fn = static_cast<const PT*>(fnew);                                                        \
         if (fd)                                                                                             \
-            k_post<PT, LT, NCP, true><<<grd, blk, 0, s>>>(fn, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p,  \
+            k_post<PT, LT, NCP, true><<<grd, blk, 0, s>>>(fn, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p,  \
                                                           rev);                                             \
         else                                                                                                \
-            k_post<PT, LT, NCP, false><<<grd, blk, 0, s>>>(fn, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, \
+            k_post<PT, LT, NCP, false><<<grd, blk, 0, s>>>(fn, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, \
                                                            rev);                                            \
     } while (0)
     VEFD_WITH_PT(p.prec, {
@@ -509,13 +519,13 @@ cudaError_t launch_post(int lattice, int ncomp, bool fd, const StepParams& p, co
 namespace {
 template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
 cudaError_t post_tma(bool fd, const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
-    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(PT);
+    constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     if (fd)
-        k_post_tma<PT, L, NCOMP, true, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
+        k_post_tma<PT, L, NCOMP, true, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
                                                                            b.status, p, rev);
     else
-        k_post_tma<PT, L, NCOMP, false, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
+        k_post_tma<PT, L, NCOMP, false, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q,
                                                                             b.status, p, rev);
     return cudaGetLastError();
 }
@@ -564,7 +574,7 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     const int zs = (p.nz + nzb - 1) / nzb;
     nzb = (p.nz + zs - 1) / zs;
     dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, p.ny / kZmBY, nzb);
-    k_post_zm<PT, NCOMP, FD><<<grd, blk, smem, s>>>(*tm, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, zs, rev);
+    k_post_zm<PT, NCOMP, FD><<<grd, blk, smem, s>>>(*tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, zs, rev);
     return cudaGetLastError();
 }
 }  // namespace
@@ -585,11 +595,11 @@ cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBu
     VEFD_WITH_PT(p.prec, {
         const PT* f = static_cast<const PT*>(b.fin);
         if (lattice == 1) {
-            if (ncomp == 2) k_pre<PT, D3Q19, 2><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
-            else k_pre<PT, D3Q19, 1><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
+            if (ncomp == 2) k_pre<PT, D3Q19, 2><<<grd, blk, 0, s>>>(f, b.frest, b.drho, b.Cin, b.Q, p);
+            else k_pre<PT, D3Q19, 1><<<grd, blk, 0, s>>>(f, b.frest, b.drho, b.Cin, b.Q, p);
         } else {
-            if (ncomp == 2) k_pre<PT, D2Q9, 2><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
-            else k_pre<PT, D2Q9, 1><<<grd, blk, 0, s>>>(f, b.drho, b.Cin, b.Q, p);
+            if (ncomp == 2) k_pre<PT, D2Q9, 2><<<grd, blk, 0, s>>>(f, b.frest, b.drho, b.Cin, b.Q, p);
+            else k_pre<PT, D2Q9, 1><<<grd, blk, 0, s>>>(f, b.frest, b.drho, b.Cin, b.Q, p);
         }
     });
     return cudaGetLastError();

@@ -39,8 +39,8 @@ __device__ __forceinline__ int y_clamped(int y, int ny, int walls) {
 __device__ __forceinline__ int tile_index(unsigned b, unsigned n, int rev) { return rev ? (int)(n - 1 - b) : (int)b; }
 
 template <class PT, class L, int NCOMP>
-__global__ void __launch_bounds__(128) k_moments(const PT* __restrict__ fd, float* __restrict__ drho,
-                                                 StepParams p, int rev) {
+__global__ void __launch_bounds__(128) k_moments(const PT* __restrict__ fd, const float* __restrict__ frest,
+                                                 float* __restrict__ drho, StepParams p, int rev) {
     const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
     const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
     const int z = tile_index(blockIdx.z, gridDim.z, rev);
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(128) k_moments(const PT* __restrict__ fd, floa
     const long long i = ((long long)z * p.ny + y) * p.nx + x;
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
-        float d = 0.0f;
+        float d = __ldg(frest + s * N + i);
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) d += pop_load(fd + (s * L::Q + a) * N + i);
+        for (int a = 1; a < L::Q; ++a) d += pop_load(fd + (s * (L::Q - 1) + a - 1) * N + i);
         drho[s * N + i] = d;
     }
 }
@@ -266,11 +266,16 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
         const float uF = st.ux * Fx + st.uy * Fy + st.uz * Fz;
         const float rsv = st.rs[s], drs = st.dr[s];
         const float base = drs - 1.5f * rsv * st.usq;
-        PT* out = static_cast<PT*>(b.fout) + (long long)s * L::Q * N;
-        // The collision conserves mass exactly (the source has no zeroth
-        // moment), so the rest population is taken as the remainder after the
-        // moving ones; the FP32 weights (sum 1 + 1.5e-8) then leave no
-        // systematic mass bias, only unbiased rounding.
+        // moving populations: plane a - 1 of component s; the rest population
+        // stays at the node, in FP32, and is updated in place
+        PT* out = static_cast<PT*>(b.fout) + (long long)s * (L::Q - 1) * N - N;
+        // The collision and the wall exchange conserve mass exactly (the source
+        // has no zeroth moment; the moving-wall terms of a node sum to zero), so
+        // the rest population is taken as the remainder after the moving ones
+        // as they are stored (after rounding to the storage type).  Kept in
+        // FP32, it carries the node's mass exactly: neither the FP32 weights
+        // (sum 1 + 1.5e-8) nor 16-bit rounding of the moving populations leave
+        // a systematic mass drift.
         float moved = 0.0f;
 #pragma unroll
         for (int a = 1; a < L::Q; a += 2) {
@@ -287,25 +292,32 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
             const float B = st.omega * e_odd + st.src_w * s_odd;
             const float fa = keep * fget(s, a) + (A + B);
             const float fb = keep * fget(s, ab) + (A - B);
-            moved += fa;
-            moved += fb;
             // a streams to x + c, its opposite to x - c; a population leaving
             // through a wall returns to this node in the opposite direction with
             // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
+            // the rest population below is the remainder after the values as stored
             if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
                 const float Uw = cy < 0 ? uw6 : -uw6;
-                out[ab * N + node] = pop_put<PT>(fa - wa * rsv * (float)cx * Uw);
+                const PT v = pop_put<PT>(fa - wa * rsv * (float)cx * Uw);
+                out[ab * N + node] = v;
+                moved += pop_get(v);
             } else {
-                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = pop_put<PT>(fa);
+                const PT v = pop_put<PT>(fa);
+                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = v;
+                moved += pop_get(v);
             }
             if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
                 const float Uw = cy > 0 ? uw6 : -uw6;
-                out[a * N + node] = pop_put<PT>(fb + wa * rsv * (float)cx * Uw);
+                const PT v = pop_put<PT>(fb + wa * rsv * (float)cx * Uw);
+                out[a * N + node] = v;
+                moved += pop_get(v);
             } else {
-                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = pop_put<PT>(fb);
+                const PT v = pop_put<PT>(fb);
+                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = v;
+                moved += pop_get(v);
             }
         }
-        out[node] = pop_put<PT>(drs - moved);
+        b.frest[s * N + node] = drs - moved;
     }
 }
 
@@ -327,7 +339,8 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
         dr[s] = 0.0f;
 #pragma unroll
         for (int a = 0; a < L::Q; ++a) {
-            f[s][a] = pop_load(static_cast<const PT*>(b.fin) + (s * L::Q + a) * N + i);
+            f[s][a] = a == 0 ? b.frest[s * N + i]
+                             : pop_load(static_cast<const PT*>(b.fin) + (s * (L::Q - 1) + a - 1) * N + i);
             dr[s] += f[s][a];
         }
     }
@@ -367,7 +380,7 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
 template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
                                                               StepParams p, int rev) {
-    constexpr int P = NCOMP * L::Q;
+    constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = BX * BY * BZ;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
     extern __shared__ __align__(128) unsigned char sraw[];
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     for (int s = 0; s < NCOMP; ++s)
 #pragma unroll
         for (int a = 1; a < L::Q; ++a) {
-            const float fa = pop_get(sf[(s * L::Q + a) * T + t]);
+            const float fa = pop_get(sf[(s * (L::Q - 1) + a - 1) * T + t]);
             if (L::cx(a)) jx += L::cx(a) * fa;
             if (L::cy(a)) jy += L::cy(a) * fa;
             if (L::cz(a)) jz += L::cz(a) * fa;
@@ -422,12 +435,13 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     b.u[N + i] = st.uy;
     if (L::D == 3) b.u[2 * N + i] = st.uz;
     // volatile reads keep the populations in shared memory instead of registers
-    collide_stream<PT, L, NCOMP>(b, p, nb, st, [&](int s, int a) { return pop_smem(sf, (s * L::Q + a) * T + t); });
+    collide_stream<PT, L, NCOMP>(b, p, nb, st,
+                                 [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
 }
 
 template <class PT, class L, int NCOMP>
 __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restrict__ rhoB,
-                          const float* __restrict__ u, PT* __restrict__ fd, StepParams p) {
+                          const float* __restrict__ u, PT* __restrict__ fd, float* __restrict__ frest, StepParams p) {
     const long long N = p.N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const float ux = u ? u[i] : 0.0f, uy = u ? u[N + i] : 0.0f;
@@ -443,11 +457,11 @@ __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restric
 #pragma unroll
             for (int a = 1; a < L::Q; ++a) {
                 const float cu = L::cx(a) * ux + L::cy(a) * uy + L::cz(a) * uz;
-                const float e = L::w(a) * (d + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-                fd[(s * L::Q + a) * N + i] = pop_put<PT>(e);
-                moved += e;
+                const PT e = pop_put<PT>(L::w(a) * (d + r * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq)));
+                fd[(s * (L::Q - 1) + a - 1) * N + i] = e;
+                moved += pop_get(e);
             }
-            fd[(s * L::Q) * N + i] = pop_put<PT>(d - moved);
+            frest[s * N + i] = d - moved;
         }
     }
 }
@@ -455,8 +469,8 @@ __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restric
 // Planes [plane0, plane0 + nplanes) of the population buffer (plane = s*Q + a):
 // stored deviations <-> absolute FP32 populations f = deviation + w_a rho_ref_s.
 template <class PT, class L>
-__global__ void k_pops_convert(PT* __restrict__ pops, float* __restrict__ absf, int plane0, int nplanes, int to_abs,
-                               StepParams p) {
+__global__ void k_pops_convert(PT* __restrict__ pops, float* __restrict__ frest, float* __restrict__ absf, int plane0,
+                               int nplanes, int to_abs, StepParams p) {
     const long long N = p.N;
     const long long total = N * nplanes;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -465,9 +479,14 @@ __global__ void k_pops_convert(PT* __restrict__ pops, float* __restrict__ absf, 
         const long long i = e % N;
         const int s = pl / L::Q, a = pl % L::Q;
         const float sh = L::w(a) * p.rho_ref[s];
-        const long long k = (long long)pl * N + i;
-        if (to_abs) absf[e] = pop_get(pops[k]) + sh;
-        else pops[k] = pop_put<PT>(absf[e] - sh);
+        if (a == 0) {
+            if (to_abs) absf[e] = frest[s * N + i] + sh;
+            else frest[s * N + i] = absf[e] - sh;
+        } else {
+            const long long k = (long long)(s * (L::Q - 1) + a - 1) * N + i;
+            if (to_abs) absf[e] = pop_get(pops[k]) + sh;
+            else pops[k] = pop_put<PT>(absf[e] - sh);
+        }
     }
 }
 
@@ -494,7 +513,7 @@ struct Tile<D2Q9> {
 template <class PT, class L, int NCOMP>
 cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
     constexpr int BX = Tile<L>::BX, BY = Tile<L>::BY, BZ = Tile<L>::BZ;
-    constexpr int smem = NCOMP * L::Q * BX * BY * BZ * (int)sizeof(PT);
+    constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     k_lattice_tma<PT, L, NCOMP, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b, p, rev);
@@ -526,10 +545,10 @@ bool make_pop_tensor_map_box(int lattice, int ncomp, int prec, int nx, int ny, i
         encode = reinterpret_cast<EncodeTiled>(fn);
     }
     const int Q = lattice == 1 ? 19 : 9;
-    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(ncomp * Q)};
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(ncomp * (Q - 1))};
     const cuuint64_t es = prec == kPrecFp32 ? 4 : 2;
     const cuuint64_t strides[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
-    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)(ncomp * Q)};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)(ncomp * (Q - 1))};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = prec == kPrecFp16   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : prec == kPrecBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -550,11 +569,11 @@ cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const St
     VEFD_WITH_PT(p.prec, {
         const PT* fin = static_cast<const PT*>(b.fin);
         if (lattice == 1) {
-            if (ncomp == 2) k_moments<PT, D3Q19, 2><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
-            else k_moments<PT, D3Q19, 1><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
+            if (ncomp == 2) k_moments<PT, D3Q19, 2><<<grd, blk, 0, s>>>(fin, b.frest, b.drho, p, rev);
+            else k_moments<PT, D3Q19, 1><<<grd, blk, 0, s>>>(fin, b.frest, b.drho, p, rev);
         } else {
-            if (ncomp == 2) k_moments<PT, D2Q9, 2><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
-            else k_moments<PT, D2Q9, 1><<<grd, blk, 0, s>>>(fin, b.drho, p, rev);
+            if (ncomp == 2) k_moments<PT, D2Q9, 2><<<grd, blk, 0, s>>>(fin, b.frest, b.drho, p, rev);
+            else k_moments<PT, D2Q9, 1><<<grd, blk, 0, s>>>(fin, b.frest, b.drho, p, rev);
         }
     });
     return cudaGetLastError();
@@ -593,29 +612,30 @@ cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepP
 }
 
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
-                                    const float* rhoB, const float* u, void* fd, cudaStream_t s) {
+                                    const float* rhoB, const float* u, void* fd, float* frest, cudaStream_t s) {
     const int g = grid_1d(p.N);
     VEFD_WITH_PT(p.prec, {
         PT* out = static_cast<PT*>(fd);
         if (lattice == 1) {
-            if (ncomp == 2) k_init_eq<PT, D3Q19, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
-            else k_init_eq<PT, D3Q19, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
+            if (ncomp == 2) k_init_eq<PT, D3Q19, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, frest, p);
+            else k_init_eq<PT, D3Q19, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, frest, p);
         } else {
-            if (ncomp == 2) k_init_eq<PT, D2Q9, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
-            else k_init_eq<PT, D2Q9, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, p);
+            if (ncomp == 2) k_init_eq<PT, D2Q9, 2><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, frest, p);
+            else k_init_eq<PT, D2Q9, 1><<<g, 256, 0, s>>>(rhoA, rhoB, u, out, frest, p);
         }
     });
     return cudaGetLastError();
 }
 
-cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, void* pops, float* absf, int plane0,
-                                int nplanes, int to_absolute, cudaStream_t s) {
+cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, void* pops, float* frest, float* absf,
+                                int plane0, int nplanes, int to_absolute, cudaStream_t s) {
     (void)ncomp;
     const int g = grid_1d(p.N * nplanes);
     VEFD_WITH_PT(p.prec, {
         PT* pp = static_cast<PT*>(pops);
-        if (lattice == 1) k_pops_convert<PT, D3Q19><<<g, 256, 0, s>>>(pp, absf, plane0, nplanes, to_absolute, p);
-        else k_pops_convert<PT, D2Q9><<<g, 256, 0, s>>>(pp, absf, plane0, nplanes, to_absolute, p);
+        if (lattice == 1)
+            k_pops_convert<PT, D3Q19><<<g, 256, 0, s>>>(pp, frest, absf, plane0, nplanes, to_absolute, p);
+        else k_pops_convert<PT, D2Q9><<<g, 256, 0, s>>>(pp, frest, absf, plane0, nplanes, to_absolute, p);
     });
     return cudaGetLastError();
 }

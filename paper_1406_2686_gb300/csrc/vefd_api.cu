@@ -36,7 +36,8 @@ struct vefd_ctx {
     void* mem = nullptr;
     size_t mem_bytes = 0;
     bool owned = false;
-    void* f[2] = {nullptr, nullptr};  // population deviations, storage type of cfg.precision
+    void* f[2] = {nullptr, nullptr};  // moving population deviations, storage type of cfg.precision
+    float* frest = nullptr;           // rest population deviations (FP32, updated in place)
     size_t psize = 4;                 // bytes per stored population value
     float* drho = nullptr;
     float* u = nullptr;
@@ -115,7 +116,7 @@ bool config_ok(const vefd_config* c, const char** why) {
 constexpr int kStagePlanes = 11;
 
 struct Layout {
-    size_t f0, f1, drho, u, c0, c1, r, dbg, q, status, dpart, dout, total;
+    size_t f0, f1, frest, drho, u, c0, c1, r, dbg, q, status, dpart, dout, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -131,8 +132,9 @@ Layout layout_of(const vefd_config* c) {
         return at;
     };
     const size_t ps = c->precision == 0 ? 4 : 2;
-    L.f0 = take(ps * c->ncomp * Q * N);
-    L.f1 = take(ps * c->ncomp * Q * N);
+    L.f0 = take(ps * c->ncomp * (Q - 1) * N);
+    L.f1 = take(ps * c->ncomp * (Q - 1) * N);
+    L.frest = take(sizeof(float) * c->ncomp * N);
     L.drho = take(sizeof(float) * 2 * N);
     L.u = take(sizeof(float) * 3 * N);
     L.c0 = take(sizeof(float) * NC * N);
@@ -152,6 +154,7 @@ void carve(vefd_ctx* c) {
     char* b = (char*)c->mem;
     c->f[0] = b + L.f0;
     c->f[1] = b + L.f1;
+    c->frest = (float*)(b + L.frest);
     c->drho = (float*)(b + L.drho);
     c->u = (float*)(b + L.u);
     c->C[0] = (float*)(b + L.c0);
@@ -210,6 +213,7 @@ StepBufs bufs_of(vefd_ctx* c) {
     StepBufs b;
     b.fin = c->f[c->cur];
     b.fout = c->f[1 - c->cur];
+    b.frest = c->frest;
     b.drho = c->drho;
     b.u = c->u;
     b.Cin = c->C[c->ccur];
@@ -443,7 +447,7 @@ vefd_status vefd_init_fields(vefd_ctx* c, const float* rho_A, const float* rho_B
     if (C0) VEFD_CUDA(c, cudaMemcpyAsync(sC, C0, plane * c->NC, kind, c->stream));
     StepParams p = params_of(c);
     VEFD_CUDA(c, launch_init_equilibrium(c->cfg.lattice, c->cfg.ncomp, p, sA, sB, u ? sU : nullptr, c->f[0],
-                                         c->stream));
+                                         c->frest, c->stream));
     if (C0) VEFD_CUDA(c, launch_tensor_shift(c->cfg.lattice, sC, c->C[0], N, -1.0f, c->stream));
     else VEFD_CUDA(c, cudaMemsetAsync(c->C[0], 0, plane * c->NC, c->stream));
     VEFD_CUDA(c, cudaMemsetAsync(c->R, 0, plane * c->NC, c->stream));
@@ -503,7 +507,8 @@ vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, siz
         for (int p0 = 0; p0 < planes; p0 += kStagePlanes) {
             const int k = planes - p0 < kStagePlanes ? planes - p0 : kStagePlanes;
             VEFD_CUDA(c, cudaMemcpyAsync(stg, (const char*)src + p0 * plane, k * plane, kind, c->stream));
-            VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], stg, p0, k, 0, c->stream));
+            VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], c->frest, stg, p0, k, 0,
+                                             c->stream));
         }
         c->drho_valid = false;
         break;
@@ -584,7 +589,8 @@ vefd_status vefd_read_field(vefd_ctx* c, vefd_field field, void* dst, size_t byt
         const size_t plane = sizeof(float) * (size_t)N;
         for (int p0 = 0; p0 < planes; p0 += kStagePlanes) {
             const int k = planes - p0 < kStagePlanes ? planes - p0 : kStagePlanes;
-            VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], stg, p0, k, 1, c->stream));
+            VEFD_CUDA(c, launch_pops_convert(c->cfg.lattice, c->cfg.ncomp, p, c->f[c->cur], c->frest, stg, p0, k, 1,
+                                             c->stream));
             VEFD_CUDA(c, cudaMemcpyAsync((char*)dst + p0 * plane, stg, k * plane,
                                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
         }
@@ -752,7 +758,7 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 2;
+    h.version = 3;
     h.lattice = c->cfg.lattice;
     h.nx = c->cfg.nx;
     h.ny = c->cfg.ny;
@@ -777,11 +783,13 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     h.rho_ref[1] = c->rho_ref[1];
     h.steps = c->steps;
     VEFD_CUDA(c, cudaMemcpyAsync(&h.status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    const size_t npb = (size_t)c->cfg.ncomp * c->Q * c->N * c->psize, nc = (size_t)c->NC * c->N;
-    std::vector<char> buf(npb + 2 * nc * 4);
+    const size_t npb = (size_t)c->cfg.ncomp * (c->Q - 1) * c->N * c->psize, nc = (size_t)c->NC * c->N;
+    const size_t nrb = (size_t)c->cfg.ncomp * c->N * 4;
+    std::vector<char> buf(npb + nrb + 2 * nc * 4);
     VEFD_CUDA(c, cudaMemcpyAsync(buf.data(), c->f[c->cur], npb, cudaMemcpyDeviceToHost, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb, c->C[c->ccur], nc * 4, cudaMemcpyDeviceToHost, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb + nc * 4, c->R, nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb, c->frest, nrb, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb + nrb, c->C[c->ccur], nc * 4, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(buf.data() + npb + nrb + nc * 4, c->R, nc * 4, cudaMemcpyDeviceToHost, c->stream));
     VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
     FILE* fh = fopen(path, "wb");
     if (!fh) return fail(c, VEFD_ERR_ARG, "cannot open %s for writing", path);
@@ -796,10 +804,11 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     FILE* fh = fopen(path, "rb");
     if (!fh) return fail(c, VEFD_ERR_ARG, "cannot open %s", path);
     CkptHeader h;
-    const size_t npb = (size_t)c->cfg.ncomp * c->Q * c->N * c->psize, nc = (size_t)c->NC * c->N;
-    std::vector<char> buf(npb + 2 * nc * 4);
+    const size_t npb = (size_t)c->cfg.ncomp * (c->Q - 1) * c->N * c->psize, nc = (size_t)c->NC * c->N;
+    const size_t nrb = (size_t)c->cfg.ncomp * c->N * 4;
+    std::vector<char> buf(npb + nrb + 2 * nc * 4);
     bool ok = fread(&h, sizeof h, 1, fh) == 1;
-    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 2 && h.precision == c->cfg.precision;
+    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 3 && h.precision == c->cfg.precision;
     ok = ok && h.lattice == c->cfg.lattice && h.nx == c->cfg.nx && h.ny == c->cfg.ny && h.nz == c->cfg.nz &&
          h.ncomp == c->cfg.ncomp && h.walls == c->cfg.walls;
     ok = ok && fread(buf.data(), 1, buf.size(), fh) == buf.size();
@@ -824,8 +833,9 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     c->cur = 0;
     c->ccur = 0;
     VEFD_CUDA(c, cudaMemcpyAsync(c->f[0], buf.data(), npb, cudaMemcpyHostToDevice, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(c->C[0], buf.data() + npb, nc * 4, cudaMemcpyHostToDevice, c->stream));
-    VEFD_CUDA(c, cudaMemcpyAsync(c->R, buf.data() + npb + nc * 4, nc * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->frest, buf.data() + npb, nrb, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->C[0], buf.data() + npb + nrb, nc * 4, cudaMemcpyHostToDevice, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(c->R, buf.data() + npb + nrb + nc * 4, nc * 4, cudaMemcpyHostToDevice, c->stream));
     VEFD_CUDA(c, cudaMemcpyAsync(c->status, &h.status, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
     VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = 1;

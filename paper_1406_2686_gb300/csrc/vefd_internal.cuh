@@ -1,7 +1,9 @@
 // Internal declarations shared by the CUDA translation units of libvefd.
 //
 // Storage (all FP32, x fastest, node i = (z*NY + y)*NX + x):
-//   populations  fd[(s*Q + a)*N + i] = f_a^s - w_a rho_ref_s   (deviation form)
+//   populations  moving a >= 1: fd[(s*(Q-1) + a-1)*N + i] = f_a^s - w_a rho_ref_s  (deviation form,
+//                storage type PT, ping-pong); rest a = 0: frest[s*N + i], always FP32,
+//                updated in place (it does not stream) and carrying each node's mass exactly
 //   densities    drho[s*N + i] = rho_s - rho_ref_s            (sum of deviations)
 //   velocity     u[k*N + i], k < D                             (Eq. equilibrium:vel)
 //   conformation Ct[k*N + i] = C_k - delta_k                   (k < NC)
@@ -179,6 +181,7 @@ constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTim
 struct StepBufs {
     const void* fin;       // populations at time n (deviation form, storage type of p.prec)
     void* fout;            // populations at time n+1
+    float* frest;          // rest populations (FP32, in place: time n before the lattice kernel, n+1 after)
     float* drho;           // densities of time n
     float* u;              // velocity of time n (written by the lattice kernel)
     const float* Cin;      // C - I at time n
@@ -228,11 +231,11 @@ bool make_pop_tensor_map_box(int lattice, int ncomp, int prec, int nx, int ny, i
 
 // Field conversions.
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
-                                    const float* rhoB, const float* u, void* fd, cudaStream_t s);
+                                    const float* rhoB, const float* u, void* fd, float* frest, cudaStream_t s);
 // Planes [plane0, plane0 + nplanes) of the population buffer: stored deviations
 // `pops` -> absolute FP32 `absf` (to_absolute) or back.
-cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, void* pops, float* absf, int plane0,
-                                int nplanes, int to_absolute, cudaStream_t s);
+cudaError_t launch_pops_convert(int lattice, int ncomp, const StepParams& p, void* pops, float* frest, float* absf,
+                                int plane0, int nplanes, int to_absolute, cudaStream_t s);
 cudaError_t launch_tensor_shift(int lattice, const float* src, float* dst, long long N, float sign,
                                 cudaStream_t s);
 // which: 0 rho_A, 1 rho_B, 2 phi, 4 C, 5 sigma_P = f(r_P) C
