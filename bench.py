@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Throughput of the hybrid LBM / FENE-P step on GB300 (one JSON line).
 
-Workload: the D3Q19 two-component Shan-Chen FENE-P confined droplet,
+Workload (default): the D3Q19 two-component Shan-Chen FENE-P confined droplet,
 128 x 128 x 64 with the 64 axis wall-normal (NX = 128, NY = 64, NZ = 128),
 droplet R = 16 at the box centre, G = 1.5, rho 2.0 / 0.1, interface width 5,
 phi noise 1e-3 (SplitMix64 seed 1), viscoelastic droplet (f_+ feedback),
@@ -13,6 +13,10 @@ One bench step = one time step of the whole hot path over the lattice.
 CUDA events on the library's stream over exactly --steps steps after
 --warmup untimed steps.  The populations (152 MB per buffer) exceed the 129 MB
 L2, so no flush is needed between steps.
+
+--workload droplet256 runs the 256 x 256 x 128 precision-variant geometry and
+--precision fp16|bf16 stores the moving population deviations in 16 bits;
+the default FP32 run also times both 16-bit variants ("variants").
 
 --impl reference times the FP64 CPU oracle (the only other place this file
 runs oracle code) on a bounded slab of the same workload.
@@ -33,24 +37,48 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-NX, NY, NZ, RADIUS = 128, 64, 128, 16.0
+WORKLOADS = {
+    # name: (NX, NY wall-normal, NZ, droplet radius); 2R/H = 0.5 in both
+    "droplet128": (128, 64, 128, 16.0),
+    "droplet256": (256, 128, 256, 32.0),
+}
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 ETA_B = 2.1 / 3.0 * 0.5
 ETA_A, ETA_P, SIGMA = 0.6 * ETA_B, 0.4 * ETA_B, 0.09
-GDOT = 0.1 * SIGMA / (RADIUS * ETA_B)
-U_WALL = GDOT * NY / 2.0
-TAU_P = 1.0 * RADIUS * ETA_B / SIGMA * ETA_B / ETA_P
-WORKLOAD = ("D3Q19 two-component Shan-Chen FENE-P confined droplet R=16, 128x128x64 "
-            "(NX=128, NY=64 wall-normal, NZ=128), G=1.5, L2=100, De=1, Ca=0.1, FP32 populations and C")
-# algorithmic bytes per node update (each value read and written once per step)
-STEP_BYTES_PER_NODE = 2 * 19 * 4 * 2 + 6 * 4 * 2 + 6 * 4 * 2   # 400
+
+
+class Setup:
+    """Droplet workload geometry and the parameters that follow from Ca = 0.1
+    and De = 1 (tau_B = 1 at rho = 2.1, eta_A = 0.6 eta_B, eta_P = 0.4 eta_B)."""
+
+    def __init__(self, workload="droplet128", precision="fp32"):
+        self.name = workload
+        self.NX, self.NY, self.NZ, self.R = WORKLOADS[workload]
+        self.prec_name = precision
+        self.prec = PRECISIONS[precision]
+        self.gdot = 0.1 * SIGMA / (self.R * ETA_B)
+        self.u_wall = self.gdot * self.NY / 2.0
+        self.tau_p = 1.0 * self.R * ETA_B / SIGMA * ETA_B / ETA_P
+        self.N = self.NX * self.NY * self.NZ
+        store = {"fp32": "FP32", "fp16": "FP16", "bf16": "BF16"}[precision]
+        self.text = ("D3Q19 two-component Shan-Chen FENE-P confined droplet R=%d, %dx%dx%d (NX=%d, NY=%d wall-normal, "
+                     "NZ=%d), G=1.5, L2=100, De=1, Ca=0.1, %s population deviations, FP32 C"
+                     % (self.R, self.NX, self.NZ, self.NY, self.NX, self.NY, self.NZ, store))
+        # algorithmic bytes per node update (each value read and written once per step):
+        # populations (moving ones in the storage type, rest in FP32) + C + AB2 history
+        pbytes = 2 * 18 * (4 if self.prec == 0 else 2) * 2 + 2 * 4 * 2
+        self.pop_bytes = pbytes
+        self.step_bytes = pbytes + 6 * 4 * 2 + 6 * 4 * 2   # 400 for FP32, 256 for 16-bit
 KERNEL_NAMES = ["moments", "lattice_collide_stream", "densities_fenep_fd"]
-# algorithmic bytes per node of each kernel class of the two-kernel step
-KERNEL_ALGO_BYTES = {
-    "moments": 0,                                   # only before the first step
-    "lattice_collide_stream": 2 * 19 * 4 * 2,       # populations read + written
-    "densities_fenep_fd": 6 * 4 * 2 + 6 * 4 * 2,    # C and AB2 history read + written (the population
-                                                    # re-read for the densities is overhead)
-}
+
+
+def kernel_algo_bytes(setup, name):
+    """Algorithmic bytes per node of each kernel class of the two-kernel step."""
+    if name == "lattice_collide_stream":
+        return setup.pop_bytes                  # populations read + written
+    if name == "densities_fenep_fd":
+        return 6 * 4 * 2 + 6 * 4 * 2            # C and AB2 history (the population re-read is overhead)
+    return 0                                    # initial densities only
 MLUPS = "MLUPS"
 
 
@@ -62,6 +90,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="droplet128", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage variant timings")
     return ap.parse_args()
 
 
@@ -158,31 +189,32 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_lattice():
+def make_lattice(S):
     from paper_1406_2686_gb300 import vefd
-    lat = vefd.Lattice(lattice=vefd.D3Q19, nx=NX, ny=NY, nz=NZ, ncomp=2, walls=1, G=1.5, eta_A=ETA_A,
-                       eta_B=ETA_B, delta=0.1)
-    lat.set_wall_shear(U_WALL)
-    lat.set_fenep(TAU_P, ETA_P, 100.0, 1e-3, 1, 1)
+    lat = vefd.Lattice(lattice=vefd.D3Q19, nx=S.NX, ny=S.NY, nz=S.NZ, ncomp=2, walls=1, G=1.5, eta_A=ETA_A,
+                       eta_B=ETA_B, delta=0.1, precision=S.prec)
+    lat.set_wall_shear(S.u_wall)
+    lat.set_fenep(S.tau_p, ETA_P, 100.0, 1e-3, 1, 1)
+    lat.init_droplet((S.NX - 1) / 2.0, (S.NY - 1) / 2.0, (S.NZ - 1) / 2.0, S.R, 2.0, 0.1, 5.0, 1, 1e-3)
     return lat
 
 
-def droplet_host_fields(torch):
+def droplet_host_fields(S, torch):
     from paper_1406_2686_gb300 import inputs
-    rA, rB = inputs.droplet_fields(NX, NY, NZ, R=RADIUS, seed=1, noise=1e-3)
+    rA, rB = inputs.droplet_fields(S.NX, S.NY, S.NZ, R=S.R, seed=1, noise=1e-3)
     a = torch.from_numpy(rA.astype("float32")).pin_memory()
     b = torch.from_numpy(rB.astype("float32")).pin_memory()
     return a, b
 
 
-def run_e2e(lat, torch, steps):
+def run_e2e(S, lat, torch, steps):
     """End to end through the C-ABI with pinned host buffers: upload the initial
     densities, run `steps` steps, read phi, u and C back to the host and take
     the FP64 diagnostics; wall-clock time around all of it."""
     import ctypes
 
     from paper_1406_2686_gb300 import vefd
-    rA, rB = droplet_host_fields(torch)
+    rA, rB = droplet_host_fields(S, torch)
     outs = {f: torch.empty(vefd.vefd_field_bytes(lat.ctx, f) // 4, dtype=torch.float32).pin_memory()
             for f in (vefd.PHI, vefd.U, vefd.C)}
     h2d = rA.numel() * 4 + rB.numel() * 4
@@ -199,15 +231,16 @@ def run_e2e(lat, torch, steps):
     return dt, h2d, d2h
 
 
-def cpu_baseline(budget_s=15.0):
+def cpu_baseline(S, budget_s=15.0):
     """The FP64 oracle as it stands, on the host cores, on the same droplet
     lattice: as many steps as fit in the budget (at least two)."""
     import oracle
     from paper_1406_2686_gb300 import inputs
     cores = oracle.set_threads(0)
-    rA, rB = inputs.droplet_fields(NX, NY, NZ, R=RADIUS, seed=1, noise=1e-3)
+    NX, NY, NZ = S.NX, S.NY, S.NZ
+    rA, rB = inputs.droplet_fields(NX, NY, NZ, R=S.R, seed=1, noise=1e-3)
     o = oracle.Oracle(lattice=1, nx=NX, ny=NY, nz=NZ, ncomp=2, walls=1, G=1.5, eta_A=ETA_A, eta_B=ETA_B,
-                      delta=0.1, u_wall=U_WALL, tau_p=TAU_P, eta_p=ETA_P, L2=100.0, kappa=1e-3, phase=1)
+                      delta=0.1, u_wall=S.u_wall, tau_p=S.tau_p, eta_p=ETA_P, L2=100.0, kappa=1e-3, phase=1)
     o.init_fields(inputs.to_f32_exact(rA), inputs.to_f32_exact(rB))
     o.step(1)
     n = 0
@@ -223,6 +256,42 @@ def cpu_baseline(budget_s=15.0):
             "sample": "%d steps of the full %dx%dx%d droplet lattice (FP64, OpenMP over nodes)" % (n, NX, NY, NZ)}
 
 
+def replica_throughput(elapsed_ms, nodes_per_rank, steps, device="cpu"):
+    """Whole-job MLUPS of independent replicas: every rank advanced
+    `nodes_per_rank` nodes for `steps` steps; the job time is the slowest
+    rank's (max over ranks).  Returns (max elapsed ms, MLUPS)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(elapsed_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, nodes_per_rank * steps * world / (ms / 1e3) / 1e6
+
+
+def time_variant(S, steps, warmup):
+    """MLUPS of one storage variant on the same workload (events on the library stream)."""
+    import torch
+    lat = make_lattice(S)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    peak, _ = measured_peak()
+    bw = S.step_bytes * S.N / (ms / steps / 1e3) / 1e9
+    out = {"value": round(S.N * steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "ms_per_step": round(ms / steps, 5),
+           "step_roofline": {"achieved": round(bw, 1), "frac": round(bw / peak, 4),
+                             "algorithmic_bytes_per_node": S.step_bytes}, "status_bits": lat.status()}
+    lat.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -234,8 +303,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     vefd.load(build_if_missing=True)
-    lat = make_lattice()
-    lat.init_droplet((NX - 1) / 2.0, (NY - 1) / 2.0, (NZ - 1) / 2.0, RADIUS, 2.0, 0.1, 5.0, 1, 1e-3)
+    S = Setup(args.workload, args.precision)
+    NX, NY, NZ = S.NX, S.NY, S.NZ
+    lat = make_lattice(S)
     stream = lat.stream
     K, W = args.steps, args.warmup
     with torch.cuda.stream(stream):
@@ -264,34 +334,26 @@ def run_ours(args):
     kms, klaunch = lat.kernel_times()
     lat.profile_kernels(False)
     status = lat.status()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     N = NX * NY * NZ
-    value = N * K * world / (ms / 1e3) / 1e6
+    ms, value = replica_throughput(ms, N, K, device="cuda")
     peak, peak_kind = measured_peak()
     # dominant kernel and its roofline
     dom = max(range(3), key=lambda k: kms[k])
     dname = KERNEL_NAMES[dom]
     avg_s = kms[dom] / max(klaunch[dom], 1) / 1e3
-    algo = KERNEL_ALGO_BYTES[dname] * N
+    algo = kernel_algo_bytes(S, dname) * N
     achieved = algo / avg_s / 1e9
-    traffic = recorded_traffic(dname)
+    traffic = recorded_traffic(dname) if (S.name, S.prec) == ("droplet128", 0) else None
     roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes_per_launch": algo,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
-    step_achieved = STEP_BYTES_PER_NODE * N / (ms / K / 1e3) / 1e9
+    step_achieved = S.step_bytes * N / (ms / K / 1e3) / 1e9
     kernels = {KERNEL_NAMES[k]: {"launches": klaunch[k], "ms_total": round(kms[k], 3),
                                  "share": round(kms[k] / max(sum(kms), 1e-12), 4)} for k in range(3)}
     e2e = None
     if not args.no_e2e:
-        dt, h2d, d2h = run_e2e(lat, torch, K)
-        e2e_val = N * K / dt / 1e6
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = N * K * world / float(t.item()) / 1e6
+        dt, h2d, d2h = run_e2e(S, lat, torch, K)
+        _, e2e_val = replica_throughput(dt * 1e3, N, K, device="cuda")
         e2e = {"value": round(e2e_val, 1), "unit": MLUPS, "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K,
                "what": "init from pinned host densities + %d steps + phi/u/C read to pinned host + diagnostics" % K}
@@ -299,21 +361,27 @@ def run_ours(args):
         "metric": "MLUPS & % HBM roofline", "value": round(value, 1), "unit": MLUPS, "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": round(ms / K, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": N, "global_nodes": N * world,
+        "config": {"workload": S.text, "nodes": N, "global_nodes": N * world, "population_storage": S.prec_name,
                    "l2": "inputs larger than L2 (152 MB per population buffer > 129 MB), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
         "step_roofline": {"achieved": round(step_achieved, 1), "peak": peak, "unit": "GB/s",
                           "frac": round(step_achieved / peak, 4),
-                          "algorithmic_bytes_per_node": STEP_BYTES_PER_NODE},
+                          "algorithmic_bytes_per_node": S.step_bytes},
         "kernels": kernels, "gpu_launches": int(K * lat.kernels_per_step()), "clocks": clk, "e2e": e2e,
         "status_bits": status, "source_sha": source_hash(),
     }
+    lat.close()
+    if not args.no_variants and S.prec == 0:
+        # NEXT-1 storage variants of the same workload, reported beside the FP32 headline
+        vsteps = max(200, K // 5)
+        line["variants"] = {pn: time_variant(Setup(S.name, pn), vsteps, min(W, 50)) for pn in ("fp16", "bf16")}
+        line["variants"]["note"] = ("16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
+                                    "and C; %d steps each" % vsteps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(S)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    lat.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -326,12 +394,14 @@ def run_reference(args):
     from paper_1406_2686_gb300 import inputs
     cores = oracle.set_threads(0)
     K, W = args.steps, args.warmup
+    S = Setup(args.workload, "fp32")
+    NX, NY, NZ = S.NX, S.NY, S.NZ
 
     def make(nz_s):
-        rA, rB = inputs.droplet_fields(NX, NY, nz_s, R=RADIUS, seed=1, noise=1e-3,
+        rA, rB = inputs.droplet_fields(NX, NY, nz_s, R=S.R, seed=1, noise=1e-3,
                                        center=((NX - 1) / 2.0, (NY - 1) / 2.0, (nz_s - 1) / 2.0))
         o = oracle.Oracle(lattice=1, nx=NX, ny=NY, nz=nz_s, ncomp=2, walls=1, G=1.5, eta_A=ETA_A, eta_B=ETA_B,
-                          delta=0.1, u_wall=U_WALL, tau_p=TAU_P, eta_p=ETA_P, L2=100.0, kappa=1e-3, phase=1)
+                          delta=0.1, u_wall=S.u_wall, tau_p=S.tau_p, eta_p=ETA_P, L2=100.0, kappa=1e-3, phase=1)
         o.init_fields(inputs.to_f32_exact(rA), inputs.to_f32_exact(rB))
         return o
 
@@ -354,7 +424,7 @@ def run_reference(args):
         "metric": "MLUPS & % HBM roofline", "value": round(value, 3), "unit": MLUPS, "impl": "reference",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": round(dt / K * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": NX * NY * NZ, "sample_nodes": n},
+        "config": {"workload": S.text, "nodes": NX * NY * NZ, "sample_nodes": n},
         "cpu_baseline": {"value": round(value, 3), "unit": MLUPS, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": MLUPS, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
