@@ -112,6 +112,14 @@ vefd_status vefd_set_body_force(vefd_ctx *ctx, double fx, double fy, double fz);
 vefd_status vefd_set_fenep(vefd_ctx *ctx, double tau_p, double eta_p, double L2, double kappa, int phase,
                            int fd_on);
 
+/* How the polymer stress reaches the fluid (Sec. 2): 0 (default) as the body
+ * force (eta_P/tau_P) div[(f C - I) m(phi)] shared by rho_sigma/rho (Eq. NS);
+ * 1 added to the second moment of each component's equilibrium with weight
+ * rho_sigma/rho (Eq. MODEtransformation), in BGK form
+ * E_a += w_a (c_a c_a - c_s^2 I):T_sigma / (2 c_s^4),
+ * T_sigma = -(rho_sigma/rho)(eta_P/tau_P)(f C - I) m(phi).  Errors: VEFD_ERR_ARG. */
+vefd_status vefd_set_polymer_coupling(vefd_ctx *ctx, int mode);
+
 /* Initial state: populations at equilibrium E(rho_sigma, u), C = C0 (or I
  * when C0 is NULL), AB2 history cleared (the next step is forward Euler).
  * rho_A (N), rho_B (N, ignored for one component), u (dim*N or NULL for

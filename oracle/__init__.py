@@ -29,7 +29,7 @@ class OrcParams(ctypes.Structure):
         ("G", ctypes.c_double), ("eta_A", ctypes.c_double), ("eta_B", ctypes.c_double),
         ("delta", ctypes.c_double), ("u_wall", ctypes.c_double), ("fext", ctypes.c_double * 3),
         ("tau_p", ctypes.c_double), ("eta_p", ctypes.c_double), ("L2", ctypes.c_double),
-        ("kappa", ctypes.c_double), ("phase", ctypes.c_int), ("fd_on", ctypes.c_int),
+        ("kappa", ctypes.c_double), ("phase", ctypes.c_int), ("fd_on", ctypes.c_int), ("coupling", ctypes.c_int),
     ]
 
 
@@ -77,7 +77,7 @@ def _f64(a):
 
 DEFAULTS = dict(lattice=D2Q9, nx=8, ny=8, nz=1, ncomp=1, walls=1, G=0.0, eta_A=1.0 / 6.0,
                 eta_B=1.0 / 6.0, delta=0.1, u_wall=0.0, fext=(0.0, 0.0, 0.0), tau_p=1000.0,
-                eta_p=0.0, L2=100.0, kappa=0.0, phase=0, fd_on=1)
+                eta_p=0.0, L2=100.0, kappa=0.0, phase=0, fd_on=1, coupling=0)
 
 
 def make_params(**kw):

@@ -23,6 +23,14 @@
  *   9. AB2           C^{n+1} = C^n + 3/2 R^n - 1/2 R^{n-1}; Euler on the first step
  * Steps 8-9 use u^n and C^n of steps 1-4.
  *
+ * Polymer feedback, two readings of Sec. 2: (a) the body force
+ * (eta_P/tau_P) div[(f C - I) m(phi)] shared by rho_sigma/rho (coupling 0), or
+ * (b) Eq. MODEtransformation: the stress T_sigma = -(rho_sigma/rho)(eta_P/tau_P)
+ * (f C - I) m(phi) added to the second moment of each component's equilibrium
+ * (coupling 1); in BGK form E_a += w_a (c_a c_a - c_s^2 I):T_sigma / (2 c_s^4),
+ * which leaves mass and momentum unchanged and adds exactly T_sigma to the
+ * second moment.
+ *
  * Boundary readings (the paper states the rules only in words):
  *   - densities seen by the Shan-Chen sum across a wall take the value of the
  *     adjacent fluid row (zero normal gradient, neutral wetting, Sec. 2);
@@ -242,6 +250,11 @@ static void compute_polymer_force(orc_state *s) {
     }
     const double pref = s->p.eta_p / s->p.tau_p;
     const int nd = ndim(s);
+    if (s->p.coupling == 1) {
+        /* the stress enters the equilibrium instead of a force */
+        memset(s->Fp, 0, sizeof(double) * 3 * N);
+        return;
+    }
     #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < s->p.nz; ++z)
         for (int y = 0; y < s->p.ny; ++y)
@@ -307,9 +320,26 @@ static void collide_stream(orc_state *s) {
                     double F[3];
                     component_force(s, i, sg, F);
                     double rs = s->rho[(long)sg * N + i];
+                    /* equilibrium stress of Eq. MODEtransformation (coupling 1) */
+                    double T[3][3] = {{0}};
+                    if (s->p.coupling == 1) {
+                        double share = rs / (s->rho[i] + s->rho[N + i]);
+                        for (int aa = 0; aa < 3; ++aa)
+                            for (int bb = 0; bb < 3; ++bb)
+                                T[aa][bb] = -share * s->p.eta_p / s->p.tau_p * s->Qs[(long)SYM[aa][bb] * N + i];
+                    }
+                    const int nd = ndim(s);
                     for (int a = 0; a < Q; ++a) {
                         double fa = s->f[((long)sg * Q + a) * N + i];
                         double E = equilibrium(s->w[a], s->c[a], rs, u);
+                        if (s->p.coupling == 1) {
+                            double cTc = 0.0, trT = 0.0;
+                            for (int aa = 0; aa < nd; ++aa) {
+                                trT += T[aa][aa];
+                                for (int bb = 0; bb < nd; ++bb) cTc += s->c[a][aa] * s->c[a][bb] * T[aa][bb];
+                            }
+                            E += s->w[a] * (cTc - CS2 * trT) / (2.0 * CS2 * CS2);
+                        }
                         double S = source(s->w[a], s->c[a], u, F);
                         /* Eq. (LB) with Lambda = 1/tau: f* = f - (f - E)/tau + (1 - 1/(2 tau)) S */
                         double fpost = fa - (fa - E) / tau + (1.0 - 0.5 / tau) * S;

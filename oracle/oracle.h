@@ -48,6 +48,8 @@ typedef struct {
     double kappa;           /* artificial stress diffusivity */
     int phase;              /* feedback modulation: 0 -> 1, +1 -> f_+, -1 -> f_- */
     int fd_on;              /* 1: evolve C; 0: C frozen (LBM only) */
+    int coupling;           /* polymer feedback: 0 body force div Q (Eq. NS);
+                               1 added to the equilibrium second moment (Eq. MODEtransformation) */
 } orc_params;
 
 typedef struct orc_state orc_state;

@@ -110,7 +110,7 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p
 //            ghost row v(-1) = 2 v(0) - v(1)).
 template <class L, int NCOMP>
 __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepParams& p, const Nbr& nb,
-                                                 float acc[2][3], float Fp[3]) {
+                                                 float acc[2][3], float Fp[3], float qloc[L::NQ]) {
     const int N = (int)p.N;
     const int i = nb.i;
 #pragma unroll
@@ -130,8 +130,16 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
         }
     }
     Fp[0] = Fp[1] = Fp[2] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < L::NQ; ++k) qloc[k] = 0.0f;
     if (p.feedback == 0.0f) return;
     const float* Q = b.Q;
+    if (p.coupling == 1) {
+        // the stress enters this node's equilibrium instead (Eq. MODEtransformation)
+#pragma unroll
+        for (int k = 0; k < L::NQ; ++k) qloc[k] = __ldg(Q + k * N + i);
+        return;
+    }
     float div[3] = {0.f, 0.f, 0.f};
     {
         const int jm = nb.at(-1, 0, 0), jp = nb.at(1, 0, 0);
@@ -169,12 +177,15 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
     for (int k = 0; k < 3; ++k) Fp[k] = p.feedback * div[k];
 }
 
-// Local state after the forces: velocity, relaxation and per-component force.
+// Local state after the forces: velocity, relaxation, per-component force and,
+// for the equilibrium coupling, the component's share of the polymer stress
+// T_s = tq[s] Q with tq[s] = -(rho_s/rho)(eta_P/tau_P).
 template <int NCOMP>
 struct Local {
     float rs[NCOMP], dr[NCOMP];
     float inv_rho, ux, uy, uz, usq, omega, src_w;
     float F[NCOMP][3];
+    float tq[NCOMP];
 };
 
 template <class L, int NCOMP>
@@ -225,6 +236,7 @@ __device__ __forceinline__ void local_state(const StepParams& p, const float dr[
         const float share = st.rs[s] * st.inv_rho;
 #pragma unroll
         for (int k = 0; k < 3; ++k) st.F[s][k] = g[s][k] + share * Fb[k];
+        st.tq[s] = p.coupling == 1 ? -share * p.feedback : 0.0f;
     }
     unsigned bits = 0;
     if (isnan(st.usq) || isnan(rho)) bits |= kStNan;
@@ -246,7 +258,7 @@ __device__ __forceinline__ void local_state(const StepParams& p, const float dr[
 //   S_even = w [9 (c.u)(c.F) - 3 u.F],                  S_odd = 3 w c.F.
 template <class PT, class L, int NCOMP, class FGet>
 __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
-                                               const Local<NCOMP>& st, FGet fget) {
+                                               const Local<NCOMP>& st, const float qloc[L::NQ], FGet fget) {
     const int N = (int)p.N;
     const int node = nb.i;
     const int* ox = nb.ox;
@@ -260,12 +272,15 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
     oy[2] = (nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
     const float uw6 = 6.0f * p.u_wall;  // 2 (c.U) / c_s^2 with U = +-u_wall along x
     const float keep = 1.0f - st.omega;
+    // trace of the local feedback stress over the lattice dimensions (equilibrium coupling)
+    const float trq = L::NQ == 6 ? qloc[0] + qloc[3] + qloc[5] : qloc[0] + qloc[2];
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
         const float Fx = st.F[s][0], Fy = st.F[s][1], Fz = st.F[s][2];
         const float uF = st.ux * Fx + st.uy * Fy + st.uz * Fz;
         const float rsv = st.rs[s], drs = st.dr[s];
         const float base = drs - 1.5f * rsv * st.usq;
+        const float tq45 = 4.5f * st.tq[s];  // w (c c - c_s^2 I):T / (2 c_s^4) = 4.5 w (c.T.c - tr T / 3)
         // moving populations: plane a - 1 of component s; the rest population
         // stays at the node, in FP32, and is updated in place
         PT* out = static_cast<PT*>(b.fout) + (long long)s * (L::Q - 1) * N - N;
@@ -284,7 +299,16 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
             const float wa = L::w(a);
             const float cu = cx * st.ux + cy * st.uy + cz * st.uz;
             const float cF = cx * Fx + cy * Fy + cz * Fz;
-            const float e_even = wa * (base + 4.5f * rsv * cu * cu);
+            float e_even = wa * (base + 4.5f * rsv * cu * cu);
+            if (p.coupling == 1) {
+                float cqc;
+                if (L::NQ == 6)
+                    cqc = cx * cx * qloc[0] + cy * cy * qloc[3] + cz * cz * qloc[5] +
+                          2.0f * (cx * cy * qloc[1] + cx * cz * qloc[2] + cy * cz * qloc[4]);
+                else
+                    cqc = cx * cx * qloc[0] + cy * cy * qloc[2] + 2.0f * cx * cy * qloc[1];
+                e_even += wa * tq45 * (cqc - trq * (1.0f / 3.0f));
+            }
             const float e_odd = 3.0f * wa * rsv * cu;
             const float s_even = wa * (9.0f * cu * cF - 3.0f * uF);
             const float s_odd = 3.0f * wa * cF;
@@ -353,8 +377,8 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
             if (L::cz(a)) jz += L::cz(a) * f[s][a];
         }
     const Nbr nb = make_nbr(x, y, z, p);
-    float acc[2][3], Fp[3];
-    neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp);
+    float acc[2][3], Fp[3], qloc[L::NQ];
+    neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp, qloc);
     Local<NCOMP> st;
     local_state<L, NCOMP>(p, dr, jx, jy, jz, acc, Fp, st, b.status);
     b.u[i] = st.ux;
@@ -372,7 +396,7 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
         }
         return;
     }
-    collide_stream<PT, L, NCOMP>(b, p, nb, st, [&](int s, int a) { return f[s][a]; });
+    collide_stream<PT, L, NCOMP>(b, p, nb, st, qloc, [&](int s, int a) { return f[s][a]; });
 }
 
 // --- TMA-staged variant --------------------------------------------------------
@@ -403,12 +427,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     // neighbour work overlaps the copy; the node's own deviations come from the
     // density buffer (bit-identical to the sum of the staged populations)
     float dr[NCOMP];
-    float acc[2][3], Fp[3];
+    float acc[2][3], Fp[3], qloc[L::NQ];
     Nbr nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
     if (active) {
 #pragma unroll
         for (int s = 0; s < NCOMP; ++s) dr[s] = __ldg(b.drho + s * N + i);
-        neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp);
+        neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp, qloc);
     }
 
     // bounded wait for the staged populations; on timeout report and leave
@@ -435,7 +459,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_co
     b.u[N + i] = st.uy;
     if (L::D == 3) b.u[2 * N + i] = st.uz;
     // volatile reads keep the populations in shared memory instead of registers
-    collide_stream<PT, L, NCOMP>(b, p, nb, st,
+    collide_stream<PT, L, NCOMP>(b, p, nb, st, qloc,
                                  [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
 }
 

@@ -26,6 +26,7 @@ struct vefd_ctx {
     double u_wall = 0.0, fext[3] = {0.0, 0.0, 0.0};
     double tau_p = 1.0, eta_p = 0.0, L2 = 100.0, kappa = 0.0;
     int phase = 0, fd_on = 1;
+    int coupling = 0;  // polymer feedback: 0 body force, 1 equilibrium stress
     double rho_ref[2] = {1.0, 1.0};
     // time-level state
     int have_prev = 0;
@@ -206,6 +207,7 @@ StepParams params_of(const vefd_ctx* c) {
     p.rho_ref[0] = (float)c->rho_ref[0];
     p.rho_ref[1] = (float)c->rho_ref[1];
     p.prec = c->cfg.precision;
+    p.coupling = c->coupling;
     return p;
 }
 
@@ -396,6 +398,13 @@ vefd_status vefd_set_fenep(vefd_ctx* c, double tau_p, double eta_p, double L2, d
     c->phase = phase;
     c->fd_on = fd_on ? 1 : 0;
     c->drho_valid = false;  // the feedback stress depends on these parameters
+    return VEFD_OK;
+}
+
+vefd_status vefd_set_polymer_coupling(vefd_ctx* c, int mode) {
+    if (!c) return VEFD_ERR_ARG;
+    if (mode != 0 && mode != 1) return fail(c, VEFD_ERR_ARG, "coupling must be 0 (body force) or 1 (equilibrium)");
+    c->coupling = mode;
     return VEFD_OK;
 }
 
@@ -747,7 +756,8 @@ struct CkptHeader {
     int32_t phase, fd_on, have_prev, precision;
     double rho_ref[2];
     int64_t steps;
-    uint32_t status, pad2;
+    uint32_t status;
+    int32_t coupling;
 };
 }  // namespace
 
@@ -779,6 +789,7 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     h.fd_on = c->fd_on;
     h.have_prev = c->have_prev;
     h.precision = c->cfg.precision;
+    h.coupling = c->coupling;
     h.rho_ref[0] = c->rho_ref[0];
     h.rho_ref[1] = c->rho_ref[1];
     h.steps = c->steps;
@@ -826,6 +837,7 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     c->kappa = h.kappa;
     c->phase = h.phase;
     c->fd_on = h.fd_on;
+    c->coupling = h.coupling;
     c->have_prev = h.have_prev;
     c->rho_ref[0] = h.rho_ref[0];
     c->rho_ref[1] = h.rho_ref[1];

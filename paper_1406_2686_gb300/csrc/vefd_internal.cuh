@@ -130,6 +130,7 @@ struct StepParams {
     int have_prev;         // AB2 history valid
     float rho_ref[2];      // deviation reference densities
     int prec;              // population storage: kPrecFp32, kPrecFp16, kPrecBf16
+    int coupling;          // polymer feedback: 0 body force div Q; 1 stress in the equilibrium
 };
 
 // --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------

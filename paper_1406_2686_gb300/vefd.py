@@ -41,7 +41,7 @@ EXPORTS = [
     "vefd_write_field", "vefd_step", "vefd_read_field", "vefd_field_bytes", "vefd_diagnostics",
     "vefd_get_status", "vefd_clear_status", "vefd_steps_done", "vefd_checkpoint", "vefd_restore",
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
-    "vefd_diagnostics_noalloc",
+    "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling",
 ]
 
 _lib = None
@@ -88,6 +88,7 @@ def load(build_if_missing=True):
         "vefd_profile_kernels": [vp, cint],
         "vefd_kernel_times": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
         "vefd_diagnostics_noalloc": [cint, cint, cint, cint, cint, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)],
+        "vefd_set_polymer_coupling": [vp, cint],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -145,6 +146,10 @@ def vefd_set_body_force(ctx, fx, fy, fz):
 def vefd_set_fenep(ctx, tau_p, eta_p, L2, kappa, phase, fd_on=1):
     return _check(ctx, load().vefd_set_fenep(ctx, float(tau_p), float(eta_p), float(L2), float(kappa), int(phase),
                                              int(fd_on)))
+
+
+def vefd_set_polymer_coupling(ctx, mode):
+    return _check(ctx, load().vefd_set_polymer_coupling(ctx, int(mode)))
 
 
 def vefd_init_fields(ctx, rhoA, rhoB, u, C0, on_device):
@@ -298,6 +303,9 @@ class Lattice:
 
     def set_fenep(self, tau_p, eta_p, L2, kappa=0.0, phase=0, fd_on=1):
         vefd_set_fenep(self.ctx, tau_p, eta_p, L2, kappa, phase, fd_on)
+
+    def set_polymer_coupling(self, mode):
+        vefd_set_polymer_coupling(self.ctx, mode)
 
     def init_fields(self, rhoA, rhoB=None, u=None, C=None):
         t = self.torch

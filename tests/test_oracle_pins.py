@@ -523,3 +523,56 @@ def test_laplace_law_shan_chen():
     for a, b in inner:
         assert abs(a / gold["rho_A_rich_A"] - 1.0) < 0.1
         assert abs(b / gold["rho_A_rich_B"] - 1.0) < 0.2
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
+@pytest.mark.parametrize("etas,etap,taup", [(0.1, 0.05, 30.0), (0.1, 0.1, 10.0)])
+def test_viscoelastic_shear_wave_dispersion(coupling, etas, etap, taup):
+    """A small transverse wave in an Oldroyd-B fluid (L^2 -> infinity) decays
+    at the slow root s of rho s (1 + tau_P s) + k^2 (eta_s (1 + tau_P s) + eta_P)
+    = 0, from the linearised Eqs. NS and FENE (tau_P dS/dt + S = tau_P du_x/dy,
+    feedback (eta_P/tau_P) dS/dy).  Holds for the body-force feedback and for
+    the equilibrium-stress feedback of Eq. MODEtransformation; the Newtonian
+    rate k^2 (eta_s + eta_P) differs by ~1.5 % and is excluded."""
+    ny, nx = 64, 2
+    k = 2 * math.pi / ny
+    y = np.arange(ny)
+    o = oracle.Oracle(lattice=oracle.D2Q9, nx=nx, ny=ny, walls=0, eta_A=etas, eta_B=etas, eta_p=etap, tau_p=taup,
+                      L2=1e10, coupling=coupling)
+    u0 = np.zeros((2, 1, ny, nx))
+    u0[0, 0] = 1e-4 * np.sin(k * y)[:, None]
+    o.init_fields(np.ones((1, ny, nx)), u=u0)
+    ts, amps = [], []
+    for t in range(0, 3000, 100):
+        if t:
+            o.step(100)
+        u = o.read(oracle.F_U)[0, 0, :, 0]
+        ts.append(t)
+        amps.append(np.dot(u, np.sin(k * y)) / np.dot(np.sin(k * y), np.sin(k * y)))
+    ts, amps = np.array(ts, float), np.array(amps)
+    sel = ts >= 1000
+    rate = -np.polyfit(ts[sel], np.log(np.abs(amps[sel])), 1)[0]
+    a, b, c = taup, 1 + k * k * etas * taup, k * k * (etas + etap)
+    slow = -(-b + math.sqrt(b * b - 4 * a * c)) / (2 * a)
+    newt = k * k * (etas + etap)
+    assert abs(rate / slow - 1) < 4e-3
+    assert abs(rate / newt - 1) > 8e-3
+
+
+@pytest.mark.slow
+def test_couette_fenep_equilibrium_coupling():
+    """With the polymer stress in the equilibrium (Eq. MODEtransformation)
+    the FENE-P Couette flow reaches the same steady-shear closed form."""
+    ny, U = 16, 0.02
+    gdot = 2 * U / ny
+    taup = 0.625 / gdot
+    o = oracle.Oracle(lattice=oracle.D2Q9, nx=4, ny=ny, eta_A=1 / 6, eta_B=1 / 6, u_wall=U, tau_p=taup,
+                      eta_p=1 / 9, L2=100.0, coupling=1)
+    o.init_fields(np.ones((1, ny, 4)))
+    o.step(int(25 * taup))
+    Cex, _ = cf.shear_conformation(-0.625, 100.0)
+    C = o.read(oracle.F_C)
+    for k, kk in enumerate((0, 1, 3, 5)):
+        assert np.max(np.abs(C[k] - Cex[kk])) < 1e-6 * max(1, abs(Cex[kk]))
+    u = o.read(oracle.F_U)[0]
+    assert np.max(np.abs(u - cf.couette_profile(ny, U)[None, :, None])) < 1e-9

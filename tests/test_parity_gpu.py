@@ -52,6 +52,11 @@ VARIANTS = {
                                  kappa=0.02, fext=(1e-5, -1e-5, 0.0)),
     "d3q19_2c_zm_segments": dict(lattice=1, nx=256, ny=40, nz=8, ncomp=2, walls=1, G=1.5, u_wall=0.02, eta_p=0.1,
                                  tau_p=20.0, L2=50.0, kappa=0.01, phase=-1),
+    # polymer stress in the equilibrium (Eq. MODEtransformation) instead of a body force
+    "d3q19_2c_eqcoupling": dict(lattice=1, nx=32, ny=8, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.15,
+                                tau_p=20.0, L2=50.0, kappa=0.01, phase=1, coupling=1),
+    "d2q9_1c_eqcoupling": dict(lattice=0, nx=37, ny=13, ncomp=1, walls=1, u_wall=0.03, eta_p=0.1, tau_p=30.0,
+                               L2=50.0, kappa=0.01, coupling=1),
 }
 
 
@@ -321,6 +326,7 @@ class PrecPair(Pair):
         self.g.set_wall_shear(p["u_wall"])
         self.g.set_body_force(*p["fext"])
         self.g.set_fenep(p["tau_p"], p["eta_p"], p["L2"], p["kappa"], p["phase"], p["fd_on"])
+        self.g.set_polymer_coupling(p["coupling"])
 
 
 @pytest.mark.parametrize("precision", [1, 2])
