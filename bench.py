@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--workload", default="droplet128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage variant timings")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-lattice ensemble timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tiles")
     return ap.parse_args()
 
 
@@ -292,6 +294,76 @@ def time_variant(S, steps, warmup):
     return out
 
 
+def ensemble_boxes(n=64, seed=7):
+    """n uneven droplet boxes: NX in {32, 64, 96}, NY and NZ multiples of 8 in
+    [16, 64], drawn from SplitMix64(seed)."""
+    from paper_1406_2686_gb300 import inputs
+    boxes = []
+    for i in range(n):
+        r = [int(inputs.splitmix64(seed, 3 * i + k)) for k in range(3)]
+        boxes.append((32 * (1 + r[0] % 3), 8 * (2 + r[1] % 7), 8 * (2 + r[2] % 7)))
+    return boxes
+
+
+def time_ensemble(steps, warmup, chunk=32):
+    """Many small independent lattices: stepped one after another on one stream
+    (plain vefd_step per lattice) versus as one ensemble (one CUDA graph with a
+    concurrent branch per lattice).  Same lattices, same steps; MLUPS of each."""
+    import torch
+
+    from paper_1406_2686_gb300 import vefd
+    boxes = ensemble_boxes()
+
+    def build():
+        lats = []
+        for (nx, ny, nz) in boxes:
+            L = vefd.Lattice(lattice=vefd.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=ETA_A,
+                             eta_B=ETA_B, delta=0.1)
+            L.set_wall_shear(0.01)
+            L.set_fenep(50.0, ETA_P, 100.0, 1e-3, 1, 1)
+            R = min(ny, nz) / 4.0
+            L.init_droplet((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0, R, 2.0, 0.1, 3.0, 1, 1e-3)
+            lats.append(L)
+        return lats
+
+    nodes = sum(a * b * c for a, b, c in boxes)
+    stream = torch.cuda.current_stream()
+    out = {"lattices": len(boxes), "nodes": nodes, "steps": steps, "chunk": chunk,
+           "boxes": "D3Q19 two-component droplets, NX in {32,64,96}, NY, NZ in {16,...,64} step 8 (SplitMix64 seed 7)"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lats = build()
+    for L in lats:
+        L.step(warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for L in lats:
+        L.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["one_stream"] = {"value": round(nodes * steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "ms": round(ms, 3)}
+    seq_state = [L.read(vefd.C) for L in lats[:2]]
+    for L in lats:
+        L.close()
+    lats = build()
+    E = vefd.Ensemble(lats, stream)
+    E.step(warmup, chunk)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    E.step(steps, chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["graph"] = {"value": round(nodes * steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "ms": round(ms, 3)}
+    import numpy as np
+    out["bit_identical"] = all(np.array_equal(a, L.read(vefd.C)) for a, L in zip(seq_state, lats[:2]))
+    out["status_bits"] = max(L.status() for L in lats)
+    E.close()
+    for L in lats:
+        L.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -308,6 +380,12 @@ def run_ours(args):
     lat = make_lattice(S)
     stream = lat.stream
     K, W = args.steps, args.warmup
+    tune = None
+    if not args.no_autotune:
+        # kernel tile choice timed on a scratch lattice of this configuration
+        times = lat.autotune(steps=50)
+        tune = {"chosen": list(lat.kernel_config()), "ms_per_50_steps": [round(t, 3) for t in times],
+                "index": "post_mode * 3 + lattice_tile; -1 = not admitted"}
     with torch.cuda.stream(stream):
         lat.step(W)
     torch.cuda.synchronize()
@@ -369,6 +447,7 @@ def run_ours(args):
                           "frac": round(step_achieved / peak, 4),
                           "algorithmic_bytes_per_node": S.step_bytes},
         "kernels": kernels, "gpu_launches": int(K * lat.kernels_per_step()), "clocks": clk, "e2e": e2e,
+        "autotune": tune,
         "status_bits": status, "source_sha": source_hash(),
     }
     lat.close()
@@ -378,6 +457,8 @@ def run_ours(args):
         line["variants"] = {pn: time_variant(Setup(S.name, pn), vsteps, min(W, 50)) for pn in ("fp16", "bf16")}
         line["variants"]["note"] = ("16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
                                     "and C; %d steps each" % vsteps)
+    if not args.no_ensemble and S.prec == 0:
+        line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(S)
     if rank == 0:

@@ -178,6 +178,61 @@ vefd_status vefd_profile_kernels(vefd_ctx *ctx, int on);
  * on or last read; then clears the record. */
 vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
 
+/* ---- kernel choice and autotuning (implementation detail; the paper has no
+ * counterpart) ---------------------------------------------------------------
+ * lattice_tile selects the node tile the collide-stream kernel (Sec. 2.1,
+ * Eqs. 1-3) stages through shared memory: D3Q19 0 = 32x4x2 (default),
+ * 1 = 32x2x4, 2 = 32x8x1 nodes (x by y by z); D2Q9 0 = 32x8 (default),
+ * 1 = 32x4, 2 = 32x16.  post_mode selects the densities / FENE-P pass: 0 =
+ * z-marching columns where the shape allows (D3Q19 with NX % 32 == 0 and
+ * NY % 8 == 0; default), 1 = 3-D tiles.  Every choice runs the same
+ * arithmetic in the same order, so results are bit-identical; a tile the
+ * lattice shape does not admit falls back to tile 0, and shapes that admit
+ * no staged tile use the unstaged kernels.  Returns VEFD_ERR_ARG for values
+ * outside these ranges.  Not to be called while steps are in flight. */
+vefd_status vefd_set_kernel_config(vefd_ctx *ctx, int lattice_tile, int post_mode);
+/* The configuration in effect: lattice_tile -1 and post_mode -1 mean the
+ * unstaged kernels; post_mode 1 also when z-marching is not admitted. */
+vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *post_mode);
+/* Times every admitted (lattice_tile, post_mode) pair for `steps` steps on a
+ * scratch lattice of the same configuration and parameters (droplet initial
+ * state; the context's own state is untouched), then applies the fastest.
+ * times_ms (host, 6 doubles or NULL) receives the times, index
+ * post_mode * 3 + lattice_tile, -1 for pairs not admitted.  Allocates and
+ * frees the scratch lattice's device memory and synchronises the context
+ * stream.  VEFD_ERR_UNSTABLE when the scratch run trips a guard. */
+vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
+
+/* ---- ensembles of independent lattices (implementation detail: the paper
+ * steps one lattice at a time) --------------------------------------------
+ * An ensemble steps many independent lattices of any sizes and
+ * configurations together: every member's step is one branch of a CUDA graph
+ * and `chunk` steps of all members are captured once and replayed, so small
+ * lattices overlap on the GPU and pay no per-launch host cost.  Members stay
+ * ordinary contexts (read, diagnose, checkpoint them as usual, between
+ * ensemble calls); the ensemble does not own them and must be destroyed
+ * before they are. */
+typedef struct vefd_ensemble vefd_ensemble;
+/* members: n distinct, initialised contexts on the current device.  stream:
+ * the caller's stream (NULL = legacy default stream); ensemble work is
+ * ordered after prior work on it and on every member's own stream, and work
+ * later enqueued on those streams is ordered after it. */
+vefd_status vefd_ensemble_create(vefd_ctx *const *members, int n, void *stream, vefd_ensemble **out);
+/* Advances every member by nsteps >= 0 steps (asynchronous), each member's
+ * results bit-identical to vefd_step on it alone.  chunk (even, >= 2) is the
+ * number of steps per graph replay: members still in their first step (the
+ * Euler start) or with densities pending take one eager step first,
+ * then nsteps / chunk replays run and the remainder runs eagerly.  The graph
+ * is re-captured whenever a member's parameters, kernel choice or buffer
+ * parity differ from the capture (for example after vefd_set_wall_shear or an
+ * odd eager remainder).  VEFD_ERR_ARG for a bad chunk, VEFD_ERR_STATE when a
+ * member is not initialised, VEFD_ERR_CUDA on capture or launch errors
+ * (see vefd_ensemble_last_error). */
+vefd_status vefd_ensemble_step(vefd_ensemble *ens, int64_t nsteps, int64_t chunk);
+const char *vefd_ensemble_last_error(const vefd_ensemble *ens);
+/* Waits for the ensemble's work and frees its streams, events and graph. */
+void vefd_ensemble_destroy(vefd_ensemble *ens);
+
 /* Allocation-free diagnostics (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory).  Some callers
  * cannot call cudaMalloc: their device memory is owned by another allocator

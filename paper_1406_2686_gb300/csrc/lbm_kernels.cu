@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
 // --- TMA-staged variant --------------------------------------------------------
 
 template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX * BY * BZ, 4) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
+__global__ void __launch_bounds__(BX * BY * BZ, 1024 / (BX * BY * BZ)) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
                                                               StepParams p, int rev) {
     constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = BX * BY * BZ;
@@ -522,26 +522,27 @@ int grid_1d(long long n) {
 
 dim3 node_grid(const StepParams& p) { return dim3((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz); }
 
-// Tile of the TMA variant per lattice.
-template <class L>
-struct Tile;
-template <>
-struct Tile<D3Q19> {
-    static constexpr int BX = 32, BY = 4, BZ = 2;
-};
-template <>
-struct Tile<D2Q9> {
-    static constexpr int BX = 32, BY = 8, BZ = 1;
-};
-
-template <class PT, class L, int NCOMP>
-cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
-    constexpr int BX = Tile<L>::BX, BY = Tile<L>::BY, BZ = Tile<L>::BZ;
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
+cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
     constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     k_lattice_tma<PT, L, NCOMP, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b, p, rev);
     return cudaGetLastError();
+}
+
+template <class PT, class L, int NCOMP>
+cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s,
+                       int tile) {
+    if constexpr (L::D == 3) {
+        if (tile == 1) return launch_tma_tile<PT, L, NCOMP, 32, 2, 4>(tm, p, b, rev, s);
+        if (tile == 2) return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+        return launch_tma_tile<PT, L, NCOMP, 32, 4, 2>(tm, p, b, rev, s);
+    } else {
+        if (tile == 1) return launch_tma_tile<PT, L, NCOMP, 32, 4, 1>(tm, p, b, rev, s);
+        if (tile == 2) return launch_tma_tile<PT, L, NCOMP, 32, 16, 1>(tm, p, b, rev, s);
+        return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+    }
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -550,8 +551,19 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 
 }  // namespace
 
-bool pop_tile_eligible(int lattice, int prec, int nx, int ny, int nz) {
-    const int bx = 32, by = lattice == 1 ? 4 : 8, bz = lattice == 1 ? 2 : 1;
+void lattice_tile_shape(int lattice, int tile, int* bx, int* by, int* bz) {
+    static const int t3[3][3] = {{32, 4, 2}, {32, 2, 4}, {32, 8, 1}};
+    static const int t2[3][3] = {{32, 8, 1}, {32, 4, 1}, {32, 16, 1}};
+    const int(*t)[3] = lattice == 1 ? t3 : t2;
+    const int k = tile < 0 || tile > 2 ? 0 : tile;
+    *bx = t[k][0];
+    *by = t[k][1];
+    *bz = t[k][2];
+}
+
+bool pop_tile_eligible(int lattice, int prec, int nx, int ny, int nz, int tile) {
+    int bx, by, bz;
+    lattice_tile_shape(lattice, tile, &bx, &by, &bz);
     const int align = prec == kPrecFp32 ? 4 : 8;  // rows must be 16-byte multiples
     return nx % align == 0 && nx >= bx && ny >= by && nz >= bz;
 }
@@ -604,15 +616,17 @@ cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const St
 }
 
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
-                           cudaStream_t s, const void* tensor_map, int rev) {
+                           cudaStream_t s, const void* tensor_map, int rev, int tile) {
     if (stream_pops && tensor_map) {
         const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map);
         cudaError_t e = cudaSuccess;
         VEFD_WITH_PT(p.prec, {
             if (lattice == 1)
-                e = ncomp == 2 ? launch_tma<PT, D3Q19, 2>(tm, p, b, rev, s) : launch_tma<PT, D3Q19, 1>(tm, p, b, rev, s);
+                e = ncomp == 2 ? launch_tma<PT, D3Q19, 2>(tm, p, b, rev, s, tile)
+                               : launch_tma<PT, D3Q19, 1>(tm, p, b, rev, s, tile);
             else
-                e = ncomp == 2 ? launch_tma<PT, D2Q9, 2>(tm, p, b, rev, s) : launch_tma<PT, D2Q9, 1>(tm, p, b, rev, s);
+                e = ncomp == 2 ? launch_tma<PT, D2Q9, 2>(tm, p, b, rev, s, tile)
+                               : launch_tma<PT, D2Q9, 1>(tm, p, b, rev, s, tile);
         });
         return e;
     }

@@ -1,6 +1,7 @@
 // C-ABI of libvefd (declared in include/vefd.h): context, memory, parameters,
 // field I/O, time stepping, diagnostics and checkpoints of the hybrid
 // lattice-Boltzmann / finite-difference viscoelastic step.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -51,8 +52,11 @@ struct vefd_ctx {
     double* diag_out = nullptr;
     std::string err;
     // TMA descriptors of the two population buffers (when the shape allows)
-    alignas(64) CUtensorMap tmap[2];
+    alignas(64) CUtensorMap tmap[2];       // lattice kernel: box = the selected staged tile
+    alignas(64) CUtensorMap tmap_post[2];  // densities/FD pass (3-D tile variant): box 32x4x2 or 32x8x1
     bool tma_ok = false;
+    int lat_tile = 0;                      // staged tile shape of the lattice kernel (lattice_tile_shape)
+    int post_mode = 0;                     // densities/FD pass: 0 z-marching when possible, 1 3-D tile
     // tensor maps with a 32 x 8 x 1 box for the z-marching densities/FD pass
     alignas(64) CUtensorMap tmap_zm[2];
     bool zm_ok = false;
@@ -150,6 +154,8 @@ Layout layout_of(const vefd_config* c) {
     return L;
 }
 
+void build_tensor_maps(vefd_ctx* c);
+
 void carve(vefd_ctx* c) {
     const Layout L = layout_of(&c->cfg);
     char* b = (char*)c->mem;
@@ -167,21 +173,37 @@ void carve(vefd_ctx* c) {
     c->diag_part = (double*)(b + L.dpart);
     c->diag_out = (double*)(b + L.dout);
     c->tma_ok = false;
+    build_tensor_maps(c);
+    if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
+}
+
+// (Re)builds the TMA descriptors of both population buffers for the selected
+// kernel configuration; shapes the staged kernels cannot take use the
+// register-only kernels.
+void build_tensor_maps(vefd_ctx* c) {
     const int prec = c->cfg.precision;
-    if (!getenv("VEFD_NO_TMA") && pop_tile_eligible(c->cfg.lattice, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz)) {
-        c->tma_ok = make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[0],
-                                        &c->tmap[0]) &&
-                    make_pop_tensor_map(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->f[1],
-                                        &c->tmap[1]);
-    }
+    const int lat = c->cfg.lattice, nc = c->cfg.ncomp, nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
+    c->tma_ok = false;
     c->zm_ok = false;
-    if (c->tma_ok && !getenv("VEFD_NO_ZMARCH") && post_zm_eligible(c->cfg.lattice, c->cfg.nx, c->cfg.ny)) {
+    if (getenv("VEFD_NO_TMA") || !pop_tile_eligible(lat, prec, nx, ny, nz, 0)) return;
+    // the densities/FD pass keeps the default tile
+    if (!(make_pop_tensor_map(lat, nc, prec, nx, ny, nz, c->f[0], &c->tmap_post[0]) &&
+          make_pop_tensor_map(lat, nc, prec, nx, ny, nz, c->f[1], &c->tmap_post[1])))
+        return;
+    int tile = pop_tile_eligible(lat, prec, nx, ny, nz, c->lat_tile) ? c->lat_tile : 0;
+    c->lat_tile = tile;
+    int bx, by, bz;
+    lattice_tile_shape(lat, tile, &bx, &by, &bz);
+    if (!(make_pop_tensor_map_box(lat, nc, prec, nx, ny, nz, c->f[0], bx, by, bz, &c->tmap[0]) &&
+          make_pop_tensor_map_box(lat, nc, prec, nx, ny, nz, c->f[1], bx, by, bz, &c->tmap[1])))
+        return;
+    c->tma_ok = true;
+    if (c->post_mode == 0 && !getenv("VEFD_NO_ZMARCH") && post_zm_eligible(lat, nx, ny)) {
         c->zm_ok = make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
                                            c->f[0], 32, 8, 1, &c->tmap_zm[0]) &&
                    make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
                                            c->f[1], 32, 8, 1, &c->tmap_zm[1]);
     }
-    if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
 }
 
 StepParams params_of(const vefd_ctx* c) {
@@ -250,7 +272,7 @@ vefd_status macro_pass(vefd_ctx* c, bool with_dbg) {
     StepBufs b = bufs_of(c);
     b.dbg = with_dbg ? c->dbg : nullptr;
     VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
-    VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, false, p, b, c->stream, nullptr, 0));
+    VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, false, p, b, c->stream, nullptr, 0, 0));
     c->drho_valid = true;
     return VEFD_OK;
 }
@@ -554,7 +576,7 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
             // populations n -> n+1, velocity of time n
             ProfScope ps(c, 1);
             VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, true, p, b, c->stream,
-                                        c->tma_ok ? (const void*)&c->tmap[c->cur] : nullptr, lat_rev));
+                                        c->tma_ok ? (const void*)&c->tmap[c->cur] : nullptr, lat_rev, c->lat_tile));
         }
         {
             // densities of time n+1 (they only depend on the new populations)
@@ -564,7 +586,7 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
                 VEFD_CUDA(c, launch_post_zm(c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_zm[1 - c->cur], c->stream,
                                             post_rev));
             else if (c->tma_ok)
-                VEFD_CUDA(c, launch_post_tma(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap[1 - c->cur],
+                VEFD_CUDA(c, launch_post_tma(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_post[1 - c->cur],
                                              c->stream, post_rev));
             else
                 VEFD_CUDA(c, launch_post(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, c->f[1 - c->cur],
@@ -854,5 +876,325 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     c->drho_valid = false;
     return VEFD_OK;
 }
+
+
+// ---- kernel configuration and autotuning ------------------------------------
+
+vefd_status vefd_set_kernel_config(vefd_ctx* c, int lattice_tile, int post_mode) {
+    if (!c) return VEFD_ERR_ARG;
+    if (lattice_tile < 0 || lattice_tile > 2) return fail(c, VEFD_ERR_ARG, "lattice_tile must be 0, 1 or 2");
+    if (post_mode < 0 || post_mode > 1) return fail(c, VEFD_ERR_ARG, "post_mode must be 0 or 1");
+    c->lat_tile = lattice_tile;
+    c->post_mode = post_mode;
+    if (c->mem) build_tensor_maps(c);
+    return VEFD_OK;
+}
+
+vefd_status vefd_get_kernel_config(const vefd_ctx* c, int* lattice_tile, int* post_mode) {
+    if (!c || !lattice_tile || !post_mode) return VEFD_ERR_ARG;
+    *lattice_tile = c->tma_ok ? c->lat_tile : -1;
+    *post_mode = c->zm_ok ? 0 : (c->tma_ok ? 1 : -1);
+    return VEFD_OK;
+}
+
+vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
+    if (!c || steps < 1) return fail(c, VEFD_ERR_ARG, "steps must be >= 1");
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    if (times_ms)
+        for (int k = 0; k < 6; ++k) times_ms[k] = -1.0;
+    // scratch lattice of the same shape and parameters, so the context's own
+    // state is not advanced
+    vefd_config cfg = c->cfg;
+    cfg.external_memory = 0;
+    vefd_ctx* t = nullptr;
+    vefd_status st = vefd_create(&cfg, c->stream, &t);
+    if (st != VEFD_OK) return fail(c, st, "autotune: cannot create the scratch lattice");
+    t->u_wall = c->u_wall;
+    for (int k = 0; k < 3; ++k) t->fext[k] = c->fext[k];
+    t->tau_p = c->tau_p;
+    t->eta_p = c->eta_p;
+    t->L2 = c->L2;
+    t->kappa = c->kappa;
+    t->phase = c->phase;
+    t->fd_on = c->fd_on;
+    t->coupling = c->coupling;
+    if (cfg.ncomp == 2)
+        st = vefd_init_droplet(t, 0.5 * (cfg.nx - 1), 0.5 * (cfg.ny - 1), 0.5 * (cfg.nz - 1),
+                               0.25 * std::min(cfg.nx, std::min(cfg.ny, cfg.lattice == VEFD_D3Q19 ? cfg.nz : cfg.ny)),
+                               2.0, 0.1, 5.0, 1, 1e-3);
+    else {
+        std::vector<float> one((size_t)t->N, 1.0f);
+        st = vefd_init_fields(t, one.data(), nullptr, nullptr, nullptr, 0);
+    }
+    if (st == VEFD_OK) st = vefd_step(t, 2);
+    double best = 1e300;
+    int best_tile = c->lat_tile, best_post = c->post_mode;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == VEFD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = VEFD_ERR_CUDA;
+    for (int pm = 0; pm < 2 && st == VEFD_OK; ++pm)
+        for (int tile = 0; tile < 3 && st == VEFD_OK; ++tile) {
+            if (!pop_tile_eligible(cfg.lattice, cfg.precision, cfg.nx, cfg.ny, cfg.nz, tile)) continue;
+            if (pm == 0 && !post_zm_eligible(cfg.lattice, cfg.nx, cfg.ny)) continue;
+            vefd_set_kernel_config(t, tile, pm);
+            if (!t->tma_ok) continue;
+            st = vefd_step(t, 2);  // warm the configuration
+            if (st != VEFD_OK) break;
+            cudaEventRecord(e0, t->stream);
+            st = vefd_step(t, steps);
+            cudaEventRecord(e1, t->stream);
+            if (st != VEFD_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                st = st != VEFD_OK ? st : VEFD_ERR_CUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (times_ms) times_ms[pm * 3 + tile] = ms;
+            if (ms < best) {
+                best = ms;
+                best_tile = tile;
+                best_post = pm;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    uint32_t bits = 0;
+    if (st == VEFD_OK && vefd_get_status(t, &bits) != VEFD_OK) st = VEFD_ERR_UNSTABLE;
+    if (st != VEFD_OK) {
+        const std::string why = vefd_last_error(t);
+        vefd_destroy(t);
+        return fail(c, st, "autotune failed: %s", why.c_str());
+    }
+    vefd_destroy(t);
+    return vefd_set_kernel_config(c, best_tile, best_post);
+}
+
+// ---- ensembles --------------------------------------------------------------
+
+}  // extern "C"
+
+struct vefd_ensemble {
+    std::vector<vefd_ctx*> members;
+    std::vector<cudaStream_t> branch;  // one capture/eager branch per member
+    std::vector<cudaEvent_t> join;
+    cudaStream_t user = nullptr;       // caller's stream
+    cudaStream_t main = nullptr;       // capture origin and graph launch stream
+    cudaEvent_t fork = nullptr, done = nullptr;
+    int64_t chunk = 0;                 // steps per graph launch
+    cudaGraphExec_t exec = nullptr;
+    std::vector<std::vector<double>> key;  // member state the graph was captured for
+    std::string err;
+};
+
+namespace {
+
+vefd_status ens_fail(vefd_ensemble* e, vefd_status st, const std::string& msg) {
+    if (e) e->err = msg;
+    return st;
+}
+
+// Everything a captured step bakes into its launches: parameters, kernel
+// choices and the ping-pong parities.
+std::vector<double> ens_key(const vefd_ctx* m) {
+    return {m->u_wall, m->fext[0], m->fext[1], m->fext[2], m->tau_p, m->eta_p, m->L2, m->kappa,
+            (double)m->phase, (double)m->fd_on, (double)m->coupling, m->rho_ref[0], m->rho_ref[1],
+            (double)m->lat_tile, (double)m->tma_ok, (double)m->zm_ok, (double)m->sched, (double)m->cur,
+            (double)m->ccur, (double)m->have_prev, (double)m->drho_valid};
+}
+
+// A member is steady when its next step is the plain AB2 step with current
+// densities (not the Euler start or the densities-on-demand pass).
+bool ens_steady(const vefd_ctx* m) { return m->drho_valid && (m->have_prev || !m->fd_on); }
+
+// `target` waits for the caller's stream and every member's own stream.
+cudaError_t ens_wait_inputs(vefd_ensemble* e, cudaStream_t target) {
+    cudaError_t ce = cudaEventRecord(e->fork, e->user);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(target, e->fork, 0);
+    for (size_t k = 0; k < e->members.size() && ce == cudaSuccess; ++k) {
+        cudaStream_t ms = e->members[k]->stream;
+        if (ms == e->user) continue;
+        ce = cudaEventRecord(e->join[k], ms);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(target, e->join[k], 0);
+    }
+    return ce;
+}
+
+// The caller's stream and every member's own stream wait for `ev`.
+cudaError_t ens_release(vefd_ensemble* e, cudaEvent_t ev) {
+    cudaError_t ce = cudaStreamWaitEvent(e->user, ev, 0);
+    for (size_t k = 0; k < e->members.size() && ce == cudaSuccess; ++k)
+        if (e->members[k]->stream != e->user) ce = cudaStreamWaitEvent(e->members[k]->stream, ev, 0);
+    return ce;
+}
+
+// n eager steps of every member, each on its own branch.
+vefd_status ens_eager(vefd_ensemble* e, int64_t n) {
+    if (n <= 0) return VEFD_OK;
+    if (ens_wait_inputs(e, e->main) != cudaSuccess || cudaEventRecord(e->fork, e->main) != cudaSuccess)
+        return ens_fail(e, VEFD_ERR_CUDA, "ordering after the inputs failed");
+    for (size_t k = 0; k < e->members.size(); ++k) {
+        vefd_ctx* m = e->members[k];
+        const cudaStream_t own = m->stream;
+        if (cudaStreamWaitEvent(e->branch[k], e->fork, 0) != cudaSuccess)
+            return ens_fail(e, VEFD_ERR_CUDA, "branch ordering failed");
+        m->stream = e->branch[k];
+        const vefd_status st = vefd_step(m, n);
+        m->stream = own;
+        if (st != VEFD_OK) return ens_fail(e, st, std::string("member step failed: ") + m->err);
+        if (cudaEventRecord(e->join[k], e->branch[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(e->main, e->join[k], 0) != cudaSuccess)
+            return ens_fail(e, VEFD_ERR_CUDA, "branch join failed");
+    }
+    if (cudaEventRecord(e->done, e->main) != cudaSuccess || ens_release(e, e->done) != cudaSuccess)
+        return ens_fail(e, VEFD_ERR_CUDA, "ordering before the caller failed");
+    return VEFD_OK;
+}
+
+// Captures `chunk` steps of every member, one branch each, into e->exec.
+vefd_status ens_capture(vefd_ensemble* e, int64_t chunk) {
+    const size_t n = e->members.size();
+    std::vector<int> cur(n), ccur(n), hp(n);
+    std::vector<int64_t> steps(n);
+    std::vector<cudaStream_t> own(n);
+    std::vector<bool> prof(n);
+    for (size_t k = 0; k < n; ++k) {
+        vefd_ctx* m = e->members[k];
+        cur[k] = m->cur;
+        ccur[k] = m->ccur;
+        hp[k] = m->have_prev;
+        steps[k] = m->steps;
+        own[k] = m->stream;
+        prof[k] = m->prof_on;
+    }
+    if (cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return ens_fail(e, VEFD_ERR_CUDA, "cannot begin capture");
+    vefd_status st = VEFD_OK;
+    std::string why;
+    cudaError_t ce = cudaEventRecord(e->fork, e->main);
+    for (size_t k = 0; k < n && ce == cudaSuccess && st == VEFD_OK; ++k) {
+        vefd_ctx* m = e->members[k];
+        ce = cudaStreamWaitEvent(e->branch[k], e->fork, 0);
+        if (ce != cudaSuccess) break;
+        m->stream = e->branch[k];
+        m->prof_on = false;
+        st = vefd_step(m, chunk);
+        if (st != VEFD_OK) why = m->err;
+        if (st == VEFD_OK) ce = cudaEventRecord(e->join[k], e->branch[k]);
+        if (st == VEFD_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(e->main, e->join[k], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce2 = cudaStreamEndCapture(e->main, &graph);
+    // capture only recorded the launches: restore the members' host state
+    for (size_t k = 0; k < n; ++k) {
+        vefd_ctx* m = e->members[k];
+        m->cur = cur[k];
+        m->ccur = ccur[k];
+        m->have_prev = hp[k];
+        m->steps = steps[k];
+        m->stream = own[k];
+        m->prof_on = prof[k];
+    }
+    if (st != VEFD_OK || ce != cudaSuccess || ce2 != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return ens_fail(e, st != VEFD_OK ? st : VEFD_ERR_CUDA, "graph capture failed: " + why);
+    }
+    ce = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        e->exec = nullptr;
+        return ens_fail(e, VEFD_ERR_CUDA, "graph instantiation failed");
+    }
+    e->chunk = chunk;
+    e->key.resize(n);
+    for (size_t k = 0; k < n; ++k) e->key[k] = ens_key(e->members[k]);
+    return VEFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vefd_status vefd_ensemble_create(vefd_ctx* const* members, int n, void* stream, vefd_ensemble** out) {
+    if (!members || n < 1 || !out) return VEFD_ERR_ARG;
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!members[k]) return VEFD_ERR_ARG;
+        for (int j = 0; j < k; ++j)
+            if (members[j] == members[k]) return fail(members[k], VEFD_ERR_ARG, "a lattice appears twice in the ensemble");
+        if (need_ready(members[k]) != VEFD_OK) return VEFD_ERR_STATE;
+    }
+    vefd_ensemble* e = new (std::nothrow) vefd_ensemble();
+    if (!e) return VEFD_ERR_ARG;
+    e->members.assign(members, members + n);
+    e->user = (cudaStream_t)stream;
+    e->branch.assign(n, nullptr);
+    e->join.assign(n, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&e->main, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < n && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&e->branch[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        vefd_ensemble_destroy(e);
+        return VEFD_ERR_CUDA;
+    }
+    *out = e;
+    return VEFD_OK;
+}
+
+void vefd_ensemble_destroy(vefd_ensemble* e) {
+    if (!e) return;
+    if (e->main) cudaStreamSynchronize(e->main);
+    for (cudaStream_t s : e->branch)
+        if (s) cudaStreamSynchronize(s);
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    for (cudaStream_t s : e->branch)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t v : e->join)
+        if (v) cudaEventDestroy(v);
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->done) cudaEventDestroy(e->done);
+    if (e->main) cudaStreamDestroy(e->main);
+    delete e;
+}
+
+vefd_status vefd_ensemble_step(vefd_ensemble* e, int64_t nsteps, int64_t chunk) {
+    if (!e) return VEFD_ERR_ARG;
+    if (nsteps < 0) return ens_fail(e, VEFD_ERR_ARG, "nsteps must be >= 0");
+    if (chunk < 2 || (chunk & 1)) return ens_fail(e, VEFD_ERR_ARG, "chunk must be even and >= 2");
+    for (vefd_ctx* m : e->members)
+        if (need_ready(m) != VEFD_OK) return ens_fail(e, VEFD_ERR_STATE, "a member is not initialised");
+    if (nsteps == 0) return VEFD_OK;
+    // every captured step must be the steady AB2 step with current densities
+    bool steady = true;
+    for (vefd_ctx* m : e->members) steady = steady && ens_steady(m);
+    if (!steady) {
+        const vefd_status st = ens_eager(e, 1);
+        if (st != VEFD_OK) return st;
+        nsteps -= 1;
+    }
+    const int64_t full = nsteps / chunk;
+    if (full > 0) {
+        bool stale = !e->exec || e->chunk != chunk;
+        for (size_t k = 0; k < e->members.size() && !stale; ++k) stale = ens_key(e->members[k]) != e->key[k];
+        if (stale) {
+            if (e->exec) cudaGraphExecDestroy(e->exec);
+            e->exec = nullptr;
+            const vefd_status st = ens_capture(e, chunk);
+            if (st != VEFD_OK) return st;
+        }
+        if (ens_wait_inputs(e, e->main) != cudaSuccess) return ens_fail(e, VEFD_ERR_CUDA, "ordering after the inputs failed");
+        for (int64_t r = 0; r < full; ++r)
+            if (cudaGraphLaunch(e->exec, e->main) != cudaSuccess) return ens_fail(e, VEFD_ERR_CUDA, "graph launch failed");
+        // an even chunk leaves every ping-pong parity where it was
+        for (vefd_ctx* m : e->members) m->steps += full * chunk;
+        if (cudaEventRecord(e->done, e->main) != cudaSuccess || ens_release(e, e->done) != cudaSuccess)
+            return ens_fail(e, VEFD_ERR_CUDA, "ordering before the caller failed");
+    }
+    return ens_eager(e, nsteps - full * chunk);
+}
+
+const char* vefd_ensemble_last_error(const vefd_ensemble* e) { return e ? e->err.c_str() : "NULL ensemble"; }
 
 }  // extern "C"

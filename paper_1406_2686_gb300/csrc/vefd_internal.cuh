@@ -199,9 +199,13 @@ struct StepBufs {
 // last (still in L2).
 cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev);
 // tensor_map: a CUtensorMap of b.fin for the TMA-staged kernel (streaming
-// steps only), or nullptr for the register-only kernel.
+// steps only), or nullptr for the register-only kernel; `tile` selects the
+// staged tile shape (lattice_tile_shape), and the map's box must match it.
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
-                           cudaStream_t s, const void* tensor_map, int rev);
+                           cudaStream_t s, const void* tensor_map, int rev, int tile);
+// Staged tile shapes of the lattice kernel: tile 0..2 ->
+// D3Q19 32x4x2, 32x2x4, 32x8x1; D2Q9 32x8x1, 32x4x1, 32x16x1.
+void lattice_tile_shape(int lattice, int tile, int* bx, int* by, int* bz);
 // Densities of the populations `fnew` into b.drho, when fd the FENE-P update
 // b.Cin -> b.Cout with the AB2 history b.R and velocity b.u, and the feedback
 // stress of the new time level into b.Q.
@@ -224,7 +228,7 @@ cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBu
 // map over one population buffer ([ncomp*Q][NZ][NY][NX] FP32) written to `out`
 // (a 64-byte aligned CUtensorMap).  Returns false when the driver entry point
 // is unavailable or the encoding is refused.
-bool pop_tile_eligible(int lattice, int prec, int nx, int ny, int nz);
+bool pop_tile_eligible(int lattice, int prec, int nx, int ny, int nz, int tile);
 bool make_pop_tensor_map(int lattice, int ncomp, int prec, int nx, int ny, int nz, const void* base, void* out);
 // Tensor map over one population buffer with an explicit box (bx, by, bz, all planes).
 bool make_pop_tensor_map_box(int lattice, int ncomp, int prec, int nx, int ny, int nz, const void* base, int bx,

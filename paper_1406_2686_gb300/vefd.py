@@ -41,7 +41,9 @@ EXPORTS = [
     "vefd_write_field", "vefd_step", "vefd_read_field", "vefd_field_bytes", "vefd_diagnostics",
     "vefd_get_status", "vefd_clear_status", "vefd_steps_done", "vefd_checkpoint", "vefd_restore",
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
-    "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling",
+    "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
+    "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
+    "vefd_ensemble_destroy",
 ]
 
 _lib = None
@@ -89,6 +91,11 @@ def load(build_if_missing=True):
         "vefd_kernel_times": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
         "vefd_diagnostics_noalloc": [cint, cint, cint, cint, cint, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)],
         "vefd_set_polymer_coupling": [vp, cint],
+        "vefd_set_kernel_config": [vp, cint, cint],
+        "vefd_get_kernel_config": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)],
+        "vefd_autotune": [vp, cint, ctypes.POINTER(dbl)],
+        "vefd_ensemble_create": [ctypes.POINTER(vp), cint, vp, ctypes.POINTER(vp)],
+        "vefd_ensemble_step": [vp, i64, i64],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -98,6 +105,10 @@ def load(build_if_missing=True):
     L.vefd_destroy.restype = None
     L.vefd_last_error.argtypes = [vp]
     L.vefd_last_error.restype = ctypes.c_char_p
+    L.vefd_ensemble_destroy.argtypes = [vp]
+    L.vefd_ensemble_destroy.restype = None
+    L.vefd_ensemble_last_error.argtypes = [vp]
+    L.vefd_ensemble_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 
@@ -243,6 +254,51 @@ def vefd_diagnostics_noalloc(lattice, nx, ny, nz, ncomp, L2, rho_A, rho_B, u, C,
     return np.array(out[:], dtype=np.float64)
 
 
+def vefd_set_kernel_config(ctx, lattice_tile, post_mode):
+    return _check(ctx, load().vefd_set_kernel_config(ctx, int(lattice_tile), int(post_mode)))
+
+
+def vefd_get_kernel_config(ctx):
+    """(lattice_tile, post_mode) in effect; -1 means the unstaged kernels."""
+    t, m = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().vefd_get_kernel_config(ctx, ctypes.byref(t), ctypes.byref(m)))
+    return t.value, m.value
+
+
+def vefd_autotune(ctx, steps):
+    """Times the admitted kernel choices and applies the fastest; returns the
+    six times in ms (index post_mode * 3 + lattice_tile, -1 when not admitted)."""
+    out = (ctypes.c_double * 6)()
+    _check(ctx, load().vefd_autotune(ctx, int(steps), out))
+    return list(out)
+
+
+def _ens_check(ens, st):
+    if st != OK:
+        msg = load().vefd_ensemble_last_error(ens) if ens else b""
+        raise VefdError(st, (msg or b"").decode())
+    return st
+
+
+def vefd_ensemble_create(ctxs, stream=0):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    h = ctypes.c_void_p()
+    _ens_check(None, load().vefd_ensemble_create(arr, len(ctxs), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def vefd_ensemble_step(ens, nsteps, chunk=32):
+    return _ens_check(ens, load().vefd_ensemble_step(ens, int(nsteps), int(chunk)))
+
+
+def vefd_ensemble_last_error(ens):
+    return (load().vefd_ensemble_last_error(ens) or b"").decode()
+
+
+def vefd_ensemble_destroy(ens):
+    load().vefd_ensemble_destroy(ens)
+
+
 # --- convenience wrapper -----------------------------------------------------
 
 def _np_ptr(a):
@@ -374,3 +430,37 @@ class Lattice:
 
     def kernel_times(self):
         return vefd_kernel_times(self.ctx)
+
+    def set_kernel_config(self, lattice_tile, post_mode=0):
+        vefd_set_kernel_config(self.ctx, lattice_tile, post_mode)
+
+    def kernel_config(self):
+        return vefd_get_kernel_config(self.ctx)
+
+    def autotune(self, steps=50):
+        return vefd_autotune(self.ctx, steps)
+
+
+class Ensemble:
+    """Independent lattices stepped together as one replayed CUDA graph
+    (one concurrent branch per lattice).  Holds references to its members."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        self.members = list(lattices)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.ens = vefd_ensemble_create([m.ctx for m in self.members], s.cuda_stream)
+
+    def step(self, n, chunk=32):
+        vefd_ensemble_step(self.ens, n, chunk)
+
+    def close(self):
+        if getattr(self, "ens", None):
+            vefd_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

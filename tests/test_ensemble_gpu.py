@@ -1,0 +1,152 @@
+"""Kernel choices, the autotuner and ensembles of lattices (GPU required).
+
+Every kernel choice runs the method's arithmetic (Sec. 2.1 collide-stream,
+Sec. 2.2 FENE-P update) in the same order, and an ensemble only changes how
+the launches of independent lattices are issued; so all comparisons here are
+bit for bit against plain stepping of one lattice.
+"""
+import numpy as np
+import pytest
+
+from paper_1406_2686_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BOXES = [
+    dict(lattice=1, nx=64, ny=16, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1, tau_p=20.0, L2=50.0,
+         kappa=0.01, phase=1),
+    dict(lattice=1, nx=36, ny=10, nz=7, ncomp=2, walls=1, G=1.5, u_wall=-0.02, eta_p=0.1, tau_p=20.0, L2=50.0,
+         kappa=0.01, phase=-1),
+    dict(lattice=1, nx=32, ny=8, nz=5, ncomp=1, walls=0, eta_p=0.1, tau_p=20.0, L2=50.0, kappa=0.02,
+         fext=(1e-5, -1e-5, 0.0)),
+    dict(lattice=0, nx=64, ny=13, ncomp=2, walls=0, G=1.5, eta_p=0.1, tau_p=30.0, L2=40.0, kappa=0.01, phase=-1),
+    dict(lattice=1, nx=32, ny=8, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.15, tau_p=20.0, L2=50.0,
+         kappa=0.01, phase=1, coupling=1),
+    dict(lattice=1, nx=9, ny=10, nz=11, ncomp=1, walls=0, fext=(3e-5, 1e-5, -2e-5), eta_p=0.2, tau_p=20.0,
+         L2=30.0, kappa=0.03),
+    dict(lattice=1, nx=64, ny=16, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1, tau_p=20.0, L2=50.0,
+         kappa=0.01, phase=1, precision=1),
+]
+
+
+def make(box, seed):
+    from paper_1406_2686_gb300 import vefd
+    p = dict(box)
+    lat = p.pop("lattice")
+    nz = p.pop("nz", 1) if lat == 1 else 1
+    L = vefd.Lattice(lattice=lat, nx=p["nx"], ny=p["ny"], nz=nz, ncomp=p["ncomp"], walls=p["walls"],
+                     G=p.get("G", 0.0), eta_A=0.2, eta_B=0.3, delta=0.1, precision=p.get("precision", 0))
+    L.set_wall_shear(p.get("u_wall", 0.0))
+    L.set_body_force(*p.get("fext", (0.0, 0.0, 0.0)))
+    L.set_fenep(p["tau_p"], p["eta_p"], p["L2"], p.get("kappa", 0.0), p.get("phase", 0), 1)
+    L.set_polymer_coupling(p.get("coupling", 0))
+    ndim, nc = (3, 6) if lat == 1 else (2, 4)
+    rA, rB, u, C = inputs.random_state(p["nx"], p["ny"], nz, ndim, p["ncomp"], nc, seed=seed)
+    L.init_fields(*[inputs.to_f32_exact(a) for a in (rA, rB, u, C)])
+    return L
+
+
+def state(L):
+    from paper_1406_2686_gb300 import vefd
+    return L.read(vefd.POPS), L.read(vefd.C), L.read(vefd.RPREV)
+
+
+def same(a, b):
+    return all(np.array_equal(x, y) for x, y in zip(state(a), state(b)))
+
+
+@pytest.mark.parametrize("k", [0, 3, 4])
+def test_kernel_choices_bit_identical(k):
+    """Every admitted (tile, densities-pass) choice gives the default's bits."""
+    ref = make(BOXES[k], seed=11)
+    ref.step(5)
+    seen = set()
+    for post in (0, 1):
+        for tile in (0, 1, 2):
+            L = make(BOXES[k], seed=11)
+            L.set_kernel_config(tile, post)
+            seen.add(L.kernel_config())
+            L.step(5)
+            assert same(L, ref), (tile, post, L.kernel_config())
+            assert L.status() == 0
+    # these 3-D boxes admit all three tiles; the 64 x 13 D2Q9 box is too low for 32 x 16
+    assert {t for t, _ in seen} == ({0, 1, 2} if BOXES[k]["lattice"] == 1 else {0, 1})
+
+
+def test_kernel_config_reports_and_rejects():
+    from paper_1406_2686_gb300 import vefd
+    L = make(BOXES[0], seed=1)
+    assert L.kernel_config() == (0, 0)  # 64 x 16 x 6 admits z-marching
+    L.set_kernel_config(2, 1)
+    assert L.kernel_config() == (2, 1)
+    S = make(BOXES[5], seed=1)  # 9 x 10 x 11: no staged tile fits
+    assert S.kernel_config() == (-1, -1)
+    for bad in ((3, 0), (-1, 0), (0, 2)):
+        with pytest.raises(vefd.VefdError) as ei:
+            L.set_kernel_config(*bad)
+        assert ei.value.status == vefd.ERR_ARG
+
+
+def test_autotune_leaves_state_and_picks_fastest():
+    L = make(BOXES[0], seed=4)
+    R = make(BOXES[0], seed=4)
+    L.step(3)
+    R.step(3)
+    times = L.autotune(steps=20)
+    assert len(times) == 6
+    measured = [(t, i) for i, t in enumerate(times) if t >= 0]
+    assert len(measured) >= 3
+    best = min(measured)[1]
+    assert L.kernel_config() == (best % 3, best // 3)
+    assert L.steps_done == 3
+    assert same(L, R)
+    L.step(4)
+    R.step(4)
+    assert same(L, R)
+
+
+def test_ensemble_matches_single_lattices():
+    """Seven uneven boxes (D3Q19/D2Q9, one/two components, both feedback
+    couplings, FP32/FP16 storage) stepped as one graph equal each box stepped
+    alone, across the Euler start, graph replays, an odd remainder, a
+    parameter change and a kernel-choice change."""
+    from paper_1406_2686_gb300 import vefd
+    ens_members = [make(b, seed=20 + i) for i, b in enumerate(BOXES)]
+    alone = [make(b, seed=20 + i) for i, b in enumerate(BOXES)]
+    E = vefd.Ensemble(ens_members)
+    E.step(37, chunk=8)             # 1 eager start, 4 replays, 4 eager steps
+    for L in alone:
+        L.step(37)
+    for a, b in zip(ens_members, alone):
+        assert a.steps_done == 37
+        assert same(a, b)
+    E.step(1, chunk=8)              # odd parity afterwards
+    E.step(16, chunk=8)             # re-captured for the other parity
+    ens_members[0].set_wall_shear(0.01)
+    ens_members[2].set_kernel_config(1, 1)
+    E.step(20, chunk=4)             # re-captured for the new parameters
+    for L in alone:
+        L.step(17)
+    alone[0].set_wall_shear(0.01)
+    for L in alone:
+        L.step(20)
+    for a, b in zip(ens_members, alone):
+        assert a.steps_done == 74 == b.steps_done
+        assert same(a, b)
+        assert a.status() == 0
+    E.close()
+
+
+def test_ensemble_errors():
+    from paper_1406_2686_gb300 import vefd
+    A = make(BOXES[2], seed=1)
+    with pytest.raises(vefd.VefdError):
+        vefd.Ensemble([A, A])
+    E = vefd.Ensemble([A])
+    for chunk in (0, 3, -2):
+        with pytest.raises(vefd.VefdError) as ei:
+            E.step(4, chunk=chunk)
+        assert ei.value.status == vefd.ERR_ARG
+    E.step(0)
+    assert A.steps_done == 0
+    E.close()
