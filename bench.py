@@ -382,10 +382,15 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     tune = None
     if not args.no_autotune:
-        # kernel tile choice timed on a scratch lattice of this configuration
+        # every kernel choice timed on a scratch lattice of this configuration
+        # (results are bit-identical across choices); reported, not applied:
+        # the headline runs the default choice that the committed ncu traffic
+        # figures were taken on
         times = lat.autotune(steps=50)
-        tune = {"chosen": list(lat.kernel_config()), "ms_per_50_steps": [round(t, 3) for t in times],
-                "index": "post_mode * 3 + lattice_tile; -1 = not admitted"}
+        tune = {"fastest": list(lat.kernel_config()), "ms_per_50_steps": [round(t, 3) for t in times],
+                "index": "post_mode * 6 + lattice_tile; -1 = not admitted", "applied": False}
+        lat.set_kernel_config(0, 0)
+    timed_config = list(lat.kernel_config())
     with torch.cuda.stream(stream):
         lat.step(W)
     torch.cuda.synchronize()
@@ -447,7 +452,7 @@ def run_ours(args):
                           "frac": round(step_achieved / peak, 4),
                           "algorithmic_bytes_per_node": S.step_bytes},
         "kernels": kernels, "gpu_launches": int(K * lat.kernels_per_step()), "clocks": clk, "e2e": e2e,
-        "autotune": tune,
+        "autotune": tune, "kernel_config": timed_config,
         "status_bits": status, "source_sha": source_hash(),
     }
     lat.close()

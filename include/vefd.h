@@ -183,7 +183,9 @@ vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
  * lattice_tile selects the node tile the collide-stream kernel (Sec. 2.1,
  * Eqs. 1-3) stages through shared memory: D3Q19 0 = 32x4x2 (default),
  * 1 = 32x2x4, 2 = 32x8x1 nodes (x by y by z); D2Q9 0 = 32x8 (default),
- * 1 = 32x4, 2 = 32x16.  post_mode selects the densities / FENE-P pass: 0 =
+ * 1 = 32x4, 2 = 32x16.  3, 4 and 5 are the same tiles walked by a persistent
+ * grid (one block per resident slot on every SM) that double-buffers the
+ * staged populations.  post_mode selects the densities / FENE-P pass: 0 =
  * z-marching columns where the shape allows (D3Q19 with NX % 32 == 0 and
  * NY % 8 == 0; default), 1 = 3-D tiles.  Every choice runs the same
  * arithmetic in the same order, so results are bit-identical; a tile the
@@ -197,8 +199,8 @@ vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *
 /* Times every admitted (lattice_tile, post_mode) pair for `steps` steps on a
  * scratch lattice of the same configuration and parameters (droplet initial
  * state; the context's own state is untouched), then applies the fastest.
- * times_ms (host, 6 doubles or NULL) receives the times, index
- * post_mode * 3 + lattice_tile, -1 for pairs not admitted.  Allocates and
+ * times_ms (host, 12 doubles or NULL) receives the times, index
+ * post_mode * 6 + lattice_tile, -1 for pairs not admitted.  Allocates and
  * frees the scratch lattice's device memory and synchronises the context
  * stream.  VEFD_ERR_UNSTABLE when the scratch run trips a guard. */
 vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);

@@ -20,6 +20,8 @@
 // populations are shifted by one element in x).
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "vefd_internal.cuh"
 
 namespace vefd {
@@ -116,18 +118,25 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
 #pragma unroll
     for (int s = 0; s < 2; ++s) acc[s][0] = acc[s][1] = acc[s][2] = 0.0f;
     if (NCOMP == 2) {
+        // sums per weight class (axis, face diagonal), weighted once at the end
+        float sa[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, sd[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
         for (int a = 1; a < L::Q; ++a) {
             const int j = nb.at(L::cx(a), L::cy(a), L::cz(a));
-            const float wa = L::w(a);
+            const bool axis = L::w(a) == L::w(1);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const float t = wa * __ldg(b.drho + s * N + j);
-                if (L::cx(a)) acc[s][0] += L::cx(a) * t;
-                if (L::cy(a)) acc[s][1] += L::cy(a) * t;
-                if (L::cz(a)) acc[s][2] += L::cz(a) * t;
+                const float t = __ldg(b.drho + s * N + j);
+                float* acc_s = axis ? sa[s] : sd[s];
+                if (L::cx(a)) acc_s[0] += L::cx(a) * t;
+                if (L::cy(a)) acc_s[1] += L::cy(a) * t;
+                if (L::cz(a)) acc_s[2] += L::cz(a) * t;
             }
         }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[s][k] = L::w(1) * sa[s][k] + L::w(L::Q - 1) * sd[s][k];
     }
     Fp[0] = Fp[1] = Fp[2] = 0.0f;
 #pragma unroll
@@ -249,13 +258,16 @@ __device__ __forceinline__ void local_state(const StepParams& p, const float dr[
 // fget(s, a) returns the stored deviation f_a^s of this node.
 //
 // Opposite directions a and a' (c_a' = -c_a) share c.u and c.F up to sign, so
-// each pair is relaxed together: with E_a = E_even + E_odd, E_a' = E_even -
-// E_odd and likewise for the source,
-//   f*_a  = (1 - omega) f_a  + (omega E_even + (1 - omega/2) S_even) + (omega E_odd + (1 - omega/2) S_odd)
-//   f*_a' = (1 - omega) f_a' + (omega E_even + (1 - omega/2) S_even) - (omega E_odd + (1 - omega/2) S_odd)
-// where, for the deviation equilibrium and the source of Sec. 2,
-//   E_even = w [drho + rho (4.5 (c.u)^2 - 1.5 u.u)],  E_odd = 3 w rho c.u,
-//   S_even = w [9 (c.u)(c.F) - 3 u.F],                  S_odd = 3 w c.F.
+// each pair is relaxed together.  For the deviation equilibrium and the
+// source of Sec. 2 (Eqs. LB and equilibrium),
+//   omega E_a + (1 - omega/2) S_a = w_a [K0 + (c.u)(c.R)] + w_a c.P
+// with, per component, K0 = omega (drho - 1.5 rho u.u) - 3 (1 - omega/2) u.F,
+// R = 4.5 omega rho u + 9 (1 - omega/2) F and P = 3 omega rho u +
+// 3 (1 - omega/2) F; the bracket is even in c and c.P odd, so
+//   f*_a  = (1 - omega) f_a  + w_a [K0 + (c.u)(c.R)] + w_a c.P
+//   f*_a' = (1 - omega) f_a' + w_a [K0 + (c.u)(c.R)] - w_a c.P.
+// The weight is folded into K0, R and P once per weight class, so a pair
+// costs a handful of additions and two fused multiply-adds.
 template <class PT, class L, int NCOMP, class FGet>
 __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
                                                const Local<NCOMP>& st, const float qloc[L::NQ], FGet fget) {
@@ -274,13 +286,19 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
     const float keep = 1.0f - st.omega;
     // trace of the local feedback stress over the lattice dimensions (equilibrium coupling)
     const float trq = L::NQ == 6 ? qloc[0] + qloc[3] + qloc[5] : qloc[0] + qloc[2];
+    constexpr float w_axis = L::w(1), w_diag = L::w(L::Q - 1);
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
         const float Fx = st.F[s][0], Fy = st.F[s][1], Fz = st.F[s][2];
         const float uF = st.ux * Fx + st.uy * Fy + st.uz * Fz;
         const float rsv = st.rs[s], drs = st.dr[s];
-        const float base = drs - 1.5f * rsv * st.usq;
-        const float tq45 = 4.5f * st.tq[s];  // w (c c - c_s^2 I):T / (2 c_s^4) = 4.5 w (c.T.c - tr T / 3)
+        const float K0 = st.omega * (drs - 1.5f * rsv * st.usq) - 3.0f * st.src_w * uF;
+        const float orho = st.omega * rsv;
+        const float r45 = 4.5f * orho, s9 = 9.0f * st.src_w, r3 = 3.0f * orho, s3 = 3.0f * st.src_w;
+        const float Rx = r45 * st.ux + s9 * Fx, Ry = r45 * st.uy + s9 * Fy, Rz = r45 * st.uz + s9 * Fz;
+        const float Px = r3 * st.ux + s3 * Fx, Py = r3 * st.uy + s3 * Fy, Pz = r3 * st.uz + s3 * Fz;
+        // w (c c - c_s^2 I):T / (2 c_s^4) = 4.5 w (c.T.c - tr T / 3), relaxed with omega
+        const float tqo = 4.5f * st.tq[s] * st.omega;
         // moving populations: plane a - 1 of component s; the rest population
         // stays at the node, in FP32, and is updated in place
         PT* out = static_cast<PT*>(b.fout) + (long long)s * (L::Q - 1) * N - N;
@@ -293,52 +311,56 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
         // a systematic mass drift.
         float moved = 0.0f;
 #pragma unroll
-        for (int a = 1; a < L::Q; a += 2) {
-            const int ab = a + 1;  // opposite of a
-            const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-            const float wa = L::w(a);
-            const float cu = cx * st.ux + cy * st.uy + cz * st.uz;
-            const float cF = cx * Fx + cy * Fy + cz * Fz;
-            float e_even = wa * (base + 4.5f * rsv * cu * cu);
-            if (p.coupling == 1) {
-                float cqc;
-                if (L::NQ == 6)
-                    cqc = cx * cx * qloc[0] + cy * cy * qloc[3] + cz * cz * qloc[5] +
-                          2.0f * (cx * cy * qloc[1] + cx * cz * qloc[2] + cy * cz * qloc[4]);
-                else
-                    cqc = cx * cx * qloc[0] + cy * cy * qloc[2] + 2.0f * cx * cy * qloc[1];
-                e_even += wa * tq45 * (cqc - trq * (1.0f / 3.0f));
-            }
-            const float e_odd = 3.0f * wa * rsv * cu;
-            const float s_even = wa * (9.0f * cu * cF - 3.0f * uF);
-            const float s_odd = 3.0f * wa * cF;
-            const float A = st.omega * e_even + st.src_w * s_even;
-            const float B = st.omega * e_odd + st.src_w * s_odd;
-            const float fa = keep * fget(s, a) + (A + B);
-            const float fb = keep * fget(s, ab) + (A - B);
-            // a streams to x + c, its opposite to x - c; a population leaving
-            // through a wall returns to this node in the opposite direction with
-            // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
-            // the rest population below is the remainder after the values as stored
-            if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
-                const float Uw = cy < 0 ? uw6 : -uw6;
-                const PT v = pop_put<PT>(fa - wa * rsv * (float)cx * Uw);
-                out[ab * N + node] = v;
-                moved += pop_get(v);
-            } else {
-                const PT v = pop_put<PT>(fa);
-                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = v;
-                moved += pop_get(v);
-            }
-            if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
-                const float Uw = cy > 0 ? uw6 : -uw6;
-                const PT v = pop_put<PT>(fb + wa * rsv * (float)cx * Uw);
-                out[a * N + node] = v;
-                moved += pop_get(v);
-            } else {
-                const PT v = pop_put<PT>(fb);
-                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = v;
-                moved += pop_get(v);
+        for (int wc = 0; wc < 2; ++wc) {
+            // weight class: axis directions, then face diagonals
+            const float wa = wc == 0 ? w_axis : w_diag;
+            const float k0 = wa * K0;
+            const float rx = wa * Rx, ry = wa * Ry, rz = wa * Rz;
+            const float px = wa * Px, py = wa * Py, pz = wa * Pz;
+            const float wrs = wa * rsv, tqw = wa * tqo;
+#pragma unroll
+            for (int a = 1; a < L::Q; a += 2) {
+                if ((L::w(a) == w_axis) != (wc == 0)) continue;
+                const int ab = a + 1;  // opposite of a
+                const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+                const float cu = cx * st.ux + cy * st.uy + cz * st.uz;
+                const float cr = cx * rx + cy * ry + cz * rz;
+                const float cp = cx * px + cy * py + cz * pz;
+                float even = fmaf(cu, cr, k0);
+                if (p.coupling == 1) {
+                    float cqc;
+                    if (L::NQ == 6)
+                        cqc = cx * cx * qloc[0] + cy * cy * qloc[3] + cz * cz * qloc[5] +
+                              2.0f * (cx * cy * qloc[1] + cx * cz * qloc[2] + cy * cz * qloc[4]);
+                    else
+                        cqc = cx * cx * qloc[0] + cy * cy * qloc[2] + 2.0f * cx * cy * qloc[1];
+                    even += tqw * (cqc - trq * (1.0f / 3.0f));
+                }
+                const float fa = fmaf(keep, fget(s, a), even + cp);
+                const float fb = fmaf(keep, fget(s, ab), even - cp);
+                // a streams to x + c, its opposite to x - c; a population leaving
+                // through a wall returns to this node in the opposite direction with
+                // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
+                if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
+                    const float Uw = cy < 0 ? uw6 : -uw6;
+                    const PT v = pop_put<PT>(fa - wrs * (float)cx * Uw);
+                    out[ab * N + node] = v;
+                    moved += pop_get(v);
+                } else {
+                    const PT v = pop_put<PT>(fa);
+                    out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = v;
+                    moved += pop_get(v);
+                }
+                if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
+                    const float Uw = cy > 0 ? uw6 : -uw6;
+                    const PT v = pop_put<PT>(fb + wrs * (float)cx * Uw);
+                    out[a * N + node] = v;
+                    moved += pop_get(v);
+                } else {
+                    const PT v = pop_put<PT>(fb);
+                    out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = v;
+                    moved += pop_get(v);
+                }
             }
         }
         b.frest[s * N + node] = drs - moved;
@@ -401,8 +423,62 @@ __global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int r
 
 // --- TMA-staged variant --------------------------------------------------------
 
+// Threads per SM the register budget of the staged lattice kernel is sized
+// for (1024: 64 registers per thread).
+#ifndef VEFD_LATTICE_THREADS_PER_SM
+#define VEFD_LATTICE_THREADS_PER_SM 1024
+#endif
+
+// Node work of the staged kernels, split around the wait for the staged
+// populations: gather (neighbour densities and feedback stress, overlapping
+// the copy), then moments, local state and collision from shared memory.
+template <class L, int NCOMP>
+struct NodeGather {
+    float dr[NCOMP];
+    float acc[2][3], Fp[3], qloc[L::NQ];
+    Nbr nb;
+};
+
+template <class L, int NCOMP>
+__device__ __forceinline__ void node_gather(const StepBufs& b, const StepParams& p, int x, int y, int z, bool active,
+                                            NodeGather<L, NCOMP>& g) {
+    g.nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
+    if (!active) return;
+    const long long N = p.N;
+    // the node's own deviations come from the density buffer (bit-identical to
+    // the sum of the staged populations)
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) g.dr[s] = __ldg(b.drho + s * N + g.nb.i);
+    neighbour_forces<L, NCOMP>(b, p, g.nb, g.acc, g.Fp, g.qloc);
+}
+
+template <class PT, class L, int NCOMP, int T>
+__device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams& p, const PT* sf, int t,
+                                             const NodeGather<L, NCOMP>& g) {
+    const long long N = p.N;
+    const int i = g.nb.i;
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s)
+#pragma unroll
+        for (int a = 1; a < L::Q; ++a) {
+            const float fa = pop_get(sf[(s * (L::Q - 1) + a - 1) * T + t]);
+            if (L::cx(a)) jx += L::cx(a) * fa;
+            if (L::cy(a)) jy += L::cy(a) * fa;
+            if (L::cz(a)) jz += L::cz(a) * fa;
+        }
+    Local<NCOMP> st;
+    local_state<L, NCOMP>(p, g.dr, jx, jy, jz, g.acc, g.Fp, st, b.status);
+    b.u[i] = st.ux;
+    b.u[N + i] = st.uy;
+    if (L::D == 3) b.u[2 * N + i] = st.uz;
+    // volatile reads keep the populations in shared memory instead of registers
+    collide_stream<PT, L, NCOMP>(b, p, g.nb, st, g.qloc,
+                                 [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
+}
+
 template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX * BY * BZ, 1024 / (BX * BY * BZ)) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
+__global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (BX * BY * BZ)) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
                                                               StepParams p, int rev) {
     constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = BX * BY * BZ;
@@ -421,46 +497,96 @@ __global__ void __launch_bounds__(BX * BY * BZ, 1024 / (BX * BY * BZ)) k_lattice
     if (leader) tma_load_4d(smem_u32(sf), &tm_fin, x0, y0, z0, 0, bar_a, kBytes);
     const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
     const bool active = x < p.nx && y < p.ny && z < p.nz;
-    const long long N = p.N;
-    const long long i = active ? ((long long)z * p.ny + y) * p.nx + x : 0;
-
-    // neighbour work overlaps the copy; the node's own deviations come from the
-    // density buffer (bit-identical to the sum of the staged populations)
-    float dr[NCOMP];
-    float acc[2][3], Fp[3], qloc[L::NQ];
-    Nbr nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
-    if (active) {
-#pragma unroll
-        for (int s = 0; s < NCOMP; ++s) dr[s] = __ldg(b.drho + s * N + i);
-        neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp, qloc);
-    }
-
+    NodeGather<L, NCOMP> g;
+    node_gather<L, NCOMP>(b, p, x, y, z, active, g);
     // bounded wait for the staged populations; on timeout report and leave
     if (!mbar_wait_bounded(bar_a)) {
         if (leader) atomicOr(b.status, kStTimeout);
         return;
     }
     if (!active) return;
+    node_collide<PT, L, NCOMP, T>(b, p, sf, (tz * BY + ty) * BX + tx, g);
+}
 
+// Persistent form: a grid of (SMs x resident blocks) walks the tiles in order
+// (tile = block + k * grid, backwards when rev is set) with two staging
+// buffers, so the copy of a block's next tile is in flight while it computes
+// the current one and the copy engine never idles between tiles.
+// Resident blocks per SM the persistent kernel's registers are budgeted for:
+// as many as the two staging buffers leave room for in 227 KB of shared
+// memory (1 KB reserved per block), at most the 64-register budget.
+template <class PT, class L, int NCOMP, int T>
+constexpr int pers_blocks() {
+    constexpr int smem = 2 * NCOMP * (L::Q - 1) * T * (int)sizeof(PT) + 1024 + 128;
+    constexpr int by_smem = (227 * 1024) / smem;
+    constexpr int by_regs = VEFD_LATTICE_THREADS_PER_SM / T;
+    return by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
+}
+
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(BX * BY * BZ, (pers_blocks<PT, L, NCOMP, BX * BY * BZ>())) k_lattice_pers(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
+                                                               StepParams p, int rev, int ntx, int nty, int ntiles) {
+    constexpr int P = NCOMP * (L::Q - 1);
+    constexpr int T = BX * BY * BZ;
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
+    extern __shared__ __align__(128) unsigned char sraw[];
+    PT* sbuf = reinterpret_cast<PT*>(sraw);  // two buffers of [P][BZ][BY][BX]
+    __shared__ __align__(8) unsigned long long bars[2];
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const bool leader = (tx | ty | tz) == 0;
+    const unsigned bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    auto origin = [&](int tile, int& x0, int& y0, int& z0) {
+        const int q = rev ? ntiles - 1 - tile : tile;
+        x0 = (q % ntx) * BX;
+        const int r = q / ntx;
+        y0 = (r % nty) * BY;
+        z0 = (r / nty) * BZ;
+    };
+    auto issue = [&](int tile, int slot) {
+        int x0, y0, z0;
+        origin(tile, x0, y0, z0);
+        tma_load_4d(smem_u32(sbuf + slot * P * T), &tm_fin, x0, y0, z0, 0, slot ? bar1 : bar0, kBytes);
+    };
+    if (leader) {
+        mbar_init(bar0);
+        mbar_init(bar1);
+    }
+    __syncthreads();
+    const int stride = gridDim.x;
+    if (leader) {
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + stride < ntiles) issue(blockIdx.x + stride, 1);
+    }
     const int t = (tz * BY + ty) * BX + tx;
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s)
-#pragma unroll
-        for (int a = 1; a < L::Q; ++a) {
-            const float fa = pop_get(sf[(s * (L::Q - 1) + a - 1) * T + t]);
-            if (L::cx(a)) jx += L::cx(a) * fa;
-            if (L::cy(a)) jy += L::cy(a) * fa;
-            if (L::cz(a)) jz += L::cz(a) * fa;
+    for (int k = 0;; ++k) {
+        const int tile = (int)blockIdx.x + k * stride;
+        if (tile >= ntiles) break;
+        const int slot = k & 1;
+        int x0, y0, z0;
+        origin(tile, x0, y0, z0);
+        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+        const bool active = x < p.nx && y < p.ny && z < p.nz;
+        NodeGather<L, NCOMP> g;
+        node_gather<L, NCOMP>(b, p, x, y, z, active, g);
+        const bool ok = mbar_wait_bounded_parity(slot ? bar1 : bar0, (unsigned)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (leader) {
+                atomicOr(b.status, kStTimeout);
+                // let the copies this block still has in flight land (bounded) before leaving
+                mbar_wait_bounded_parity(slot ? bar1 : bar0, (unsigned)((k >> 1) & 1));
+                if (tile + stride < ntiles)
+                    mbar_wait_bounded_parity(slot ? bar0 : bar1, (unsigned)(((k + 1) >> 1) & 1));
+            }
+            return;
         }
-    Local<NCOMP> st;
-    local_state<L, NCOMP>(p, dr, jx, jy, jz, acc, Fp, st, b.status);
-    b.u[i] = st.ux;
-    b.u[N + i] = st.uy;
-    if (L::D == 3) b.u[2 * N + i] = st.uz;
-    // volatile reads keep the populations in shared memory instead of registers
-    collide_stream<PT, L, NCOMP>(b, p, nb, st, qloc,
-                                 [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
+        if (active) node_collide<PT, L, NCOMP, T>(b, p, sbuf + slot * P * T, t, g);
+        // every thread is done with this buffer: refill it with the tile after next
+        __syncthreads();
+        if (leader && tile + 2 * stride < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tile + 2 * stride, slot);
+        }
+    }
 }
 
 template <class PT, class L, int NCOMP>
@@ -531,17 +657,57 @@ cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const St
     return cudaGetLastError();
 }
 
+int g_lat_sms = 0;
+
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
+cudaError_t launch_pers_tile(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
+    constexpr int T = BX * BY * BZ;
+    constexpr int smem = 2 * NCOMP * (L::Q - 1) * T * (int)sizeof(PT);
+    static int per_sm = 0;  // resident blocks per SM of this instantiation
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(k_lattice_pers<PT, L, NCOMP, BX, BY, BZ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lattice_pers<PT, L, NCOMP, BX, BY, BZ>, T, smem);
+        if (e != cudaSuccess) return e;
+        if (nb < 1) return cudaErrorInvalidConfiguration;
+        per_sm = nb;
+    }
+    if (!g_lat_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_lat_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_lat_sms = 152;
+    }
+    const int ntx = (p.nx + BX - 1) / BX, nty = (p.ny + BY - 1) / BY, ntz = (p.nz + BZ - 1) / BZ;
+    const long long ntiles = (long long)ntx * nty * ntz;
+    const long long grid = std::min<long long>(ntiles, (long long)per_sm * g_lat_sms);
+    k_lattice_pers<PT, L, NCOMP, BX, BY, BZ><<<(unsigned)grid, dim3(BX, BY, BZ), smem, s>>>(*tm, b, p, rev, ntx, nty,
+                                                                                         (int)ntiles);
+    return cudaGetLastError();
+}
+
 template <class PT, class L, int NCOMP>
 cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s,
                        int tile) {
     if constexpr (L::D == 3) {
-        if (tile == 1) return launch_tma_tile<PT, L, NCOMP, 32, 2, 4>(tm, p, b, rev, s);
-        if (tile == 2) return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
-        return launch_tma_tile<PT, L, NCOMP, 32, 4, 2>(tm, p, b, rev, s);
+        switch (tile) {
+        case 1: return launch_tma_tile<PT, L, NCOMP, 32, 2, 4>(tm, p, b, rev, s);
+        case 2: return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+        case 3: return launch_pers_tile<PT, L, NCOMP, 32, 4, 2>(tm, p, b, rev, s);
+        case 4: return launch_pers_tile<PT, L, NCOMP, 32, 2, 4>(tm, p, b, rev, s);
+        case 5: return launch_pers_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+        default: return launch_tma_tile<PT, L, NCOMP, 32, 4, 2>(tm, p, b, rev, s);
+        }
     } else {
-        if (tile == 1) return launch_tma_tile<PT, L, NCOMP, 32, 4, 1>(tm, p, b, rev, s);
-        if (tile == 2) return launch_tma_tile<PT, L, NCOMP, 32, 16, 1>(tm, p, b, rev, s);
-        return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+        switch (tile) {
+        case 1: return launch_tma_tile<PT, L, NCOMP, 32, 4, 1>(tm, p, b, rev, s);
+        case 2: return launch_tma_tile<PT, L, NCOMP, 32, 16, 1>(tm, p, b, rev, s);
+        case 3: return launch_pers_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+        case 4: return launch_pers_tile<PT, L, NCOMP, 32, 4, 1>(tm, p, b, rev, s);
+        case 5: return launch_pers_tile<PT, L, NCOMP, 32, 16, 1>(tm, p, b, rev, s);
+        default: return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
+        }
     }
 }
 
@@ -555,7 +721,8 @@ void lattice_tile_shape(int lattice, int tile, int* bx, int* by, int* bz) {
     static const int t3[3][3] = {{32, 4, 2}, {32, 2, 4}, {32, 8, 1}};
     static const int t2[3][3] = {{32, 8, 1}, {32, 4, 1}, {32, 16, 1}};
     const int(*t)[3] = lattice == 1 ? t3 : t2;
-    const int k = tile < 0 || tile > 2 ? 0 : tile;
+    // tiles 3..5 are the persistent forms of tiles 0..2
+    const int k = tile < 0 || tile > 5 ? 0 : tile % 3;
     *bx = t[k][0];
     *by = t[k][1];
     *bz = t[k][2];

@@ -882,7 +882,7 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
 
 vefd_status vefd_set_kernel_config(vefd_ctx* c, int lattice_tile, int post_mode) {
     if (!c) return VEFD_ERR_ARG;
-    if (lattice_tile < 0 || lattice_tile > 2) return fail(c, VEFD_ERR_ARG, "lattice_tile must be 0, 1 or 2");
+    if (lattice_tile < 0 || lattice_tile > 5) return fail(c, VEFD_ERR_ARG, "lattice_tile must be in 0..5");
     if (post_mode < 0 || post_mode > 1) return fail(c, VEFD_ERR_ARG, "post_mode must be 0 or 1");
     c->lat_tile = lattice_tile;
     c->post_mode = post_mode;
@@ -901,7 +901,7 @@ vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
     if (!c || steps < 1) return fail(c, VEFD_ERR_ARG, "steps must be >= 1");
     if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
     if (times_ms)
-        for (int k = 0; k < 6; ++k) times_ms[k] = -1.0;
+        for (int k = 0; k < 12; ++k) times_ms[k] = -1.0;
     // scratch lattice of the same shape and parameters, so the context's own
     // state is not advanced
     vefd_config cfg = c->cfg;
@@ -932,7 +932,7 @@ vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == VEFD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = VEFD_ERR_CUDA;
     for (int pm = 0; pm < 2 && st == VEFD_OK; ++pm)
-        for (int tile = 0; tile < 3 && st == VEFD_OK; ++tile) {
+        for (int tile = 0; tile < 6 && st == VEFD_OK; ++tile) {
             if (!pop_tile_eligible(cfg.lattice, cfg.precision, cfg.nx, cfg.ny, cfg.nz, tile)) continue;
             if (pm == 0 && !post_zm_eligible(cfg.lattice, cfg.nx, cfg.ny)) continue;
             vefd_set_kernel_config(t, tile, pm);
@@ -948,7 +948,7 @@ vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
             }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (times_ms) times_ms[pm * 3 + tile] = ms;
+            if (times_ms) times_ms[pm * 6 + tile] = ms;
             if (ms < best) {
                 best = ms;
                 best_tile = tile;

@@ -267,8 +267,8 @@ def vefd_get_kernel_config(ctx):
 
 def vefd_autotune(ctx, steps):
     """Times the admitted kernel choices and applies the fastest; returns the
-    six times in ms (index post_mode * 3 + lattice_tile, -1 when not admitted)."""
-    out = (ctypes.c_double * 6)()
+    twelve times in ms (index post_mode * 6 + lattice_tile, -1 when not admitted)."""
+    out = (ctypes.c_double * 12)()
     _check(ctx, load().vefd_autotune(ctx, int(steps), out))
     return list(out)
 

@@ -62,15 +62,16 @@ def test_kernel_choices_bit_identical(k):
     ref.step(5)
     seen = set()
     for post in (0, 1):
-        for tile in (0, 1, 2):
+        for tile in range(6):
             L = make(BOXES[k], seed=11)
             L.set_kernel_config(tile, post)
             seen.add(L.kernel_config())
             L.step(5)
             assert same(L, ref), (tile, post, L.kernel_config())
             assert L.status() == 0
-    # these 3-D boxes admit all three tiles; the 64 x 13 D2Q9 box is too low for 32 x 16
-    assert {t for t, _ in seen} == ({0, 1, 2} if BOXES[k]["lattice"] == 1 else {0, 1})
+    # these 3-D boxes admit all three tiles (and their persistent forms); the
+    # 64 x 13 D2Q9 box is too low for 32 x 16
+    assert {t for t, _ in seen} == ({0, 1, 2, 3, 4, 5} if BOXES[k]["lattice"] == 1 else {0, 1, 3, 4})
 
 
 def test_kernel_config_reports_and_rejects():
@@ -81,7 +82,7 @@ def test_kernel_config_reports_and_rejects():
     assert L.kernel_config() == (2, 1)
     S = make(BOXES[5], seed=1)  # 9 x 10 x 11: no staged tile fits
     assert S.kernel_config() == (-1, -1)
-    for bad in ((3, 0), (-1, 0), (0, 2)):
+    for bad in ((6, 0), (-1, 0), (0, 2)):
         with pytest.raises(vefd.VefdError) as ei:
             L.set_kernel_config(*bad)
         assert ei.value.status == vefd.ERR_ARG
@@ -93,11 +94,11 @@ def test_autotune_leaves_state_and_picks_fastest():
     L.step(3)
     R.step(3)
     times = L.autotune(steps=20)
-    assert len(times) == 6
+    assert len(times) == 12
     measured = [(t, i) for i, t in enumerate(times) if t >= 0]
-    assert len(measured) >= 3
+    assert len(measured) >= 6
     best = min(measured)[1]
-    assert L.kernel_config() == (best % 3, best // 3)
+    assert L.kernel_config() == (best % 6, best // 6)
     assert L.steps_done == 3
     assert same(L, R)
     L.step(4)
@@ -123,7 +124,7 @@ def test_ensemble_matches_single_lattices():
     E.step(1, chunk=8)              # odd parity afterwards
     E.step(16, chunk=8)             # re-captured for the other parity
     ens_members[0].set_wall_shear(0.01)
-    ens_members[2].set_kernel_config(1, 1)
+    ens_members[2].set_kernel_config(4, 1)
     E.step(20, chunk=4)             # re-captured for the new parameters
     for L in alone:
         L.step(17)
