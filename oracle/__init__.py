@@ -30,6 +30,7 @@ class OrcParams(ctypes.Structure):
         ("delta", ctypes.c_double), ("u_wall", ctypes.c_double), ("fext", ctypes.c_double * 3),
         ("tau_p", ctypes.c_double), ("eta_p", ctypes.c_double), ("L2", ctypes.c_double),
         ("kappa", ctypes.c_double), ("phase", ctypes.c_int), ("fd_on", ctypes.c_int), ("coupling", ctypes.c_int),
+        ("collision", ctypes.c_int), ("tau_M", ctypes.c_double), ("tau_g", ctypes.c_double), ("chol", ctypes.c_int),
     ]
 
 
@@ -62,6 +63,11 @@ def lib():
         L.orc_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
         L.orc_source.argtypes = [ctypes.c_int, dp, dp, dp]
         L.orc_fenep_point.argtypes = [dp, dp, ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_long]
+        L.orc_fenep_point_form.argtypes = [dp, dp, ip, dp, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                           ctypes.c_int]
+        L.orc_chol_rates.argtypes = [dp, dp, ctypes.c_double, dp, dp]
+        L.orc_chol_to_C.argtypes = [dp, ctypes.c_double, dp]
+        L.orc_mrt_basis.argtypes = [ctypes.c_int, dp, ip]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
@@ -77,7 +83,8 @@ def _f64(a):
 
 DEFAULTS = dict(lattice=D2Q9, nx=8, ny=8, nz=1, ncomp=1, walls=1, G=0.0, eta_A=1.0 / 6.0,
                 eta_B=1.0 / 6.0, delta=0.1, u_wall=0.0, fext=(0.0, 0.0, 0.0), tau_p=1000.0,
-                eta_p=0.0, L2=100.0, kappa=0.0, phase=0, fd_on=1, coupling=0)
+                eta_p=0.0, L2=100.0, kappa=0.0, phase=0, fd_on=1, coupling=0, collision=0, tau_M=1.0,
+                tau_g=1.0, chol=0)
 
 
 def make_params(**kw):
@@ -213,12 +220,39 @@ def source(lat, u, F):
     return out
 
 
-def fenep_point(C, gradu, tau_p, L2, nsteps, Rprev=None, have_prev=False):
+def fenep_point(C, gradu, tau_p, L2, nsteps, Rprev=None, have_prev=False, chol=0):
     """Advance a uniform conformation tensor C (6 comps xx xy xz yy yz zz)
-    under a prescribed velocity gradient gradu[i][j] = d_i u_j."""
+    under a prescribed velocity gradient gradu[i][j] = d_i u_j (chol 1: the
+    Cholesky scheme on sigma_P; the history then holds log-Cholesky rates)."""
     CC = _f64(C).copy()
     R = _f64(Rprev).copy() if Rprev is not None else np.zeros(6)
     hp = ctypes.c_int(1 if have_prev else 0)
     g = _f64(gradu).reshape(-1)
-    lib().orc_fenep_point(_dptr(CC), _dptr(R), ctypes.byref(hp), _dptr(g), float(tau_p), float(L2), int(nsteps))
+    lib().orc_fenep_point_form(_dptr(CC), _dptr(R), ctypes.byref(hp), _dptr(g), float(tau_p), float(L2),
+                               int(nsteps), int(chol))
     return CC, R, bool(hp.value)
+
+
+def chol_rates(C, Cdot, L2):
+    """(lam, lam_dot): log-Cholesky variables of sigma_P = f(r_P) C and their
+    rates for a given dC/dt (6 comps xx xy xz yy yz zz each)."""
+    CC, Cd = _f64(C).copy(), _f64(Cdot).copy()
+    lam, rl = np.zeros(6), np.zeros(6)
+    lib().orc_chol_rates(_dptr(CC), _dptr(Cd), float(L2), _dptr(lam), _dptr(rl))
+    return lam, rl
+
+
+def chol_to_C(lam, L2):
+    out = np.zeros(6)
+    lib().orc_chol_to_C(_dptr(_f64(lam).copy()), float(L2), _dptr(out))
+    return out
+
+
+def mrt_basis(lat):
+    """(M, kind): the MRT moment basis, M[k, a] for row k and direction a, and
+    each row's relaxation kind (0 density, 1 bulk, 2 momentum, 3 shear, 4 other)."""
+    Q = 19 if lat == D3Q19 else 9
+    M = np.zeros(Q * Q)
+    kind = np.zeros(Q, dtype=np.int32)
+    lib().orc_mrt_basis(lat, _dptr(M), kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return M.reshape(Q, Q), kind

@@ -31,6 +31,25 @@
  * which leaves mass and momentum unchanged and adds exactly T_sigma to the
  * second moment.
  *
+ * Collision, two readings of Sec. 2: (a) a single relaxation time, the local
+ * tau of the viscosity field (collision 0); (b) the paper's relaxation in
+ * moment space (collision 1): every component's populations are mapped to
+ * the orthogonal moments of Premnath & Abraham's transformation (the
+ * polynomial rows of d'Humieres et al. for D3Q19, of Lallemand & Luo for
+ * D2Q9), each moment relaxes towards the moment of E with its own time -
+ * the shear and bulk modes with the local tau (tau_b = tau_s), the species
+ * momentum with tau_M, all other modes with tau_g (the paper uses
+ * tau_M = tau_g = 1) - and the source enters as (I - Lambda/2) S in the same
+ * moment space.
+ *
+ * Conformation update, two readings of Sec. 2: (a) AB2 on C (chol 0); (b) the
+ * Cholesky scheme (chol 1): sigma_P = f(r_P) C = L L^T with L lower
+ * triangular; the same right-hand side dC/dt gives d sigma_P/dt = f dC/dt +
+ * sigma_P f tr(dC/dt)/(L^2 - 3), then dL/dt = L Phi(L^-1 (d sigma_P/dt) L^-T)
+ * with Phi the lower triangle with the diagonal halved; AB2 advances ln l_ii
+ * and l_ij (i > j), and C = sigma_P / f with f = (L^2 - 3 + tr sigma_P)/L^2,
+ * so C stays SPD with tr C < L^2 by construction.
+ *
  * Boundary readings (the paper states the rules only in words):
  *   - densities seen by the Shan-Chen sum across a wall take the value of the
  *     adjacent fluid row (zero normal gradient, neutral wetting, Sec. 2);
@@ -93,6 +112,10 @@ struct orc_state {
     double *Fp;            /* [3][N] polymer body force */
     double *u;             /* [3][N] equilibrium velocity */
     double *tau;           /* [N] local relaxation time */
+    /* moment basis of the MRT collision */
+    double Mb[19][19];
+    double Mnorm[19];
+    int Mkind[19];
 };
 
 static int opposite(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
@@ -173,6 +196,148 @@ static double source(double w, const int c[3], const double u[3], const double F
     double s = 0.0;
     for (int k = 0; k < 3; ++k) s += ((c[k] - u[k]) / CS2 + cu * c[k] / (CS2 * CS2)) * F[k];
     return w * s;
+}
+
+/* ---- moment basis of the MRT collision (Sec. 2) -----------------------------
+ * Rows are orthogonal polynomials in c evaluated on the lattice velocities:
+ *   D3Q19: 1, 19c^2 - 30, (21c^4 - 53c^2 + 24)/2, c_x, (5c^2 - 9)c_x, c_y,
+ *          (5c^2 - 9)c_y, c_z, (5c^2 - 9)c_z, 3c_x^2 - c^2,
+ *          (3c^2 - 5)(3c_x^2 - c^2), c_y^2 - c_z^2, (3c^2 - 5)(c_y^2 - c_z^2),
+ *          c_x c_y, c_y c_z, c_x c_z, (c_y^2 - c_z^2)c_x, (c_z^2 - c_x^2)c_y,
+ *          (c_x^2 - c_y^2)c_z
+ *   D2Q9:  1, 3c^2 - 4, (9c^4 - 21c^2 + 8)/2, c_x, (3c^2 - 5)c_x, c_y,
+ *          (3c^2 - 5)c_y, c_x^2 - c_y^2, c_x c_y
+ * and each row has a relaxation kind. */
+enum { MK_RHO = 0, MK_BULK = 1, MK_MOM = 2, MK_SHEAR = 3, MK_GHOST = 4 };
+
+static double mrt_row(int lattice, int k, const int c[3], int *kind) {
+    const double x = c[0], y = c[1], z = c[2];
+    const double c2 = x * x + y * y + z * z;
+    if (lattice == ORC_D3Q19) {
+        switch (k) {
+        case 0: *kind = MK_RHO; return 1.0;
+        case 1: *kind = MK_BULK; return 19.0 * c2 - 30.0;
+        case 2: *kind = MK_GHOST; return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+        case 3: *kind = MK_MOM; return x;
+        case 4: *kind = MK_GHOST; return (5.0 * c2 - 9.0) * x;
+        case 5: *kind = MK_MOM; return y;
+        case 6: *kind = MK_GHOST; return (5.0 * c2 - 9.0) * y;
+        case 7: *kind = MK_MOM; return z;
+        case 8: *kind = MK_GHOST; return (5.0 * c2 - 9.0) * z;
+        case 9: *kind = MK_SHEAR; return 3.0 * x * x - c2;
+        case 10: *kind = MK_GHOST; return (3.0 * c2 - 5.0) * (3.0 * x * x - c2);
+        case 11: *kind = MK_SHEAR; return y * y - z * z;
+        case 12: *kind = MK_GHOST; return (3.0 * c2 - 5.0) * (y * y - z * z);
+        case 13: *kind = MK_SHEAR; return x * y;
+        case 14: *kind = MK_SHEAR; return y * z;
+        case 15: *kind = MK_SHEAR; return x * z;
+        case 16: *kind = MK_GHOST; return (y * y - z * z) * x;
+        case 17: *kind = MK_GHOST; return (z * z - x * x) * y;
+        default: *kind = MK_GHOST; return (x * x - y * y) * z;
+        }
+    }
+    switch (k) {
+    case 0: *kind = MK_RHO; return 1.0;
+    case 1: *kind = MK_BULK; return 3.0 * c2 - 4.0;
+    case 2: *kind = MK_GHOST; return (9.0 * c2 * c2 - 21.0 * c2 + 8.0) / 2.0;
+    case 3: *kind = MK_MOM; return x;
+    case 4: *kind = MK_GHOST; return (3.0 * c2 - 5.0) * x;
+    case 5: *kind = MK_MOM; return y;
+    case 6: *kind = MK_GHOST; return (3.0 * c2 - 5.0) * y;
+    case 7: *kind = MK_SHEAR; return x * x - y * y;
+    default: *kind = MK_SHEAR; return x * y;
+    }
+}
+
+static int mrt_basis_fill(int lattice, double M[19][19], double norm[19], int kind[19]) {
+    const int Q = lattice == ORC_D3Q19 ? 19 : 9;
+    const int (*c)[3] = lattice == ORC_D3Q19 ? C19 : C9;
+    for (int k = 0; k < Q; ++k) {
+        norm[k] = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            M[k][a] = mrt_row(lattice, k, c[a], &kind[k]);
+            norm[k] += M[k][a] * M[k][a];
+        }
+    }
+    return Q;
+}
+
+/* ---- Cholesky scheme for sigma_P = f(r_P) C (Sec. 2) ----------------------- */
+
+/* log-Cholesky variables of sigma_P and their rates for a given dC/dt */
+static void chol_rates_node(const double C6[6], const double Cd6[6], double L2, double lam[6], double rl[6]) {
+    const double fr = fene_f(L2, C6[0] + C6[3] + C6[5]);
+    const double trCd = Cd6[0] + Cd6[3] + Cd6[5];
+    double S[3][3], Sd[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            S[a][b] = fr * C6[SYM[a][b]];
+            Sd[a][b] = fr * Cd6[SYM[a][b]] + S[a][b] * fr * trCd / (L2 - 3.0);
+        }
+    /* S = L L^T */
+    double L[3][3] = {{0}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = S[i][j];
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = (i == j) ? sqrt(v) : v / L[j][j];
+        }
+    /* inverse of the lower-triangular factor */
+    double Li[3][3] = {{0}};
+    for (int j = 0; j < 3; ++j) {
+        Li[j][j] = 1.0 / L[j][j];
+        for (int i = j + 1; i < 3; ++i) {
+            double v = 0.0;
+            for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
+            Li[i][j] = v / L[i][i];
+        }
+    }
+    /* A = L^-1 Sd L^-T; Phi(A) = lower triangle of A with the diagonal halved */
+    double T[3][3], A[3][3], P[3][3] = {{0}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += Li[i][k] * Sd[k][j];
+            T[i][j] = v;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += T[i][k] * Li[j][k];
+            A[i][j] = v;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) P[i][j] = (i == j) ? 0.5 * A[i][i] : A[i][j];
+    /* dL/dt = L Phi(A) */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = 0.0;
+            for (int k = j; k <= i; ++k) v += L[i][k] * P[k][j];
+            if (i == j) {
+                lam[SYM[i][i]] = log(L[i][i]);
+                rl[SYM[i][i]] = v / L[i][i];
+            } else {
+                lam[SYM[i][j]] = L[i][j];
+                rl[SYM[i][j]] = v;
+            }
+        }
+}
+
+/* C from the log-Cholesky variables of sigma_P */
+static void chol_to_C_node(const double lam[6], double L2, double C6[6]) {
+    double L[3][3] = {{0}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) L[i][j] = (i == j) ? exp(lam[SYM[i][i]]) : lam[SYM[i][j]];
+    double S[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += L[a][k] * L[b][k];
+            S[a][b] = v;
+        }
+    const double fr = (L2 - 3.0 + S[0][0] + S[1][1] + S[2][2]) / L2;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) C6[SYM[a][b]] = S[a][b] / fr;
 }
 
 /* ---- derived fields ------------------------------------------------------- */
@@ -329,8 +494,9 @@ static void collide_stream(orc_state *s) {
                                 T[aa][bb] = -share * s->p.eta_p / s->p.tau_p * s->Qs[(long)SYM[aa][bb] * N + i];
                     }
                     const int nd = ndim(s);
+                    double fl[19], El[19], Sl[19], fp[19];
                     for (int a = 0; a < Q; ++a) {
-                        double fa = s->f[((long)sg * Q + a) * N + i];
+                        fl[a] = s->f[((long)sg * Q + a) * N + i];
                         double E = equilibrium(s->w[a], s->c[a], rs, u);
                         if (s->p.coupling == 1) {
                             double cTc = 0.0, trT = 0.0;
@@ -340,9 +506,40 @@ static void collide_stream(orc_state *s) {
                             }
                             E += s->w[a] * (cTc - CS2 * trT) / (2.0 * CS2 * CS2);
                         }
-                        double S = source(s->w[a], s->c[a], u, F);
+                        El[a] = E;
+                        Sl[a] = source(s->w[a], s->c[a], u, F);
+                    }
+                    if (s->p.collision == 1) {
+                        /* Eq. (LB) in moment space: m = M f, relaxation of each moment
+                         * towards M E with its rate, source (1 - rate/2) M S, back with
+                         * M^-1 = M^T diag(1/|row|^2) */
+                        double d[19];
+                        for (int k = 0; k < Q; ++k) {
+                            double m = 0.0, meq = 0.0, ms = 0.0;
+                            for (int a = 0; a < Q; ++a) {
+                                m += s->Mb[k][a] * fl[a];
+                                meq += s->Mb[k][a] * El[a];
+                                ms += s->Mb[k][a] * Sl[a];
+                            }
+                            double rate;
+                            switch (s->Mkind[k]) {
+                            case MK_MOM: rate = 1.0 / s->p.tau_M; break;
+                            case MK_GHOST: rate = 1.0 / s->p.tau_g; break;
+                            default: rate = 1.0 / tau; break; /* shear, bulk (conserved density: no change) */
+                            }
+                            d[k] = -rate * (m - meq) + (1.0 - 0.5 * rate) * ms;
+                        }
+                        for (int a = 0; a < Q; ++a) {
+                            double v = fl[a];
+                            for (int k = 0; k < Q; ++k) v += s->Mb[k][a] * d[k] / s->Mnorm[k];
+                            fp[a] = v;
+                        }
+                    } else {
                         /* Eq. (LB) with Lambda = 1/tau: f* = f - (f - E)/tau + (1 - 1/(2 tau)) S */
-                        double fpost = fa - (fa - E) / tau + (1.0 - 0.5 / tau) * S;
+                        for (int a = 0; a < Q; ++a) fp[a] = fl[a] - (fl[a] - El[a]) / tau + (1.0 - 0.5 / tau) * Sl[a];
+                    }
+                    for (int a = 0; a < Q; ++a) {
+                        double fpost = fp[a];
                         int xt = wrap(x + s->c[a][0], s->p.nx);
                         int zt = wrap(z + s->c[a][2], s->p.nz);
                         int yt = y + s->c[a][1];
@@ -407,6 +604,20 @@ static void fenep_update(orc_state *s, double *Cnew) {
                     }
                 }
                 fenep_rhs_node(Cm, Gu, adv, lap, s->p.tau_p, s->p.L2, s->p.kappa, R);
+                if (s->p.chol) {
+                    /* AB2 on the log-Cholesky variables of sigma_P; the history holds their rates */
+                    double C6[6], lam[6], rl[6], lamn[6], Cn[6];
+                    for (int k = 0; k < 6; ++k) C6[k] = s->C[(long)k * N + i];
+                    chol_rates_node(C6, R, s->p.L2, lam, rl);
+                    for (int k = 0; k < 6; ++k) {
+                        double inc = s->have_prev ? 1.5 * rl[k] - 0.5 * s->Rp[(long)k * N + i] : rl[k];
+                        lamn[k] = lam[k] + inc;
+                        s->Rp[(long)k * N + i] = rl[k];
+                    }
+                    chol_to_C_node(lamn, s->p.L2, Cn);
+                    for (int k = 0; k < 6; ++k) Cnew[(long)k * N + i] = Cn[k];
+                    continue;
+                }
                 for (int k = 0; k < 6; ++k) {
                     double inc = s->have_prev ? 1.5 * R[k] - 0.5 * s->Rp[(long)k * N + i] : R[k];
                     Cnew[(long)k * N + i] = s->C[(long)k * N + i] + inc;
@@ -468,6 +679,9 @@ static int params_ok(const orc_params *p) {
     if (p->walls && p->ny < 2) return 0;
     if (p->ncomp != 1 && p->ncomp != 2) return 0;
     if (!(p->L2 > 3.0) || !(p->tau_p > 0.0) || !(p->delta > 0.0)) return 0;
+    if (p->collision != 0 && p->collision != 1) return 0;
+    if (p->collision == 1 && (!(p->tau_M > 0.5) || !(p->tau_g > 0.5))) return 0;
+    if (p->chol != 0 && p->chol != 1) return 0;
     return 1;
 }
 
@@ -485,6 +699,7 @@ orc_state *orc_create(const orc_params *p) {
         s->c = C9;
         s->w = W9;
     }
+    mrt_basis_fill(p->lattice, s->Mb, s->Mnorm, s->Mkind);
     s->N = (long)p->nx * p->ny * p->nz;
     long N = s->N;
     s->f = (double *)calloc((size_t)2 * s->Q * N, sizeof(double));
@@ -740,6 +955,11 @@ int orc_source(int lattice, const double u[3], const double F[3], double *out) {
 
 int orc_fenep_point(double *C, double *Rprev, int *have_prev, const double gradu[9], double tau_p, double L2,
                     long nsteps) {
+    return orc_fenep_point_form(C, Rprev, have_prev, gradu, tau_p, L2, nsteps, 0);
+}
+
+int orc_fenep_point_form(double *C, double *Rprev, int *have_prev, const double gradu[9], double tau_p,
+                         double L2, long nsteps, int chol) {
     /* uniform fields: the advection and diffusion terms vanish */
     const double zero[6] = {0, 0, 0, 0, 0, 0};
     double Gu[3][3];
@@ -750,13 +970,44 @@ int orc_fenep_point(double *C, double *Rprev, int *have_prev, const double gradu
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) Cm[a][b] = C[SYM[a][b]];
         fenep_rhs_node(Cm, Gu, zero, zero, tau_p, L2, 0.0, R);
-        for (int k = 0; k < 6; ++k) {
-            C[k] += *have_prev ? 1.5 * R[k] - 0.5 * Rprev[k] : R[k];
-            Rprev[k] = R[k];
+        if (chol) {
+            double lam[6], rl[6];
+            chol_rates_node(C, R, L2, lam, rl);
+            for (int k = 0; k < 6; ++k) {
+                lam[k] += *have_prev ? 1.5 * rl[k] - 0.5 * Rprev[k] : rl[k];
+                Rprev[k] = rl[k];
+            }
+            chol_to_C_node(lam, L2, C);
+        } else {
+            for (int k = 0; k < 6; ++k) {
+                C[k] += *have_prev ? 1.5 * R[k] - 0.5 * Rprev[k] : R[k];
+                Rprev[k] = R[k];
+            }
         }
         *have_prev = 1;
     }
     return 0;
+}
+
+int orc_chol_rates(const double C[6], const double Cdot[6], double L2, double lam[6], double lam_dot[6]) {
+    chol_rates_node(C, Cdot, L2, lam, lam_dot);
+    return 0;
+}
+
+int orc_chol_to_C(const double lam[6], double L2, double C[6]) {
+    chol_to_C_node(lam, L2, C);
+    return 0;
+}
+
+int orc_mrt_basis(int lattice, double *M, int *kind) {
+    double Mb[19][19], norm[19];
+    int kd[19];
+    const int Q = mrt_basis_fill(lattice, Mb, norm, kd);
+    for (int k = 0; k < Q; ++k) {
+        if (kind) kind[k] = kd[k];
+        for (int a = 0; a < Q; ++a) M[k * Q + a] = Mb[k][a];
+    }
+    return Q;
 }
 
 int orc_set_threads(int n) {

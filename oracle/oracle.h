@@ -50,6 +50,13 @@ typedef struct {
     int fd_on;              /* 1: evolve C; 0: C frozen (LBM only) */
     int coupling;           /* polymer feedback: 0 body force div Q (Eq. NS);
                                1 added to the equilibrium second moment (Eq. MODEtransformation) */
+    int collision;          /* 0: single relaxation time tau (BGK form of Eq. LB);
+                               1: relaxation in moment space (Sec. 2, MRT): shear and bulk
+                                  modes with the local tau (tau_b = tau_s), the species
+                                  momentum with tau_M, every other mode with tau_g */
+    double tau_M, tau_g;    /* MRT relaxation times of the momentum and non-hydrodynamic modes */
+    int chol;               /* conformation update: 0 AB2 on C; 1 AB2 on the Cholesky factor of
+                               sigma_P = f(r_P) C with log diagonal (Sec. 2, Cholesky scheme) */
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -85,6 +92,23 @@ int orc_source(int lattice, const double u[3], const double F[3], double *out);
  * (6, in/out), have_prev (in/out). */
 int orc_fenep_point(double *C, double *Rprev, int *have_prev,
                     const double gradu[9], double tau_p, double L2, long nsteps);
+
+/* Pointwise ODE as orc_fenep_point, with the conformation update chosen by
+ * chol (0: AB2 on C; 1: AB2 on the log-Cholesky variables of sigma_P). */
+int orc_fenep_point_form(double *C, double *Rprev, int *have_prev, const double gradu[9], double tau_p,
+                         double L2, long nsteps, int chol);
+
+/* Log-Cholesky variables of sigma_P = f(r_P) C (lam, 6 values in the tensor
+ * slots: lam_ii = ln l_ii, lam_ij = l_ij for i > j) and their rates for a
+ * given dC/dt (both C and dC/dt as 6 components xx xy xz yy yz zz). */
+int orc_chol_rates(const double C[6], const double Cdot[6], double L2, double lam[6], double lam_dot[6]);
+/* C of given log-Cholesky variables: sigma = L L^T, f = (L^2 - 3 + tr sigma)/L^2, C = sigma / f. */
+int orc_chol_to_C(const double lam[6], double L2, double C[6]);
+
+/* Moment basis of the MRT collision: M[k*Q + a] (row k, direction a) and the
+ * relaxation kind of each row (0 conserved density, 1 bulk, 2 species
+ * momentum, 3 shear, 4 non-hydrodynamic).  Returns Q. */
+int orc_mrt_basis(int lattice, double *M, int *kind);
 
 /* OpenMP threads used by node loops (n <= 0 leaves it unchanged); returns the count in use */
 int orc_set_threads(int n);
