@@ -120,6 +120,24 @@ vefd_status vefd_set_fenep(vefd_ctx *ctx, double tau_p, double eta_p, double L2,
  * T_sigma = -(rho_sigma/rho)(eta_P/tau_P)(f C - I) m(phi).  Errors: VEFD_ERR_ARG. */
 vefd_status vefd_set_polymer_coupling(vefd_ctx *ctx, int mode);
 
+/* Collision operator of Eq. (LB) (Sec. 2): 0 (default) a single relaxation
+ * time, the local tau of Eq. smoothingvisco; 1 relaxation in moment space
+ * with the paper's times (Eq. TRANSPORTCOEFF and the text after it): shear
+ * and bulk modes tau_s = tau_b = the local tau, species momentum tau_M = 1
+ * (mobility 1/2), non-hydrodynamic modes 1, on the orthogonal moment basis
+ * of the D3Q19 (D2Q9) lattice; the source enters as (I - Lambda/2) S.
+ * Errors: VEFD_ERR_ARG. */
+vefd_status vefd_set_collision(vefd_ctx *ctx, int model);
+
+/* Conformation-tensor time stepping (Sec. 2): 0 (default) AB2 on C; 1 the
+ * Cholesky scheme: AB2 on ln l_ii and l_ij (i > j) of sigma_P = f(r_P) C =
+ * L L^T, driven by the same right-hand side, which keeps C symmetric positive
+ * definite with tr C < L^2.  The stored field stays C; the AB2 history
+ * (VEFD_RPREV) then holds the rates of the log-Cholesky variables in the C
+ * component slots.  Changing the scheme clears the history (the next step is
+ * forward Euler).  Errors: VEFD_ERR_ARG. */
+vefd_status vefd_set_conformation_update(vefd_ctx *ctx, int scheme);
+
 /* Initial state: populations at equilibrium E(rho_sigma, u), C = C0 (or I
  * when C0 is NULL), AB2 history cleared (the next step is forward Euler).
  * rho_A (N), rho_B (N, ignored for one component), u (dim*N or NULL for

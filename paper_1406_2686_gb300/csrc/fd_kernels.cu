@@ -9,6 +9,8 @@
 // first derivative one-sided and the second derivative vanish.
 // Stored variable: Ct = C - I, so (f C - I) = f Ct + (f - 1) I with
 // f - 1 = tr Ct / (L^2 - 3 - tr Ct), evaluated without cancellation.
+// Optionally (StepParams::chol) the AB2 step advances the log-Cholesky factor
+// of sigma_P = f C instead of C (the Cholesky scheme of Sec. 2).
 // The update runs in the same pass as the densities of the new populations
 // (k_post), since both only wait for the lattice kernel.
 #include <cuda.h>
@@ -45,6 +47,116 @@ __device__ __forceinline__ constexpr int row_of(int k) {
 template <int NC>
 __device__ __forceinline__ constexpr int col_of(int k) {
     return NC == 6 ? (k == 0 ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : (k == 3 ? 1 : 2)))) : (k == 0 ? 0 : (k <= 2 ? 1 : 2));
+}
+
+// Cholesky scheme (Sec. 2): sigma_P = f(r_P) C = L L^T with L lower
+// triangular.  For the right-hand side dC/dt of the direct scheme,
+//   d sigma_P/dt = f dC/dt + sigma_P f tr(dC/dt) / (L^2 - 3),
+//   dL/dt = L Phi(L^-1 (d sigma_P/dt) L^-T),  Phi = lower triangle, diagonal halved,
+// and AB2 advances lambda = (ln l_ii, l_ij for i > j) with the history of its
+// rates.  The new C = L L^T / f with f = (L^2 - 3 + tr L L^T)/L^2 is SPD with
+// tr C < L^2 whenever lambda is finite.  c and cnew hold C - I; Rk is dC/dt;
+// Rprev and Rnew the lambda rates, in the stored component slots.
+template <int NC>
+__device__ __forceinline__ void chol_step(const float c[NC], const float Rk[NC], const float Rprev[NC], int have_prev,
+                                          float L2m3, float cnew[NC], float Rnew[NC]) {
+    float C[3][3], Cd[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int k = tidx<NC>(a, b);
+            C[a][b] = (k < 0 ? 0.0f : c[k]) + (a == b ? 1.0f : 0.0f);
+            Cd[a][b] = k < 0 ? 0.0f : Rk[k];
+        }
+    const float trt = NC == 6 ? c[0] + c[3] + c[5] : c[0] + c[2] + c[3];
+    const float f = L2m3 / (L2m3 - trt);
+    const float trd = Cd[0][0] + Cd[1][1] + Cd[2][2];
+    const float g = f * trd / L2m3;
+    float S[3][3], Sd[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            S[a][b] = f * C[a][b];
+            Sd[a][b] = f * Cd[a][b] + S[a][b] * g;
+        }
+    // S = L L^T and the inverse of L
+    float L[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            float v = S[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = (i == j) ? sqrtf(v) : v / L[j][j];
+        }
+    float Li[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        Li[j][j] = 1.0f / L[j][j];
+#pragma unroll
+        for (int i = j + 1; i < 3; ++i) {
+            float v = 0.0f;
+#pragma unroll
+            for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
+            Li[i][j] = v / L[i][i];
+        }
+    }
+    // A = L^-1 Sd L^-T (symmetric; lower triangle), Phi(A), dL/dt = L Phi(A)
+    float T[3][3], P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float v = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= i; ++k) v += Li[i][k] * Sd[k][j];
+            T[i][j] = v;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float v = 0.0f;
+            if (j <= i) {
+#pragma unroll
+                for (int k = 0; k <= j; ++k) v += T[i][k] * Li[j][k];
+                if (i == j) v *= 0.5f;
+            }
+            P[i][j] = v;
+        }
+    float Ln[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int i = col_of<NC>(k), j = row_of<NC>(k);  // lower-triangle entry (i >= j)
+        float ld = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (q >= j && q <= i) ld += L[i][q] * P[q][j];
+        const float lam = (i == j) ? logf(L[i][i]) : L[i][j];
+        const float rl = (i == j) ? ld / L[i][i] : ld;
+        const float lamn = lam + (have_prev ? 1.5f * rl - 0.5f * Rprev[k] : rl);
+        Ln[i][j] = (i == j) ? expf(lamn) : lamn;
+        Rnew[k] = rl;
+    }
+    float Sn[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float v = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) v += Ln[a][q] * Ln[b][q];
+            Sn[a][b] = v;
+        }
+    const float inv_fn = (L2m3 + 3.0f) / (L2m3 + Sn[0][0] + Sn[1][1] + Sn[2][2]);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int a = row_of<NC>(k), b = col_of<NC>(k);
+        cnew[k] = Sn[a][b] * inv_fn - (a == b ? 1.0f : 0.0f);
+    }
 }
 
 // FENE-P update at one node from its gathered stencil.  v(k, d) returns field
@@ -94,8 +206,7 @@ __device__ __forceinline__ unsigned fenep_compute(V v, float hy1, float hy2, con
             const int k = tidx<NC>(a, b);
             Cm[a][b] = (k < 0 ? 0.0f : c[k]) + (a == b ? 1.0f : 0.0f);
         }
-    float trn = 0.0f;
-    bool bad = false;
+    float Rc[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
         const int a = row_of<NC>(k), b = col_of<NC>(k);
@@ -103,13 +214,24 @@ __device__ __forceinline__ unsigned fenep_compute(V v, float hy1, float hy2, con
 #pragma unroll
         for (int e = 0; e < D; ++e) up += Cm[a][e] * Gu[e][b] + Gu[e][a] * Cm[e][b];
         const float relax = (f * c[k] + (is_diag<NC>(k) ? fm1 : 0.0f)) * p.inv_tau_p;
-        const float Rk = -adv[k] + up - relax + p.kappa * lap[k];
-        const float inc = p.have_prev ? 1.5f * Rk - 0.5f * Rprev[k] : Rk;
-        const float cn = c[k] + inc;
-        cnew[k] = cn;
-        Rnew[k] = Rk;
-        if (is_diag<NC>(k)) trn += cn;
-        bad |= isnan(cn);
+        Rc[k] = -adv[k] + up - relax + p.kappa * lap[k];
+    }
+    if (p.chol) {
+        chol_step<NC>(c, Rc, Rprev, p.have_prev, p.L2m3, cnew, Rnew);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const float inc = p.have_prev ? 1.5f * Rc[k] - 0.5f * Rprev[k] : Rc[k];
+            cnew[k] = c[k] + inc;
+            Rnew[k] = Rc[k];
+        }
+    }
+    float trn = 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        if (is_diag<NC>(k)) trn += cnew[k];
+        bad |= isnan(cnew[k]);
     }
     if (bad || isnan(tr)) return kStNan;
     if (trn >= p.L2m3 || tr >= p.L2m3) return kStTrace;

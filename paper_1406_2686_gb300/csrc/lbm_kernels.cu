@@ -1,593 +1,11 @@
-// Lattice-Boltzmann kernels of the hybrid step (Sec. 2 of Gupta,
-// Sbragaglia & Scagliarini):
-//   k_moments     rho_s - rho_ref_s = sum_a fd_a^s                    (Sec. 2, moments)
-//   k_lattice     per node: moments, Shan-Chen force (Eq. SCforce), polymer
-//                 feedback (eta_P/tau_P) div[(f C - I) m(phi)] (Eq. NS and the
-//                 last equation of Sec. 2) from the per-node stress written by
-//                 the densities/FD pass, velocity (Eq. equilibrium:vel),
-//                 viscosity (Eq. smoothingvisco), forced BGK collision (Eq. LB)
-//                 and push streaming with half-way bounce-back on moving walls.
-//                 Populations held in registers; used for any lattice size and
-//                 for the macroscopic (non-streaming) passes.
-//   k_lattice_tma the same step for lattices whose rows are 16-byte multiples:
-//                 one TMA copy stages the block's populations (all components
-//                 and directions of a 32 x BY x BZ tile) in shared memory while
-//                 the threads gather the neighbour densities and the feedback
-//                 stress; the collision then reads its populations from shared
-//                 memory, which keeps register use low and the memory system busy.
-// One thread per node; a warp covers 32 consecutive x, so every population
-// plane is read and written as contiguous 128-byte rows (writes of moving
-// populations are shifted by one element in x).
-#include <cuda.h>
-
-#include <algorithm>
-
-#include "vefd_internal.cuh"
+// Instantiations of the lattice kernels for the single-relaxation-time
+// collision, the initial equilibrium, the population conversions and the
+// tensor maps of the staged kernels (templates in lbm_impl.cuh).
+#include "lbm_impl.cuh"
 
 namespace vefd {
 
 namespace {
-
-__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// Row index of a neighbour in y: periodic, or clamped to the wall row (the
-// Shan-Chen density across a wall equals the adjacent fluid row).
-__device__ __forceinline__ int y_clamped(int y, int ny, int walls) {
-    if (walls) return y < 0 ? 0 : (y >= ny ? ny - 1 : y);
-    return wrap1(y, ny);
-}
-
-// Tile coordinate along one grid axis, optionally traversed backwards.
-__device__ __forceinline__ int tile_index(unsigned b, unsigned n, int rev) { return rev ? (int)(n - 1 - b) : (int)b; }
-
-template <class PT, class L, int NCOMP>
-__global__ void __launch_bounds__(128) k_moments(const PT* __restrict__ fd, const float* __restrict__ frest,
-                                                 float* __restrict__ drho, StepParams p, int rev) {
-    const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
-    const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
-    const int z = tile_index(blockIdx.z, gridDim.z, rev);
-    if (x >= p.nx || y >= p.ny) return;
-    const long long N = p.N;
-    const long long i = ((long long)z * p.ny + y) * p.nx + x;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        float d = __ldg(frest + s * N + i);
-#pragma unroll
-        for (int a = 1; a < L::Q; ++a) d += pop_load(fd + (s * (L::Q - 1) + a - 1) * N + i);
-        drho[s * N + i] = d;
-    }
-}
-
-// index of tensor component (i, j) in the stored order
-template <class L>
-__device__ __forceinline__ constexpr int sym(int i, int j) {
-    if (L::NC == 6) {
-        return (i == 0) ? j : (i == 1 ? (j == 0 ? 1 : (j == 1 ? 3 : 4)) : (j == 0 ? 2 : (j == 1 ? 4 : 5)));
-    } else {  // xx xy yy zz
-        return (i == 0) ? (j == 0 ? 0 : (j == 1 ? 1 : -1))
-             : (i == 1 ? (j == 0 ? 1 : (j == 1 ? 2 : -1)) : (j == 2 ? 3 : -1));
-    }
-}
-
-// index of feedback-stress component (i, j), i, j < D, in the stored order
-template <class L>
-__device__ __forceinline__ constexpr int qidx(int i, int j) {
-    return L::D == 3 ? sym<L>(i, j) : (i + j);  // 2D: xx 0, xy 1, yy 2
-}
-
-// Neighbour offsets of one node (periodic images and wall clamping folded in),
-// as 32-bit node-index differences: lattices are limited to fewer than 2^31
-// population entries, so every plane offset fits.
-struct Nbr {
-    int x, y, z, ny, i;
-    int ox[3], oy[3], oz[3];  // for d = -1, 0, +1 along x, y (clamped at walls), z
-    __device__ __forceinline__ int at(int dx, int dy, int dz) const { return i + ox[dx + 1] + oy[dy + 1] + oz[dz + 1]; }
-};
-
-__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p) {
-    Nbr n;
-    n.x = x;
-    n.y = y;
-    n.z = z;
-    n.ny = p.ny;
-    const int nx = p.nx, plane = p.nx * p.ny;
-    n.i = (z * p.ny + y) * nx + x;
-    n.ox[0] = wrap1(x - 1, nx) - x;
-    n.ox[1] = 0;
-    n.ox[2] = wrap1(x + 1, nx) - x;
-    n.oy[0] = (y_clamped(y - 1, p.ny, p.walls) - y) * nx;
-    n.oy[1] = 0;
-    n.oy[2] = (y_clamped(y + 1, p.ny, p.walls) - y) * nx;
-    n.oz[0] = (wrap1(z - 1, p.nz) - z) * plane;
-    n.oz[1] = 0;
-    n.oz[2] = (wrap1(z + 1, p.nz) - z) * plane;
-    return n;
-}
-
-// Neighbour part of the forces at one node:
-//   acc[s] = sum_{a>0} w_a (rho_s(x + c_a) - rho_ref_s) c_a   (Shan-Chen lattice sum;
-//            sum_a w_a c_a rho_ref = 0 so deviations suffice)
-//   Fp     = (eta_P / tau_P) div Q, Q = (f C - I) m(phi) precomputed per node,
-//            central differences, one-sided at walls (the linear-extrapolation
-//            ghost row v(-1) = 2 v(0) - v(1)).
-template <class L, int NCOMP>
-__device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepParams& p, const Nbr& nb,
-                                                 float acc[2][3], float Fp[3], float qloc[L::NQ]) {
-    const int N = (int)p.N;
-    const int i = nb.i;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) acc[s][0] = acc[s][1] = acc[s][2] = 0.0f;
-    if (NCOMP == 2) {
-        // sums per weight class (axis, face diagonal), weighted once at the end
-        float sa[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, sd[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int a = 1; a < L::Q; ++a) {
-            const int j = nb.at(L::cx(a), L::cy(a), L::cz(a));
-            const bool axis = L::w(a) == L::w(1);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float t = __ldg(b.drho + s * N + j);
-                float* acc_s = axis ? sa[s] : sd[s];
-                if (L::cx(a)) acc_s[0] += L::cx(a) * t;
-                if (L::cy(a)) acc_s[1] += L::cy(a) * t;
-                if (L::cz(a)) acc_s[2] += L::cz(a) * t;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) acc[s][k] = L::w(1) * sa[s][k] + L::w(L::Q - 1) * sd[s][k];
-    }
-    Fp[0] = Fp[1] = Fp[2] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < L::NQ; ++k) qloc[k] = 0.0f;
-    if (p.feedback == 0.0f) return;
-    const float* Q = b.Q;
-    if (p.coupling == 1) {
-        // the stress enters this node's equilibrium instead (Eq. MODEtransformation)
-#pragma unroll
-        for (int k = 0; k < L::NQ; ++k) qloc[k] = __ldg(Q + k * N + i);
-        return;
-    }
-    float div[3] = {0.f, 0.f, 0.f};
-    {
-        const int jm = nb.at(-1, 0, 0), jp = nb.at(1, 0, 0);
-#pragma unroll
-        for (int jj = 0; jj < L::D; ++jj) {
-            const int k = qidx<L>(0, jj);
-            div[jj] += 0.5f * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
-        }
-    }
-    {
-        int jm = nb.at(0, -1, 0), jp = nb.at(0, 1, 0);
-        float h = 0.5f;
-        if (p.walls && nb.y == 0) {
-            jm = i;
-            h = 1.0f;
-        } else if (p.walls && nb.y == nb.ny - 1) {
-            jp = i;
-            h = 1.0f;
-        }
-#pragma unroll
-        for (int jj = 0; jj < L::D; ++jj) {
-            const int k = qidx<L>(1, jj);
-            div[jj] += h * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
-        }
-    }
-    if (L::D == 3) {
-        const int jm = nb.at(0, 0, -1), jp = nb.at(0, 0, 1);
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-            const int k = qidx<L>(2, jj);
-            div[jj] += 0.5f * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Fp[k] = p.feedback * div[k];
-}
-
-// Local state after the forces: velocity, relaxation, per-component force and,
-// for the equilibrium coupling, the component's share of the polymer stress
-// T_s = tq[s] Q with tq[s] = -(rho_s/rho)(eta_P/tau_P).
-template <int NCOMP>
-struct Local {
-    float rs[NCOMP], dr[NCOMP];
-    float inv_rho, ux, uy, uz, usq, omega, src_w;
-    float F[NCOMP][3];
-    float tq[NCOMP];
-};
-
-template <class L, int NCOMP>
-__device__ __forceinline__ void local_state(const StepParams& p, const float dr[NCOMP], float jx, float jy, float jz,
-                                            const float acc[2][3], const float Fp[3], Local<NCOMP>& st,
-                                            unsigned* status) {
-    float rho = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        st.dr[s] = dr[s];
-        st.rs[s] = p.rho_ref[s] + dr[s];
-        rho += st.rs[s];
-    }
-    st.inv_rho = 1.0f / rho;
-    // Shan-Chen: force on A from B's neighbourhood and on B from A's
-    float g[NCOMP][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (NCOMP == 2) {
-            g[0][k] = -p.G * st.rs[0] * acc[1][k];
-            g[NCOMP - 1][k] = -p.G * st.rs[NCOMP - 1] * acc[0][k];
-        } else {
-            g[0][k] = 0.0f;
-        }
-    }
-    float Fb[3], Ftot[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        Fb[k] = Fp[k] + p.fext[k];
-        Ftot[k] = Fb[k];
-#pragma unroll
-        for (int s = 0; s < NCOMP; ++s) Ftot[k] += g[s][k];
-    }
-    // velocity with half the total force (Eq. equilibrium:vel)
-    st.ux = (jx + 0.5f * Ftot[0]) * st.inv_rho;
-    st.uy = (jy + 0.5f * Ftot[1]) * st.inv_rho;
-    st.uz = L::D == 3 ? (jz + 0.5f * Ftot[2]) * st.inv_rho : 0.0f;
-    st.usq = st.ux * st.ux + st.uy * st.uy + st.uz * st.uz;
-    // rho c_s^2 (tau - 1/2) = eta_A f_+(phi) + eta_B f_-(phi); one component: phi = 1
-    const float phi = NCOMP == 2 ? (st.rs[0] - st.rs[NCOMP - 1]) * st.inv_rho : 1.0f;
-    const float t = tanhf(phi * p.inv_delta);
-    const float eta = p.eta_A * 0.5f * (1.0f + t) + p.eta_B * 0.5f * (1.0f - t);
-    const float tau = 0.5f + eta * 3.0f * st.inv_rho;
-    st.omega = 1.0f / tau;
-    st.src_w = 1.0f - 0.5f * st.omega;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        const float share = st.rs[s] * st.inv_rho;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) st.F[s][k] = g[s][k] + share * Fb[k];
-        st.tq[s] = p.coupling == 1 ? -share * p.feedback : 0.0f;
-    }
-    unsigned bits = 0;
-    if (isnan(st.usq) || isnan(rho)) bits |= kStNan;
-    else if (st.usq > 0.09f) bits |= kStMach;
-    if (!(rho > 0.0f) && !isnan(rho)) bits |= kStRho;
-    if (bits) atomicOr(status, bits);
-}
-
-// Collision of every population of every component and push streaming.
-// fget(s, a) returns the stored deviation f_a^s of this node.
-//
-// Opposite directions a and a' (c_a' = -c_a) share c.u and c.F up to sign, so
-// each pair is relaxed together.  For the deviation equilibrium and the
-// source of Sec. 2 (Eqs. LB and equilibrium),
-//   omega E_a + (1 - omega/2) S_a = w_a [K0 + (c.u)(c.R)] + w_a c.P
-// with, per component, K0 = omega (drho - 1.5 rho u.u) - 3 (1 - omega/2) u.F,
-// R = 4.5 omega rho u + 9 (1 - omega/2) F and P = 3 omega rho u +
-// 3 (1 - omega/2) F; the bracket is even in c and c.P odd, so
-//   f*_a  = (1 - omega) f_a  + w_a [K0 + (c.u)(c.R)] + w_a c.P
-//   f*_a' = (1 - omega) f_a' + w_a [K0 + (c.u)(c.R)] - w_a c.P.
-// The weight is folded into K0, R and P once per weight class, so a pair
-// costs a handful of additions and two fused multiply-adds.
-template <class PT, class L, int NCOMP, class FGet>
-__device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
-                                               const Local<NCOMP>& st, const float qloc[L::NQ], FGet fget) {
-    const int N = (int)p.N;
-    const int node = nb.i;
-    const int* ox = nb.ox;
-    const int* oz = nb.oz;
-    // streaming offsets in y are periodic (walls are handled by bounce-back)
-    const int nx = p.nx;
-    int oy[3];
-    const bool wall_lo = p.walls && nb.y == 0, wall_hi = p.walls && nb.y == nb.ny - 1;
-    oy[0] = (nb.y == 0 ? nb.ny - 1 : -1) * nx;
-    oy[1] = 0;
-    oy[2] = (nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
-    const float uw6 = 6.0f * p.u_wall;  // 2 (c.U) / c_s^2 with U = +-u_wall along x
-    const float keep = 1.0f - st.omega;
-    // trace of the local feedback stress over the lattice dimensions (equilibrium coupling)
-    const float trq = L::NQ == 6 ? qloc[0] + qloc[3] + qloc[5] : qloc[0] + qloc[2];
-    constexpr float w_axis = L::w(1), w_diag = L::w(L::Q - 1);
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        const float Fx = st.F[s][0], Fy = st.F[s][1], Fz = st.F[s][2];
-        const float uF = st.ux * Fx + st.uy * Fy + st.uz * Fz;
-        const float rsv = st.rs[s], drs = st.dr[s];
-        const float K0 = st.omega * (drs - 1.5f * rsv * st.usq) - 3.0f * st.src_w * uF;
-        const float orho = st.omega * rsv;
-        const float r45 = 4.5f * orho, s9 = 9.0f * st.src_w, r3 = 3.0f * orho, s3 = 3.0f * st.src_w;
-        const float Rx = r45 * st.ux + s9 * Fx, Ry = r45 * st.uy + s9 * Fy, Rz = r45 * st.uz + s9 * Fz;
-        const float Px = r3 * st.ux + s3 * Fx, Py = r3 * st.uy + s3 * Fy, Pz = r3 * st.uz + s3 * Fz;
-        // w (c c - c_s^2 I):T / (2 c_s^4) = 4.5 w (c.T.c - tr T / 3), relaxed with omega
-        const float tqo = 4.5f * st.tq[s] * st.omega;
-        // moving populations: plane a - 1 of component s; the rest population
-        // stays at the node, in FP32, and is updated in place
-        PT* out = static_cast<PT*>(b.fout) + (long long)s * (L::Q - 1) * N - N;
-        // The collision and the wall exchange conserve mass exactly (the source
-        // has no zeroth moment; the moving-wall terms of a node sum to zero), so
-        // the rest population is taken as the remainder after the moving ones
-        // as they are stored (after rounding to the storage type).  Kept in
-        // FP32, it carries the node's mass exactly: neither the FP32 weights
-        // (sum 1 + 1.5e-8) nor 16-bit rounding of the moving populations leave
-        // a systematic mass drift.
-        float moved = 0.0f;
-#pragma unroll
-        for (int wc = 0; wc < 2; ++wc) {
-            // weight class: axis directions, then face diagonals
-            const float wa = wc == 0 ? w_axis : w_diag;
-            const float k0 = wa * K0;
-            const float rx = wa * Rx, ry = wa * Ry, rz = wa * Rz;
-            const float px = wa * Px, py = wa * Py, pz = wa * Pz;
-            const float wrs = wa * rsv, tqw = wa * tqo;
-#pragma unroll
-            for (int a = 1; a < L::Q; a += 2) {
-                if ((L::w(a) == w_axis) != (wc == 0)) continue;
-                const int ab = a + 1;  // opposite of a
-                const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-                const float cu = cx * st.ux + cy * st.uy + cz * st.uz;
-                const float cr = cx * rx + cy * ry + cz * rz;
-                const float cp = cx * px + cy * py + cz * pz;
-                float even = fmaf(cu, cr, k0);
-                if (p.coupling == 1) {
-                    float cqc;
-                    if (L::NQ == 6)
-                        cqc = cx * cx * qloc[0] + cy * cy * qloc[3] + cz * cz * qloc[5] +
-                              2.0f * (cx * cy * qloc[1] + cx * cz * qloc[2] + cy * cz * qloc[4]);
-                    else
-                        cqc = cx * cx * qloc[0] + cy * cy * qloc[2] + 2.0f * cx * cy * qloc[1];
-                    even += tqw * (cqc - trq * (1.0f / 3.0f));
-                }
-                const float fa = fmaf(keep, fget(s, a), even + cp);
-                const float fb = fmaf(keep, fget(s, ab), even - cp);
-                // a streams to x + c, its opposite to x - c; a population leaving
-                // through a wall returns to this node in the opposite direction with
-                // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
-                if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
-                    const float Uw = cy < 0 ? uw6 : -uw6;
-                    const PT v = pop_put<PT>(fa - wrs * (float)cx * Uw);
-                    out[ab * N + node] = v;
-                    moved += pop_get(v);
-                } else {
-                    const PT v = pop_put<PT>(fa);
-                    out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = v;
-                    moved += pop_get(v);
-                }
-                if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
-                    const float Uw = cy > 0 ? uw6 : -uw6;
-                    const PT v = pop_put<PT>(fb + wrs * (float)cx * Uw);
-                    out[a * N + node] = v;
-                    moved += pop_get(v);
-                } else {
-                    const PT v = pop_put<PT>(fb);
-                    out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = v;
-                    moved += pop_get(v);
-                }
-            }
-        }
-        b.frest[s * N + node] = drs - moved;
-    }
-}
-
-template <class PT, class L, int NCOMP, bool STREAM>
-__global__ void __launch_bounds__(128) k_lattice(StepBufs b, StepParams p, int rev) {
-    const int x = tile_index(blockIdx.x, gridDim.x, rev) * blockDim.x + threadIdx.x;
-    const int y = tile_index(blockIdx.y, gridDim.y, rev) * blockDim.y + threadIdx.y;
-    const int z = tile_index(blockIdx.z, gridDim.z, rev);
-    if (x >= p.nx || y >= p.ny) return;
-    const long long N = p.N;
-    const long long i = ((long long)z * p.ny + y) * p.nx + x;
-
-    // moments (same summation order as k_moments)
-    float f[NCOMP][L::Q];
-    float dr[NCOMP];
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) {
-        dr[s] = 0.0f;
-#pragma unroll
-        for (int a = 0; a < L::Q; ++a) {
-            f[s][a] = a == 0 ? b.frest[s * N + i]
-                             : pop_load(static_cast<const PT*>(b.fin) + (s * (L::Q - 1) + a - 1) * N + i);
-            dr[s] += f[s][a];
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s)
-#pragma unroll
-        for (int a = 1; a < L::Q; ++a) {
-            if (L::cx(a)) jx += L::cx(a) * f[s][a];
-            if (L::cy(a)) jy += L::cy(a) * f[s][a];
-            if (L::cz(a)) jz += L::cz(a) * f[s][a];
-        }
-    const Nbr nb = make_nbr(x, y, z, p);
-    float acc[2][3], Fp[3], qloc[L::NQ];
-    neighbour_forces<L, NCOMP>(b, p, nb, acc, Fp, qloc);
-    Local<NCOMP> st;
-    local_state<L, NCOMP>(p, dr, jx, jy, jz, acc, Fp, st, b.status);
-    b.u[i] = st.ux;
-    b.u[N + i] = st.uy;
-    if (L::D == 3) b.u[2 * N + i] = st.uz;
-    if (!STREAM) {
-        if (b.dbg) {
-            // g_s from the lattice sums; F_p; tau
-            for (int k = 0; k < 3; ++k) {
-                b.dbg[k * N + i] = NCOMP == 2 ? -p.G * st.rs[0] * acc[1][k] : 0.0f;
-                b.dbg[(3 + k) * N + i] = NCOMP == 2 ? -p.G * st.rs[NCOMP - 1] * acc[0][k] : 0.0f;
-                b.dbg[(6 + k) * N + i] = Fp[k];
-            }
-            b.dbg[9 * N + i] = 1.0f / st.omega;
-        }
-        return;
-    }
-    collide_stream<PT, L, NCOMP>(b, p, nb, st, qloc, [&](int s, int a) { return f[s][a]; });
-}
-
-// --- TMA-staged variant --------------------------------------------------------
-
-// Threads per SM the register budget of the staged lattice kernel is sized
-// for (1024: 64 registers per thread).
-#ifndef VEFD_LATTICE_THREADS_PER_SM
-#define VEFD_LATTICE_THREADS_PER_SM 1024
-#endif
-
-// Node work of the staged kernels, split around the wait for the staged
-// populations: gather (neighbour densities and feedback stress, overlapping
-// the copy), then moments, local state and collision from shared memory.
-template <class L, int NCOMP>
-struct NodeGather {
-    float dr[NCOMP];
-    float acc[2][3], Fp[3], qloc[L::NQ];
-    Nbr nb;
-};
-
-template <class L, int NCOMP>
-__device__ __forceinline__ void node_gather(const StepBufs& b, const StepParams& p, int x, int y, int z, bool active,
-                                            NodeGather<L, NCOMP>& g) {
-    g.nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
-    if (!active) return;
-    const long long N = p.N;
-    // the node's own deviations come from the density buffer (bit-identical to
-    // the sum of the staged populations)
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) g.dr[s] = __ldg(b.drho + s * N + g.nb.i);
-    neighbour_forces<L, NCOMP>(b, p, g.nb, g.acc, g.Fp, g.qloc);
-}
-
-template <class PT, class L, int NCOMP, int T>
-__device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams& p, const PT* sf, int t,
-                                             const NodeGather<L, NCOMP>& g) {
-    const long long N = p.N;
-    const int i = g.nb.i;
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s)
-#pragma unroll
-        for (int a = 1; a < L::Q; ++a) {
-            const float fa = pop_get(sf[(s * (L::Q - 1) + a - 1) * T + t]);
-            if (L::cx(a)) jx += L::cx(a) * fa;
-            if (L::cy(a)) jy += L::cy(a) * fa;
-            if (L::cz(a)) jz += L::cz(a) * fa;
-        }
-    Local<NCOMP> st;
-    local_state<L, NCOMP>(p, g.dr, jx, jy, jz, g.acc, g.Fp, st, b.status);
-    b.u[i] = st.ux;
-    b.u[N + i] = st.uy;
-    if (L::D == 3) b.u[2 * N + i] = st.uz;
-    // volatile reads keep the populations in shared memory instead of registers
-    collide_stream<PT, L, NCOMP>(b, p, g.nb, st, g.qloc,
-                                 [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
-}
-
-template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (BX * BY * BZ)) k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
-                                                              StepParams p, int rev) {
-    constexpr int P = NCOMP * (L::Q - 1);  // moving populations
-    constexpr int T = BX * BY * BZ;
-    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
-    extern __shared__ __align__(128) unsigned char sraw[];
-    PT* sf = reinterpret_cast<PT*>(sraw);  // [P][BZ][BY][BX], the TMA box layout
-    __shared__ __align__(8) unsigned long long bar;
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int x0 = tile_index(blockIdx.x, gridDim.x, rev) * BX;
-    const int y0 = tile_index(blockIdx.y, gridDim.y, rev) * BY;
-    const int z0 = tile_index(blockIdx.z, gridDim.z, rev) * BZ;
-    const bool leader = (tx | ty | tz) == 0;
-    const unsigned bar_a = smem_u32(&bar);
-    if (leader) mbar_init(bar_a);
-    __syncthreads();
-    if (leader) tma_load_4d(smem_u32(sf), &tm_fin, x0, y0, z0, 0, bar_a, kBytes);
-    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-    const bool active = x < p.nx && y < p.ny && z < p.nz;
-    NodeGather<L, NCOMP> g;
-    node_gather<L, NCOMP>(b, p, x, y, z, active, g);
-    // bounded wait for the staged populations; on timeout report and leave
-    if (!mbar_wait_bounded(bar_a)) {
-        if (leader) atomicOr(b.status, kStTimeout);
-        return;
-    }
-    if (!active) return;
-    node_collide<PT, L, NCOMP, T>(b, p, sf, (tz * BY + ty) * BX + tx, g);
-}
-
-// Persistent form: a grid of (SMs x resident blocks) walks the tiles in order
-// (tile = block + k * grid, backwards when rev is set) with two staging
-// buffers, so the copy of a block's next tile is in flight while it computes
-// the current one and the copy engine never idles between tiles.
-// Resident blocks per SM the persistent kernel's registers are budgeted for:
-// as many as the two staging buffers leave room for in 227 KB of shared
-// memory (1 KB reserved per block), at most the 64-register budget.
-template <class PT, class L, int NCOMP, int T>
-constexpr int pers_blocks() {
-    constexpr int smem = 2 * NCOMP * (L::Q - 1) * T * (int)sizeof(PT) + 1024 + 128;
-    constexpr int by_smem = (227 * 1024) / smem;
-    constexpr int by_regs = VEFD_LATTICE_THREADS_PER_SM / T;
-    return by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
-}
-
-template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
-__global__ void __launch_bounds__(BX * BY * BZ, (pers_blocks<PT, L, NCOMP, BX * BY * BZ>())) k_lattice_pers(const __grid_constant__ CUtensorMap tm_fin, StepBufs b,
-                                                               StepParams p, int rev, int ntx, int nty, int ntiles) {
-    constexpr int P = NCOMP * (L::Q - 1);
-    constexpr int T = BX * BY * BZ;
-    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
-    extern __shared__ __align__(128) unsigned char sraw[];
-    PT* sbuf = reinterpret_cast<PT*>(sraw);  // two buffers of [P][BZ][BY][BX]
-    __shared__ __align__(8) unsigned long long bars[2];
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const bool leader = (tx | ty | tz) == 0;
-    const unsigned bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
-    auto origin = [&](int tile, int& x0, int& y0, int& z0) {
-        const int q = rev ? ntiles - 1 - tile : tile;
-        x0 = (q % ntx) * BX;
-        const int r = q / ntx;
-        y0 = (r % nty) * BY;
-        z0 = (r / nty) * BZ;
-    };
-    auto issue = [&](int tile, int slot) {
-        int x0, y0, z0;
-        origin(tile, x0, y0, z0);
-        tma_load_4d(smem_u32(sbuf + slot * P * T), &tm_fin, x0, y0, z0, 0, slot ? bar1 : bar0, kBytes);
-    };
-    if (leader) {
-        mbar_init(bar0);
-        mbar_init(bar1);
-    }
-    __syncthreads();
-    const int stride = gridDim.x;
-    if (leader) {
-        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-        if ((int)blockIdx.x + stride < ntiles) issue(blockIdx.x + stride, 1);
-    }
-    const int t = (tz * BY + ty) * BX + tx;
-    for (int k = 0;; ++k) {
-        const int tile = (int)blockIdx.x + k * stride;
-        if (tile >= ntiles) break;
-        const int slot = k & 1;
-        int x0, y0, z0;
-        origin(tile, x0, y0, z0);
-        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-        const bool active = x < p.nx && y < p.ny && z < p.nz;
-        NodeGather<L, NCOMP> g;
-        node_gather<L, NCOMP>(b, p, x, y, z, active, g);
-        const bool ok = mbar_wait_bounded_parity(slot ? bar1 : bar0, (unsigned)((k >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (leader) {
-                atomicOr(b.status, kStTimeout);
-                // let the copies this block still has in flight land (bounded) before leaving
-                mbar_wait_bounded_parity(slot ? bar1 : bar0, (unsigned)((k >> 1) & 1));
-                if (tile + stride < ntiles)
-                    mbar_wait_bounded_parity(slot ? bar0 : bar1, (unsigned)(((k + 1) >> 1) & 1));
-            }
-            return;
-        }
-        if (active) node_collide<PT, L, NCOMP, T>(b, p, sbuf + slot * P * T, t, g);
-        // every thread is done with this buffer: refill it with the tile after next
-        __syncthreads();
-        if (leader && tile + 2 * stride < ntiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(tile + 2 * stride, slot);
-        }
-    }
-}
 
 template <class PT, class L, int NCOMP>
 __global__ void k_init_eq(const float* __restrict__ rhoA, const float* __restrict__ rhoB,
@@ -645,75 +63,6 @@ int grid_1d(long long n) {
     if (b > 152 * 16) b = 152 * 16;
     return (int)(b < 1 ? 1 : b);
 }
-
-dim3 node_grid(const StepParams& p) { return dim3((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz); }
-
-template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
-cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
-    constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
-    static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
-    dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
-    k_lattice_tma<PT, L, NCOMP, BX, BY, BZ><<<grd, blk, smem, s>>>(*tm, b, p, rev);
-    return cudaGetLastError();
-}
-
-int g_lat_sms = 0;
-
-template <class PT, class L, int NCOMP, int BX, int BY, int BZ>
-cudaError_t launch_pers_tile(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
-    constexpr int T = BX * BY * BZ;
-    constexpr int smem = 2 * NCOMP * (L::Q - 1) * T * (int)sizeof(PT);
-    static int per_sm = 0;  // resident blocks per SM of this instantiation
-    if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(k_lattice_pers<PT, L, NCOMP, BX, BY, BZ>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lattice_pers<PT, L, NCOMP, BX, BY, BZ>, T, smem);
-        if (e != cudaSuccess) return e;
-        if (nb < 1) return cudaErrorInvalidConfiguration;
-        per_sm = nb;
-    }
-    if (!g_lat_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&g_lat_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_lat_sms = 152;
-    }
-    const int ntx = (p.nx + BX - 1) / BX, nty = (p.ny + BY - 1) / BY, ntz = (p.nz + BZ - 1) / BZ;
-    const long long ntiles = (long long)ntx * nty * ntz;
-    const long long grid = std::min<long long>(ntiles, (long long)per_sm * g_lat_sms);
-    k_lattice_pers<PT, L, NCOMP, BX, BY, BZ><<<(unsigned)grid, dim3(BX, BY, BZ), smem, s>>>(*tm, b, p, rev, ntx, nty,
-                                                                                         (int)ntiles);
-    return cudaGetLastError();
-}
-
-template <class PT, class L, int NCOMP>
-cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s,
-                       int tile) {
-    if constexpr (L::D == 3) {
-        switch (tile) {
-        case 1: return launch_tma_tile<PT, L, NCOMP, 32, 2, 4>(tm, p, b, rev, s);
-        case 2: return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
-        case 3: return launch_pers_tile<PT, L, NCOMP, 32, 4, 2>(tm, p, b, rev, s);
-        case 4: return launch_pers_tile<PT, L, NCOMP, 32, 2, 4>(tm, p, b, rev, s);
-        case 5: return launch_pers_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
-        default: return launch_tma_tile<PT, L, NCOMP, 32, 4, 2>(tm, p, b, rev, s);
-        }
-    } else {
-        switch (tile) {
-        case 1: return launch_tma_tile<PT, L, NCOMP, 32, 4, 1>(tm, p, b, rev, s);
-        case 2: return launch_tma_tile<PT, L, NCOMP, 32, 16, 1>(tm, p, b, rev, s);
-        case 3: return launch_pers_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
-        case 4: return launch_pers_tile<PT, L, NCOMP, 32, 4, 1>(tm, p, b, rev, s);
-        case 5: return launch_pers_tile<PT, L, NCOMP, 32, 16, 1>(tm, p, b, rev, s);
-        default: return launch_tma_tile<PT, L, NCOMP, 32, 8, 1>(tm, p, b, rev, s);
-        }
-    }
-}
-
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 }  // namespace
 
@@ -784,35 +133,21 @@ cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const St
 
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
                            cudaStream_t s, const void* tensor_map, int rev, int tile) {
-    if (stream_pops && tensor_map) {
-        const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map);
-        cudaError_t e = cudaSuccess;
-        VEFD_WITH_PT(p.prec, {
-            if (lattice == 1)
-                e = ncomp == 2 ? launch_tma<PT, D3Q19, 2>(tm, p, b, rev, s, tile)
-                               : launch_tma<PT, D3Q19, 1>(tm, p, b, rev, s, tile);
-            else
-                e = ncomp == 2 ? launch_tma<PT, D2Q9, 2>(tm, p, b, rev, s, tile)
-                               : launch_tma<PT, D2Q9, 1>(tm, p, b, rev, s, tile);
-        });
-        return e;
+    if (stream_pops) {
+        if (p.collision == 1) return launch_lattice_mrt(lattice, ncomp, p, b, s, tensor_map, rev, tile);
+        return launch_lattice_coll<0>(lattice, ncomp, p, b, s, tensor_map, rev, tile);
     }
+    // macroscopic pass (moments, forces, velocity; no streaming)
     dim3 blk(32, 4, 1), grd = node_grid(p);
-#define VEFD_LAT(LT, NCP)                                                              \
-    do {                                                                               \
-        if (stream_pops) k_lattice<PT, LT, NCP, true><<<grd, blk, 0, s>>>(b, p, rev);  \
-        else k_lattice<PT, LT, NCP, false><<<grd, blk, 0, s>>>(b, p, rev);             \
-    } while (0)
     VEFD_WITH_PT(p.prec, {
         if (lattice == 1) {
-            if (ncomp == 2) VEFD_LAT(D3Q19, 2);
-            else VEFD_LAT(D3Q19, 1);
+            if (ncomp == 2) k_lattice<PT, D3Q19, 2, false, 0><<<grd, blk, 0, s>>>(b, p, rev);
+            else k_lattice<PT, D3Q19, 1, false, 0><<<grd, blk, 0, s>>>(b, p, rev);
         } else {
-            if (ncomp == 2) VEFD_LAT(D2Q9, 2);
-            else VEFD_LAT(D2Q9, 1);
+            if (ncomp == 2) k_lattice<PT, D2Q9, 2, false, 0><<<grd, blk, 0, s>>>(b, p, rev);
+            else k_lattice<PT, D2Q9, 1, false, 0><<<grd, blk, 0, s>>>(b, p, rev);
         }
     });
-#undef VEFD_LAT
     return cudaGetLastError();
 }
 

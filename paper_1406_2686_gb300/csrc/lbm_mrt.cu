@@ -1,0 +1,13 @@
+// Instantiations of the lattice kernels for the moment-space collision of
+// Sec. 2 (relaxation times: shear and bulk modes tau, momentum and
+// non-hydrodynamic modes 1; templates in lbm_impl.cuh).
+#include "lbm_impl.cuh"
+
+namespace vefd {
+
+cudaError_t launch_lattice_mrt(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                               const void* tensor_map, int rev, int tile) {
+    return launch_lattice_coll<1>(lattice, ncomp, p, b, s, tensor_map, rev, tile);
+}
+
+}  // namespace vefd

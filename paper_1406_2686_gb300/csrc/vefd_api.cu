@@ -28,6 +28,8 @@ struct vefd_ctx {
     double tau_p = 1.0, eta_p = 0.0, L2 = 100.0, kappa = 0.0;
     int phase = 0, fd_on = 1;
     int coupling = 0;  // polymer feedback: 0 body force, 1 equilibrium stress
+    int collision = 0;  // 0 single relaxation time, 1 moment space (paper's rates)
+    int chol = 0;       // conformation update: 0 AB2 on C, 1 log-Cholesky of f C
     double rho_ref[2] = {1.0, 1.0};
     // time-level state
     int have_prev = 0;
@@ -230,6 +232,8 @@ StepParams params_of(const vefd_ctx* c) {
     p.rho_ref[1] = (float)c->rho_ref[1];
     p.prec = c->cfg.precision;
     p.coupling = c->coupling;
+    p.collision = c->collision;
+    p.chol = c->chol;
     return p;
 }
 
@@ -427,6 +431,21 @@ vefd_status vefd_set_polymer_coupling(vefd_ctx* c, int mode) {
     if (!c) return VEFD_ERR_ARG;
     if (mode != 0 && mode != 1) return fail(c, VEFD_ERR_ARG, "coupling must be 0 (body force) or 1 (equilibrium)");
     c->coupling = mode;
+    return VEFD_OK;
+}
+
+vefd_status vefd_set_collision(vefd_ctx* c, int model) {
+    if (!c) return VEFD_ERR_ARG;
+    if (model != 0 && model != 1) return fail(c, VEFD_ERR_ARG, "collision must be 0 (single time) or 1 (moment space)");
+    c->collision = model;
+    return VEFD_OK;
+}
+
+vefd_status vefd_set_conformation_update(vefd_ctx* c, int scheme) {
+    if (!c) return VEFD_ERR_ARG;
+    if (scheme != 0 && scheme != 1) return fail(c, VEFD_ERR_ARG, "scheme must be 0 (C) or 1 (log-Cholesky)");
+    if (scheme != c->chol) c->have_prev = 0;  // the history holds rates of the other variables
+    c->chol = scheme;
     return VEFD_OK;
 }
 
@@ -780,6 +799,7 @@ struct CkptHeader {
     int64_t steps;
     uint32_t status;
     int32_t coupling;
+    int32_t collision, chol;
 };
 }  // namespace
 
@@ -790,7 +810,7 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     CkptHeader h;
     memset(&h, 0, sizeof h);
     memcpy(h.magic, kMagic, 8);
-    h.version = 3;
+    h.version = 4;
     h.lattice = c->cfg.lattice;
     h.nx = c->cfg.nx;
     h.ny = c->cfg.ny;
@@ -812,6 +832,8 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
     h.have_prev = c->have_prev;
     h.precision = c->cfg.precision;
     h.coupling = c->coupling;
+    h.collision = c->collision;
+    h.chol = c->chol;
     h.rho_ref[0] = c->rho_ref[0];
     h.rho_ref[1] = c->rho_ref[1];
     h.steps = c->steps;
@@ -841,7 +863,7 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     const size_t nrb = (size_t)c->cfg.ncomp * c->N * 4;
     std::vector<char> buf(npb + nrb + 2 * nc * 4);
     bool ok = fread(&h, sizeof h, 1, fh) == 1;
-    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 3 && h.precision == c->cfg.precision;
+    ok = ok && memcmp(h.magic, kMagic, 8) == 0 && h.version == 4 && h.precision == c->cfg.precision;
     ok = ok && h.lattice == c->cfg.lattice && h.nx == c->cfg.nx && h.ny == c->cfg.ny && h.nz == c->cfg.nz &&
          h.ncomp == c->cfg.ncomp && h.walls == c->cfg.walls;
     ok = ok && fread(buf.data(), 1, buf.size(), fh) == buf.size();
@@ -860,6 +882,8 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
     c->phase = h.phase;
     c->fd_on = h.fd_on;
     c->coupling = h.coupling;
+    c->collision = h.collision;
+    c->chol = h.chol;
     c->have_prev = h.have_prev;
     c->rho_ref[0] = h.rho_ref[0];
     c->rho_ref[1] = h.rho_ref[1];
@@ -918,6 +942,8 @@ vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
     t->phase = c->phase;
     t->fd_on = c->fd_on;
     t->coupling = c->coupling;
+    t->collision = c->collision;
+    t->chol = c->chol;
     if (cfg.ncomp == 2)
         st = vefd_init_droplet(t, 0.5 * (cfg.nx - 1), 0.5 * (cfg.ny - 1), 0.5 * (cfg.nz - 1),
                                0.25 * std::min(cfg.nx, std::min(cfg.ny, cfg.lattice == VEFD_D3Q19 ? cfg.nz : cfg.ny)),
@@ -996,7 +1022,7 @@ vefd_status ens_fail(vefd_ensemble* e, vefd_status st, const std::string& msg) {
 // choices and the ping-pong parities.
 std::vector<double> ens_key(const vefd_ctx* m) {
     return {m->u_wall, m->fext[0], m->fext[1], m->fext[2], m->tau_p, m->eta_p, m->L2, m->kappa,
-            (double)m->phase, (double)m->fd_on, (double)m->coupling, m->rho_ref[0], m->rho_ref[1],
+            (double)m->phase, (double)m->fd_on, (double)m->coupling, (double)m->collision, (double)m->chol, m->rho_ref[0], m->rho_ref[1],
             (double)m->lat_tile, (double)m->tma_ok, (double)m->zm_ok, (double)m->sched, (double)m->cur,
             (double)m->ccur, (double)m->have_prev, (double)m->drho_valid};
 }

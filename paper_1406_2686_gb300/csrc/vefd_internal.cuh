@@ -131,6 +131,8 @@ struct StepParams {
     float rho_ref[2];      // deviation reference densities
     int prec;              // population storage: kPrecFp32, kPrecFp16, kPrecBf16
     int coupling;          // polymer feedback: 0 body force div Q; 1 stress in the equilibrium
+    int collision;         // 0: single relaxation time; 1: moment space with the paper's rates
+    int chol;              // conformation update: 0 AB2 on C; 1 AB2 on the log-Cholesky factor of f C
 };
 
 // --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------
@@ -203,6 +205,10 @@ cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const St
 // staged tile shape (lattice_tile_shape), and the map's box must match it.
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
                            cudaStream_t s, const void* tensor_map, int rev, int tile);
+// The streaming launch with the moment-space collision (instantiated in its
+// own translation unit); same arguments as launch_lattice.
+cudaError_t launch_lattice_mrt(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                               const void* tensor_map, int rev, int tile);
 // Staged tile shapes of the lattice kernel: tile 0..2 ->
 // D3Q19 32x4x2, 32x2x4, 32x8x1; D2Q9 32x8x1, 32x4x1, 32x16x1.
 void lattice_tile_shape(int lattice, int tile, int* bx, int* by, int* bz);

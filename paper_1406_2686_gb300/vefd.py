@@ -43,7 +43,7 @@ EXPORTS = [
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
     "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
     "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
-    "vefd_ensemble_destroy",
+    "vefd_ensemble_destroy", "vefd_set_collision", "vefd_set_conformation_update",
 ]
 
 _lib = None
@@ -92,6 +92,8 @@ def load(build_if_missing=True):
         "vefd_diagnostics_noalloc": [cint, cint, cint, cint, cint, dbl, vp, vp, vp, vp, vp, ctypes.POINTER(dbl)],
         "vefd_set_polymer_coupling": [vp, cint],
         "vefd_set_kernel_config": [vp, cint, cint],
+        "vefd_set_collision": [vp, cint],
+        "vefd_set_conformation_update": [vp, cint],
         "vefd_get_kernel_config": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)],
         "vefd_autotune": [vp, cint, ctypes.POINTER(dbl)],
         "vefd_ensemble_create": [ctypes.POINTER(vp), cint, vp, ctypes.POINTER(vp)],
@@ -254,6 +256,14 @@ def vefd_diagnostics_noalloc(lattice, nx, ny, nz, ncomp, L2, rho_A, rho_B, u, C,
     return np.array(out[:], dtype=np.float64)
 
 
+def vefd_set_collision(ctx, model):
+    return _check(ctx, load().vefd_set_collision(ctx, int(model)))
+
+
+def vefd_set_conformation_update(ctx, scheme):
+    return _check(ctx, load().vefd_set_conformation_update(ctx, int(scheme)))
+
+
 def vefd_set_kernel_config(ctx, lattice_tile, post_mode):
     return _check(ctx, load().vefd_set_kernel_config(ctx, int(lattice_tile), int(post_mode)))
 
@@ -362,6 +372,12 @@ class Lattice:
 
     def set_polymer_coupling(self, mode):
         vefd_set_polymer_coupling(self.ctx, mode)
+
+    def set_collision(self, model):
+        vefd_set_collision(self.ctx, model)
+
+    def set_conformation_update(self, scheme):
+        vefd_set_conformation_update(self.ctx, scheme)
 
     def init_fields(self, rhoA, rhoB=None, u=None, C=None):
         t = self.torch

@@ -23,7 +23,7 @@ def gpu_fields():
 
 PARAM_DEFAULTS = dict(lattice=1, nx=8, ny=6, nz=5, ncomp=2, walls=1, G=1.5, eta_A=0.2, eta_B=0.3, delta=0.1,
                       u_wall=0.0, fext=(0.0, 0.0, 0.0), tau_p=100.0, eta_p=0.0, L2=100.0, kappa=0.0, phase=0,
-                      fd_on=1, coupling=0)
+                      fd_on=1, coupling=0, collision=0, chol=0)
 
 
 class Pair:
@@ -41,6 +41,8 @@ class Pair:
         self.g.set_body_force(*p["fext"])
         self.g.set_fenep(p["tau_p"], p["eta_p"], p["L2"], p["kappa"], p["phase"], p["fd_on"])
         self.g.set_polymer_coupling(p["coupling"])
+        self.g.set_collision(p["collision"])
+        self.g.set_conformation_update(p["chol"])
         self.gf = gpu_fields()
 
     def init(self, rhoA, rhoB=None, u=None, C=None):

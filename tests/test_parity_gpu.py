@@ -57,6 +57,26 @@ VARIANTS = {
                                 tau_p=20.0, L2=50.0, kappa=0.01, phase=1, coupling=1),
     "d2q9_1c_eqcoupling": dict(lattice=0, nx=37, ny=13, ncomp=1, walls=1, u_wall=0.03, eta_p=0.1, tau_p=30.0,
                                L2=50.0, kappa=0.01, coupling=1),
+    # moment-space collision with the paper's relaxation times (Sec. 2), on the
+    # register, TMA and z-marching paths
+    "d3q19_2c_mrt_walls": dict(lattice=1, nx=35, ny=7, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.04, eta_p=0.12,
+                               tau_p=50.0, L2=100.0, kappa=1e-3, phase=1, fext=(1e-5, 0.0, 2e-6), collision=1),
+    "d3q19_2c_mrt_zm": dict(lattice=1, nx=64, ny=16, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1,
+                            tau_p=20.0, L2=50.0, kappa=0.01, phase=-1, collision=1),
+    "d2q9_2c_mrt_tma": dict(lattice=0, nx=64, ny=13, ncomp=2, walls=0, G=1.5, eta_p=0.1, tau_p=30.0, L2=40.0,
+                            kappa=0.01, phase=-1, collision=1),
+    "d2q9_1c_mrt_walls": dict(lattice=0, nx=37, ny=13, ncomp=1, walls=1, u_wall=0.03, fext=(2e-5, -1e-5, 0.0),
+                              eta_p=0.05, tau_p=40.0, L2=50.0, kappa=0.02, collision=1),
+    # Cholesky scheme for the conformation tensor (Sec. 2)
+    "d3q19_2c_chol_zm": dict(lattice=1, nx=64, ny=16, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1,
+                             tau_p=20.0, L2=50.0, kappa=0.01, phase=1, chol=1),
+    "d2q9_1c_chol_walls": dict(lattice=0, nx=37, ny=13, ncomp=1, walls=1, u_wall=0.03, fext=(2e-5, -1e-5, 0.0),
+                               eta_p=0.05, tau_p=40.0, L2=50.0, kappa=0.02, chol=1),
+    "d3q19_1c_chol_tma": dict(lattice=1, nx=36, ny=10, nz=7, ncomp=1, walls=1, u_wall=0.03, eta_p=0.1, tau_p=20.0,
+                              L2=50.0, kappa=0.01, chol=1),
+    # the paper's combination: moment space, stress in the equilibrium, Cholesky
+    "d3q19_2c_paper": dict(lattice=1, nx=32, ny=8, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.15,
+                           tau_p=20.0, L2=50.0, kappa=0.01, phase=1, coupling=1, collision=1, chol=1),
 }
 
 
@@ -94,7 +114,8 @@ def test_steps_match_oracle(name, nsteps):
 
 
 @pytest.mark.parametrize("name", ["d3q19_2c_tma_ragged", "d2q9_2c_tma_periodic", "d2q9_1c_tma_walls",
-                                  "d3q19_2c_zm_walls", "d3q19_1c_zm_periodic", "d3q19_2c_zm_segments"])
+                                  "d3q19_2c_zm_walls", "d3q19_1c_zm_periodic", "d3q19_2c_zm_segments",
+                                  "d3q19_2c_mrt_zm", "d2q9_2c_mrt_tma", "d3q19_2c_chol_zm", "d3q19_2c_paper"])
 def test_tma_and_register_kernels_agree(name, monkeypatch):
     """The TMA-staged kernels (lattice; densities/FD pass, z-marching where the
     shape allows) and the register-only kernels run the same arithmetic in the
@@ -153,6 +174,23 @@ def test_droplet_2000_steps():
     after 2000 steps the relative L2 error of u and C is within 1e-5 and the
     per-component mass drift within 1e-6."""
     P = _droplet_pair(40, 24, 40, 6.0)
+    m0 = P.g.diagnostics()[:2]
+    P.step(2000)
+    for fld in ("u", "C"):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    m1 = P.g.diagnostics()[:2]
+    assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
+    assert P.g.status() == 0
+
+
+@pytest.mark.parametrize("variant", [dict(collision=1), dict(chol=1), dict(collision=1, coupling=1, chol=1)],
+                         ids=["mrt", "chol", "paper"])
+def test_droplet_2000_steps_variants(variant):
+    """The scaled droplet with the paper-faithful variants of Sec. 2 (moment
+    space collision, Cholesky scheme, stress in the equilibrium): same 1e-5
+    relative L2 contract after 2000 steps and mass drift within 1e-6."""
+    P = _droplet_pair(40, 24, 40, 6.0, **variant)
     m0 = P.g.diagnostics()[:2]
     P.step(2000)
     for fld in ("u", "C"):
@@ -246,10 +284,12 @@ def test_guards_flag_instability():
     assert P.g.status() == 0
 
 
-def test_checkpoint_restore_bit_identical(tmp_path):
-    """A restored context continues bit-identically."""
+@pytest.mark.parametrize("variant", [dict(), dict(collision=1, coupling=1, chol=1)], ids=["default", "paper"])
+def test_checkpoint_restore_bit_identical(tmp_path, variant):
+    """A restored context continues bit-identically (the collision, coupling
+    and conformation scheme are part of the checkpoint)."""
     from paper_1406_2686_gb300 import vefd
-    P = _droplet_pair(24, 16, 20, 4.0)
+    P = _droplet_pair(24, 16, 20, 4.0, **variant)
     P.g.step(7)
     path = str(tmp_path / "ck.bin")
     P.g.checkpoint(path)
