@@ -191,12 +191,20 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_lattice(S):
+# the paper-faithful choices of Sec. 2 (reported beside the headline)
+PAPER_MODEL = dict(collision=1, coupling=1, chol=1)
+
+
+def make_lattice(S, model=None):
     from paper_1406_2686_gb300 import vefd
     lat = vefd.Lattice(lattice=vefd.D3Q19, nx=S.NX, ny=S.NY, nz=S.NZ, ncomp=2, walls=1, G=1.5, eta_A=ETA_A,
                        eta_B=ETA_B, delta=0.1, precision=S.prec)
     lat.set_wall_shear(S.u_wall)
     lat.set_fenep(S.tau_p, ETA_P, 100.0, 1e-3, 1, 1)
+    m = model or {}
+    lat.set_collision(m.get("collision", 0))
+    lat.set_polymer_coupling(m.get("coupling", 0))
+    lat.set_conformation_update(m.get("chol", 0))
     lat.init_droplet((S.NX - 1) / 2.0, (S.NY - 1) / 2.0, (S.NZ - 1) / 2.0, S.R, 2.0, 0.1, 5.0, 1, 1e-3)
     return lat
 
@@ -273,10 +281,10 @@ def replica_throughput(elapsed_ms, nodes_per_rank, steps, device="cpu"):
     return ms, nodes_per_rank * steps * world / (ms / 1e3) / 1e6
 
 
-def time_variant(S, steps, warmup):
-    """MLUPS of one storage variant on the same workload (events on the library stream)."""
+def time_variant(S, steps, warmup, model=None):
+    """MLUPS of one storage or model variant on the same workload (events on the library stream)."""
     import torch
-    lat = make_lattice(S)
+    lat = make_lattice(S, model)
     lat.step(warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -460,8 +468,12 @@ def run_ours(args):
         # NEXT-1 storage variants of the same workload, reported beside the FP32 headline
         vsteps = max(200, K // 5)
         line["variants"] = {pn: time_variant(Setup(S.name, pn), vsteps, min(W, 50)) for pn in ("fp16", "bf16")}
-        line["variants"]["note"] = ("16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
-                                    "and C; %d steps each" % vsteps)
+        for name, model in (("mrt", dict(collision=1)), ("cholesky", dict(chol=1)), ("paper_sec2", PAPER_MODEL)):
+            line["variants"][name] = time_variant(S, vsteps, min(W, 50), model)
+        line["variants"]["note"] = ("fp16/bf16: 16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
+                                    "and C; mrt: moment-space collision with the paper's relaxation times; cholesky: "
+                                    "log-Cholesky conformation update; paper_sec2: both plus the polymer stress in the "
+                                    "equilibrium; %d steps each" % vsteps)
     if not args.no_ensemble and S.prec == 0:
         line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
