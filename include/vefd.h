@@ -203,22 +203,32 @@ vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
  * 1 = 32x2x4, 2 = 32x8x1 nodes (x by y by z); D2Q9 0 = 32x8 (default),
  * 1 = 32x4, 2 = 32x16.  3, 4 and 5 are the same tiles walked by a persistent
  * grid (one block per resident slot on every SM) that double-buffers the
- * staged populations.  post_mode selects the densities / FENE-P pass: 0 =
- * z-marching columns where the shape allows (D3Q19 with NX % 32 == 0 and
- * NY % 8 == 0; default), 1 = 3-D tiles.  Every choice runs the same
- * arithmetic in the same order, so results are bit-identical; a tile the
- * lattice shape does not admit falls back to tile 0, and shapes that admit
- * no staged tile use the unstaged kernels.  Returns VEFD_ERR_ARG for values
- * outside these ranges.  Not to be called while steps are in flight. */
+ * staged populations.  post_mode selects how the densities of the new
+ * populations and the FENE-P update are done: 0 = a column-marching lattice
+ * kernel (32 x 8 columns walked along z) that also sums the new densities,
+ * followed by a z-marching FENE-P pass that adds the populations which
+ * crossed a column side or segment end (D3Q19 with NX % 32 == 0 and
+ * NY % 8 == 0; lattice_tile is then unused; it moves fewer bytes but issues
+ * about 2.7 times the lattice kernel's instructions); 1 = a 3-D tiled
+ * densities/FENE-P pass; 2 (default) = the z-marching densities/FENE-P pass
+ * after the tiled lattice kernel.  Post modes 1 and 2 with tiles 0-2 run the same arithmetic in the
+ * same order and give bit-identical results; the persistent tiles (separately
+ * compiled, multiply-adds contracted as the compiler sees fit) and post mode 0
+ * (each node's new density summed in another order) agree to FP32 rounding.  A tile the lattice shape
+ * does not admit falls back to tile 0, post_mode 0 or 2 falls back to 1 where
+ * the column does not fit, and shapes that admit no staged tile use the
+ * unstaged kernels.  Returns VEFD_ERR_ARG for values outside these ranges.
+ * Not to be called while steps are in flight. */
 vefd_status vefd_set_kernel_config(vefd_ctx *ctx, int lattice_tile, int post_mode);
 /* The configuration in effect: lattice_tile -1 and post_mode -1 mean the
- * unstaged kernels; post_mode 1 also when z-marching is not admitted. */
+ * unstaged kernels; post_mode 1 also when the column does not fit. */
 vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *post_mode);
 /* Times every admitted (lattice_tile, post_mode) pair for `steps` steps on a
  * scratch lattice of the same configuration and parameters (droplet initial
  * state; the context's own state is untouched), then applies the fastest.
- * times_ms (host, 12 doubles or NULL) receives the times, index
- * post_mode * 6 + lattice_tile, -1 for pairs not admitted.  Allocates and
+ * times_ms (host, 18 doubles or NULL) receives the times, index
+ * post_mode * 6 + lattice_tile, -1 for pairs not admitted (post_mode 0 is
+ * timed with lattice_tile 0 only).  Allocates and
  * frees the scratch lattice's device memory and synchronises the context
  * stream.  VEFD_ERR_UNSTABLE when the scratch run trips a guard. */
 vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);

@@ -430,21 +430,26 @@ constexpr int zm_smem_bytes() {
     return NCOMP * 18 * kZmBX * kZmBY * (int)sizeof(PT) + 4 * kZmPlane * (int)sizeof(float);
 }
 
-template <class PT, int NCOMP, bool FD>
+// FUSED: after the column-marching lattice kernel.  drho then holds each
+// node's partial density (the rest population and every population that
+// arrived from inside its 32 x 8 column and lattice-kernel z-segment of
+// length zl); the pass adds, from fnew, the populations that crossed a column
+// side or a segment end, in direction order, and needs no population copy.
+template <class PT, int NCOMP, bool FD, bool FUSED>
 __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
                                                                const float* __restrict__ frest,
                                                                float* __restrict__ drho, const float* __restrict__ Ct,
                                                                float* __restrict__ Cout, float* __restrict__ R,
                                                                const float* __restrict__ u, float* __restrict__ Q,
                                                                unsigned* __restrict__ status, StepParams p, int zs,
-                                                               int rev) {
+                                                               int rev, const PT* __restrict__ fnew, int zl) {
     using L = D3Q19;
     constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = kZmBX * kZmBY;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
     extern __shared__ __align__(128) unsigned char sraw[];
-    PT* sP = reinterpret_cast<PT*>(sraw);                           // [P][BY][BX] populations of the current plane
-    float* ring = reinterpret_cast<float*>(sraw + P * T * sizeof(PT));  // [4][NF][HY][HX]
+    PT* sP = reinterpret_cast<PT*>(sraw);  // [P][BY][BX] populations of the current plane (not FUSED)
+    float* ring = reinterpret_cast<float*>(sraw + (FUSED ? 0 : P * T * sizeof(PT)));  // [4][NF][HY][HX]
     __shared__ __align__(8) unsigned long long bar;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -518,11 +523,12 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
     const int rym = wall_lo ? ry : ry - 1, ryp = wall_hi ? ry : ry + 1;
     const int t = ty * kZmBX + tx;
 
+    const ColumnTopo topo{nx == 32, ny == 8 && !p.walls, nz == 1};
     for (int k = 0; k < z1 - z0; ++k) {
         const int z = z0 + k;
         // new populations of this plane: one bulk copy (the buffer was released
         // by every thread at the barrier ending the previous iteration)
-        if (leader) {
+        if (!FUSED && leader) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tma_load_4d(smem_u32(sP), &tm_fnew, x0, y0, z, 0, bar_a, kBytes);
         }
@@ -531,8 +537,29 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
         if (more) load_plane(z + 2, vi, vh);
         const int i = z * plane + y * nx + x;
         float rest[NCOMP];
+        if (FUSED) {
+            // partial density plus what crossed a column side or a segment end
+            const bool wlo = p.walls && y == 0, whi = p.walls && y == ny - 1;
+            const int zs_lo = (z / zl) * zl, zs_hi = min(zs_lo + zl, nz);  // this plane's lattice-kernel segment
 #pragma unroll
-        for (int s = 0; s < NCOMP; ++s) rest[s] = __ldg(frest + s * N + i);
+            for (int s = 0; s < NCOMP; ++s) {
+                float d = drho[s * N + i];
+#pragma unroll
+                for (int a = 1; a < L::Q; ++a) {
+                    const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+                    if ((cy > 0 && wlo) || (cy < 0 && whi)) continue;  // bounce-back: counted in the partial
+                    const int zsrc = z - cz;
+                    const bool same_seg = topo.nz1 || (zsrc >= zs_lo && zsrc < zs_hi);
+                    const bool same_col = (topo.nx32 || (unsigned)(tx - cx) < 32u) && (topo.ny8p || (unsigned)(ty - cy) < 8u);
+                    if (same_seg && same_col) continue;
+                    d += pop_get(fnew[(s * (L::Q - 1) + a - 1) * N + i]);
+                }
+                rest[s] = d;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < NCOMP; ++s) rest[s] = __ldg(frest + s * N + i);
+        }
         float c[6];
         if (FD) {
             const float* pm = ring + (k % 4) * kZmPlane;
@@ -566,18 +593,29 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
             for (int q = 0; q < 6; ++q) c[q] = pc[(q * kZmHY + ry) * kZmHX + rc];
         }
         // densities of the new populations (same summation order as elsewhere)
-        const bool ok = mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));
-        if (__syncthreads_or(!ok)) {
-            if (leader) atomicOr(status, kStTimeout);
-            return;
-        }
         float d[NCOMP];
+        if (FUSED) {
 #pragma unroll
-        for (int s = 0; s < NCOMP; ++s) {
-            d[s] = rest[s];
+            for (int s = 0; s < NCOMP; ++s) {
+                d[s] = rest[s];
+                drho[s * N + i] = d[s];
+            }
+        } else {
+            const bool ok = mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));
+            if (__syncthreads_or(!ok)) {
+                if (leader) {
+                    atomicOr(status, kStTimeout);
+                    mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));  // bounded: let the copy land
+                }
+                return;
+            }
 #pragma unroll
-            for (int a = 1; a < L::Q; ++a) d[s] += pop_get(sP[(s * (L::Q - 1) + a - 1) * T + t]);
-            drho[s * N + i] = d[s];
+            for (int s = 0; s < NCOMP; ++s) {
+                d[s] = rest[s];
+#pragma unroll
+                for (int a = 1; a < L::Q; ++a) d[s] += pop_get(sP[(s * (L::Q - 1) + a - 1) * T + t]);
+                drho[s * N + i] = d[s];
+            }
         }
         if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
         if (more) store_plane((k + 3) % 4, vi, vh);
@@ -673,13 +711,13 @@ bool post_zm_eligible(int lattice, int nx, int ny) { return lattice == 1 && nx %
 namespace {
 int g_sm_count = 0;
 
-template <class PT, int NCOMP, bool FD>
-cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev) {
-    constexpr int smem = zm_smem_bytes<PT, NCOMP>();
+template <class PT, int NCOMP, bool FD, bool FUSED>
+cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev, int zl) {
+    constexpr int smem = FUSED ? 4 * kZmPlane * (int)sizeof(float) : zm_smem_bytes<PT, NCOMP>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_post_zm<PT, NCOMP, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_post_zm<PT, NCOMP, FD, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -696,7 +734,12 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     const int zs = (p.nz + nzb - 1) / nzb;
     nzb = (p.nz + zs - 1) / zs;
     dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, p.ny / kZmBY, nzb);
-    k_post_zm<PT, NCOMP, FD><<<grd, blk, smem, s>>>(*tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p, zs, rev);
+    // FUSED reads the partial densities of the new time level and completes them in place
+    float* dens = FUSED ? b.drho_next : b.drho;
+    const CUtensorMap dummy{};
+    k_post_zm<PT, NCOMP, FD, FUSED><<<grd, blk, smem, s>>>(FUSED ? dummy : *tm, b.frest, dens, b.Cin, b.Cout, b.R, b.u,
+                                                           b.Q, b.status, p, zs, rev,
+                                                           static_cast<const PT*>(b.fout), zl);
     return cudaGetLastError();
 }
 }  // namespace
@@ -706,8 +749,22 @@ cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBu
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map_fnew);
     cudaError_t e = cudaSuccess;
     VEFD_WITH_PT(p.prec, {
-        if (ncomp == 2) e = fd ? post_zm<PT, 2, true>(tm, p, b, s, rev) : post_zm<PT, 2, false>(tm, p, b, s, rev);
-        else e = fd ? post_zm<PT, 1, true>(tm, p, b, s, rev) : post_zm<PT, 1, false>(tm, p, b, s, rev);
+        if (ncomp == 2)
+            e = fd ? post_zm<PT, 2, true, false>(tm, p, b, s, rev, 1) : post_zm<PT, 2, false, false>(tm, p, b, s, rev, 1);
+        else
+            e = fd ? post_zm<PT, 1, true, false>(tm, p, b, s, rev, 1) : post_zm<PT, 1, false, false>(tm, p, b, s, rev, 1);
+    });
+    return e;
+}
+
+cudaError_t launch_post_zm_fused(int ncomp, bool fd, const StepParams& p, const StepBufs& b, cudaStream_t s, int zs,
+                                 int rev) {
+    cudaError_t e = cudaSuccess;
+    VEFD_WITH_PT(p.prec, {
+        if (ncomp == 2)
+            e = fd ? post_zm<PT, 2, true, true>(nullptr, p, b, s, rev, zs) : post_zm<PT, 2, false, true>(nullptr, p, b, s, rev, zs);
+        else
+            e = fd ? post_zm<PT, 1, true, true>(nullptr, p, b, s, rev, zs) : post_zm<PT, 1, false, true>(nullptr, p, b, s, rev, zs);
     });
     return e;
 }

@@ -305,21 +305,16 @@ __device__ __forceinline__ void pi_add(float pi[6], int a, float fa) {
 // 3c^2 - 4, c_x^2 - c_y^2, c_x c_y with norms 36, 4, 4).  The bracket is even
 // in c, so pairs are again relaxed together and the populations enter only
 // through Pi(f).
-template <class PT, class L, int NCOMP, int COLL, class FGet>
-__device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
-                                               const Local<NCOMP>& st, const float qloc[L::NQ],
-                                               const float (*pif)[6], FGet fget) {
-    const int N = (int)p.N;
-    const int node = nb.i;
-    const int* ox = nb.ox;
-    const int* oz = nb.oz;
-    // streaming offsets in y are periodic (walls are handled by bounce-back)
-    const int nx = p.nx;
-    int oy[3];
-    const bool wall_lo = p.walls && nb.y == 0, wall_hi = p.walls && nb.y == nb.ny - 1;
-    oy[0] = (nb.y == 0 ? nb.ny - 1 : -1) * nx;
-    oy[1] = 0;
-    oy[2] = (nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
+//
+// collide_emit computes every pair's post-collision values, applies the
+// moving-wall term to a population that leaves through a wall (it returns to
+// this node in the opposite direction), rounds to the storage type and hands
+// the stored values to emit(s, a, va, vb, bounced_a, bounced_b) for a and its
+// opposite a + 1; rest[s] receives the component's rest population.
+template <class PT, class L, int NCOMP, int COLL, class FGet, class Emit>
+__device__ __forceinline__ void collide_emit(const StepParams& p, const Local<NCOMP>& st, const float qloc[L::NQ],
+                                             const float (*pif)[6], bool wall_lo, bool wall_hi, FGet fget, Emit emit,
+                                             float rest[NCOMP]) {
     const float uw6 = 6.0f * p.u_wall;  // 2 (c.U) / c_s^2 with U = +-u_wall along x
     const float keep = 1.0f - st.omega;
     constexpr bool mrt = COLL == 1;
@@ -401,9 +396,6 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
             // w (c c - c_s^2 I):T / (2 c_s^4) = 4.5 w (c.T.c - tr T / 3), relaxed with omega
             tqo = 4.5f * st.tq[s] * st.omega;
         }
-        // moving populations: plane a - 1 of component s; the rest population
-        // stays at the node, in FP32, and is updated in place
-        PT* out = static_cast<PT*>(b.fout) + (long long)s * (L::Q - 1) * N - N;
         // The collision and the wall exchange conserve mass exactly (the source
         // has no zeroth moment; the moving-wall terms of a node sum to zero), so
         // the rest population is taken as the remainder after the moving ones
@@ -452,30 +444,54 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
                 // a streams to x + c, its opposite to x - c; a population leaving
                 // through a wall returns to this node in the opposite direction with
                 // the moving-wall term -2 w rho_s (c.U)/c_s^2 (+U lower, -U upper)
-                if ((cy > 0 && wall_hi) || (cy < 0 && wall_lo)) {
-                    const float Uw = cy < 0 ? uw6 : -uw6;
-                    const PT v = pop_put<PT>(fa - wrs * (float)cx * Uw);
-                    out[ab * N + node] = v;
-                    moved += pop_get(v);
-                } else {
-                    const PT v = pop_put<PT>(fa);
-                    out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = v;
-                    moved += pop_get(v);
-                }
-                if ((cy < 0 && wall_hi) || (cy > 0 && wall_lo)) {
-                    const float Uw = cy > 0 ? uw6 : -uw6;
-                    const PT v = pop_put<PT>(fb + wrs * (float)cx * Uw);
-                    out[a * N + node] = v;
-                    moved += pop_get(v);
-                } else {
-                    const PT v = pop_put<PT>(fb);
-                    out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = v;
-                    moved += pop_get(v);
-                }
+                const bool ba = (cy > 0 && wall_hi) || (cy < 0 && wall_lo);
+                const bool bb = (cy < 0 && wall_hi) || (cy > 0 && wall_lo);
+                const PT va = pop_put<PT>(ba ? fa - wrs * (float)cx * (cy < 0 ? uw6 : -uw6) : fa);
+                moved += pop_get(va);
+                const PT vb = pop_put<PT>(bb ? fb + wrs * (float)cx * (cy > 0 ? uw6 : -uw6) : fb);
+                moved += pop_get(vb);
+                emit(s, a, va, vb, ba, bb);
             }
         }
-        b.frest[s * N + node] = drs - moved;
+        rest[s] = drs - moved;
     }
+}
+
+// Collision and push streaming: each stored value goes to its destination
+// node (periodic offsets in x, y, z), a bounced one to this node's opposite
+// direction; the rest population is updated in place.
+template <class PT, class L, int NCOMP, int COLL, class FGet>
+__device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
+                                               const Local<NCOMP>& st, const float qloc[L::NQ],
+                                               const float (*pif)[6], FGet fget) {
+    const int N = (int)p.N;
+    const int node = nb.i;
+    const int* ox = nb.ox;
+    const int* oz = nb.oz;
+    // streaming offsets in y are periodic (walls are handled by bounce-back)
+    const int nx = p.nx;
+    int oy[3];
+    const bool wall_lo = p.walls && nb.y == 0, wall_hi = p.walls && nb.y == nb.ny - 1;
+    oy[0] = (nb.y == 0 ? nb.ny - 1 : -1) * nx;
+    oy[1] = 0;
+    oy[2] = (nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
+    float rest[NCOMP];
+    collide_emit<PT, L, NCOMP, COLL>(
+        p, st, qloc, pif, wall_lo, wall_hi, fget,
+        [&](int s, int a, PT va, PT vb, bool ba, bool bb) {
+            // moving populations: plane a - 1 of component s
+            PT* out = static_cast<PT*>(b.fout) + (long long)s * (L::Q - 1) * N - N;
+            const int ab = a + 1;
+            const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+            if (ba) out[ab * N + node] = va;
+            else out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = va;
+            if (bb) out[a * N + node] = vb;
+            else out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
+        },
+        rest);
+    // the rest population stays at the node, in FP32, and is updated in place
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) b.frest[s * N + node] = rest[s];
 }
 
 template <class PT, class L, int NCOMP, bool STREAM, int COLL>
@@ -722,6 +738,161 @@ cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const St
     return cudaGetLastError();
 }
 
+// Column-marching form (D3Q19, NX % 32 == 0, NY % 8 == 0) that also yields
+// the densities of the new populations, so the densities pass does not read
+// them again.  A block owns a 32 x 8 column and walks the planes [z0, z1) of
+// its z-segment; per plane:
+//   1. one TMA copy stages the plane's moving populations f^n (box 32 x 8 x 1
+//      x P) while the threads gather neighbour densities and feedback stress;
+//   2. each thread collides its node and writes the values leaving the node
+//      back into its own staging slots (bounced ones with the wall term);
+//      values bound for another column or segment are stored straight to
+//      their destination nodes in global memory;
+//   3. after a barrier each thread pulls, for its own (x, y), the values
+//      arriving from inside the column: at (x, y, z + c_z) from
+//      (x - c_x, y - c_y, z), and bounce-backs at (x, y, z); it stores them
+//      (aligned, coalesced rows) and adds them, with the rest population, to
+//      partial densities of planes z - 1, z, z + 1 in a fixed order;
+//   4. plane z - 1 has then received everything from inside the segment and
+//      its partial density is written to b.drho_next.
+template <class PT, int NCOMP, int COLL>
+__global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
+    k_lattice_zm(const __grid_constant__ CUtensorMap tm_fin, StepBufs b, StepParams p, int zs, int rev) {
+    using L = D3Q19;
+    constexpr int P = NCOMP * (L::Q - 1);
+    constexpr int T = 256;
+    constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
+    extern __shared__ __align__(128) unsigned char sraw[];
+    PT* sP = reinterpret_cast<PT*>(sraw);  // [P][8][32]: f^n of the plane, then the values leaving each node
+    __shared__ __align__(8) unsigned long long bar;
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+    const int nx = p.nx, ny = p.ny, nz = p.nz, N = (int)p.N;
+    const int x0 = tile_index(blockIdx.x, gridDim.x, rev) * 32;
+    const int y0 = tile_index(blockIdx.y, gridDim.y, rev) * 8;
+    const int z0 = tile_index(blockIdx.z, gridDim.z, rev) * zs;
+    const int z1 = min(z0 + zs, nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool leader = t == 0;
+    const unsigned bar_a = smem_u32(&bar);
+    if (leader) mbar_init(bar_a);
+    __syncthreads();
+    const ColumnTopo topo{nx == 32, ny == 8 && !p.walls, nz == 1};
+    const bool wall_lo = p.walls && y == 0, wall_hi = p.walls && y == ny - 1;
+    PT* fout = static_cast<PT*>(b.fout);
+    float pm[NCOMP], pc[NCOMP], pn[NCOMP];  // partial densities of planes z - 1, z, z + 1
+#pragma unroll
+    for (int s = 0; s < NCOMP; ++s) pm[s] = pc[s] = pn[s] = 0.0f;
+    for (int k = 0; k < z1 - z0; ++k) {
+        const int z = z0 + k;
+        if (leader) {
+            // every thread released the buffer at the barrier ending the previous plane
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_load_4d(smem_u32(sP), &tm_fin, x0, y0, z, 0, bar_a, kBytes);
+        }
+        NodeGather<L, NCOMP> g;
+        node_gather<L, NCOMP>(b, p, x, y, z, true, g);
+        const bool ok = mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));
+        if (__syncthreads_or(!ok)) {
+            if (leader) {
+                atomicOr(b.status, kStTimeout);
+                mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));  // bounded: let the copy land before leaving
+            }
+            return;
+        }
+        const int node = g.nb.i;
+        // moments of the staged populations (second moments for the moment-space collision)
+        float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+        float pif[NCOMP][6];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) pif[s][q] = 0.0f;
+#pragma unroll
+            for (int a = 1; a < L::Q; ++a) {
+                const float fa = pop_get(sP[(s * (L::Q - 1) + a - 1) * T + t]);
+                if (L::cx(a)) jx += L::cx(a) * fa;
+                if (L::cy(a)) jy += L::cy(a) * fa;
+                if (L::cz(a)) jz += L::cz(a) * fa;
+                if (COLL == 1) pi_add<L>(pif[s], a, fa);
+            }
+        }
+        Local<NCOMP> st;
+        local_state<L, NCOMP>(p, g.dr, jx, jy, jz, g.acc, g.Fp, st, b.status);
+        b.u[node] = st.ux;
+        b.u[N + node] = st.uy;
+        b.u[2 * N + node] = st.uz;
+        float rest[NCOMP];
+        collide_emit<PT, L, NCOMP, COLL>(
+            p, st, g.qloc, pif, wall_lo, wall_hi,
+            [&](int s, int a) { return pop_smem(sP, (s * (L::Q - 1) + a - 1) * T + t); },
+            [&](int s, int a, PT va, PT vb, bool ba, bool bb) {
+                const int ab = a + 1;
+                const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+                // this thread's own slots: its reads of them are done
+                sP[(s * (L::Q - 1) + a - 1) * T + t] = va;
+                sP[(s * (L::Q - 1) + ab - 1) * T + t] = vb;
+                if (!ba && !zm_inner(tx + cx, ty + cy, z + cz, z0, z1, topo)) {
+                    const int xd = wrap1(x + cx, nx), yd = wrap1(y + cy, ny), zd = wrap1(z + cz, nz);
+                    fout[(long long)(s * (L::Q - 1) + a - 1) * N + (zd * ny + yd) * nx + xd] = va;
+                }
+                if (!bb && !zm_inner(tx - cx, ty - cy, z - cz, z0, z1, topo)) {
+                    const int xd = wrap1(x - cx, nx), yd = wrap1(y - cy, ny), zd = wrap1(z - cz, nz);
+                    fout[(long long)(s * (L::Q - 1) + ab - 1) * N + (zd * ny + yd) * nx + xd] = vb;
+                }
+            },
+            rest);
+        // the rest population stays at the node, in FP32, updated in place
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) {
+            b.frest[s * N + node] = rest[s];
+            pc[s] += rest[s];
+        }
+        __syncthreads();
+        // values arriving at this (x, y) from inside the column and segment
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) {
+#pragma unroll
+            for (int a = 1; a < L::Q; ++a) {
+                const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+                const long long plane_a = (long long)(s * (L::Q - 1) + a - 1) * N;
+                if ((cy > 0 && wall_lo) || (cy < 0 && wall_hi)) {
+                    // the opposite population left through the wall and came back
+                    const PT v = sP[(s * (L::Q - 1) + opposite(a) - 1) * T + t];
+                    fout[plane_a + node] = v;
+                    pc[s] += pop_get(v);
+                } else if (zm_inner(tx - cx, ty - cy, z + cz, z0, z1, topo)) {
+                    const int src = ((ty - cy) & 7) * 32 + ((tx - cx) & 31);
+                    const PT v = sP[(s * (L::Q - 1) + a - 1) * T + src];
+                    const int zd = topo.nz1 ? z : z + cz;
+                    fout[plane_a + (zd * ny + y) * nx + x] = v;
+                    const float fv = pop_get(v);
+                    if (cz == 0 || topo.nz1) pc[s] += fv;
+                    else if (cz < 0) pm[s] += fv;
+                    else pn[s] += fv;
+                }
+            }
+        }
+        // plane z - 1 is complete within the segment
+        if (k > 0) {
+#pragma unroll
+            for (int s = 0; s < NCOMP; ++s) b.drho_next[s * N + node - nx * ny] = pm[s];
+        }
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) {
+            pm[s] = pc[s];
+            pc[s] = pn[s];
+            pn[s] = 0.0f;
+        }
+        __syncthreads();  // the pulls are done before the next copy overwrites the buffer
+    }
+    // the segment's last plane: what arrives from the next segment comes through memory
+    if (z1 > z0) {
+        const int node = ((z1 - 1) * ny + y) * nx + x;
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) b.drho_next[s * N + node] = pm[s];
+    }
+}
+
 inline int lattice_sm_count() {
     static int n = 0;
     if (!n) {
@@ -753,6 +924,36 @@ cudaError_t launch_pers_tile(const CUtensorMap* tm, const StepParams& p, const S
     k_lattice_pers<PT, L, NCOMP, BX, BY, BZ><<<(unsigned)grid, dim3(BX, BY, BZ), smem, s>>>(*tm, b, p, rev, ntx, nty,
                                                                                          (int)ntiles);
     return cudaGetLastError();
+}
+
+// Segment length of the column-marching kernel: one wave of
+// (SMs x resident blocks) blocks over the columns and z-segments.
+inline int zm_segment_length(const StepParams& p) {
+    const int cols = (p.nx / 32) * (p.ny / 8);
+    int nseg = (VEFD_LATTICE_THREADS_PER_SM / 256) * lattice_sm_count() / (cols > 0 ? cols : 1);
+    if (nseg < 1) nseg = 1;
+    if (nseg > p.nz) nseg = p.nz;
+    return (p.nz + nseg - 1) / nseg;
+}
+
+template <class PT, int NCOMP, int COLL>
+cudaError_t launch_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int zs, int rev, cudaStream_t s) {
+    constexpr int smem = NCOMP * 18 * 256 * (int)sizeof(PT);
+    static_assert(smem <= 48 * 1024, "the staged plane must fit the default shared-memory limit");
+    dim3 blk(32, 8, 1), grd(p.nx / 32, p.ny / 8, (p.nz + zs - 1) / zs);
+    k_lattice_zm<PT, NCOMP, COLL><<<grd, blk, smem, s>>>(*tm, b, p, zs, rev);
+    return cudaGetLastError();
+}
+
+template <int COLL>
+cudaError_t launch_zm_coll(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s, const void* tensor_map,
+                           int zs, int rev) {
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map);
+    cudaError_t e = cudaSuccess;
+    VEFD_WITH_PT(p.prec, {
+        e = ncomp == 2 ? launch_zm<PT, 2, COLL>(tm, p, b, zs, rev, s) : launch_zm<PT, 1, COLL>(tm, p, b, zs, rev, s);
+    });
+    return e;
 }
 
 // Tiles 0..2 staged per block; 3..5 the persistent forms (single relaxation

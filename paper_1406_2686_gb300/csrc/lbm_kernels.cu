@@ -151,6 +151,14 @@ cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepP
     return cudaGetLastError();
 }
 
+cudaError_t launch_lattice_zm(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                              const void* tensor_map, int zs, int rev) {
+    if (p.collision == 1) return launch_lattice_zm_mrt(ncomp, p, b, s, tensor_map, zs, rev);
+    return launch_zm_coll<0>(ncomp, p, b, s, tensor_map, zs, rev);
+}
+
+int lattice_zm_segment(const StepParams& p) { return zm_segment_length(p); }
+
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
                                     const float* rhoB, const float* u, void* fd, float* frest, cudaStream_t s) {
     const int g = grid_1d(p.N);

@@ -10,4 +10,9 @@ cudaError_t launch_lattice_mrt(int lattice, int ncomp, const StepParams& p, cons
     return launch_lattice_coll<1>(lattice, ncomp, p, b, s, tensor_map, rev, tile);
 }
 
+cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                                  const void* tensor_map, int zs, int rev) {
+    return launch_zm_coll<1>(ncomp, p, b, s, tensor_map, zs, rev);
+}
+
 }  // namespace vefd

@@ -2,6 +2,7 @@
 // field I/O, time stepping, diagnostics and checkpoints of the hybrid
 // lattice-Boltzmann / finite-difference viscoelastic step.
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -43,7 +44,8 @@ struct vefd_ctx {
     void* f[2] = {nullptr, nullptr};  // moving population deviations, storage type of cfg.precision
     float* frest = nullptr;           // rest population deviations (FP32, updated in place)
     size_t psize = 4;                 // bytes per stored population value
-    float* drho = nullptr;
+    float* drho = nullptr;      // densities of the current time level
+    float* drho_alt = nullptr;  // the other density buffer (column-marching step writes the next level here)
     float* u = nullptr;
     float* C[2] = {nullptr, nullptr};
     float* R = nullptr;
@@ -58,10 +60,13 @@ struct vefd_ctx {
     alignas(64) CUtensorMap tmap_post[2];  // densities/FD pass (3-D tile variant): box 32x4x2 or 32x8x1
     bool tma_ok = false;
     int lat_tile = 0;                      // staged tile shape of the lattice kernel (lattice_tile_shape)
-    int post_mode = 0;                     // densities/FD pass: 0 z-marching when possible, 1 3-D tile
+    int post_mode = 2;                     // 0 column march with fused densities, 1 3-D tiles, 2 separate z-march pass
     // tensor maps with a 32 x 8 x 1 box for the z-marching densities/FD pass
     alignas(64) CUtensorMap tmap_zm[2];
     bool zm_ok = false;
+    // column-marching lattice kernel with the densities fused in (post_mode 0)
+    bool fused_ok = false;
+    int zm_seg_fixed = 0;  // z-segment length of the column march (0: one wave of blocks)
     // densities and feedback stress of the current state are in drho and Q
     bool drho_valid = false;
     // tile traversal: bit0 lattice kernel backwards, bit1 densities/FD kernel
@@ -142,7 +147,7 @@ Layout layout_of(const vefd_config* c) {
     L.f0 = take(ps * c->ncomp * (Q - 1) * N);
     L.f1 = take(ps * c->ncomp * (Q - 1) * N);
     L.frest = take(sizeof(float) * c->ncomp * N);
-    L.drho = take(sizeof(float) * 2 * N);
+    L.drho = take(sizeof(float) * 4 * N);
     L.u = take(sizeof(float) * 3 * N);
     L.c0 = take(sizeof(float) * NC * N);
     L.c1 = take(sizeof(float) * NC * N);
@@ -165,6 +170,7 @@ void carve(vefd_ctx* c) {
     c->f[1] = b + L.f1;
     c->frest = (float*)(b + L.frest);
     c->drho = (float*)(b + L.drho);
+    c->drho_alt = c->drho + 2 * (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz;
     c->u = (float*)(b + L.u);
     c->C[0] = (float*)(b + L.c0);
     c->C[1] = (float*)(b + L.c1);
@@ -177,6 +183,7 @@ void carve(vefd_ctx* c) {
     c->tma_ok = false;
     build_tensor_maps(c);
     if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
+    if (const char* e = getenv("VEFD_ZM_SEGMENT")) c->zm_seg_fixed = atoi(e) > 0 ? atoi(e) : 0;
 }
 
 // (Re)builds the TMA descriptors of both population buffers for the selected
@@ -187,6 +194,7 @@ void build_tensor_maps(vefd_ctx* c) {
     const int lat = c->cfg.lattice, nc = c->cfg.ncomp, nx = c->cfg.nx, ny = c->cfg.ny, nz = c->cfg.nz;
     c->tma_ok = false;
     c->zm_ok = false;
+    c->fused_ok = false;
     if (getenv("VEFD_NO_TMA") || !pop_tile_eligible(lat, prec, nx, ny, nz, 0)) return;
     // the densities/FD pass keeps the default tile
     if (!(make_pop_tensor_map(lat, nc, prec, nx, ny, nz, c->f[0], &c->tmap_post[0]) &&
@@ -200,11 +208,12 @@ void build_tensor_maps(vefd_ctx* c) {
           make_pop_tensor_map_box(lat, nc, prec, nx, ny, nz, c->f[1], bx, by, bz, &c->tmap[1])))
         return;
     c->tma_ok = true;
-    if (c->post_mode == 0 && !getenv("VEFD_NO_ZMARCH") && post_zm_eligible(lat, nx, ny)) {
+    if (c->post_mode != 1 && !getenv("VEFD_NO_ZMARCH") && post_zm_eligible(lat, nx, ny)) {
         c->zm_ok = make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
                                            c->f[0], 32, 8, 1, &c->tmap_zm[0]) &&
                    make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
                                            c->f[1], 32, 8, 1, &c->tmap_zm[1]);
+        c->fused_ok = c->zm_ok && c->post_mode == 0 && !getenv("VEFD_NO_FUSED");
     }
 }
 
@@ -243,6 +252,7 @@ StepBufs bufs_of(vefd_ctx* c) {
     b.fout = c->f[1 - c->cur];
     b.frest = c->frest;
     b.drho = c->drho;
+    b.drho_next = c->drho_alt;
     b.u = c->u;
     b.Cin = c->C[c->ccur];
     b.Cout = c->C[1 - c->ccur];
@@ -591,6 +601,28 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
             ProfScope ps(c, 0);
             VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
         }
+        if (c->fused_ok) {
+            // populations n -> n+1, velocity of time n and the partial densities of
+            // n+1; then the densities completed, and the FENE-P update
+            const int zs = c->zm_seg_fixed > 0 ? std::min(c->zm_seg_fixed, c->cfg.nz) : lattice_zm_segment(p);
+            {
+                ProfScope ps(c, 1);
+                VEFD_CUDA(c, launch_lattice_zm(c->cfg.ncomp, p, b, c->stream, &c->tmap_zm[c->cur], zs, lat_rev));
+            }
+            {
+                ProfScope ps(c, 2);
+                VEFD_CUDA(c, launch_post_zm_fused(c->cfg.ncomp, c->fd_on != 0, p, b, c->stream, zs, post_rev));
+            }
+            std::swap(c->drho, c->drho_alt);
+            if (c->fd_on) {
+                c->ccur ^= 1;
+                c->have_prev = 1;
+            }
+            c->drho_valid = true;
+            c->cur ^= 1;
+            c->steps++;
+            continue;
+        }
         {
             // populations n -> n+1, velocity of time n
             ProfScope ps(c, 1);
@@ -907,7 +939,7 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
 vefd_status vefd_set_kernel_config(vefd_ctx* c, int lattice_tile, int post_mode) {
     if (!c) return VEFD_ERR_ARG;
     if (lattice_tile < 0 || lattice_tile > 5) return fail(c, VEFD_ERR_ARG, "lattice_tile must be in 0..5");
-    if (post_mode < 0 || post_mode > 1) return fail(c, VEFD_ERR_ARG, "post_mode must be 0 or 1");
+    if (post_mode < 0 || post_mode > 2) return fail(c, VEFD_ERR_ARG, "post_mode must be 0, 1 or 2");
     c->lat_tile = lattice_tile;
     c->post_mode = post_mode;
     if (c->mem) build_tensor_maps(c);
@@ -917,7 +949,7 @@ vefd_status vefd_set_kernel_config(vefd_ctx* c, int lattice_tile, int post_mode)
 vefd_status vefd_get_kernel_config(const vefd_ctx* c, int* lattice_tile, int* post_mode) {
     if (!c || !lattice_tile || !post_mode) return VEFD_ERR_ARG;
     *lattice_tile = c->tma_ok ? c->lat_tile : -1;
-    *post_mode = c->zm_ok ? 0 : (c->tma_ok ? 1 : -1);
+    *post_mode = c->fused_ok ? 0 : (c->zm_ok ? 2 : (c->tma_ok ? 1 : -1));
     return VEFD_OK;
 }
 
@@ -925,7 +957,7 @@ vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
     if (!c || steps < 1) return fail(c, VEFD_ERR_ARG, "steps must be >= 1");
     if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
     if (times_ms)
-        for (int k = 0; k < 12; ++k) times_ms[k] = -1.0;
+        for (int k = 0; k < 18; ++k) times_ms[k] = -1.0;
     // scratch lattice of the same shape and parameters, so the context's own
     // state is not advanced
     vefd_config cfg = c->cfg;
@@ -957,12 +989,13 @@ vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
     int best_tile = c->lat_tile, best_post = c->post_mode;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == VEFD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = VEFD_ERR_CUDA;
-    for (int pm = 0; pm < 2 && st == VEFD_OK; ++pm)
+    for (int pm = 0; pm < 3 && st == VEFD_OK; ++pm)
         for (int tile = 0; tile < 6 && st == VEFD_OK; ++tile) {
             if (!pop_tile_eligible(cfg.lattice, cfg.precision, cfg.nx, cfg.ny, cfg.nz, tile)) continue;
-            if (pm == 0 && !post_zm_eligible(cfg.lattice, cfg.nx, cfg.ny)) continue;
+            if (pm != 1 && !post_zm_eligible(cfg.lattice, cfg.nx, cfg.ny)) continue;
             vefd_set_kernel_config(t, tile, pm);
             if (!t->tma_ok) continue;
+            if (pm == 0 && (!t->fused_ok || tile != 0)) continue;  // the column march has its own tile
             st = vefd_step(t, 2);  // warm the configuration
             if (st != VEFD_OK) break;
             cudaEventRecord(e0, t->stream);
@@ -1023,7 +1056,8 @@ vefd_status ens_fail(vefd_ensemble* e, vefd_status st, const std::string& msg) {
 std::vector<double> ens_key(const vefd_ctx* m) {
     return {m->u_wall, m->fext[0], m->fext[1], m->fext[2], m->tau_p, m->eta_p, m->L2, m->kappa,
             (double)m->phase, (double)m->fd_on, (double)m->coupling, (double)m->collision, (double)m->chol, m->rho_ref[0], m->rho_ref[1],
-            (double)m->lat_tile, (double)m->tma_ok, (double)m->zm_ok, (double)m->sched, (double)m->cur,
+            (double)m->lat_tile, (double)m->tma_ok, (double)m->zm_ok, (double)m->fused_ok,
+            (double)(m->drho < m->drho_alt), (double)m->sched, (double)m->cur,
             (double)m->ccur, (double)m->have_prev, (double)m->drho_valid};
 }
 
@@ -1082,8 +1116,11 @@ vefd_status ens_capture(vefd_ensemble* e, int64_t chunk) {
     std::vector<int64_t> steps(n);
     std::vector<cudaStream_t> own(n);
     std::vector<bool> prof(n);
+    std::vector<float*> dr(n), dra(n);
     for (size_t k = 0; k < n; ++k) {
         vefd_ctx* m = e->members[k];
+        dr[k] = m->drho;
+        dra[k] = m->drho_alt;
         cur[k] = m->cur;
         ccur[k] = m->ccur;
         hp[k] = m->have_prev;
@@ -1118,6 +1155,8 @@ vefd_status ens_capture(vefd_ensemble* e, int64_t chunk) {
         m->steps = steps[k];
         m->stream = own[k];
         m->prof_on = prof[k];
+        m->drho = dr[k];
+        m->drho_alt = dra[k];
     }
     if (st != VEFD_OK || ce != cudaSuccess || ce2 != cudaSuccess || !graph) {
         if (graph) cudaGraphDestroy(graph);

@@ -177,6 +177,25 @@ __device__ __forceinline__ bool mbar_wait_bounded_parity(unsigned bar, unsigned 
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar) { return mbar_wait_bounded_parity(bar, 0u); }
 
+// --- column-marching step with fused densities (D3Q19) ----------------------
+// The lattice kernel k_lattice_zm walks 32 x 8 columns along z in segments of
+// planes [z0, z1).  A population that moves from a source node to a
+// destination node inside the same column and segment is stored by the
+// destination's thread and counted in that node's partial density; every other
+// population (crossing a column side or a segment end) is stored by the
+// source's thread, and the densities pass adds it.  Half-way bounce-back
+// returns to the node itself and always counts as inside.  `lane` and `row`
+// are column-relative, before wrapping.
+struct ColumnTopo {
+    bool nx32;  // NX == 32: the column spans x (periodic wrap inside the warp)
+    bool ny8p;  // NY == 8 and periodic in y: the column spans y
+    bool nz1;   // NZ == 1: z neighbours are the plane itself
+};
+
+__device__ __forceinline__ bool zm_inner(int lane, int row, int zp, int z0, int z1, ColumnTopo t) {
+    return (t.nx32 || (unsigned)lane < 32u) && (t.ny8p || (unsigned)row < 8u) && (t.nz1 || (zp >= z0 && zp < z1));
+}
+
 // Device guard bits (mirror VEFD_ST_*).
 constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTimeout = 16u;
 
@@ -186,6 +205,7 @@ struct StepBufs {
     void* fout;            // populations at time n+1
     float* frest;          // rest populations (FP32, in place: time n before the lattice kernel, n+1 after)
     float* drho;           // densities of time n
+    float* drho_next;      // densities of time n+1 (column-marching step: partial, completed by the densities pass)
     float* u;              // velocity of time n (written by the lattice kernel)
     const float* Cin;      // C - I at time n
     float* Cout;           // C - I at time n+1
@@ -209,6 +229,15 @@ cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepP
 // own translation unit); same arguments as launch_lattice.
 cudaError_t launch_lattice_mrt(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
                                const void* tensor_map, int rev, int tile);
+// Column-marching lattice kernel with fused partial densities (D3Q19,
+// NX % 32 == 0, NY % 8 == 0): reads b.fin through `tensor_map` (box 32 x 8 x 1
+// x P), writes b.fout, b.frest, b.u and the partial densities into
+// b.drho_next; zs is the z-segment length (the densities pass needs the same).
+cudaError_t launch_lattice_zm(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                              const void* tensor_map, int zs, int rev);
+int lattice_zm_segment(const StepParams& p);
+cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                                  const void* tensor_map, int zs, int rev);
 // Staged tile shapes of the lattice kernel: tile 0..2 ->
 // D3Q19 32x4x2, 32x2x4, 32x8x1; D2Q9 32x8x1, 32x4x1, 32x16x1.
 void lattice_tile_shape(int lattice, int tile, int* bx, int* by, int* bz);
@@ -226,6 +255,12 @@ cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p
 bool post_zm_eligible(int lattice, int nx, int ny);
 cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBufs& b, const void* tensor_map_fnew,
                            cudaStream_t s, int rev);
+// The same pass after k_lattice_zm: completes the partial densities in
+// b.drho_next with the populations that crossed a column side or a segment
+// end (segment length zs of the lattice kernel), then the FENE-P update and
+// the feedback stress.
+cudaError_t launch_post_zm_fused(int ncomp, bool fd, const StepParams& p, const StepBufs& b, cudaStream_t s,
+                                 int zs, int rev);
 // Densities of b.fin and the feedback stress of (b.fin, b.Cin): the derived
 // state the lattice kernel needs, for the initial state and after writes.
 cudaError_t launch_pre(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s);

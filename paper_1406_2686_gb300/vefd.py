@@ -277,8 +277,8 @@ def vefd_get_kernel_config(ctx):
 
 def vefd_autotune(ctx, steps):
     """Times the admitted kernel choices and applies the fastest; returns the
-    twelve times in ms (index post_mode * 6 + lattice_tile, -1 when not admitted)."""
-    out = (ctypes.c_double * 12)()
+    eighteen times in ms (index post_mode * 6 + lattice_tile, -1 when not admitted)."""
+    out = (ctypes.c_double * 18)()
     _check(ctx, load().vefd_autotune(ctx, int(steps), out))
     return list(out)
 

@@ -57,18 +57,33 @@ def same(a, b):
 
 @pytest.mark.parametrize("k", [0, 3, 4])
 def test_kernel_choices_bit_identical(k):
-    """Every admitted (tile, densities-pass) choice gives the default's bits."""
+    """Tiles 0-2 with the tiled (1) or z-marching (2) densities pass give the
+    same bits.  The persistent tiles (3-5) are compiled separately and may
+    contract multiply-adds differently, and the column march with fused
+    densities (0) sums each new density in another order: both agree to FP32
+    rounding."""
     ref = make(BOXES[k], seed=11)
+    ref.set_kernel_config(0, 1)
     ref.step(5)
     seen = set()
-    for post in (0, 1):
+    for post in (1, 2):
         for tile in range(6):
             L = make(BOXES[k], seed=11)
             L.set_kernel_config(tile, post)
             seen.add(L.kernel_config())
             L.step(5)
-            assert same(L, ref), (tile, post, L.kernel_config())
+            if tile < 3:
+                assert same(L, ref), (tile, post, L.kernel_config())
+            else:
+                for a, r in zip(state(L), state(ref)):
+                    assert np.linalg.norm(a - r) <= 1e-6 * np.linalg.norm(r), (tile, post)
             assert L.status() == 0
+    F = make(BOXES[k], seed=11)
+    F.set_kernel_config(0, 0)
+    F.step(5)
+    for a, r in zip(state(F), state(ref)):
+        assert np.linalg.norm(a - r) <= 1e-6 * np.linalg.norm(r)
+    assert F.status() == 0
     # these 3-D boxes admit all three tiles (and their persistent forms); the
     # 64 x 13 D2Q9 box is too low for 32 x 16
     assert {t for t, _ in seen} == ({0, 1, 2, 3, 4, 5} if BOXES[k]["lattice"] == 1 else {0, 1, 3, 4})
@@ -77,12 +92,18 @@ def test_kernel_choices_bit_identical(k):
 def test_kernel_config_reports_and_rejects():
     from paper_1406_2686_gb300 import vefd
     L = make(BOXES[0], seed=1)
-    assert L.kernel_config() == (0, 0)  # 64 x 16 x 6 admits z-marching
+    assert L.kernel_config() == (0, 2)  # 64 x 16 x 6: default tiles + z-marching pass
+    L.set_kernel_config(0, 0)
+    assert L.kernel_config() == (0, 0)  # and it admits the column march
     L.set_kernel_config(2, 1)
     assert L.kernel_config() == (2, 1)
+    L.set_kernel_config(4, 2)
+    assert L.kernel_config() == (4, 2)
+    T = make(BOXES[1], seed=1)  # 36 x 10 x 7: tiles fit, the column does not
+    assert T.kernel_config() == (0, 1)
     S = make(BOXES[5], seed=1)  # 9 x 10 x 11: no staged tile fits
     assert S.kernel_config() == (-1, -1)
-    for bad in ((6, 0), (-1, 0), (0, 2)):
+    for bad in ((6, 0), (-1, 0), (0, 3)):
         with pytest.raises(vefd.VefdError) as ei:
             L.set_kernel_config(*bad)
         assert ei.value.status == vefd.ERR_ARG
@@ -94,13 +115,14 @@ def test_autotune_leaves_state_and_picks_fastest():
     L.step(3)
     R.step(3)
     times = L.autotune(steps=20)
-    assert len(times) == 12
+    assert len(times) == 18
     measured = [(t, i) for i, t in enumerate(times) if t >= 0]
-    assert len(measured) >= 6
+    assert len(measured) >= 13  # 1 fused + 6 tiled + 6 z-marching
     best = min(measured)[1]
     assert L.kernel_config() == (best % 6, best // 6)
     assert L.steps_done == 3
     assert same(L, R)
+    R.set_kernel_config(*L.kernel_config())
     L.step(4)
     R.step(4)
     assert same(L, R)
@@ -129,6 +151,7 @@ def test_ensemble_matches_single_lattices():
     for L in alone:
         L.step(17)
     alone[0].set_wall_shear(0.01)
+    alone[2].set_kernel_config(4, 1)
     for L in alone:
         L.step(20)
     for a, b in zip(ens_members, alone):
