@@ -462,6 +462,8 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
     const bool leader = (tx | ty) == 0;
     const unsigned bar_a = smem_u32(&bar);
     if (leader) mbar_init(bar_a);
+    // everything below reads or overwrites data of the preceding lattice kernel
+    pdl_wait();
 
     // which ring cells this thread stages: its own (interior) cell and, for
     // some warps, one halo cell (rows y0-1 / y0+8, columns x0-1 / x0+32)
@@ -526,6 +528,8 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
     const ColumnTopo topo{nx == 32, ny == 8 && !p.walls, nz == 1};
     for (int k = 0; k < z1 - z0; ++k) {
         const int z = z0 + k;
+        // the next step's lattice kernel may be scheduled once every block is on its last plane
+        if (k == z1 - z0 - 1) pdl_trigger();
         // new populations of this plane: one bulk copy (the buffer was released
         // by every thread at the barrier ending the previous iteration)
         if (!FUSED && leader) {
@@ -737,10 +741,9 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     // FUSED reads the partial densities of the new time level and completes them in place
     float* dens = FUSED ? b.drho_next : b.drho;
     const CUtensorMap dummy{};
-    k_post_zm<PT, NCOMP, FD, FUSED><<<grd, blk, smem, s>>>(FUSED ? dummy : *tm, b.frest, dens, b.Cin, b.Cout, b.R, b.u,
-                                                           b.Q, b.status, p, zs, rev,
-                                                           static_cast<const PT*>(b.fout), zl);
-    return cudaGetLastError();
+    return launch_pdl(p.pdl != 0, k_post_zm<PT, NCOMP, FD, FUSED>, grd, blk, smem, s, FUSED ? dummy : *tm,
+                      (const float*)b.frest, dens, (const float*)b.Cin, b.Cout, b.R, (const float*)b.u, b.Q, b.status,
+                      p, zs, rev, static_cast<const PT*>(b.fout), zl);
 }
 }  // namespace
 

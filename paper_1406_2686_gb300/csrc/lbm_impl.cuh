@@ -631,9 +631,13 @@ __global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (B
     const unsigned bar_a = smem_u32(&bar);
     if (leader) mbar_init(bar_a);
     __syncthreads();
+    // the populations of time n are complete before this kernel can start
     if (leader) tma_load_4d(smem_u32(sf), &tm_fin, x0, y0, z0, 0, bar_a, kBytes);
     const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
     const bool active = x < p.nx && y < p.ny && z < p.nz;
+    // densities, feedback stress, velocity and rest populations are shared with
+    // the preceding densities/FENE-P pass
+    pdl_wait();
     NodeGather<L, NCOMP> g;
     node_gather<L, NCOMP>(b, p, x, y, z, active, g);
     // bounded wait for the staged populations; on timeout report and leave
@@ -641,6 +645,7 @@ __global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (B
         if (leader) atomicOr(b.status, kStTimeout);
         return;
     }
+    pdl_trigger();
     if (!active) return;
     node_collide<PT, L, NCOMP, T, COLL>(b, p, sf, (tz * BY + ty) * BX + tx, g);
 }
@@ -734,8 +739,7 @@ cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const St
     constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
-    k_lattice_tma<PT, L, NCOMP, BX, BY, BZ, COLL><<<grd, blk, smem, s>>>(*tm, b, p, rev);
-    return cudaGetLastError();
+    return launch_pdl(p.pdl != 0, k_lattice_tma<PT, L, NCOMP, BX, BY, BZ, COLL>, grd, blk, smem, s, *tm, b, p, rev);
 }
 
 // Column-marching form (D3Q19, NX % 32 == 0, NY % 8 == 0) that also yields

@@ -67,6 +67,7 @@ struct vefd_ctx {
     // column-marching lattice kernel with the densities fused in (post_mode 0)
     bool fused_ok = false;
     int zm_seg_fixed = 0;  // z-segment length of the column march (0: one wave of blocks)
+    bool pdl = true;       // programmatic dependent launch between the step's kernels
     // densities and feedback stress of the current state are in drho and Q
     bool drho_valid = false;
     // tile traversal: bit0 lattice kernel backwards, bit1 densities/FD kernel
@@ -184,6 +185,7 @@ void carve(vefd_ctx* c) {
     build_tensor_maps(c);
     if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
     if (const char* e = getenv("VEFD_ZM_SEGMENT")) c->zm_seg_fixed = atoi(e) > 0 ? atoi(e) : 0;
+    if (getenv("VEFD_NO_PDL")) c->pdl = false;
 }
 
 // (Re)builds the TMA descriptors of both population buffers for the selected
@@ -243,6 +245,7 @@ StepParams params_of(const vefd_ctx* c) {
     p.coupling = c->coupling;
     p.collision = c->collision;
     p.chol = c->chol;
+    p.pdl = c->pdl ? 1 : 0;
     return p;
 }
 

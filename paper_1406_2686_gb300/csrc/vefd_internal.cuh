@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <utility>
 #include <stdint.h>
 
 namespace vefd {
@@ -133,6 +134,7 @@ struct StepParams {
     int coupling;          // polymer feedback: 0 body force div Q; 1 stress in the equilibrium
     int collision;         // 0: single relaxation time; 1: moment space with the paper's rates
     int chol;              // conformation update: 0 AB2 on C; 1 AB2 on the log-Cholesky factor of f C
+    int pdl;               // launch the step's kernels with programmatic dependencies
 };
 
 // --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------
@@ -176,6 +178,33 @@ __device__ __forceinline__ bool mbar_wait_bounded_parity(unsigned bar, unsigned 
 }
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar) { return mbar_wait_bounded_parity(bar, 0u); }
+
+// --- programmatic dependent launch ------------------------------------------
+// The two kernels of a step are launched so that the next one may start while
+// the previous one drains.  pdl_wait() blocks until the preceding kernel in
+// the stream has completed and its memory is visible (a no-op when the launch
+// carried no programmatic dependency); pdl_trigger() lets the next kernel
+// launch once every block of this one has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches kernel<<<grid, block, smem, stream>>>(args...) with programmatic
+// stream serialisation unless disabled (pdl == false).
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // --- column-marching step with fused densities (D3Q19) ----------------------
 // The lattice kernel k_lattice_zm walks 32 x 8 columns along z in segments of
