@@ -459,8 +459,10 @@ __device__ __forceinline__ void collide_emit(const StepParams& p, const Local<NC
 
 // Collision and push streaming: each stored value goes to its destination
 // node (periodic offsets in x, y, z), a bounced one to this node's opposite
-// direction; the rest population is updated in place.
-template <class PT, class L, int NCOMP, int COLL, class FGet>
+// direction; the rest population is updated in place.  EDGE = false is for
+// nodes known to have y-neighbours inside the lattice (no wall row, no
+// periodic wrap in y), which skips the bounce-back and wrap logic.
+template <class PT, class L, int NCOMP, int COLL, bool EDGE = true, class FGet>
 __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
                                                const Local<NCOMP>& st, const float qloc[L::NQ],
                                                const float (*pif)[6], FGet fget) {
@@ -471,10 +473,10 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
     // streaming offsets in y are periodic (walls are handled by bounce-back)
     const int nx = p.nx;
     int oy[3];
-    const bool wall_lo = p.walls && nb.y == 0, wall_hi = p.walls && nb.y == nb.ny - 1;
-    oy[0] = (nb.y == 0 ? nb.ny - 1 : -1) * nx;
+    const bool wall_lo = EDGE && p.walls && nb.y == 0, wall_hi = EDGE && p.walls && nb.y == nb.ny - 1;
+    oy[0] = (EDGE && nb.y == 0 ? nb.ny - 1 : -1) * nx;
     oy[1] = 0;
-    oy[2] = (nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
+    oy[2] = (EDGE && nb.y == nb.ny - 1 ? 1 - nb.ny : 1) * nx;
     float rest[NCOMP];
     collide_emit<PT, L, NCOMP, COLL>(
         p, st, qloc, pif, wall_lo, wall_hi, fget,
@@ -584,7 +586,7 @@ __device__ __forceinline__ void node_gather(const StepBufs& b, const StepParams&
     neighbour_forces<L, NCOMP>(b, p, g.nb, g.acc, g.Fp, g.qloc);
 }
 
-template <class PT, class L, int NCOMP, int T, int COLL>
+template <class PT, class L, int NCOMP, int T, int COLL, bool EDGE = true>
 __device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams& p, const PT* sf, int t,
                                              const NodeGather<L, NCOMP>& g) {
     const long long N = p.N;
@@ -610,7 +612,7 @@ __device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams
     b.u[N + i] = st.uy;
     if (L::D == 3) b.u[2 * N + i] = st.uz;
     // volatile reads keep the populations in shared memory instead of registers
-    collide_stream<PT, L, NCOMP, COLL>(b, p, g.nb, st, g.qloc, pif,
+    collide_stream<PT, L, NCOMP, COLL, EDGE>(b, p, g.nb, st, g.qloc, pif,
                                  [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
 }
 
@@ -647,7 +649,12 @@ __global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (B
     }
     pdl_trigger();
     if (!active) return;
-    node_collide<PT, L, NCOMP, T, COLL>(b, p, sf, (tz * BY + ty) * BX + tx, g);
+    // tiles whose rows all have both y-neighbours inside the lattice take the
+    // path without bounce-back and y-wrap logic (block-uniform branch)
+    if (y0 > 0 && y0 + BY < p.ny)
+        node_collide<PT, L, NCOMP, T, COLL, false>(b, p, sf, (tz * BY + ty) * BX + tx, g);
+    else
+        node_collide<PT, L, NCOMP, T, COLL, true>(b, p, sf, (tz * BY + ty) * BX + tx, g);
 }
 
 // Persistent form (single-relaxation-time collision): a grid of (SMs x
