@@ -37,6 +37,7 @@ def sources():
 def _deps():
     files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "vefd.h"))
+    files.append(os.path.join(INCLUDE, "vefd_nn.h"))
     files.append(os.path.abspath(__file__))
     return files
 
