@@ -83,7 +83,7 @@ template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const __nv_bfloat16* __restrict__ A, int lda, const __nv_bfloat16* __restrict__ B, int ldb,
                 float* __restrict__ C, int ldc, int M, int N, int K, int accumulate, unsigned lbo, unsigned sbo,
-                int desc_swap, unsigned* __restrict__ status) {
+                int desc_swap, int k_split, long long c_split_stride, unsigned* __restrict__ status) {
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "tcgen05 M = 128 needs N in [16, 256], a multiple of 16");
     constexpr unsigned kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
     __shared__ __align__(128) unsigned char sA[kBM * kBK * 2];
@@ -92,6 +92,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ unsigned tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    // split K: block z reduces K range [kb, ke) into its own slice of C
+    const int kb = blockIdx.z * k_split, ke = min(K, kb + k_split);
+    C += blockIdx.z * c_split_stride;
     const unsigned bar_a = smem_addr(&bar);
     if (threadIdx.x == 0) mbar_init1(bar_a);
     if (warp == 0) {
@@ -105,12 +108,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
     constexpr uint32_t idesc = instr_desc(kBM, BN);
-    const int nk = (K + kBK - 1) / kBK;
+    const int nk = (ke - kb + kBK - 1) / kBK;
     bool ok = true;
     int last = -1;  // last chunk whose matrix operations were committed
     for (int kt = 0; kt < nk && ok; ++kt) {
-        load_tile(sA, A, lda, M, K, m0, kt * kBK, kBM, lbo, sbo);
-        load_tile(sB, B, ldb, N, K, n0, kt * kBK, BN, lbo, sbo);
+        load_tile(sA, A, lda, M, ke, m0, kb + kt * kBK, kBM, lbo, sbo);
+        load_tile(sB, B, ldb, N, ke, n0, kb + kt * kBK, BN, lbo, sbo);
         // generic-proxy writes of the tiles become visible to the tensor cores
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = !__syncthreads_or(!done);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (ok) {
+    if (ok && nk > 0) {
         // accumulator row 32 * warp + lane, 16 columns per load
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -179,17 +182,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 using namespace vefd_nn;
 
-extern "C" int vefd_nn_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N,
-                                 int K, int accumulate, unsigned* status, void* stream) {
-    return vefd_nn_gemm_bf16_layout(A, lda, B, ldb, C, ldc, M, N, K, accumulate, 128u, 1024u, 0, status, stream);
-}
-
-extern "C" int vefd_nn_gemm_bf16_layout(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M,
-                                        int N, int K, int accumulate, unsigned lbo, unsigned sbo, int desc_swap,
-                                        unsigned* status, void* stream) {
+namespace {
+int launch_gemm(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K, int accumulate,
+                unsigned lbo, unsigned sbo, int desc_swap, int k_split, long long c_split_stride, unsigned* status,
+                void* stream) {
     if (!A || !B || !C || !status || M < 1 || N < 1 || K < 8) return VEFD_NN_ERR_ARG;
     if (K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N) return VEFD_NN_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) return VEFD_NN_ERR_ARG;
+    if (k_split < kBK || k_split % kBK != 0) return VEFD_NN_ERR_ARG;
     const int bn = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
     // the layout must keep every 16-byte core-matrix row of both tiles inside
     // its staging buffer: last row group at (rows/8 - 1) * sbo, last K block
@@ -197,16 +197,43 @@ extern "C" int vefd_nn_gemm_bf16_layout(const void* A, int lda, const void* B, i
     if (lbo % 16 || sbo % 16 || lbo == 0 || sbo == 0) return VEFD_NN_ERR_ARG;
     if (15u * sbo + 7u * lbo + 128u > (unsigned)(kBM * kBK * 2)) return VEFD_NN_ERR_ARG;
     if ((unsigned)(bn / 8 - 1) * sbo + 7u * lbo + 128u > (unsigned)(bn * kBK * 2)) return VEFD_NN_ERR_ARG;
+    const int splits = (K + k_split - 1) / k_split;
+    if (splits > 65535) return VEFD_NN_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    dim3 grd((M + kBM - 1) / kBM, (N + bn - 1) / bn);
+    dim3 grd((M + kBM - 1) / kBM, (N + bn - 1) / bn, splits);
     const __nv_bfloat16* a = (const __nv_bfloat16*)A;
     const __nv_bfloat16* b = (const __nv_bfloat16*)B;
     if (bn == 32)
-        k_gemm_bf16<32><<<grd, kThreads, 0, s>>>(a, lda, b, ldb, C, ldc, M, N, K, accumulate, lbo, sbo, desc_swap, status);
+        k_gemm_bf16<32><<<grd, kThreads, 0, s>>>(a, lda, b, ldb, C, ldc, M, N, K, accumulate, lbo, sbo, desc_swap,
+                                                 k_split, c_split_stride, status);
     else if (bn == 64)
-        k_gemm_bf16<64><<<grd, kThreads, 0, s>>>(a, lda, b, ldb, C, ldc, M, N, K, accumulate, lbo, sbo, desc_swap, status);
+        k_gemm_bf16<64><<<grd, kThreads, 0, s>>>(a, lda, b, ldb, C, ldc, M, N, K, accumulate, lbo, sbo, desc_swap,
+                                                 k_split, c_split_stride, status);
     else
         k_gemm_bf16<128><<<grd, kThreads, 0, s>>>(a, lda, b, ldb, C, ldc, M, N, K, accumulate, lbo, sbo, desc_swap,
-                                                  status);
+                                                  k_split, c_split_stride, status);
     return cudaGetLastError() == cudaSuccess ? VEFD_NN_OK : VEFD_NN_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" int vefd_nn_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N,
+                                 int K, int accumulate, unsigned* status, void* stream) {
+    const int ks = ((K + kBK - 1) / kBK) * kBK;
+    return launch_gemm(A, lda, B, ldb, C, ldc, M, N, K, accumulate, 128u, 1024u, 0, ks < kBK ? kBK : ks, 0, status,
+                       stream);
+}
+
+extern "C" int vefd_nn_gemm_bf16_splitk(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M,
+                                        int N, int K, int k_split, long long c_split_stride, unsigned* status,
+                                        void* stream) {
+    if (c_split_stride < (long long)M * ldc) return VEFD_NN_ERR_ARG;
+    return launch_gemm(A, lda, B, ldb, C, ldc, M, N, K, 0, 128u, 1024u, 0, k_split, c_split_stride, status, stream);
+}
+
+extern "C" int vefd_nn_gemm_bf16_layout(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M,
+                                        int N, int K, int accumulate, unsigned lbo, unsigned sbo, int desc_swap,
+                                        unsigned* status, void* stream) {
+    const int ks = ((K + kBK - 1) / kBK) * kBK;
+    return launch_gemm(A, lda, B, ldb, C, ldc, M, N, K, accumulate, lbo, sbo, desc_swap, ks < kBK ? kBK : ks, 0,
+                       status, stream);
 }

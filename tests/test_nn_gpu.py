@@ -80,3 +80,105 @@ def test_gemm_rejects_bad_arguments():
     B = torch.zeros(32, 64, dtype=torch.bfloat16, device="cuda")
     with pytest.raises(nn.NNError):
         nn.gemm(A, B, layout=(4096, 4096, 0))  # would leave the staged tile
+
+
+# --- convolution layers and the network against PyTorch CPU autograd (FP64) ----
+
+def _torch_weight(lay):
+    """Our w[o][((dz*3+dy)*3+dx)*Cin + c] (BF16-rounded) as torch [Cout, Cin, 3, 3, 3]."""
+    import torch
+    w = lay.w.cpu().to(torch.bfloat16).double()
+    return w.view(lay.cout, 3, 3, 3, lay.cin).permute(0, 4, 1, 2, 3).contiguous()
+
+
+def _ncdhw(x):
+    return x.permute(0, 4, 1, 2, 3)
+
+
+def _rel(a, b):
+    import torch
+    return float(torch.linalg.norm((a - b).flatten()) / max(1e-30, float(torch.linalg.norm(b.flatten()))))
+
+
+@pytest.mark.parametrize("cin,cout,stride,relu,shape", [(5, 16, 1, True, (1, 8, 8, 16)), (16, 32, 2, True, (2, 8, 16, 8)),
+                                                        (24, 8, 1, False, (1, 16, 8, 8))])
+def test_conv_layer_matches_torch(cin, cout, stride, relu, shape):
+    """Forward values and the gradients of input, weights and bias of one
+    convolution layer agree with FP64 autograd of the same BF16-rounded
+    weights (the GEMM operands are BF16: a few 1e-3 relative)."""
+    import torch
+    import torch.nn.functional as F
+    from paper_1406_2686_gb300 import nn
+    g = torch.Generator().manual_seed(cin + cout)
+    lay = nn.Conv3d(cin, cout, stride, relu, gen=g)
+    lay.b.copy_(torch.randn(cout, generator=g).cuda() * 0.1)
+    x = torch.randn(*shape, cin, generator=g)
+    y = lay.forward(x.cuda().contiguous())
+    dy = torch.randn(*y.shape, generator=g)
+    dx = lay.backward(dy.cuda())
+    torch.cuda.synchronize()
+    xr = _ncdhw(x.to(torch.bfloat16).double()).requires_grad_(True)
+    wr = _torch_weight(lay).requires_grad_(True)
+    br = lay.b.cpu().double().requires_grad_(True)
+    yr = F.conv3d(xr, wr, br, stride=stride, padding=1)
+    if relu:
+        yr = F.relu(yr)
+    yr.backward(_ncdhw(dy.double()))
+    assert _rel(_ncdhw(y.cpu().double()), yr.detach()) < 1e-2
+    assert _rel(_ncdhw(dx.cpu().double()), xr.grad) < 2e-2
+    dwr = wr.grad.permute(0, 2, 3, 4, 1).reshape(cout, -1)
+    assert _rel(lay.dw.cpu().double(), dwr) < 2e-2
+    assert _rel(lay.db.cpu().double(), br.grad) < 1e-3
+    assert int(lay.status.item()) == 0
+
+
+def test_unet_gradients_match_torch():
+    """The whole U-Net (forward, MSE loss, backward through every layer, skip
+    and upsampling) against FP64 autograd of the same weights."""
+    import torch
+    import torch.nn.functional as F
+    from paper_1406_2686_gb300 import nn
+    net = nn.UNet(5, 8, c=8, seed=3)
+    g = torch.Generator().manual_seed(5)
+    for lay in net.layers:
+        lay.b.copy_(torch.randn(lay.cout, generator=g).cuda() * 0.05)
+    x = torch.randn(1, 16, 16, 16, 5, generator=g)
+    t = torch.randn(1, 16, 16, 16, 8, generator=g)
+    out = net.forward(x.cuda().contiguous())
+    loss_parts, grad = nn.mse(out, t.cuda().contiguous())
+    net.backward(grad)
+    torch.cuda.synchronize()
+    loss = float(loss_parts.sum()) / out.numel()
+
+    W = {id(l): _torch_weight(l).requires_grad_(True) for l in net.layers}
+    Bv = {id(l): l.b.cpu().double().requires_grad_(True) for l in net.layers}
+
+    def run(layers, h):
+        for l in layers:
+            h = F.conv3d(h, W[id(l)], Bv[id(l)], stride=l.stride, padding=1)
+            if l.relu:
+                h = F.relu(h)
+        return h
+
+    up = lambda h: F.interpolate(h, scale_factor=2, mode="nearest")
+    xr = _ncdhw(x.double())
+    s0 = run(net.e0, xr)
+    s1 = run(net.e1, s0)
+    s2 = run(net.e2, s1)
+    s3 = run(net.e3, s2)
+    u2 = run(net.d2, torch.cat([up(s3), s2], 1))
+    u1 = run(net.d1, torch.cat([up(u2), s1], 1))
+    o = run(net.d0, torch.cat([up(u1), s0], 1))
+    lr = ((o - _ncdhw(t.double())) ** 2).mean()
+    lr.backward()
+    assert abs(loss / float(lr.detach()) - 1) < 2e-2
+    assert _rel(_ncdhw(out.cpu().double()), o.detach()) < 3e-2
+    # every GEMM rounds its operands (activations, gradients) to BF16, so the
+    # error grows along the backward chain: direction and size are compared
+    for l in net.layers:
+        dwr = W[id(l)].grad.permute(0, 2, 3, 4, 1).reshape(l.cout, -1)
+        for a, r in ((l.dw.cpu().double(), dwr), (l.db.cpu().double(), Bv[id(l)].grad)):
+            cos = float((a * r).sum() / (torch.linalg.norm(a) * torch.linalg.norm(r)))
+            assert cos > 0.995 and abs(float(torch.linalg.norm(a) / torch.linalg.norm(r)) - 1) < 0.05, (l.cout, cos)
+            assert _rel(a, r) < 0.1
+    assert net.status() == 0
