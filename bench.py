@@ -95,6 +95,12 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage variant timings")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-lattice ensemble timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tiles")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="measure time to steady deformation, warm start from the trained network vs cold start")
+    ap.add_argument("--ws-train", type=int, default=64, help="training set-ups for --warmstart")
+    ap.add_argument("--ws-eval", type=int, default=8, help="held-out set-ups for --warmstart")
+    ap.add_argument("--ws-epochs", type=int, default=40)
+    ap.add_argument("--ws-tol", type=float, default=1e-5)
     return ap.parse_args()
 
 
@@ -485,6 +491,52 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_warmstart(args):
+    """Time to steady deformation of held-out droplet set-ups, cold start
+    versus a start from the trained network's prediction (one JSON line)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2686_gb300 import nn, warmstart as ws
+    torch.cuda.set_device(0)
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    t0 = time.perf_counter()
+    train_setups = ws.sample_setups(args.ws_train, seed=11)
+    eval_setups = ws.sample_setups(args.ws_eval, seed=29)
+    X, Y, rec = ws.make_dataset(train_setups, tol=args.ws_tol, log=log)
+    t_data = time.perf_counter() - t0
+    net = nn.UNet(ws.N_IN, ws.N_OUT, c=16, seed=0)
+    t1 = time.perf_counter()
+    losses = ws.train(net, X, Y, epochs=args.ws_epochs, lr=1e-3, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    res = ws.evaluate(net, eval_setups, tol=args.ws_tol, log=log)
+    cold = np.array([r["cold_seconds"] for r in res])
+    warm = np.array([r["warm_seconds"] for r in res])
+    derr = np.array([r["D_rel_err"] for r in res])
+    speed = cold / warm
+    line = {
+        "metric": "time-to-steady deformation, warm-start vs plain", "value": round(float(np.median(speed)), 3),
+        "unit": "x (cold / warm wall time, median over held-out set-ups)", "higher_is_better": True,
+        "n_gpus": 1, "data": "synthetic (steady states generated by the lattice-Boltzmann/FENE-P step)",
+        "config": {"box": "64^3 D3Q19 two-component droplet, walls in y", "train_setups": len(train_setups),
+                   "eval_setups": len(eval_setups), "steady_rule": "|dD| < %g per tau_em over 5 consecutive tau_em (mid-plane, smooth indicator)"
+                   % args.ws_tol, "network": "3-D U-Net, %d parameters, BF16 tcgen05 GEMMs, FP32 accumulate"
+                   % net.n_params(), "epochs": args.ws_epochs},
+        "steps": {"cold_median": int(np.median([r["cold_steps"] for r in res])),
+                  "warm_median": int(np.median([r["warm_steps"] for r in res]))},
+        "seconds": {"cold_median": round(float(np.median(cold)), 4), "warm_median": round(float(np.median(warm)), 4),
+                    "predict_median": round(float(np.median([r["predict_seconds"] for r in res])), 4),
+                    "dataset": round(t_data, 2), "training": round(t_train, 2)},
+        "D_rel_err": {"median": float(np.median(derr)), "max": float(np.max(derr)),
+                      "within_1pct": int(np.sum(derr <= 0.01))},
+        "speedup_per_setup": [round(float(v), 3) for v in speed], "loss_first_last": [losses[0], losses[-1]],
+        "all_converged": bool(all(r["cold_converged"] and r["warm_converged"] for r in res)),
+        "status": net.status(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -534,6 +586,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.warmstart:
+        run_warmstart(args)
     else:
         run_ours(args)
 

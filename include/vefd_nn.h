@@ -75,6 +75,15 @@ int vefd_nn_split(const float *dy, int Ca, int Cb, long long V, float *da, float
 int vefd_nn_mse(const float *p, const float *t, long long n, float *sq, float *grad, void *stream);
 /* y = a + b elementwise. */
 int vefd_nn_add(const float *a, const float *b, long long n, float *y, void *stream);
+/* Warm-start fields of a lattice from a network output out[v][16] (phi - phi0,
+ * u / u_wall, (C - I) / c_scale, 6 unused): rho_A, rho_B = rho_tot (1 +- phi)/2
+ * with phi clipped to [-0.95, 0.95]; u planes [3][V]; C planes [6][V] (xx xy
+ * xz yy yz zz) = I + t c_scale c^ with the largest t in {1, 1/2, ..., 2^-10, 0}
+ * giving a symmetric positive definite C with tr C < L2 - 1. */
+int vefd_nn_to_fields(const float *out, const float *phi0, long long V, float u_wall, float c_scale, float rho_tot,
+                      float L2, float *rhoA, float *rhoB, float *u, float *C, void *stream);
+/* x *= factor elementwise. */
+int vefd_nn_scale(float *x, long long n, float factor, void *stream);
 /* One Adam step (bias-corrected, step >= 1) on w with gradient g and moments m, v. */
 int vefd_nn_adam(float *w, const float *g, float *m, float *v, long long n, float lr, float beta1, float beta2,
                  float eps, int step, void *stream);

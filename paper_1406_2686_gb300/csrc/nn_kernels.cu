@@ -245,9 +245,46 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
     }
 }
 
+__global__ void k_scale(float* __restrict__ x, long long n, float f) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        x[e] *= f;
+}
+
 __global__ void k_add(const float* __restrict__ a, const float* __restrict__ b, long long n, float* __restrict__ y) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         y[e] = a[e] + b[e];
+}
+
+// Warm-start fields from a network output out[v][16] (channels: phi - phi0,
+// u / U, (C - I) / c_scale): rho_A, rho_B = rho_tot (1 +- phi) / 2 with phi
+// clipped to [-0.95, 0.95]; u; C = I + t c_scale c^ with the largest t in
+// {1, 1/2, ..., 2^-10, 0} for which C is symmetric positive definite
+// (leading minors) with tr C < L2 - 3 + 3 (t = 0 gives I).  Layouts as the
+// lattice's init_fields: planes of N for u (3) and C (xx xy xz yy yz zz).
+__global__ void k_to_fields(const float* __restrict__ out, const float* __restrict__ phi0, long long V, float u_wall,
+                            float c_scale, float rho_tot, float L2, float* __restrict__ rhoA, float* __restrict__ rhoB,
+                            float* __restrict__ u, float* __restrict__ C) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const float* o = out + v * 16;
+        const float phi = fminf(fmaxf(phi0[v] + o[0], -0.95f), 0.95f);
+        rhoA[v] = 0.5f * rho_tot * (1.0f + phi);
+        rhoB[v] = 0.5f * rho_tot * (1.0f - phi);
+        for (int k = 0; k < 3; ++k) u[k * V + v] = o[1 + k] * u_wall;
+        float c[6];
+        for (int k = 0; k < 6; ++k) c[k] = o[4 + k] * c_scale;
+        float t = 1.0f;
+        for (int it = 0; it <= 11; ++it) {
+            if (it == 11) t = 0.0f;
+            const float xx = 1.0f + t * c[0], xy = t * c[1], xz = t * c[2], yy = 1.0f + t * c[3], yz = t * c[4],
+                        zz = 1.0f + t * c[5];
+            const float m2 = xx * yy - xy * xy;
+            const float m3 = xx * (yy * zz - yz * yz) - xy * (xy * zz - yz * xz) + xz * (xy * yz - yy * xz);
+            if ((xx > 1e-3f && m2 > 1e-6f && m3 > 1e-9f && xx + yy + zz < L2 - 1.0f) || it == 11) break;
+            t *= 0.5f;
+        }
+        const float e[6] = {1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 1.0f};
+        for (int k = 0; k < 6; ++k) C[k * V + v] = e[k] + t * c[k];
+    }
 }
 
 bool bad_geo(int B, int D, int H, int W, int C, int s) {
@@ -360,6 +397,20 @@ int vefd_nn_mse(const float* p, const float* t, long long n, float* sq, float* g
 int vefd_nn_add(const float* a, const float* b, long long n, float* y, void* stream) {
     if (!a || !b || !y || n < 1) return VEFD_NN_ERR_ARG;
     k_add<<<grid_for(n), kT, 0, static_cast<cudaStream_t>(stream)>>>(a, b, n, y);
+    return done();
+}
+
+int vefd_nn_to_fields(const float* out, const float* phi0, long long V, float u_wall, float c_scale, float rho_tot,
+                      float L2, float* rhoA, float* rhoB, float* u, float* C, void* stream) {
+    if (!out || !phi0 || !rhoA || !rhoB || !u || !C || V < 1 || !(L2 > 3.0f)) return VEFD_NN_ERR_ARG;
+    k_to_fields<<<grid_for(V), kT, 0, static_cast<cudaStream_t>(stream)>>>(out, phi0, V, u_wall, c_scale, rho_tot, L2,
+                                                                         rhoA, rhoB, u, C);
+    return done();
+}
+
+int vefd_nn_scale(float* x, long long n, float factor, void* stream) {
+    if (!x || n < 1) return VEFD_NN_ERR_ARG;
+    k_scale<<<grid_for(n), kT, 0, static_cast<cudaStream_t>(stream)>>>(x, n, factor);
     return done();
 }
 

@@ -82,6 +82,8 @@ _MORE = {
     "vefd_nn_mse": "vp vp ll vp vp vp",
     "vefd_nn_add": "vp vp ll vp vp",
     "vefd_nn_adam": "vp vp vp vp ll f f f f i vp",
+    "vefd_nn_to_fields": "vp vp ll f f f f vp vp vp vp vp",
+    "vefd_nn_scale": "vp ll f vp",
 }
 NN_EXPORTS += list(_MORE) + ["vefd_nn_colsum_scratch"]
 _more_done = False
@@ -330,3 +332,30 @@ class UNet:
 
     def status(self):
         return max(int(lay.status.item()) for lay in self.layers)
+
+
+def to_fields(out, phi0, u_wall, c_scale, rho_tot, L2):
+    """Device fields (rho_A, rho_B, u [3, ...], C [6, ...]) for a lattice from a network output [D, H, W, 16]."""
+    import torch
+    V = phi0.numel()
+    rA, rB = torch.empty_like(phi0), torch.empty_like(phi0)
+    u = torch.empty(3, *phi0.shape, device="cuda")
+    C = torch.empty(6, *phi0.shape, device="cuda")
+    _check(L().vefd_nn_to_fields(_p(out.contiguous()), _p(phi0.contiguous()), V, float(u_wall), float(c_scale),
+                                 float(rho_tot), float(L2), _p(rA), _p(rB), _p(u), _p(C), _stream()), "to_fields")
+    return rA, rB, u, C
+
+
+def total(x):
+    """Sum of all elements of a device FP32 tensor (fixed-order reduction), as a host float."""
+    import torch
+    n = x.numel()
+    assert n % 8 == 0
+    out = torch.empty(8, device="cuda")
+    scratch = torch.empty(L().vefd_nn_colsum_scratch(n // 8, 8), device="cuda")
+    _check(L().vefd_nn_colsum(_p(x.contiguous()), n // 8, 8, _p(scratch), _p(out), 0, _stream()), "colsum")
+    return float(sum(out.cpu().tolist()))
+
+
+def scale(x, factor):
+    _check(L().vefd_nn_scale(_p(x), x.numel(), float(factor), _stream()), "scale")
