@@ -32,6 +32,24 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(vefd.EXPORTS) == names
 
 
+def test_network_kernels_are_exported(lib):
+    """Every entry point of include/vefd_nn.h (the warm-start network) is
+    exported and bound; arguments are checked on the host."""
+    from paper_1406_2686_gb300 import nn
+    src = open(os.path.join(ROOT, "include", "vefd_nn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(vefd_nn_[a-z_0-9]+)\s*\(", src)))
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(nn.NN_EXPORTS) == names
+    L = nn.L()
+    # K not a multiple of 8, NULL operands: refused before any launch
+    assert L.vefd_nn_gemm_bf16(None, 8, None, 8, None, 8, 128, 16, 16, 0, None, None) == nn.ERR_ARG
+    assert L.vefd_nn_im2col3d(None, 1, 8, 8, 8, 4, 1, 112, None, None, None) == nn.ERR_ARG
+    assert L.vefd_nn_adam(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 1, None) == nn.ERR_ARG
+
+
 def test_build_targets_sm_103a():
     assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
