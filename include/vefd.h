@@ -236,9 +236,11 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
 /* ---- ensembles of independent lattices (implementation detail: the paper
  * steps one lattice at a time) --------------------------------------------
  * An ensemble steps many independent lattices of any sizes and
- * configurations together: every member's step is one branch of a CUDA graph
- * and `chunk` steps of all members are captured once and replayed, so small
- * lattices overlap on the GPU and pay no per-launch host cost.  Members stay
+ * configurations together: `chunk` steps of all members are captured once as
+ * a CUDA graph and replayed, either as two batched launches per step over the
+ * tiles of all members (vefd_ensemble_set_batched) or with every member's
+ * step as one graph branch, so small lattices fill the GPU together and pay
+ * no per-launch host cost.  Members stay
  * ordinary contexts (read, diagnose, checkpoint them as usual, between
  * ensemble calls); the ensemble does not own them and must be destroyed
  * before they are. */
@@ -249,7 +251,8 @@ typedef struct vefd_ensemble vefd_ensemble;
  * later enqueued on those streams is ordered after it. */
 vefd_status vefd_ensemble_create(vefd_ctx *const *members, int n, void *stream, vefd_ensemble **out);
 /* Advances every member by nsteps >= 0 steps (asynchronous), each member's
- * results bit-identical to vefd_step on it alone.  chunk (even, >= 2) is the
+ * results those of vefd_step on it alone (bit-identical with graph branches,
+ * to FP32 rounding with batched launches).  chunk (even, >= 2) is the
  * number of steps per graph replay: members still in their first step (the
  * Euler start) or with densities pending take one eager step first,
  * then nsteps / chunk replays run and the remainder runs eagerly.  The graph
@@ -259,6 +262,24 @@ vefd_status vefd_ensemble_create(vefd_ctx *const *members, int n, void *stream, 
  * member is not initialised, VEFD_ERR_CUDA on capture or launch errors
  * (see vefd_ensemble_last_error). */
 vefd_status vefd_ensemble_step(vefd_ensemble *ens, int64_t nsteps, int64_t chunk);
+/* Batched launches (default on): when every member is D3Q19 with the same
+ * component count, storage type, collision operator, FENE-P switch and
+ * programmatic-launch setting, and each takes the staged lattice kernel and
+ * the separate z-marching densities/FENE-P pass (NX % 32 == 0, NY % 8 == 0,
+ * kernel config post mode 2), a replayed step is ONE lattice-kernel launch
+ * over the 32 x 4 x 2 tiles of all members and ONE densities/FENE-P launch
+ * over their 32 x 8 columns.  Each block finds its member by binary search
+ * over a device table holding the member's parameters, the buffers and
+ * tensor maps of both ping-pong parities, and its tile counts; the table is
+ * rebuilt with every re-capture.  Per node the arithmetic is the member's own
+ * kernels' (results agree with vefd_step to FP32 rounding: the batched
+ * kernels are separate instantiations, so floating-point contraction may
+ * differ in the last ulp).  on = 0 keeps one graph branch per member.
+ * VEFD_ERR_ARG for a NULL ensemble or on not 0/1; takes effect at the next
+ * replay (after waiting for earlier replays). */
+vefd_status vefd_ensemble_set_batched(vefd_ensemble *ens, int on);
+/* 1 when the currently captured graph uses the batched launches, else 0. */
+int vefd_ensemble_is_batched(const vefd_ensemble *ens);
 const char *vefd_ensemble_last_error(const vefd_ensemble *ens);
 /* Waits for the ensemble's work and frees its streams, events and graph. */
 void vefd_ensemble_destroy(vefd_ensemble *ens);

@@ -435,14 +435,15 @@ constexpr int zm_smem_bytes() {
 // arrived from inside its 32 x 8 column and lattice-kernel z-segment of
 // length zl); the pass adds, from fnew, the populations that crossed a column
 // side or a segment end, in direction order, and needs no population copy.
+// One 32 x 8 column (origin x0, y0) over the planes [z0, z0 + zs) of the
+// pass; tm_fnew is the tensor map of the new populations (box 32 x 8 x 1 x P).
 template <class PT, int NCOMP, bool FD, bool FUSED>
-__global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
-                                                               const float* __restrict__ frest,
-                                                               float* __restrict__ drho, const float* __restrict__ Ct,
-                                                               float* __restrict__ Cout, float* __restrict__ R,
-                                                               const float* __restrict__ u, float* __restrict__ Q,
-                                                               unsigned* __restrict__ status, StepParams p, int zs,
-                                                               int rev, const PT* __restrict__ fnew, int zl) {
+__device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const float* __restrict__ frest,
+                                            float* __restrict__ drho, const float* __restrict__ Ct,
+                                            float* __restrict__ Cout, float* __restrict__ R,
+                                            const float* __restrict__ u, float* __restrict__ Q,
+                                            unsigned* __restrict__ status, const StepParams& p, int x0, int y0, int z0,
+                                            int zs, const PT* __restrict__ fnew, int zl) {
     using L = D3Q19;
     constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = kZmBX * kZmBY;
@@ -454,9 +455,6 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int N = (int)p.N, plane = nx * ny;
-    const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * kZmBX;
-    const int y0 = (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kZmBY;
-    const int z0 = (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z) * zs;
     const int z1 = min(z0 + zs, nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool leader = (tx | ty) == 0;
@@ -534,7 +532,7 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
         // by every thread at the barrier ending the previous iteration)
         if (!FUSED && leader) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_load_4d(smem_u32(sP), &tm_fnew, x0, y0, z, 0, bar_a, kBytes);
+            tma_load_4d(smem_u32(sP), tm_fnew, x0, y0, z, 0, bar_a, kBytes);
         }
         // stage plane z+2 while this plane is computed
         const bool more = z + 2 <= z1;
@@ -625,6 +623,40 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
         if (more) store_plane((k + 3) % 4, vi, vh);
         __syncthreads();
     }
+}
+
+template <class PT, int NCOMP, bool FD, bool FUSED>
+__global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
+                                                               const float* __restrict__ frest,
+                                                               float* __restrict__ drho, const float* __restrict__ Ct,
+                                                               float* __restrict__ Cout, float* __restrict__ R,
+                                                               const float* __restrict__ u, float* __restrict__ Q,
+                                                               unsigned* __restrict__ status, StepParams p, int zs,
+                                                               int rev, const PT* __restrict__ fnew, int zl) {
+    const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * kZmBX;
+    const int y0 = (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kZmBY;
+    const int z0 = (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z) * zs;
+    post_column<PT, NCOMP, FD, FUSED>(&tm_fnew, frest, drho, Ct, Cout, R, u, Q, status, p, x0, y0, z0, zs, fnew, zl);
+}
+
+// Batched ensemble form: block i (taken in reverse order, so the pass starts on
+// the tiles the lattice kernel touched last) runs column item i - start[m] of
+// member m: columns x-fastest, then y, then z-segments of the member's zs planes.
+template <class PT, int NCOMP, bool FD>
+__global__ void __launch_bounds__(kZmBX * kZmBY, 2)
+    k_post_batch(const EnsMember* __restrict__ members, const int* __restrict__ start, int nm, int parity) {
+    const int item = (int)(gridDim.x - 1 - blockIdx.x);
+    const int m = batch_member(start, nm, item);
+    const EnsMember& M = members[m];
+    const int t = item - start[m];
+    const StepParams p = M.p;
+    const StepBufs b = M.b[parity];
+    const int r = t / M.ncx;
+    const CUtensorMap* tm = &M.tm_post[1 - (M.cur0 ^ parity)];      // the populations just written
+    if ((threadIdx.x | threadIdx.y) == 0) tensormap_acquire(tm);  // the thread that issues the copies
+    post_column<PT, NCOMP, FD, false>(tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p,
+                                      (t % M.ncx) * kZmBX, (r % M.ncy) * kZmBY, (r / M.ncy) * M.zs, M.zs,
+                                      static_cast<const PT*>(b.fout), 1);
 }
 
 // Densities and feedback stress of a given state (no time step).
@@ -768,6 +800,36 @@ cudaError_t launch_post_zm_fused(int ncomp, bool fd, const StepParams& p, const 
             e = fd ? post_zm<PT, 2, true, true>(nullptr, p, b, s, rev, zs) : post_zm<PT, 2, false, true>(nullptr, p, b, s, rev, zs);
         else
             e = fd ? post_zm<PT, 1, true, true>(nullptr, p, b, s, rev, zs) : post_zm<PT, 1, false, true>(nullptr, p, b, s, rev, zs);
+    });
+    return e;
+}
+
+namespace {
+template <class PT, int NCOMP, bool FD>
+cudaError_t post_batch(const EnsMember* members, const int* start, int nm, int items, int parity, bool pdl,
+                       cudaStream_t s) {
+    constexpr int smem = zm_smem_bytes<PT, NCOMP>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_post_batch<PT, NCOMP, FD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return launch_pdl(pdl, k_post_batch<PT, NCOMP, FD>, dim3(items), dim3(kZmBX, kZmBY, 1), smem, s, members, start,
+                      nm, parity);
+}
+}  // namespace
+
+cudaError_t launch_post_batch(int ncomp, int prec, bool fd, const EnsMember* members, const int* start, int nm,
+                              int items, int parity, bool pdl, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    VEFD_WITH_PT(prec, {
+        if (ncomp == 2)
+            e = fd ? post_batch<PT, 2, true>(members, start, nm, items, parity, pdl, s)
+                   : post_batch<PT, 2, false>(members, start, nm, items, parity, pdl, s);
+        else
+            e = fd ? post_batch<PT, 1, true>(members, start, nm, items, parity, pdl, s)
+                   : post_batch<PT, 1, false>(members, start, nm, items, parity, pdl, s);
     });
     return e;
 }

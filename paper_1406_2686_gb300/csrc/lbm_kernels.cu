@@ -159,6 +159,12 @@ cudaError_t launch_lattice_zm(int ncomp, const StepParams& p, const StepBufs& b,
 
 int lattice_zm_segment(const StepParams& p) { return zm_segment_length(p); }
 
+cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, const EnsMember* members, const int* start, int nm,
+                                 int items, int parity, bool pdl, cudaStream_t s) {
+    if (coll == 1) return launch_lattice_batch_mrt(ncomp, prec, members, start, nm, items, parity, pdl, s);
+    return launch_lattice_batch_coll<0>(ncomp, prec, members, start, nm, items, parity, pdl, s);
+}
+
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,
                                     const float* rhoB, const float* u, void* fd, float* frest, cudaStream_t s) {
     const int g = grid_1d(p.N);

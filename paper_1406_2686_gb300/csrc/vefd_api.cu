@@ -1045,6 +1045,16 @@ struct vefd_ensemble {
     cudaGraphExec_t exec = nullptr;
     std::vector<std::vector<double>> key;  // member state the graph was captured for
     std::string err;
+    // batched launches: one lattice kernel and one densities/FENE-P pass per
+    // step over the tiles of all members, from a device table of members
+    int batched_pref = 1;       // use them when the members allow
+    bool batched = false;       // the captured graph uses them
+    std::vector<EnsMember> table;
+    std::vector<int> start;     // lattice tiles then z-march columns: first item of each member
+    EnsMember* d_table = nullptr;
+    int* d_start = nullptr;
+    size_t d_cap = 0;           // members the device table holds
+    int lat_items = 0, post_items = 0;
 };
 
 namespace {
@@ -1061,7 +1071,146 @@ std::vector<double> ens_key(const vefd_ctx* m) {
             (double)m->phase, (double)m->fd_on, (double)m->coupling, (double)m->collision, (double)m->chol, m->rho_ref[0], m->rho_ref[1],
             (double)m->lat_tile, (double)m->tma_ok, (double)m->zm_ok, (double)m->fused_ok,
             (double)(m->drho < m->drho_alt), (double)m->sched, (double)m->cur,
-            (double)m->ccur, (double)m->have_prev, (double)m->drho_valid};
+            (double)m->ccur, (double)m->have_prev, (double)m->drho_valid, (double)m->pdl,
+            (double)(uintptr_t)m->mem, (double)m->zm_seg_fixed};
+}
+
+// Members can share batched launches when they agree on everything the
+// kernels are specialised for and each takes the 32 x 4 x 2 staged lattice
+// tile and the separate z-marching densities/FENE-P pass.
+bool ens_batchable(const vefd_ensemble* e) {
+    const vefd_ctx* a = e->members[0];
+    for (const vefd_ctx* m : e->members) {
+        if (m->cfg.lattice != VEFD_D3Q19 || m->cfg.ncomp != a->cfg.ncomp || m->cfg.precision != a->cfg.precision ||
+            m->collision != a->collision || m->fd_on != a->fd_on || m->pdl != a->pdl)
+            return false;
+        if (!m->tma_ok || !m->zm_ok || m->fused_ok) return false;
+    }
+    return true;
+}
+
+// z-segment length of the batched z-march pass: fewest (waves x planes per
+// block), counting two planes of ring prologue per block.
+int ens_post_segment(const vefd_ensemble* e, int sms) {
+    int maxnz = 1;
+    for (const vefd_ctx* m : e->members) maxnz = std::max(maxnz, m->cfg.nz);
+    const long long slots = 2LL * sms;  // two blocks per SM
+    int best = maxnz;
+    long long best_cost = -1;
+    for (int zs = 1; zs <= maxnz; ++zs) {
+        long long items = 0;
+        for (const vefd_ctx* m : e->members) {
+            const int z = std::min(zs, m->cfg.nz);
+            items += (long long)(m->cfg.nx / 32) * (m->cfg.ny / 8) * ((m->cfg.nz + z - 1) / z);
+        }
+        const long long cost = ((items + slots - 1) / slots) * (zs + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = zs;
+        }
+    }
+    return best;
+}
+
+// Builds and uploads the member table (both ping-pong parities of every
+// member) for the batched launches; the upload is ordered on e->main after
+// every earlier replay that reads the old table.
+vefd_status ens_build_table(vefd_ensemble* e) {
+    const size_t n = e->members.size();
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+    const int zs = ens_post_segment(e, sms);
+    e->table.assign(n, EnsMember{});
+    e->start.assign(2 * n, 0);
+    long long lat = 0, post = 0;
+    for (size_t k = 0; k < n; ++k) {
+        vefd_ctx* m = e->members[k];
+        EnsMember& M = e->table[k];
+        M.p = params_of(m);
+        M.cur0 = m->cur;
+        for (int k = 0; k < 2; ++k) {
+            M.tm_lat[k] = m->tmap_post[k];  // box 32 x 4 x 2
+            M.tm_post[k] = m->tmap_zm[k];   // box 32 x 8 x 1
+        }
+        for (int par = 0; par < 2; ++par) {
+            const int cur = m->cur ^ par, ccur = m->ccur ^ (m->fd_on ? par : 0);
+            StepBufs b = bufs_of(m);
+            b.fin = m->f[cur];
+            b.fout = m->f[1 - cur];
+            b.Cin = m->C[ccur];
+            b.Cout = m->C[1 - ccur];
+            M.b[par] = b;
+        }
+        M.ntx = (m->cfg.nx + 31) / 32;
+        M.nty = (m->cfg.ny + 3) / 4;
+        M.ntz = (m->cfg.nz + 1) / 2;
+        M.ncx = m->cfg.nx / 32;
+        M.ncy = m->cfg.ny / 8;
+        M.zs = std::min(zs, m->cfg.nz);
+        M.nseg = (m->cfg.nz + M.zs - 1) / M.zs;
+        e->start[k] = (int)lat;
+        e->start[n + k] = (int)post;
+        lat += (long long)M.ntx * M.nty * M.ntz;
+        post += (long long)M.ncx * M.ncy * M.nseg;
+    }
+    if (lat > 0x7fffffffLL || post > 0x7fffffffLL) return ens_fail(e, VEFD_ERR_ARG, "ensemble too large for one launch");
+    e->lat_items = (int)lat;
+    e->post_items = (int)post;
+    if (e->d_cap < n) {
+        if (e->main) cudaStreamSynchronize(e->main);
+        if (e->d_table) cudaFree(e->d_table);
+        if (e->d_start) cudaFree(e->d_start);
+        e->d_table = nullptr;
+        e->d_start = nullptr;
+        e->d_cap = 0;
+        if (cudaMalloc((void**)&e->d_table, n * sizeof(EnsMember)) != cudaSuccess ||
+            cudaMalloc((void**)&e->d_start, 2 * n * sizeof(int)) != cudaSuccess)
+            return ens_fail(e, VEFD_ERR_CUDA, "cannot allocate the member table");
+        e->d_cap = n;
+    }
+    if (cudaMemcpyAsync(e->d_table, e->table.data(), n * sizeof(EnsMember), cudaMemcpyHostToDevice, e->main) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(e->d_start, e->start.data(), 2 * n * sizeof(int), cudaMemcpyHostToDevice, e->main) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(e->main) != cudaSuccess)
+        return ens_fail(e, VEFD_ERR_CUDA, "cannot upload the member table");
+    return VEFD_OK;
+}
+
+// Captures `chunk` steps of all members as two batched launches per step.
+vefd_status ens_capture_batched(vefd_ensemble* e, int64_t chunk) {
+    vefd_status st = ens_build_table(e);
+    if (st != VEFD_OK) return st;
+    const vefd_ctx* a = e->members[0];
+    const int nm = (int)e->members.size();
+    const int nc = a->cfg.ncomp, prec = a->cfg.precision;
+    const bool fd = a->fd_on != 0, pdl = a->pdl;
+    if (cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return ens_fail(e, VEFD_ERR_CUDA, "cannot begin capture");
+    cudaError_t ce = cudaSuccess;
+    for (int64_t k = 0; k < chunk && ce == cudaSuccess; ++k) {
+        const int par = (int)(k & 1);
+        ce = launch_lattice_batch(nc, prec, a->collision, e->d_table, e->d_start, nm, e->lat_items, par, pdl, e->main);
+        if (ce == cudaSuccess)
+            ce = launch_post_batch(nc, prec, fd, e->d_table, e->d_start + nm, nm, e->post_items, par, pdl, e->main);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce2 = cudaStreamEndCapture(e->main, &graph);
+    if (ce != cudaSuccess || ce2 != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return ens_fail(e, VEFD_ERR_CUDA, std::string("batched graph capture failed: ") +
+                                              cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+    }
+    ce = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        e->exec = nullptr;
+        return ens_fail(e, VEFD_ERR_CUDA, "graph instantiation failed");
+    }
+    e->batched = true;
+    return VEFD_OK;
 }
 
 // A member is steady when its next step is the plain AB2 step with current
@@ -1172,9 +1321,7 @@ vefd_status ens_capture(vefd_ensemble* e, int64_t chunk) {
         e->exec = nullptr;
         return ens_fail(e, VEFD_ERR_CUDA, "graph instantiation failed");
     }
-    e->chunk = chunk;
-    e->key.resize(n);
-    for (size_t k = 0; k < n; ++k) e->key[k] = ens_key(e->members[k]);
+    e->batched = false;
     return VEFD_OK;
 }
 
@@ -1217,6 +1364,8 @@ void vefd_ensemble_destroy(vefd_ensemble* e) {
     for (cudaStream_t s : e->branch)
         if (s) cudaStreamSynchronize(s);
     if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->d_table) cudaFree(e->d_table);
+    if (e->d_start) cudaFree(e->d_start);
     for (cudaStream_t s : e->branch)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t v : e->join)
@@ -1249,8 +1398,12 @@ vefd_status vefd_ensemble_step(vefd_ensemble* e, int64_t nsteps, int64_t chunk) 
         if (stale) {
             if (e->exec) cudaGraphExecDestroy(e->exec);
             e->exec = nullptr;
-            const vefd_status st = ens_capture(e, chunk);
+            const vefd_status st =
+                e->batched_pref && ens_batchable(e) ? ens_capture_batched(e, chunk) : ens_capture(e, chunk);
             if (st != VEFD_OK) return st;
+            e->chunk = chunk;
+            e->key.resize(e->members.size());
+            for (size_t k = 0; k < e->members.size(); ++k) e->key[k] = ens_key(e->members[k]);
         }
         if (ens_wait_inputs(e, e->main) != cudaSuccess) return ens_fail(e, VEFD_ERR_CUDA, "ordering after the inputs failed");
         for (int64_t r = 0; r < full; ++r)
@@ -1262,6 +1415,22 @@ vefd_status vefd_ensemble_step(vefd_ensemble* e, int64_t nsteps, int64_t chunk) 
     }
     return ens_eager(e, nsteps - full * chunk);
 }
+
+vefd_status vefd_ensemble_set_batched(vefd_ensemble* e, int on) {
+    if (!e || (on != 0 && on != 1)) return VEFD_ERR_ARG;
+    if (e->batched_pref != on) {
+        // the next replay re-captures; earlier replays may still be in flight
+        if (e->exec) {
+            cudaStreamSynchronize(e->main);
+            cudaGraphExecDestroy(e->exec);
+        }
+        e->exec = nullptr;
+        e->batched_pref = on;
+    }
+    return VEFD_OK;
+}
+
+int vefd_ensemble_is_batched(const vefd_ensemble* e) { return e && e->exec && e->batched ? 1 : 0; }
 
 const char* vefd_ensemble_last_error(const vefd_ensemble* e) { return e ? e->err.c_str() : "NULL ensemble"; }
 

@@ -16,6 +16,7 @@
 // below); all arithmetic stays FP32 and C stays FP32.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -67,6 +68,26 @@ __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1)
 // --- population storage types: FP32, FP16 or BF16 deviations ------------------
 
 enum { kPrecFp32 = 0, kPrecFp16 = 1, kPrecBf16 = 2 };
+
+// A tensor map the host copied into global memory (rather than passed as a
+// kernel parameter) is made visible to the tensor-map proxy before use; the
+// bulk tensor copies would otherwise be allowed to use a descriptor cached from
+// earlier contents at the same address.
+__device__ __forceinline__ void tensormap_acquire(const void* tm) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(tm) : "memory");
+}
+
+// Member of a batched ensemble that work item `item` belongs to: the last m
+// with start[m] <= item (start is increasing, start[0] = 0).
+__device__ __forceinline__ int batch_member(const int* __restrict__ start, int nm, int item) {
+    int lo = 0, hi = nm - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ float pop_load(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float pop_load(const __half* p) { return __half2float(__ldg(p)); }
@@ -245,6 +266,24 @@ struct StepBufs {
                            // densities/FD pass overwrites it with time n+1)
 };
 
+// One lattice of a batched ensemble step, as the batched kernels read it from
+// device memory: parameters, the buffers of both ping-pong parities, the tensor
+// maps of the two population buffers f[0], f[1] (lattice kernel: 32 x 4 x 2
+// tiles; densities/FENE-P pass: 32 x 8 x 1 planes), the buffer parity 0 reads
+// (cur0; parity q reads f[cur0 ^ q] and writes the other), and the work split
+// (lattice tiles; z-marching columns and segments of zs planes).  The tensor
+// maps depend on the buffers only, so rebuilding the table for the other
+// parity rewrites them with the same bytes.
+struct alignas(64) EnsMember {
+    CUtensorMap tm_lat[2];
+    CUtensorMap tm_post[2];
+    StepParams p;
+    StepBufs b[2];
+    int cur0;
+    int ntx, nty, ntz;
+    int ncx, ncy, nseg, zs;
+};
+
 // Launchers (return cudaGetLastError of the launch).  `rev` walks the tiles in
 // reverse order, so that a kernel starts on the data its predecessor touched
 // last (still in L2).
@@ -267,6 +306,16 @@ cudaError_t launch_lattice_zm(int ncomp, const StepParams& p, const StepBufs& b,
 int lattice_zm_segment(const StepParams& p);
 cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
                                   const void* tensor_map, int zs, int rev);
+// Batched ensemble step: one launch of the lattice kernel over the tiles of
+// every member (item i belongs to the last member m with start[m] <= i), then
+// one launch of the z-marching densities/FENE-P pass over their columns; all
+// members share lattice D3Q19, ncomp, storage type, collision and fd_on.
+cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, const EnsMember* members, const int* start, int nm,
+                                 int items, int parity, bool pdl, cudaStream_t s);
+cudaError_t launch_lattice_batch_mrt(int ncomp, int prec, const EnsMember* members, const int* start, int nm,
+                                     int items, int parity, bool pdl, cudaStream_t s);
+cudaError_t launch_post_batch(int ncomp, int prec, bool fd, const EnsMember* members, const int* start, int nm,
+                              int items, int parity, bool pdl, cudaStream_t s);
 // Staged tile shapes of the lattice kernel: tile 0..2 ->
 // D3Q19 32x4x2, 32x2x4, 32x8x1; D2Q9 32x8x1, 32x4x1, 32x16x1.
 void lattice_tile_shape(int lattice, int tile, int* bx, int* by, int* bz);

@@ -43,7 +43,7 @@ EXPORTS = [
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
     "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
     "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
-    "vefd_ensemble_destroy", "vefd_set_collision", "vefd_set_conformation_update",
+    "vefd_ensemble_destroy", "vefd_ensemble_set_batched", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
 ]
 
 _lib = None
@@ -98,6 +98,7 @@ def load(build_if_missing=True):
         "vefd_autotune": [vp, cint, ctypes.POINTER(dbl)],
         "vefd_ensemble_create": [ctypes.POINTER(vp), cint, vp, ctypes.POINTER(vp)],
         "vefd_ensemble_step": [vp, i64, i64],
+        "vefd_ensemble_set_batched": [vp, cint],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -107,6 +108,8 @@ def load(build_if_missing=True):
     L.vefd_destroy.restype = None
     L.vefd_last_error.argtypes = [vp]
     L.vefd_last_error.restype = ctypes.c_char_p
+    L.vefd_ensemble_is_batched.argtypes = [vp]
+    L.vefd_ensemble_is_batched.restype = cint
     L.vefd_ensemble_destroy.argtypes = [vp]
     L.vefd_ensemble_destroy.restype = None
     L.vefd_ensemble_last_error.argtypes = [vp]
@@ -301,6 +304,14 @@ def vefd_ensemble_step(ens, nsteps, chunk=32):
     return _ens_check(ens, load().vefd_ensemble_step(ens, int(nsteps), int(chunk)))
 
 
+def vefd_ensemble_set_batched(ens, on):
+    return _ens_check(ens, load().vefd_ensemble_set_batched(ens, int(on)))
+
+
+def vefd_ensemble_is_batched(ens):
+    return bool(load().vefd_ensemble_is_batched(ens))
+
+
 def vefd_ensemble_last_error(ens):
     return (load().vefd_ensemble_last_error(ens) or b"").decode()
 
@@ -458,8 +469,9 @@ class Lattice:
 
 
 class Ensemble:
-    """Independent lattices stepped together as one replayed CUDA graph
-    (one concurrent branch per lattice).  Holds references to its members."""
+    """Independent lattices stepped together as one replayed CUDA graph: two
+    batched launches per step over all members when they allow it, else one
+    concurrent branch per lattice.  Holds references to its members."""
 
     def __init__(self, lattices, stream=None):
         import torch
@@ -469,6 +481,16 @@ class Ensemble:
 
     def step(self, n, chunk=32):
         vefd_ensemble_step(self.ens, n, chunk)
+
+    def set_batched(self, on):
+        """One launch per kernel phase over all members (default), or one
+        graph branch per member."""
+        vefd_ensemble_set_batched(self.ens, 1 if on else 0)
+
+    @property
+    def batched(self):
+        """True when the captured graph uses the batched launches."""
+        return vefd_ensemble_is_batched(self.ens)
 
     def close(self):
         if getattr(self, "ens", None):

@@ -174,3 +174,135 @@ def test_ensemble_errors():
     E.step(0)
     assert A.steps_done == 0
     E.close()
+
+
+# D3Q19 boxes that admit the batched launches (NX % 32 == 0, NY % 8 == 0):
+# uneven sizes, an odd NZ (a half-empty last lattice tile), walls on and off,
+# both feedback couplings, and a box only one lattice tile deep (NZ 2)
+BATCH_BOXES = [
+    dict(lattice=1, nx=64, ny=16, nz=6, ncomp=2, walls=1, G=1.5, u_wall=0.03, eta_p=0.1, tau_p=20.0, L2=50.0,
+         kappa=0.01, phase=1),
+    dict(lattice=1, nx=32, ny=8, nz=5, ncomp=2, walls=0, G=1.5, eta_p=0.1, tau_p=20.0, L2=50.0, kappa=0.02,
+         fext=(1e-5, -1e-5, 0.0), phase=-1),
+    dict(lattice=1, nx=96, ny=24, nz=9, ncomp=2, walls=1, G=1.5, u_wall=-0.02, eta_p=0.15, tau_p=20.0, L2=50.0,
+         kappa=0.01, phase=1, coupling=1),
+    dict(lattice=1, nx=32, ny=16, nz=2, ncomp=2, walls=1, G=1.5, u_wall=0.01, eta_p=0.1, tau_p=25.0, L2=40.0,
+         kappa=0.01, phase=-1),
+    dict(lattice=1, nx=32, ny=8, nz=12, ncomp=2, walls=1, G=1.2, u_wall=0.02, eta_p=0.1, tau_p=20.0, L2=60.0,
+         kappa=0.0, phase=1),
+]
+
+
+def close_state(a, b, rel=1e-6):
+    """Populations and C within `rel` (relative L2); the AB2 history R, the
+    FENE-P right-hand side, is a difference of nearly cancelling terms and is
+    allowed 20 times more."""
+    return all(np.linalg.norm(x - y) <= r * np.linalg.norm(y)
+               for x, y, r in zip(state(a), state(b), (rel, rel, 20 * rel)))
+
+
+def _batched_vs_alone(boxes, prep, steps=(23, 1, 16)):
+    """Steps an ensemble of `boxes` (after prep(L)) with batched launches and
+    the same boxes alone; returns both lists."""
+    from paper_1406_2686_gb300 import vefd
+    ens = [make(b, seed=40 + i) for i, b in enumerate(boxes)]
+    alone = [make(b, seed=40 + i) for i, b in enumerate(boxes)]
+    for L in ens + alone:
+        prep(L)
+    E = vefd.Ensemble(ens)
+    for seg, n in enumerate(steps):
+        E.step(n, chunk=4)
+        if n >= 8:
+            assert E.batched
+        for L in alone:
+            L.step(n)
+        for k, (a, r) in enumerate(zip(ens, alone)):
+            assert close_state(a, r, 1e-3 if a.cfg.precision else 1e-6), (seg, k)
+    E.close()
+    return ens, alone
+
+
+def test_batched_ensemble_matches_single_lattices():
+    """Two launches per step over all boxes' tiles give each box's own step:
+    the same arithmetic as the per-lattice kernels (separately compiled, so
+    multiply-add contraction may differ in the last ulp), across the Euler
+    start, replays of both parities and an odd remainder."""
+    ens, alone = _batched_vs_alone(BATCH_BOXES, lambda L: None)
+    for a, b in zip(ens, alone):
+        assert a.steps_done == b.steps_done == 40
+        assert close_state(a, b)
+        assert a.status() == 0
+
+
+@pytest.mark.parametrize("variant", ["fp16", "mrt_chol", "one_component"])
+def test_batched_ensemble_variants(variant):
+    """The batched kernels for 16-bit storage, the moment-space collision with
+    the log-Cholesky conformation update, and one-component boxes."""
+    boxes = [dict(b) for b in BATCH_BOXES[:3]]
+    prep = lambda L: None
+    if variant == "fp16":
+        for b in boxes:
+            b["precision"] = 1
+    elif variant == "mrt_chol":
+        def prep(L):
+            L.set_collision(1)
+            L.set_conformation_update(1)
+    else:
+        for b in boxes:
+            b.update(ncomp=1, G=0.0, phase=0)
+    ens, alone = _batched_vs_alone(boxes, prep)
+    for a, b in zip(ens, alone):
+        assert close_state(a, b, 1e-6 if variant != "fp16" else 1e-3)
+        assert a.status() == 0
+
+
+def test_batched_ensemble_selection():
+    """Batched launches only where every member allows them; otherwise (and on
+    request) one graph branch per member, bit for bit equal to stepping alone."""
+    from paper_1406_2686_gb300 import vefd
+    A = make(BATCH_BOXES[0], seed=3)
+    B = make(BATCH_BOXES[4], seed=4)
+    E = vefd.Ensemble([A, B])
+    E.step(9, chunk=4)
+    assert E.batched
+    E.set_batched(False)
+    E.step(8, chunk=4)
+    assert not E.batched
+    E.set_batched(True)
+    E.step(8, chunk=4)
+    assert E.batched
+    B.set_kernel_config(0, 1)  # tiled densities pass: not batchable
+    E.step(8, chunk=4)
+    assert not E.batched
+    E.close()
+    # branch mode is bit-identical
+    C = make(BATCH_BOXES[0], seed=5)
+    D = make(BATCH_BOXES[0], seed=5)
+    E = vefd.Ensemble([C])
+    E.set_batched(False)
+    E.step(13, chunk=4)
+    D.step(13)
+    assert same(C, D)
+    E.close()
+    with pytest.raises(vefd.VefdError):
+        vefd.vefd_ensemble_set_batched(None, 1)
+
+
+def test_batched_ensemble_many_members():
+    """Forty boxes, two launches per step, each equal to the box stepped alone."""
+    from paper_1406_2686_gb300 import vefd
+    boxes = []
+    for i in range(40):
+        b = dict(BATCH_BOXES[i % 5])
+        boxes.append(b)
+    ens = [make(b, seed=100 + i) for i, b in enumerate(boxes)]
+    alone = [make(b, seed=100 + i) for i, b in enumerate(boxes)]
+    E = vefd.Ensemble(ens)
+    E.step(17, chunk=8)
+    assert E.batched
+    for L in alone:
+        L.step(17)
+    for a, b in zip(ens, alone):
+        assert close_state(a, b)
+        assert a.status() == 0
+    E.close()
