@@ -320,7 +320,12 @@ def ensemble_boxes(n=64, seed=7):
     return boxes
 
 
-def time_ensemble(steps, warmup, chunk=32):
+def small_boxes(n=256):
+    """n equal small droplet boxes, 32 x 16 x 16 (8192 nodes each)."""
+    return [(32, 16, 16)] * n
+
+
+def time_ensemble(steps, warmup, chunk=32, boxes=None, label=None):
     """Many small independent lattices: stepped one after another on one stream
     (plain vefd_step per lattice) versus as one ensemble, either one CUDA graph
     with a concurrent branch per lattice or two batched launches per step over
@@ -328,7 +333,9 @@ def time_ensemble(steps, warmup, chunk=32):
     import torch
 
     from paper_1406_2686_gb300 import vefd
-    boxes = ensemble_boxes()
+    if boxes is None:
+        boxes = ensemble_boxes()
+        label = "D3Q19 two-component droplets, NX in {32,64,96}, NY, NZ in {16,...,64} step 8 (SplitMix64 seed 7)"
 
     def build():
         lats = []
@@ -344,8 +351,7 @@ def time_ensemble(steps, warmup, chunk=32):
 
     nodes = sum(a * b * c for a, b, c in boxes)
     stream = torch.cuda.current_stream()
-    out = {"lattices": len(boxes), "nodes": nodes, "steps": steps, "chunk": chunk,
-           "boxes": "D3Q19 two-component droplets, NX in {32,64,96}, NY, NZ in {16,...,64} step 8 (SplitMix64 seed 7)"}
+    out = {"lattices": len(boxes), "nodes": nodes, "steps": steps, "chunk": chunk, "boxes": label}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lats = build()
     for L in lats:
@@ -492,6 +498,8 @@ def run_ours(args):
                                     "equilibrium; %d steps each" % vsteps)
     if not args.no_ensemble and S.prec == 0:
         line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
+        line["ensemble_small"] = time_ensemble(max(100, K // 20), min(W, 20), boxes=small_boxes(),
+                                               label="256 D3Q19 two-component droplets, 32 x 16 x 16 each")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(S)
     if rank == 0:

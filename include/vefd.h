@@ -46,8 +46,8 @@ typedef enum {
     VEFD_OK = 0,
     VEFD_ERR_ARG = -1,       /* bad argument or size; nothing was changed */
     VEFD_ERR_CUDA = -2,      /* a CUDA call failed; see vefd_last_error */
-    VEFD_ERR_UNSTABLE = -3,  /* the device guard word is set (NaN, tr C >= L^2, |u| > 0.3, rho <= 0, wait timeout) */
-    VEFD_ERR_TIMEOUT = -4,   /* reserved for bounded device waits */
+    VEFD_ERR_UNSTABLE = -3,  /* the device guard word is set (NaN, tr C >= L^2, |u| > 0.3, rho <= 0) */
+    VEFD_ERR_TIMEOUT = -4,   /* a bounded device wait ran out (guard bit VEFD_ST_TIMEOUT) */
     VEFD_ERR_STATE = -5      /* call out of order (e.g. memory not bound, fields not initialised) */
 } vefd_status;
 
@@ -172,8 +172,22 @@ vefd_status vefd_field_bytes(const vefd_ctx *ctx, vefd_field field, size_t *byte
  *  12, 13 droplet centroid x, y in that plane  14 droplet volume (phi > 0)
  *  15 <tr sigma_P> - 3 */
 vefd_status vefd_diagnostics(vefd_ctx *ctx, double out[16]);
-/* Reads the guard word (synchronises); returns VEFD_ERR_UNSTABLE when any bit is set. */
+/* Reads the guard word (synchronises); returns VEFD_ERR_TIMEOUT when the
+ * wait-timeout bit is set, else VEFD_ERR_UNSTABLE when any other bit is set. */
 vefd_status vefd_get_status(vefd_ctx *ctx, uint32_t *bits);
+/* Exercises the bounded-wait guard without a fault (the paper has no
+ * counterpart).  Every device wait of the library (the mbarrier waits of the
+ * bulk tensor copies and of the tensor-core GEMM) gives up after 2^31 SM
+ * cycles of clock64 (about one second) or 2^22 polls, sets VEFD_ST_TIMEOUT
+ * and leaves its kernel with no copy in flight.  This call runs one such wait
+ * on the context's stream, with a budget of 2^24 cycles (about 8 ms), on an
+ * mbarrier that one thread completes (arrive = 1: no bit is set) or that
+ * nothing completes (arrive = 0: the wait runs out and VEFD_ST_TIMEOUT is set,
+ * so vefd_get_status returns VEFD_ERR_TIMEOUT; vefd_clear_status resets it and
+ * the context stays usable).  Asynchronous.  VEFD_ERR_ARG for a NULL context
+ * or arrive not 0/1, VEFD_ERR_STATE without bound memory, VEFD_ERR_CUDA on a
+ * launch error. */
+vefd_status vefd_wait_selftest(vefd_ctx *ctx, int arrive);
 vefd_status vefd_clear_status(vefd_ctx *ctx);
 vefd_status vefd_steps_done(const vefd_ctx *ctx, int64_t *n);
 /* Raw binary checkpoint of populations, C, AB2 history, counters and

@@ -400,7 +400,10 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
         }
     }
     if (!mbar_wait_bounded(bar_a)) {
-        if (leader) atomicOr(status, kStTimeout);
+        if (leader) {
+            atomicOr(status, kStTimeout);
+            mbar_wait_bounded(bar_a);  // bounded: let the copy land before leaving
+        }
         return;
     }
     if (!active) return;

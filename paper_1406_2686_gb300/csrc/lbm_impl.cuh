@@ -115,13 +115,9 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const StepParams& p
 //   Fp     = (eta_P / tau_P) div Q, Q = (f C - I) m(phi) precomputed per node,
 //            central differences, one-sided at walls (the linear-extrapolation
 //            ghost row v(-1) = 2 v(0) - v(1)).
-// HX > 0: the density deviations come from a shared-memory halo box of
-// HX x HY x (HN / (HX HY)) nodes per component (stride HN), sdc pointing at
-// this node; otherwise from global memory.
-template <class L, int NCOMP, int HX = 0, int HY = 0, int HN = 0>
+template <class L, int NCOMP>
 __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepParams& p, const Nbr& nb,
-                                                 float acc[2][3], float Fp[3], float qloc[L::NQ],
-                                                 const float* sdc = nullptr) {
+                                                 float acc[2][3], float Fp[3], float qloc[L::NQ]) {
     const int N = (int)p.N;
     const int i = nb.i;
 #pragma unroll
@@ -135,8 +131,7 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
             const bool axis = L::w(a) == L::w(1);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const float t = HX > 0 ? sdc[s * HN + L::cx(a) + L::cy(a) * HX + L::cz(a) * HX * HY]
-                                       : __ldg(b.drho + s * N + j);
+                const float t = __ldg(b.drho + s * N + j);
                 float* acc_s = axis ? sa[s] : sd[s];
                 if (L::cx(a)) acc_s[0] += L::cx(a) * t;
                 if (L::cy(a)) acc_s[1] += L::cy(a) * t;
@@ -591,54 +586,6 @@ __device__ __forceinline__ void node_gather(const StepBufs& b, const StepParams&
     neighbour_forces<L, NCOMP>(b, p, g.nb, g.acc, g.Fp, g.qloc);
 }
 
-// Density deviations of a BX x BY x BZ tile and its one-node halo (periodic
-// in x and z, clamped to the wall rows or periodic in y, as make_nbr) into
-// shared memory sd[s][HZ][HY][HX], one warp per halo row; every index stays
-// inside the lattice for the tile shapes pop_tile_eligible admits (a halo
-// coordinate is at most one tile beyond the lattice, and the lattice is at
-// least one tile wide).
-template <class L, int BX, int BY, int BZ>
-struct DensityHalo {
-    static_assert(BX == 32, "one warp per halo row");
-    static constexpr int HX = BX + 2, HY = BY + 2, HZ = L::D == 3 ? BZ + 2 : 1, HN = HX * HY * HZ;
-    static constexpr int bytes = 2 * HN * (int)sizeof(float);
-    __device__ __forceinline__ static void stage(float* sd, const float* __restrict__ drho, const StepParams& p,
-                                                 int x0, int y0, int z0, int lt) {
-        constexpr int NW = BX * BY * BZ / 32;
-        const int lane = lt & 31, w = lt >> 5;
-        const int nx = p.nx, ny = p.ny, N = (int)p.N;
-        const int xa = wrap1(x0 - 1 + lane, nx);
-        const bool has_b = lane < HX - 32;
-        const int xb = has_b ? wrap1(x0 + 31 + lane, nx) : 0;
-        for (int r = w; r < HY * HZ; r += NW) {
-            const int yq = r % HY, zq = r / HY;
-            const int gy = y_clamped(y0 - 1 + yq, ny, p.walls);
-            const int gz = L::D == 3 ? wrap1(z0 - 1 + zq, p.nz) : 0;
-            const int base = (gz * ny + gy) * nx;
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                sd[s * HN + r * HX + lane] = __ldg(drho + s * N + base + xa);
-                if (has_b) sd[s * HN + r * HX + 32 + lane] = __ldg(drho + s * N + base + xb);
-            }
-        }
-    }
-    // this thread's node in the halo box
-    __device__ __forceinline__ static const float* centre(const float* sd, int tx, int ty, int tz) {
-        return sd + ((L::D == 3 ? tz + 1 : 0) * HY + ty + 1) * HX + tx + 1;
-    }
-};
-
-// node_gather with the density deviations read from a staged halo box.
-template <class L, int NCOMP, class H>
-__device__ __forceinline__ void node_gather_staged(const StepBufs& b, const StepParams& p, int x, int y, int z,
-                                                   bool active, const float* sdc, NodeGather<L, NCOMP>& g) {
-    g.nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
-    if (!active) return;
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) g.dr[s] = sdc[s * H::HN];
-    neighbour_forces<L, NCOMP, H::HX, H::HY, H::HN>(b, p, g.nb, g.acc, g.Fp, g.qloc, sdc);
-}
-
 template <class PT, class L, int NCOMP, int T, int COLL, bool EDGE = true>
 __device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams& p, const PT* sf, int t,
                                              const NodeGather<L, NCOMP>& g) {
@@ -693,20 +640,13 @@ __device__ __forceinline__ void lattice_tile(const CUtensorMap* tm_fin, const St
     // the preceding densities/FENE-P pass
     pdl_wait();
     NodeGather<L, NCOMP> g;
-    if constexpr (NCOMP == 2) {
-        // the Shan-Chen sums read the densities of the tile and its halo from
-        // shared memory, staged once per block in coalesced rows
-        using H = DensityHalo<L, BX, BY, BZ>;
-        float* sd = reinterpret_cast<float*>(sraw + P * T * sizeof(PT));
-        H::stage(sd, b.drho, p, x0, y0, z0, (tz * BY + ty) * BX + tx);
-        __syncthreads();
-        node_gather_staged<L, NCOMP, H>(b, p, x, y, z, active, H::centre(sd, tx, ty, tz), g);
-    } else {
-        node_gather<L, NCOMP>(b, p, x, y, z, active, g);
-    }
+    node_gather<L, NCOMP>(b, p, x, y, z, active, g);
     // bounded wait for the staged populations; on timeout report and leave
     if (!mbar_wait_bounded(bar_a)) {
-        if (leader) atomicOr(b.status, kStTimeout);
+        if (leader) {
+            atomicOr(b.status, kStTimeout);
+            mbar_wait_bounded(bar_a);  // bounded: let the copy land before leaving
+        }
         return;
     }
     pdl_trigger();
@@ -760,8 +700,8 @@ cudaError_t launch_lattice_batch_coll(int ncomp, int prec, const EnsMember* memb
     VEFD_WITH_PT(prec, {
         constexpr int smem_unit = 18 * 256 * (int)sizeof(PT);
         if (ncomp == 2)
-            e = launch_pdl(pdl, k_lattice_batch<PT, 2, COLL>, dim3(items), dim3(32, 4, 2),
-                           2 * smem_unit + DensityHalo<D3Q19, 32, 4, 2>::bytes, s, members, start, nm, parity);
+            e = launch_pdl(pdl, k_lattice_batch<PT, 2, COLL>, dim3(items), dim3(32, 4, 2), 2 * smem_unit, s,
+                           members, start, nm, parity);
         else
             e = launch_pdl(pdl, k_lattice_batch<PT, 1, COLL>, dim3(items), dim3(32, 4, 2), smem_unit, s, members,
                            start, nm, parity);
@@ -855,8 +795,7 @@ dim3 node_grid(const StepParams& p) { return dim3((p.nx + 31) / 32, (p.ny + 3) /
 
 template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL>
 cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
-    constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT) +
-                         (NCOMP == 2 ? DensityHalo<L, BX, BY, BZ>::bytes : 0);
+    constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     return launch_pdl(p.pdl != 0, k_lattice_tma<PT, L, NCOMP, BX, BY, BZ, COLL>, grd, blk, smem, s, *tm, b, p, rev);

@@ -159,6 +159,23 @@ cudaError_t launch_lattice_zm(int ncomp, const StepParams& p, const StepBufs& b,
 
 int lattice_zm_segment(const StepParams& p) { return zm_segment_length(p); }
 
+namespace {
+__global__ void k_wait_selftest(unsigned* status, int arrive, long long cycles) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned a = smem_u32(&bar);
+    if (threadIdx.x == 0) mbar_init(a);  // one arrival completes the phase
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+    const bool ok = mbar_wait_budget(a, 0u, cycles);
+    if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(unsigned* status, int arrive, long long cycles, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status, arrive, cycles);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, const EnsMember* members, const int* start, int nm,
                                  int items, int parity, bool pdl, cudaStream_t s) {
     if (coll == 1) return launch_lattice_batch_mrt(ncomp, prec, members, start, nm, items, parity, pdl, s);

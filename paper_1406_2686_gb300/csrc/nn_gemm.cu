@@ -45,16 +45,21 @@ __device__ __forceinline__ void mbar_init1(unsigned bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Bounded wait for the phase with the given parity: at most 2^31 SM cycles
+// of clock64 (about one second at 2.07 GHz) and 2^22 polls.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
+    const long long t0 = clock64();
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(bar), "r"(parity)
             : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 31)) break;
     }
-    return done != 0;
+    return false;
 }
 
 // Byte offset of element (r, k) of a rows x 64 K-major tile in the core-matrix

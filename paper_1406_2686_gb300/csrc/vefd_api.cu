@@ -767,7 +767,16 @@ vefd_status vefd_get_status(vefd_ctx* c, uint32_t* bits) {
     VEFD_CUDA(c, cudaMemcpyAsync(&v, c->status, sizeof v, cudaMemcpyDeviceToHost, c->stream));
     VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
     *bits = v;
-    return v ? VEFD_ERR_UNSTABLE : VEFD_OK;
+    if (!v) return VEFD_OK;
+    return (v & kStTimeout) ? VEFD_ERR_TIMEOUT : VEFD_ERR_UNSTABLE;
+}
+
+vefd_status vefd_wait_selftest(vefd_ctx* c, int arrive) {
+    if (!c || (arrive != 0 && arrive != 1)) return VEFD_ERR_ARG;
+    if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
+    // a budget of 2^24 cycles: about 8 ms at the maximum SM clock
+    VEFD_CUDA(c, launch_wait_selftest(c->status, arrive, 1LL << 24, c->stream));
+    return VEFD_OK;
 }
 
 vefd_status vefd_clear_status(vefd_ctx* c) {

@@ -186,16 +186,34 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const void* tmap, int 
 // Waits for the given phase parity of the barrier for a bounded number of
 // polls; returns false when the copy has not landed (the caller reports a
 // timeout).
-__device__ __forceinline__ bool mbar_wait_bounded_parity(unsigned bar, unsigned parity) {
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
+// Budget of every bounded wait: 2^31 SM cycles (about one second at the
+// 2.07 GHz maximum clock), and at most 2^22 polls whatever the clock reads.
+constexpr long long kWaitCycles = 1LL << 31;
+
+__device__ __forceinline__ unsigned mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done;
+}
+
+// Waits for the phase with the given parity to complete; false when the
+// budget (`cycles` of clock64, or 2^22 polls) runs out first.
+__device__ __forceinline__ bool mbar_wait_budget(unsigned bar, unsigned parity, long long cycles) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > cycles) break;
     }
-    return done != 0;
+    return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded_parity(unsigned bar, unsigned parity) {
+    return mbar_wait_budget(bar, parity, kWaitCycles);
 }
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar) { return mbar_wait_bounded_parity(bar, 0u); }
@@ -310,6 +328,9 @@ cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs
 // every member (item i belongs to the last member m with start[m] <= i), then
 // one launch of the z-marching densities/FENE-P pass over their columns; all
 // members share lattice D3Q19, ncomp, storage type, collision and fd_on.
+// One bounded wait on an mbarrier that one thread completes (arrive != 0) or
+// that nothing completes; on running out of `cycles` it sets kStTimeout.
+cudaError_t launch_wait_selftest(unsigned* status, int arrive, long long cycles, cudaStream_t s);
 cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, const EnsMember* members, const int* start, int nm,
                                  int items, int parity, bool pdl, cudaStream_t s);
 cudaError_t launch_lattice_batch_mrt(int ncomp, int prec, const EnsMember* members, const int* start, int nm,

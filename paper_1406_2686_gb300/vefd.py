@@ -17,7 +17,7 @@ D2Q9, D3Q19 = 0, 1
 FP32, FP16, BF16 = 0, 1, 2
 RHO_A, RHO_B, PHI, U, C, SIGMA_P, POPS, RPREV, G_A, G_B, F_P, TAU = range(12)
 OK, ERR_ARG, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5
-ST_NAN, ST_TRACE, ST_MACH, ST_RHO = 1, 2, 4, 8
+ST_NAN, ST_TRACE, ST_MACH, ST_RHO, ST_TIMEOUT = 1, 2, 4, 8, 16
 
 
 class VefdError(RuntimeError):
@@ -43,7 +43,7 @@ EXPORTS = [
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
     "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
     "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
-    "vefd_ensemble_destroy", "vefd_ensemble_set_batched", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
+    "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
 ]
 
 _lib = None
@@ -99,6 +99,7 @@ def load(build_if_missing=True):
         "vefd_ensemble_create": [ctypes.POINTER(vp), cint, vp, ctypes.POINTER(vp)],
         "vefd_ensemble_step": [vp, i64, i64],
         "vefd_ensemble_set_batched": [vp, cint],
+        "vefd_wait_selftest": [vp, cint],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -204,9 +205,13 @@ def vefd_get_status(ctx):
     """Returns the guard bits (0 when stable); never raises on instability."""
     bits = ctypes.c_uint32()
     st = load().vefd_get_status(ctx, ctypes.byref(bits))
-    if st not in (OK, ERR_UNSTABLE):
+    if st not in (OK, ERR_UNSTABLE, ERR_TIMEOUT):
         _check(ctx, st)
     return int(bits.value)
+
+
+def vefd_wait_selftest(ctx, arrive):
+    return _check(ctx, load().vefd_wait_selftest(ctx, int(arrive)))
 
 
 def vefd_clear_status(ctx):
@@ -435,6 +440,11 @@ class Lattice:
 
     def status(self):
         return vefd_get_status(self.ctx)
+
+    def wait_selftest(self, arrive):
+        """One bounded device wait that completes (arrive=True) or runs out
+        and sets ST_TIMEOUT (arrive=False); no fault either way."""
+        vefd_wait_selftest(self.ctx, 1 if arrive else 0)
 
     def clear_status(self):
         vefd_clear_status(self.ctx)

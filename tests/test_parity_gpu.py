@@ -5,6 +5,7 @@ rounding of ~6e-8 relative, so stage-wise comparisons use 1e-5 relative L2;
 after 2000 steps the contract is 1e-5 relative L2 in u and C and 1e-6
 relative total-mass drift.
 """
+import ctypes
 import math
 import os
 
@@ -327,6 +328,32 @@ def test_guards_flag_instability():
     assert P.g.status() & vefd.ST_MACH
     P.g.clear_status()
     assert P.g.status() == 0
+
+
+def test_bounded_wait_reports_timeout():
+    """A device wait that nothing completes runs out of its clock64 budget,
+    sets the timeout bit and returns (no hang, no fault); the host reads
+    VEFD_ERR_TIMEOUT, clears the word, and the context keeps stepping with
+    the same results as an untouched one."""
+    from paper_1406_2686_gb300 import vefd
+    P = Pair(lattice=1, nx=32, ny=8, nz=4, ncomp=1, walls=1, eta_p=0.1, tau_p=10.0, L2=20.0)
+    P.init(np.ones((4, 8, 32)))
+    Q = Pair(lattice=1, nx=32, ny=8, nz=4, ncomp=1, walls=1, eta_p=0.1, tau_p=10.0, L2=20.0)
+    Q.init(np.ones((4, 8, 32)))
+    P.g.wait_selftest(True)
+    assert P.g.status() == 0
+    P.g.wait_selftest(False)
+    bits = ctypes.c_uint32()
+    assert vefd.load().vefd_get_status(P.g.ctx, ctypes.byref(bits)) == vefd.ERR_TIMEOUT
+    assert bits.value == vefd.ST_TIMEOUT
+    P.g.clear_status()
+    P.g.step(3)
+    Q.g.step(3)
+    assert P.g.status() == 0
+    assert np.array_equal(P.g.read(vefd.POPS), Q.g.read(vefd.POPS))
+    with pytest.raises(vefd.VefdError) as ei:
+        vefd.vefd_wait_selftest(P.g.ctx, 2)
+    assert ei.value.status == vefd.ERR_ARG
 
 
 @pytest.mark.parametrize("variant", [dict(), dict(collision=1, coupling=1, chol=1)], ids=["default", "paper"])

@@ -13,12 +13,12 @@ def test_network_prediction_beats_cold_start():
     import torch
     from paper_1406_2686_gb300 import nn, vefd, warmstart as ws
     N = 32
-    train = ws.sample_setups(16, seed=11, N=N)
+    train = ws.sample_setups(32, seed=11, N=N)
     held = ws.sample_setups(3, seed=29, N=N)
     X, Y, rec = ws.make_dataset(train, tol=1e-5, max_steps=30000)
     assert all(r["converged"] for r in rec)
     net = nn.UNet(ws.N_IN, ws.N_OUT, c=8, seed=0)
-    losses = ws.train(net, X, Y, epochs=30, lr=1e-3)
+    losses = ws.train(net, X, Y, epochs=60, lr=1e-3)
     assert losses[-1] < losses[0] / 3
     Xh, Yh, _ = ws.make_dataset(held, tol=1e-5, max_steps=30000)
     err_net, err_cold = [], []
