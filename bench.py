@@ -309,49 +309,57 @@ def time_variant(S, steps, warmup, model=None):
     return out
 
 
-def ensemble_boxes(n=64, seed=7):
-    """n uneven droplet boxes: NX in {32, 64, 96}, NY and NZ multiples of 8 in
-    [16, 64], drawn from SplitMix64(seed)."""
+def ensemble_setups(n=64, seed=7, umax=0.08):
+    """n uneven sheared-droplet boxes sweeping the set-up: NX in {32, 64, 96},
+    NY and NZ in {32, 40, ..., 96}; Ca in [0.05, 0.3], De in [0.1, 4]
+    (log-uniform), 2R/H in [0.3, 0.8], viscosity ratio in [0.5, 2]
+    (log-uniform), droplet or matrix viscoelastic; all drawn from
+    SplitMix64(seed).  Draws whose droplet does not fit the box (2R above 0.8
+    of NX or NZ) or whose wall speed would exceed umax are skipped."""
+    import math
+
     from paper_1406_2686_gb300 import inputs
-    boxes = []
-    for i in range(n):
-        r = [int(inputs.splitmix64(seed, 3 * i + k)) for k in range(3)]
-        boxes.append((32 * (1 + r[0] % 3), 8 * (2 + r[1] % 7), 8 * (2 + r[2] % 7)))
-    return boxes
+    from paper_1406_2686_gb300 import warmstart as ws
+    out, k = [], 0
+    while len(out) < n:
+        r = [int(inputs.splitmix64(seed, 8 * k + j)) for j in range(3)]
+        u = [inputs.splitmix64(seed, 8 * k + 3 + j) / 2.0 ** 64 for j in range(5)]
+        k += 1
+        dims = (32 * (1 + r[0] % 3), 8 * (4 + r[1] % 9), 8 * (4 + r[2] % 9))
+        s = ws.Setup(0.05 + 0.25 * u[0], math.exp(math.log(0.1) + u[1] * math.log(40.0)), 0.3 + 0.5 * u[2],
+                     2.0 ** (2.0 * u[3] - 1.0), 1 if u[4] < 0.5 else -1, dims=dims)
+        if 2.0 * s.R <= 0.8 * min(dims[0], dims[2]) and s.u_wall <= umax:
+            out.append(s)
+    return out
 
 
-def small_boxes(n=256):
-    """n equal small droplet boxes, 32 x 16 x 16 (8192 nodes each)."""
-    return [(32, 16, 16)] * n
+def small_setups(n=256):
+    """n small sheared-droplet boxes, 32 x 16 x 16 (8192 nodes each), one set-up."""
+    from paper_1406_2686_gb300 import warmstart as ws
+    return [ws.Setup(0.1, 1.0, 0.5, 1.0, 1, dims=(32, 16, 16))] * n
 
 
-def time_ensemble(steps, warmup, chunk=32, boxes=None, label=None):
-    """Many small independent lattices: stepped one after another on one stream
-    (plain vefd_step per lattice) versus as one ensemble, either one CUDA graph
-    with a concurrent branch per lattice or two batched launches per step over
-    the tiles of all lattices.  Same lattices, same steps; MLUPS of each."""
+def time_ensemble(steps, warmup, chunk=32, setups=None, label=None):
+    """Many independent sheared-droplet lattices: stepped one after another on
+    one stream (plain vefd_step per lattice) versus as one ensemble, either one
+    CUDA graph with a concurrent branch per lattice or two batched launches per
+    step over the tiles of all lattices.  Same lattices, same steps; MLUPS of
+    each."""
     import torch
 
     from paper_1406_2686_gb300 import vefd
-    if boxes is None:
-        boxes = ensemble_boxes()
-        label = "D3Q19 two-component droplets, NX in {32,64,96}, NY, NZ in {16,...,64} step 8 (SplitMix64 seed 7)"
+    if setups is None:
+        setups = ensemble_setups()
+        label = ("64 D3Q19 two-component sheared droplets, NX in {32,64,96}, NY, NZ in {32,...,96} step 8; "
+                 "Ca in [0.05,0.3], De in [0.1,4], 2R/H in [0.3,0.8], lambda in [0.5,2], either phase "
+                 "viscoelastic (SplitMix64 seed 7)")
 
     def build():
-        lats = []
-        for (nx, ny, nz) in boxes:
-            L = vefd.Lattice(lattice=vefd.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=ETA_A,
-                             eta_B=ETA_B, delta=0.1)
-            L.set_wall_shear(0.01)
-            L.set_fenep(50.0, ETA_P, 100.0, 1e-3, 1, 1)
-            R = min(ny, nz) / 4.0
-            L.init_droplet((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0, R, 2.0, 0.1, 3.0, 1, 1e-3)
-            lats.append(L)
-        return lats
+        return [s.cold(seed=1 + i) for i, s in enumerate(setups)]
 
-    nodes = sum(a * b * c for a, b, c in boxes)
+    nodes = sum(a * b * c for a, b, c in (s.dims for s in setups))
     stream = torch.cuda.current_stream()
-    out = {"lattices": len(boxes), "nodes": nodes, "steps": steps, "chunk": chunk, "boxes": label}
+    out = {"lattices": len(setups), "nodes": nodes, "steps": steps, "chunk": chunk, "boxes": label}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lats = build()
     for L in lats:
@@ -381,7 +389,7 @@ def time_ensemble(steps, warmup, chunk=32, boxes=None, label=None):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         out[key] = {"value": round(nodes * steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "ms": round(ms, 3),
-                    "launches_per_step": 2 if E.batched else 2 * len(boxes)}
+                    "launches_per_step": 2 if E.batched else 2 * len(setups)}
         got = [L.read(vefd.C) for L in lats[:2]]
         out[key]["bit_identical"] = all(np.array_equal(a, g) for a, g in zip(seq_state, got))
         out[key]["max_rel_diff"] = float(max(np.linalg.norm(g - a) / np.linalg.norm(a) for a, g in zip(seq_state, got)))
@@ -498,8 +506,8 @@ def run_ours(args):
                                     "equilibrium; %d steps each" % vsteps)
     if not args.no_ensemble and S.prec == 0:
         line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
-        line["ensemble_small"] = time_ensemble(max(100, K // 20), min(W, 20), boxes=small_boxes(),
-                                               label="256 D3Q19 two-component droplets, 32 x 16 x 16 each")
+        line["ensemble_small"] = time_ensemble(max(100, K // 20), min(W, 20), setups=small_setups(),
+                                               label="256 D3Q19 two-component sheared droplets, 32 x 16 x 16 each")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(S)
     if rank == 0:

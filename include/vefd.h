@@ -294,6 +294,26 @@ vefd_status vefd_ensemble_step(vefd_ensemble *ens, int64_t nsteps, int64_t chunk
 vefd_status vefd_ensemble_set_batched(vefd_ensemble *ens, int on);
 /* 1 when the currently captured graph uses the batched launches, else 0. */
 int vefd_ensemble_is_batched(const vefd_ensemble *ens);
+/* Kernel choices of the replayed steps: batched (0/1, as
+ * vefd_ensemble_set_batched) and the z-segment length, in planes, of the
+ * batched densities/FENE-P pass (0: automatic, the length that fills two
+ * blocks per SM with the fewest planes per block; otherwise clamped to each
+ * member's NZ).  Results do not depend on the segment length.  Takes effect
+ * at the next replay.  VEFD_ERR_ARG for a NULL ensemble, batched not 0/1 or
+ * a negative segment. */
+vefd_status vefd_ensemble_set_config(vefd_ensemble *ens, int batched, int post_segment);
+vefd_status vefd_ensemble_get_config(const vefd_ensemble *ens, int *batched, int *post_segment);
+/* The ensemble's own autotuner.  It times four configurations: graph branches,
+ * and batched launches with the automatic z-segment, twice it and half of it.
+ * Each is timed as `steps` replayed steps (after one untimed replay that
+ * captures it), and the fastest is kept.  The timed steps are real steps:
+ * every member advances by 4 (steps + chunk) steps (plus one eager step if its
+ * Euler start is pending), its results those of vefd_step to FP32 rounding.
+ * times_ms (4 slots, or NULL) receives each configuration's milliseconds, -1
+ * where the members do not allow batched launches.  Synchronises.
+ * VEFD_ERR_ARG unless steps is a positive multiple of an even chunk;
+ * otherwise as vefd_ensemble_step. */
+vefd_status vefd_ensemble_autotune(vefd_ensemble *ens, int64_t steps, int64_t chunk, double *times_ms);
 const char *vefd_ensemble_last_error(const vefd_ensemble *ens);
 /* Waits for the ensemble's work and frees its streams, events and graph. */
 void vefd_ensemble_destroy(vefd_ensemble *ens);

@@ -1057,6 +1057,7 @@ struct vefd_ensemble {
     // batched launches: one lattice kernel and one densities/FENE-P pass per
     // step over the tiles of all members, from a device table of members
     int batched_pref = 1;       // use them when the members allow
+    int post_seg = 0;           // z-segment of the batched densities pass: 0 automatic, else planes
     bool batched = false;       // the captured graph uses them
     std::vector<EnsMember> table;
     std::vector<int> start;     // lattice tiles then z-march columns: first item of each member
@@ -1098,6 +1099,8 @@ bool ens_batchable(const vefd_ensemble* e) {
     return true;
 }
 
+constexpr int kEnsTuneSlots = 4;  // configurations vefd_ensemble_autotune times
+
 // z-segment length of the batched z-march pass: fewest (waves x planes per
 // block), counting two planes of ring prologue per block.
 int ens_post_segment(const vefd_ensemble* e, int sms) {
@@ -1129,7 +1132,7 @@ vefd_status ens_build_table(vefd_ensemble* e) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
-    const int zs = ens_post_segment(e, sms);
+    const int zs = e->post_seg > 0 ? e->post_seg : ens_post_segment(e, sms);
     e->table.assign(n, EnsMember{});
     e->start.assign(2 * n, 0);
     long long lat = 0, post = 0;
@@ -1138,9 +1141,9 @@ vefd_status ens_build_table(vefd_ensemble* e) {
         EnsMember& M = e->table[k];
         M.p = params_of(m);
         M.cur0 = m->cur;
-        for (int k = 0; k < 2; ++k) {
-            M.tm_lat[k] = m->tmap_post[k];  // box 32 x 4 x 2
-            M.tm_post[k] = m->tmap_zm[k];   // box 32 x 8 x 1
+        for (int j = 0; j < 2; ++j) {
+            M.tm_lat[j] = m->tmap_post[j];  // box 32 x 4 x 2
+            M.tm_post[j] = m->tmap_zm[j];   // box 32 x 8 x 1
         }
         for (int par = 0; par < 2; ++par) {
             const int cur = m->cur ^ par, ccur = m->ccur ^ (m->fd_on ? par : 0);
@@ -1425,18 +1428,88 @@ vefd_status vefd_ensemble_step(vefd_ensemble* e, int64_t nsteps, int64_t chunk) 
     return ens_eager(e, nsteps - full * chunk);
 }
 
-vefd_status vefd_ensemble_set_batched(vefd_ensemble* e, int on) {
-    if (!e || (on != 0 && on != 1)) return VEFD_ERR_ARG;
-    if (e->batched_pref != on) {
+vefd_status vefd_ensemble_set_config(vefd_ensemble* e, int batched, int post_segment) {
+    if (!e || (batched != 0 && batched != 1) || post_segment < 0) return VEFD_ERR_ARG;
+    if (e->batched_pref != batched || e->post_seg != post_segment) {
         // the next replay re-captures; earlier replays may still be in flight
         if (e->exec) {
             cudaStreamSynchronize(e->main);
             cudaGraphExecDestroy(e->exec);
         }
         e->exec = nullptr;
-        e->batched_pref = on;
+        e->batched_pref = batched;
+        e->post_seg = post_segment;
     }
     return VEFD_OK;
+}
+
+vefd_status vefd_ensemble_get_config(const vefd_ensemble* e, int* batched, int* post_segment) {
+    if (!e || !batched || !post_segment) return VEFD_ERR_ARG;
+    *batched = e->batched_pref;
+    *post_segment = e->post_seg;
+    return VEFD_OK;
+}
+
+vefd_status vefd_ensemble_set_batched(vefd_ensemble* e, int on) {
+    if (!e) return VEFD_ERR_ARG;
+    return vefd_ensemble_set_config(e, on, e->post_seg);
+}
+
+vefd_status vefd_ensemble_autotune(vefd_ensemble* e, int64_t steps, int64_t chunk, double* times_ms) {
+    if (!e) return VEFD_ERR_ARG;
+    if (chunk < 2 || (chunk & 1) || steps < chunk || steps % chunk)
+        return ens_fail(e, VEFD_ERR_ARG, "steps must be a positive multiple of an even chunk");
+    for (vefd_ctx* m : e->members)
+        if (need_ready(m) != VEFD_OK) return ens_fail(e, VEFD_ERR_STATE, "a member is not initialised");
+    // the Euler start or pending densities first, so that every timed step is a replay
+    bool steady = true;
+    for (vefd_ctx* m : e->members) steady = steady && ens_steady(m);
+    if (!steady) {
+        const vefd_status st = ens_eager(e, 1);
+        if (st != VEFD_OK) return st;
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+    const int auto_zs = ens_post_segment(e, sms);
+    // graph branches; batched with the automatic z-segment, twice and half as long
+    const int cand[kEnsTuneSlots][2] = {{0, 0}, {1, 0}, {1, 2 * auto_zs}, {1, std::max(1, auto_zs / 2)}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return ens_fail(e, VEFD_ERR_CUDA, "cannot create timing events");
+    }
+    const int keep_b = e->batched_pref, keep_s = e->post_seg;
+    vefd_status st = VEFD_OK;
+    double best = 1e300;
+    int best_k = -1;
+    for (int k = 0; k < kEnsTuneSlots && st == VEFD_OK; ++k) {
+        if (times_ms) times_ms[k] = -1.0;
+        st = vefd_ensemble_set_config(e, cand[k][0], cand[k][1]);
+        // one untimed replay, which captures the graph
+        if (st == VEFD_OK) st = vefd_ensemble_step(e, chunk, chunk);
+        if (st != VEFD_OK) break;
+        if (cand[k][0] == 1 && !e->batched) continue;  // the members do not allow batched launches
+        if (cudaEventRecord(e0, e->main) != cudaSuccess) st = VEFD_ERR_CUDA;
+        if (st == VEFD_OK) st = vefd_ensemble_step(e, steps, chunk);
+        if (st == VEFD_OK && (cudaEventRecord(e1, e->main) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            st = VEFD_ERR_CUDA;
+        if (st != VEFD_OK) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (times_ms) times_ms[k] = ms;
+        if (ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != VEFD_OK || best_k < 0) {
+        vefd_ensemble_set_config(e, keep_b, keep_s);
+        return st != VEFD_OK ? st : ens_fail(e, VEFD_ERR_CUDA, "no configuration was timed");
+    }
+    return vefd_ensemble_set_config(e, cand[best_k][0], cand[best_k][1]);
 }
 
 int vefd_ensemble_is_batched(const vefd_ensemble* e) { return e && e->exec && e->batched ? 1 : 0; }

@@ -292,7 +292,7 @@ struct StepBufs {
 // (lattice tiles; z-marching columns and segments of zs planes).  The tensor
 // maps depend on the buffers only, so rebuilding the table for the other
 // parity rewrites them with the same bytes.
-struct alignas(64) EnsMember {
+struct EnsMember {  // aligned as CUtensorMap
     CUtensorMap tm_lat[2];
     CUtensorMap tm_post[2];
     StepParams p;

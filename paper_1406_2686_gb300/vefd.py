@@ -43,7 +43,8 @@ EXPORTS = [
     "vefd_last_error", "vefd_kernels_per_step", "vefd_profile_kernels", "vefd_kernel_times",
     "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
     "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
-    "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
+    "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_set_config",
+    "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
 ]
 
 _lib = None
@@ -100,6 +101,9 @@ def load(build_if_missing=True):
         "vefd_ensemble_step": [vp, i64, i64],
         "vefd_ensemble_set_batched": [vp, cint],
         "vefd_wait_selftest": [vp, cint],
+        "vefd_ensemble_set_config": [vp, cint, cint],
+        "vefd_ensemble_get_config": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)],
+        "vefd_ensemble_autotune": [vp, i64, i64, ctypes.POINTER(dbl)],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -313,6 +317,22 @@ def vefd_ensemble_set_batched(ens, on):
     return _ens_check(ens, load().vefd_ensemble_set_batched(ens, int(on)))
 
 
+def vefd_ensemble_set_config(ens, batched, post_segment=0):
+    return _ens_check(ens, load().vefd_ensemble_set_config(ens, int(batched), int(post_segment)))
+
+
+def vefd_ensemble_get_config(ens):
+    b, z = ctypes.c_int(), ctypes.c_int()
+    _ens_check(ens, load().vefd_ensemble_get_config(ens, ctypes.byref(b), ctypes.byref(z)))
+    return b.value, z.value
+
+
+def vefd_ensemble_autotune(ens, steps=64, chunk=32):
+    t = (ctypes.c_double * 4)()
+    _ens_check(ens, load().vefd_ensemble_autotune(ens, int(steps), int(chunk), t))
+    return [float(v) for v in t]
+
+
 def vefd_ensemble_is_batched(ens):
     return bool(load().vefd_ensemble_is_batched(ens))
 
@@ -501,6 +521,19 @@ class Ensemble:
     def batched(self):
         """True when the captured graph uses the batched launches."""
         return vefd_ensemble_is_batched(self.ens)
+
+    def set_config(self, batched, post_segment=0):
+        vefd_ensemble_set_config(self.ens, 1 if batched else 0, post_segment)
+
+    @property
+    def config(self):
+        """(batched, post z-segment) requested for the replays."""
+        return vefd_ensemble_get_config(self.ens)
+
+    def autotune(self, steps=64, chunk=32):
+        """Times graph branches and batched launches with three z-segments,
+        keeps the fastest; the timed steps advance every member."""
+        return vefd_ensemble_autotune(self.ens, steps, chunk)
 
     def close(self):
         if getattr(self, "ens", None):

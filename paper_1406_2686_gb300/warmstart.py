@@ -39,7 +39,8 @@ def _uniform(seed, idx):
 
 
 class Setup:
-    """One sheared-droplet set-up in an N^3 box (walls in y).
+    """One sheared-droplet set-up in an N^3 box, or an nx x ny x nz box when
+    dims is given (walls in y; the wall distance H = ny sets R and U).
 
     Viscoelastic droplet (phase +1): Newtonian matrix eta_B = eta_ref, droplet
     total viscosity lambda eta_B split 60/40 between solvent eta_A and polymer
@@ -48,9 +49,11 @@ class Setup:
     total viscosity eta_M: shear rate Ca sigma / (R eta_M), wall speed
     U = rate N / 2, tau_P = De tau_em eta_M / eta_P, tau_em = R eta_M / sigma."""
 
-    def __init__(self, Ca, De, conf, lam, phase, N=64):
+    def __init__(self, Ca, De, conf, lam, phase, N=64, dims=None):
         self.Ca, self.De, self.conf, self.lam, self.phase, self.N = Ca, De, conf, lam, int(phase), N
-        self.R = conf * N / 2.0
+        self.dims = tuple(dims) if dims is not None else (N, N, N)
+        H = self.dims[1]
+        self.R = conf * H / 2.0
         if self.phase > 0:
             self.eta_B = ETA_REF
             tot = lam * ETA_REF
@@ -61,7 +64,7 @@ class Setup:
             self.eta_A = lam * ETA_REF
             self.eta_M = ETA_REF
         self.gdot = Ca * SIGMA / (self.R * self.eta_M)
-        self.u_wall = self.gdot * N / 2.0
+        self.u_wall = self.gdot * H / 2.0
         self.tau_em = self.R * self.eta_M / SIGMA
         self.tau_p = De * self.tau_em * self.eta_M / self.eta_P
 
@@ -71,8 +74,8 @@ class Setup:
                          (self.conf - 0.475) / 0.125, math.log2(self.lam), float(self.phase)])
 
     def lattice(self):
-        N = self.N
-        lat = vefd.Lattice(lattice=vefd.D3Q19, nx=N, ny=N, nz=N, ncomp=2, walls=1, G=1.5, eta_A=self.eta_A,
+        nx, ny, nz = self.dims
+        lat = vefd.Lattice(lattice=vefd.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=self.eta_A,
                            eta_B=self.eta_B, delta=0.1)
         lat.set_wall_shear(self.u_wall)
         lat.set_fenep(self.tau_p, self.eta_P, L2, KAPPA, self.phase, 1)
@@ -80,8 +83,8 @@ class Setup:
 
     def cold(self, seed=1):
         lat = self.lattice()
-        c = (self.N - 1) / 2.0
-        lat.init_droplet(c, c, c, self.R, RHO_IN, RHO_OUT, 5.0, seed, 1e-3)
+        nx, ny, nz = self.dims
+        lat.init_droplet((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0, self.R, RHO_IN, RHO_OUT, 5.0, seed, 1e-3)
         return lat
 
 

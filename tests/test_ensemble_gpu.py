@@ -306,3 +306,47 @@ def test_batched_ensemble_many_members():
         assert close_state(a, b)
         assert a.status() == 0
     E.close()
+
+
+def test_ensemble_config_and_autotune():
+    """The ensemble's own autotuner times graph branches and batched launches
+    with three z-segment lengths of the densities pass, keeps the fastest, and
+    its timed steps are ordinary steps (results as stepping alone); an
+    ensemble the batched kernels cannot take only times the branches."""
+    from paper_1406_2686_gb300 import vefd
+    boxes = BATCH_BOXES[:3]
+    ens = [make(b, seed=60 + i) for i, b in enumerate(boxes)]
+    alone = [make(b, seed=60 + i) for i, b in enumerate(boxes)]
+    E = vefd.Ensemble(ens)
+    assert E.config == (1, 0)
+    E.set_config(True, 3)
+    assert E.config == (1, 3)
+    E.step(9, chunk=4)                      # 1 eager start, 2 replays with 3-plane segments
+    assert E.batched
+    times = E.autotune(steps=8, chunk=4)    # 4 x (8 + 4) steps
+    assert len(times) == 4 and all(t > 0 for t in times)
+    best = int(np.argmin(times))
+    b, z = E.config
+    assert b == (0 if best == 0 else 1)
+    E.step(8, chunk=4)
+    total = 9 + 4 * 12 + 8
+    for L in alone:
+        L.step(total)
+    for a, r in zip(ens, alone):
+        assert a.steps_done == total
+        assert close_state(a, r)
+        assert a.status() == 0
+    for bad in ((2, 0), (1, -1)):
+        with pytest.raises(vefd.VefdError) as ei:
+            vefd.vefd_ensemble_set_config(E.ens, *bad)
+        assert ei.value.status == vefd.ERR_ARG
+    with pytest.raises(vefd.VefdError) as ei:
+        E.autotune(steps=6, chunk=4)
+    assert ei.value.status == vefd.ERR_ARG
+    E.close()
+    # a D2Q9 member: no batched launches, only the branches are timed
+    F = vefd.Ensemble([make(BOXES[3], seed=5), make(BATCH_BOXES[0], seed=6)])
+    times = F.autotune(steps=4, chunk=2)
+    assert times[0] > 0 and times[1:] == [-1.0, -1.0, -1.0]
+    assert F.config[0] == 0
+    F.close()
