@@ -26,12 +26,12 @@ __global__ void k_derived(int which, int ncomp, const float* __restrict__ drho, 
     const long long N = p.N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         if (which == 0) {
-            dst[i] = p.rho_ref[0] + drho[i];
+            dst[i] = p.rho_ref[0] + drho[i * ncomp];
         } else if (which == 1) {
-            dst[i] = ncomp == 2 ? p.rho_ref[1] + drho[N + i] : 0.0f;
+            dst[i] = ncomp == 2 ? p.rho_ref[1] + drho[2 * i + 1] : 0.0f;
         } else if (which == 2) {
             if (ncomp == 2) {
-                const float a = p.rho_ref[0] + drho[i], b = p.rho_ref[1] + drho[N + i];
+                const float a = p.rho_ref[0] + drho[2 * i], b = p.rho_ref[1] + drho[2 * i + 1];
                 dst[i] = (a - b) / (a + b);
             } else {
                 dst[i] = 1.0f;
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) k_diag_partial(const float* __restrict__ 
         const long long r = i / p.nx;
         const int y = (int)(r % p.ny);
         const int z = (int)(r / p.ny);
-        const double dA = drho[i];
-        const double dB = ncomp == 2 ? (double)drho[N + i] : 0.0;
+        const double dA = drho[i * ncomp];
+        const double dB = ncomp == 2 ? (double)drho[2 * i + 1] : 0.0;
         const double rA = (double)p.rho_ref[0] + dA;
         const double rB = ncomp == 2 ? (double)p.rho_ref[1] + dB : 0.0;
         const double rho = rA + rB;

@@ -352,8 +352,7 @@ __global__ void __launch_bounds__(128) k_post(const PT* __restrict__ fnew, const
 #pragma unroll
         for (int k = 0; k < L::NC; ++k) c[k] = __ldg(Ct + k * N + i);
     }
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) drho[s * N + i] = d[s];
+    dens_store<NCOMP>(drho, i, d);
     if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
 }
 
@@ -414,8 +413,8 @@ __global__ void __launch_bounds__(BX * BY * BZ) k_post_tma(const __grid_constant
         d[s] = rest[s];
 #pragma unroll
         for (int a = 1; a < L::Q; ++a) d[s] += pop_get(sf[(s * (L::Q - 1) + a - 1) * T + t]);
-        drho[s * N + i] = d[s];
     }
+    dens_store<NCOMP>(drho, i, d);
     if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
 }
 
@@ -546,9 +545,11 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
             // partial density plus what crossed a column side or a segment end
             const bool wlo = p.walls && y == 0, whi = p.walls && y == ny - 1;
             const int zs_lo = (z / zl) * zl, zs_hi = min(zs_lo + zl, nz);  // this plane's lattice-kernel segment
+            float part[NCOMP];
+            dens_get<NCOMP>(drho, i, part);
 #pragma unroll
             for (int s = 0; s < NCOMP; ++s) {
-                float d = drho[s * N + i];
+                float d = part[s];
 #pragma unroll
                 for (int a = 1; a < L::Q; ++a) {
                     const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
@@ -601,10 +602,8 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
         float d[NCOMP];
         if (FUSED) {
 #pragma unroll
-            for (int s = 0; s < NCOMP; ++s) {
-                d[s] = rest[s];
-                drho[s * N + i] = d[s];
-            }
+            for (int s = 0; s < NCOMP; ++s) d[s] = rest[s];
+            dens_store<NCOMP>(drho, i, d);
         } else {
             const bool ok = mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));
             if (__syncthreads_or(!ok)) {
@@ -619,8 +618,8 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
                 d[s] = rest[s];
 #pragma unroll
                 for (int a = 1; a < L::Q; ++a) d[s] += pop_get(sP[(s * (L::Q - 1) + a - 1) * T + t]);
-                drho[s * N + i] = d[s];
             }
+            dens_store<NCOMP>(drho, i, d);
         }
         if (p.feedback != 0.0f) store_feedback<L, NCOMP>(c, d, p, Q, N, i);
         if (more) store_plane((k + 3) % 4, vi, vh);
@@ -679,8 +678,8 @@ __global__ void __launch_bounds__(128) k_pre(const PT* __restrict__ f, const flo
         d[s] = __ldg(frest + s * N + i);
 #pragma unroll
         for (int a = 1; a < L::Q; ++a) d[s] += pop_load(f + (s * (L::Q - 1) + a - 1) * N + i);
-        drho[s * N + i] = d[s];
     }
+    dens_store<NCOMP>(drho, i, d);
     float c[L::NC];
 #pragma unroll
     for (int k = 0; k < L::NC; ++k) c[k] = __ldg(Ct + k * N + i);

@@ -54,13 +54,14 @@ __global__ void __launch_bounds__(128) k_moments(const PT* __restrict__ fd, cons
     if (x >= p.nx || y >= p.ny) return;
     const long long N = p.N;
     const long long i = ((long long)z * p.ny + y) * p.nx + x;
+    float d[NCOMP];
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) {
-        float d = __ldg(frest + s * N + i);
+        d[s] = __ldg(frest + s * N + i);
 #pragma unroll
-        for (int a = 1; a < L::Q; ++a) d += pop_load(fd + (s * (L::Q - 1) + a - 1) * N + i);
-        drho[s * N + i] = d;
+        for (int a = 1; a < L::Q; ++a) d[s] += pop_load(fd + (s * (L::Q - 1) + a - 1) * N + i);
     }
+    dens_store<NCOMP>(drho, i, d);
 }
 
 // index of tensor component (i, j) in the stored order
@@ -129,9 +130,11 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
         for (int a = 1; a < L::Q; ++a) {
             const int j = nb.at(L::cx(a), L::cy(a), L::cz(a));
             const bool axis = L::w(a) == L::w(1);
+            float dj[2];
+            dens_ldg<2>(b.drho, j, dj);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const float t = __ldg(b.drho + s * N + j);
+                const float t = dj[s];
                 float* acc_s = axis ? sa[s] : sd[s];
                 if (L::cx(a)) acc_s[0] += L::cx(a) * t;
                 if (L::cy(a)) acc_s[1] += L::cy(a) * t;
@@ -581,8 +584,7 @@ __device__ __forceinline__ void node_gather(const StepBufs& b, const StepParams&
     const long long N = p.N;
     // the node's own deviations come from the density buffer (bit-identical to
     // the sum of the staged populations)
-#pragma unroll
-    for (int s = 0; s < NCOMP; ++s) g.dr[s] = __ldg(b.drho + s * N + g.nb.i);
+    dens_ldg<NCOMP>(b.drho, g.nb.i, g.dr);
     neighbour_forces<L, NCOMP>(b, p, g.nb, g.acc, g.Fp, g.qloc);
 }
 
@@ -936,10 +938,7 @@ __global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
             }
         }
         // plane z - 1 is complete within the segment
-        if (k > 0) {
-#pragma unroll
-            for (int s = 0; s < NCOMP; ++s) b.drho_next[s * N + node - nx * ny] = pm[s];
-        }
+        if (k > 0) dens_store<NCOMP>(b.drho_next, node - nx * ny, pm);
 #pragma unroll
         for (int s = 0; s < NCOMP; ++s) {
             pm[s] = pc[s];
@@ -951,8 +950,7 @@ __global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
     // the segment's last plane: what arrives from the next segment comes through memory
     if (z1 > z0) {
         const int node = ((z1 - 1) * ny + y) * nx + x;
-#pragma unroll
-        for (int s = 0; s < NCOMP; ++s) b.drho_next[s * N + node] = pm[s];
+        dens_store<NCOMP>(b.drho_next, node, pm);
     }
 }
 

@@ -4,7 +4,8 @@
 //   populations  moving a >= 1: fd[(s*(Q-1) + a-1)*N + i] = f_a^s - w_a rho_ref_s  (deviation form,
 //                storage type PT, ping-pong); rest a = 0: frest[s*N + i], always FP32,
 //                updated in place (it does not stream) and carrying each node's mass exactly
-//   densities    drho[s*N + i] = rho_s - rho_ref_s            (sum of deviations)
+//   densities    drho[i*ncomp + s] = rho_s - rho_ref_s        (sum of deviations; interleaved so a
+//                node's densities are one 8-byte access)
 //   velocity     u[k*N + i], k < D                             (Eq. equilibrium:vel)
 //   conformation Ct[k*N + i] = C_k - delta_k                   (k < NC)
 //   AB2 history  R[k*N + i]                                    (right-hand side of the last FD step)
@@ -68,6 +69,34 @@ __host__ __device__ constexpr int opposite(int a) { return a == 0 ? 0 : ((a & 1)
 // --- population storage types: FP32, FP16 or BF16 deviations ------------------
 
 enum { kPrecFp32 = 0, kPrecFp16 = 1, kPrecBf16 = 2 };
+
+// Densities of node i (interleaved by node, see above).
+template <int NCOMP>
+__device__ __forceinline__ void dens_store(float* drho, long long i, const float d[NCOMP]) {
+    if constexpr (NCOMP == 2) reinterpret_cast<float2*>(drho)[i] = make_float2(d[0], d[1]);
+    else drho[i] = d[0];
+}
+template <int NCOMP>
+__device__ __forceinline__ void dens_ldg(const float* __restrict__ drho, long long i, float d[NCOMP]) {
+    if constexpr (NCOMP == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(drho) + i);
+        d[0] = v.x;
+        d[1] = v.y;
+    } else {
+        d[0] = __ldg(drho + i);
+    }
+}
+// plain (coherent) read, for values this kernel also writes
+template <int NCOMP>
+__device__ __forceinline__ void dens_get(const float* drho, long long i, float d[NCOMP]) {
+    if constexpr (NCOMP == 2) {
+        const float2 v = reinterpret_cast<const float2*>(drho)[i];
+        d[0] = v.x;
+        d[1] = v.y;
+    } else {
+        d[0] = drho[i];
+    }
+}
 
 // A tensor map the host copied into global memory (rather than passed as a
 // kernel parameter) is made visible to the tensor-map proxy before use; the
