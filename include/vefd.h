@@ -246,6 +246,31 @@ vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *
  * frees the scratch lattice's device memory and synchronises the context
  * stream.  VEFD_ERR_UNSTABLE when the scratch run trips a guard. */
 vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
+/* Pipelined step graph (implementation detail; the paper steps the whole
+ * lattice).  With slabs >= 2, vefd_step runs whole chunks of `chunk` steps
+ * (even, >= 2) as a replayed CUDA graph in which the lattice is split into
+ * `slabs` slabs of NY / slabs rows.  Each slab's lattice kernel and
+ * densities/FENE-P pass is a graph node that waits only for the nodes of the
+ * neighbouring slabs it exchanges data with: its lattice kernel of step n+1
+ * waits for the passes of step n on slabs k-1, k, k+1, and its pass of step n
+ * waits for the lattice kernels of step n on those slabs.  Work on different
+ * slabs then overlaps, and a slab's new populations can be re-read while
+ * still in L2.  The kernels and their per-node arithmetic are those of the eager
+ * step, so results are bit-identical.
+ * The graph is used when: the lattice is D3Q19; the kernel configuration is
+ * a staged tile 0-2 with post mode 2; NY is a multiple of 8 * slabs; kernel
+ * timing is off; and the context stream is not being captured.  The Euler
+ * start, steps with pending densities, and the remainder of nsteps after
+ * whole chunks run eagerly.  The graph is re-captured when the parameters,
+ * kernel choice or buffer parity change.  slabs = 0 turns it off;
+ * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64,
+ * 4 when of 32, otherwise none (on the 128 x 64 x 128 droplet 2 slabs were
+ * 1.6 % slower than eager stepping, 4 slabs 0.8 % and 8 slabs 2.0 % faster).
+ * VEFD_ERR_ARG for slabs 1, below -1 or above 64, or a bad chunk (default 32). */
+vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
+/* The slab count in effect (0: none), the chunk, and active = 1 when the next
+ * vefd_step would use the graph. */
+vefd_status vefd_get_step_graph(vefd_ctx *ctx, int *slabs, int *chunk, int *active);
 
 /* ---- ensembles of independent lattices (implementation detail: the paper
  * steps one lattice at a time) --------------------------------------------

@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_const
                                                                unsigned* __restrict__ status, StepParams p, int zs,
                                                                int rev, const PT* __restrict__ fnew, int zl) {
     const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * kZmBX;
-    const int y0 = (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kZmBY;
+    const int y0 = p.ylo + (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kZmBY;
     const int z0 = (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z) * zs;
     post_column<PT, NCOMP, FD, FUSED>(&tm_fnew, frest, drho, Ct, Cout, R, u, Q, status, p, x0, y0, z0, zs, fnew, zl);
 }
@@ -771,7 +771,7 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     if (nzb > p.nz) nzb = p.nz;
     const int zs = (p.nz + nzb - 1) / nzb;
     nzb = (p.nz + zs - 1) / zs;
-    dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, p.ny / kZmBY, nzb);
+    dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, (p.yhi - p.ylo) / kZmBY, nzb);
     // FUSED reads the partial densities of the new time level and completes them in place
     float* dens = FUSED ? b.drho_next : b.drho;
     const CUtensorMap dummy{};

@@ -665,7 +665,7 @@ template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL>
 __global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (BX * BY * BZ))
     k_lattice_tma(const __grid_constant__ CUtensorMap tm_fin, StepBufs b, StepParams p, int rev) {
     lattice_tile<PT, L, NCOMP, BX, BY, BZ, COLL>(&tm_fin, b, p, tile_index(blockIdx.x, gridDim.x, rev) * BX,
-                                                 tile_index(blockIdx.y, gridDim.y, rev) * BY,
+                                                 p.ylo + tile_index(blockIdx.y, gridDim.y, rev) * BY,
                                                  tile_index(blockIdx.z, gridDim.z, rev) * BZ);
 }
 
@@ -799,7 +799,7 @@ template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL>
 cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s) {
     constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
-    dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
+    dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.yhi - p.ylo + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     return launch_pdl(p.pdl != 0, k_lattice_tma<PT, L, NCOMP, BX, BY, BZ, COLL>, grd, blk, smem, s, *tm, b, p, rev);
 }
 

@@ -185,6 +185,8 @@ struct StepParams {
     int collision;         // 0: single relaxation time; 1: moment space with the paper's rates
     int chol;              // conformation update: 0 AB2 on C; 1 AB2 on the log-Cholesky factor of f C
     int pdl;               // launch the step's kernels with programmatic dependencies
+    int ylo, yhi;          // rows [ylo, yhi) the staged lattice and z-marching launches cover
+                           // (0, ny: the whole lattice; a y-slab of the pipelined step graph)
 };
 
 // --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------

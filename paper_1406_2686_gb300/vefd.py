@@ -44,7 +44,7 @@ EXPORTS = [
     "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
     "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
     "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_set_config",
-    "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
+    "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_set_step_graph", "vefd_get_step_graph", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
 ]
 
 _lib = None
@@ -104,6 +104,8 @@ def load(build_if_missing=True):
         "vefd_ensemble_set_config": [vp, cint, cint],
         "vefd_ensemble_get_config": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)],
         "vefd_ensemble_autotune": [vp, i64, i64, ctypes.POINTER(dbl)],
+        "vefd_set_step_graph": [vp, cint, cint],
+        "vefd_get_step_graph": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -212,6 +214,16 @@ def vefd_get_status(ctx):
     if st not in (OK, ERR_UNSTABLE, ERR_TIMEOUT):
         _check(ctx, st)
     return int(bits.value)
+
+
+def vefd_set_step_graph(ctx, slabs, chunk=32):
+    return _check(ctx, load().vefd_set_step_graph(ctx, int(slabs), int(chunk)))
+
+
+def vefd_get_step_graph(ctx):
+    s, c, a = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().vefd_get_step_graph(ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(a)))
+    return s.value, c.value, bool(a.value)
 
 
 def vefd_wait_selftest(ctx, arrive):
@@ -460,6 +472,15 @@ class Lattice:
 
     def status(self):
         return vefd_get_status(self.ctx)
+
+    def set_step_graph(self, slabs, chunk=32):
+        """Pipelined y-slab step graph (slabs >= 2; 0 off; -1 automatic)."""
+        vefd_set_step_graph(self.ctx, slabs, chunk)
+
+    @property
+    def step_graph(self):
+        """(slabs, chunk, active)."""
+        return vefd_get_step_graph(self.ctx)
 
     def wait_selftest(self, arrive):
         """One bounded device wait that completes (arrive=True) or runs out

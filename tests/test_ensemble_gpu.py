@@ -350,3 +350,42 @@ def test_ensemble_config_and_autotune():
     assert times[0] > 0 and times[1:] == [-1.0, -1.0, -1.0]
     assert F.config[0] == 0
     F.close()
+
+
+@pytest.mark.parametrize("case", ["walls", "periodic", "equilibrium_coupling", "fp16"])
+def test_step_graph_bit_identical(case):
+    """The pipelined y-slab step graph (each slab's lattice kernel and
+    densities/FENE-P pass a node waiting only for its neighbouring slabs) runs
+    the eager step's kernels on row ranges: bit-identical results, across the
+    Euler start, replays of both parities and eager remainders."""
+    from paper_1406_2686_gb300 import vefd
+    box = {"walls": dict(BATCH_BOXES[0], ny=32),
+           "periodic": dict(BATCH_BOXES[1], ny=16, nz=6),
+           "equilibrium_coupling": dict(BATCH_BOXES[2], ny=32),
+           "fp16": dict(BATCH_BOXES[0], ny=32, precision=1)}[case]
+    for slabs in ((2, 4) if box["ny"] == 32 else (2,)):
+        G = make(box, seed=71)
+        R = make(box, seed=71)
+        G.set_step_graph(slabs, 4)
+        assert G.step_graph == (slabs, 4, True)
+        for n in (11, 1, 8, 5):
+            G.step(n)
+            R.step(n)
+            assert same(G, R), (slabs, n)
+        assert G.status() == 0 and G.steps_done == 25
+        G.set_wall_shear(0.005)            # a parameter change re-captures
+        R.set_wall_shear(0.005)
+        G.step(8)
+        R.step(8)
+        assert same(G, R)
+    # shapes or choices the graph cannot take step eagerly
+    H = make(box, seed=72)
+    H.set_step_graph(3, 4)                 # NY not a multiple of 8 * 3
+    assert H.step_graph[2] is False
+    H.set_step_graph(2, 4)
+    H.set_kernel_config(3, 2)              # persistent tile
+    assert H.step_graph[2] is False
+    for bad in ((1, 4), (2, 3), (-1, 4)):
+        with pytest.raises(vefd.VefdError) as ei:
+            H.set_step_graph(*bad)
+        assert ei.value.status == vefd.ERR_ARG
