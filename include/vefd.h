@@ -264,9 +264,12 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * whole chunks run eagerly.  The graph is re-captured when the parameters,
  * kernel choice or buffer parity change.  slabs = 0 turns it off;
  * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64,
- * 4 when of 32, otherwise none (on the 128 x 64 x 128 droplet 2 slabs were
- * 1.6 % slower than eager stepping, 4 slabs 0.8 % and 8 slabs 2.0 % faster).
- * VEFD_ERR_ARG for slabs 1, below -1 or above 64, or a bad chunk (default 32). */
+ * 4 when of 32, otherwise none (on the 128 x 64 x 128 droplet, against eager
+ * stepping: 8 slabs +7.0 %, 4 slabs +5.3 %).
+ * Each slab's densities/FENE-P pass marches z-segments of 8 planes (shorter
+ * blocks than the whole-lattice pass, so a slab's pass, which the next lattice
+ * kernels of its neighbours wait for, finishes sooner).  VEFD_ERR_ARG for
+ * slabs 1, below -1 or above 64, or a bad chunk (default 64). */
 vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
 /* The slab count in effect (0: none), the chunk, and active = 1 when the next
  * vefd_step would use the graph. */

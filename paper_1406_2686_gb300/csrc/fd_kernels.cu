@@ -769,7 +769,7 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     int nzb = (2 * g_sm_count) / bxy;
     if (nzb < 1) nzb = 1;
     if (nzb > p.nz) nzb = p.nz;
-    const int zs = (p.nz + nzb - 1) / nzb;
+    const int zs = p.post_zs > 0 ? (p.post_zs < p.nz ? p.post_zs : p.nz) : (p.nz + nzb - 1) / nzb;
     nzb = (p.nz + zs - 1) / zs;
     dim3 blk(kZmBX, kZmBY, 1), grd(p.nx / kZmBX, (p.yhi - p.ylo) / kZmBY, nzb);
     // FUSED reads the partial densities of the new time level and completes them in place

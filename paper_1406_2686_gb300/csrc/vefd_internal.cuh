@@ -187,6 +187,7 @@ struct StepParams {
     int pdl;               // launch the step's kernels with programmatic dependencies
     int ylo, yhi;          // rows [ylo, yhi) the staged lattice and z-marching launches cover
                            // (0, ny: the whole lattice; a y-slab of the pipelined step graph)
+    int post_zs;           // z-segment of the z-marching pass (0: fill two blocks per SM)
 };
 
 // --- TMA staging helpers (inline PTX, sm_90 and later) -----------------------

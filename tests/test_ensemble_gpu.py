@@ -366,6 +366,8 @@ def test_step_graph_bit_identical(case):
     for slabs in ((2, 4) if box["ny"] == 32 else (2,)):
         G = make(box, seed=71)
         R = make(box, seed=71)
+        R.set_step_graph(0)                # eager launch pairs
+        assert R.step_graph[2] is False
         G.set_step_graph(slabs, 4)
         assert G.step_graph == (slabs, 4, True)
         for n in (11, 1, 8, 5):
@@ -378,6 +380,10 @@ def test_step_graph_bit_identical(case):
         G.step(8)
         R.step(8)
         assert same(G, R)
+    # the automatic choice: 8 slabs for NY a multiple of 64, 4 for 32, else none
+    assert make(dict(box, ny=64), seed=1).step_graph == (8, 64, True)
+    assert make(dict(box, ny=32), seed=1).step_graph == (4, 64, True)
+    assert make(dict(box, ny=16), seed=1).step_graph[0] == 0
     # shapes or choices the graph cannot take step eagerly
     H = make(box, seed=72)
     H.set_step_graph(3, 4)                 # NY not a multiple of 8 * 3
@@ -385,7 +391,7 @@ def test_step_graph_bit_identical(case):
     H.set_step_graph(2, 4)
     H.set_kernel_config(3, 2)              # persistent tile
     assert H.step_graph[2] is False
-    for bad in ((1, 4), (2, 3), (-1, 4)):
+    for bad in ((1, 4), (2, 3), (-2, 4)):
         with pytest.raises(vefd.VefdError) as ei:
             H.set_step_graph(*bad)
         assert ei.value.status == vefd.ERR_ARG
