@@ -265,8 +265,8 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * kernel choice or buffer parity change.  slabs = 0 turns it off;
  * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64,
  * 4 when of 32, otherwise none (on the 128 x 64 x 128 droplet, against eager
- * stepping: 8 slabs +7.0 %, 4 slabs +5.3 %).
- * Each slab's densities/FENE-P pass marches z-segments of 8 planes (shorter
+ * stepping: 8 slabs +7 to +8 %, 4 slabs +5 %).
+ * Each slab's densities/FENE-P pass marches z-segments of 12 planes (shorter
  * blocks than the whole-lattice pass, so a slab's pass, which the next lattice
  * kernels of its neighbours wait for, finishes sooner).  VEFD_ERR_ARG for
  * slabs 1, below -1 or above 64, or a bad chunk (default 64). */

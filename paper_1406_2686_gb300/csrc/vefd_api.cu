@@ -79,7 +79,8 @@ struct vefd_ctx {
     // neighbouring slabs; `slab_chunk` steps per replayed graph
     int slabs = -1;  // -1 automatic (slab_count), 0 off
     int slab_chunk = 64;
-    int slab_zs = 8;                       // z-segment of the slab passes (planes marched per block)
+    int slab_zs = 12;                      // z-segment of the slab passes (planes marched per block)
+    bool slab_pdl = false;                 // programmatic launch between a slab's consecutive kernels
     cudaStream_t cap = nullptr;            // capture origin
     std::vector<cudaStream_t> slab_s;      // one capture stream per slab
     std::vector<cudaEvent_t> slab_evL, slab_evP;
@@ -198,7 +199,8 @@ void carve(vefd_ctx* c) {
     if (const char* e = getenv("VEFD_SCHEDULE")) c->sched = atoi(e) & 3;
     if (const char* e = getenv("VEFD_ZM_SEGMENT")) c->zm_seg_fixed = atoi(e) > 0 ? atoi(e) : 0;
     if (getenv("VEFD_NO_PDL")) c->pdl = false;
-    if (const char* e = getenv("VEFD_SLAB_SEGMENT")) c->slab_zs = atoi(e) > 0 ? atoi(e) : 8;
+    if (const char* e = getenv("VEFD_SLAB_SEGMENT")) c->slab_zs = atoi(e) > 0 ? atoi(e) : 12;
+    if (const char* e = getenv("VEFD_SLAB_PDL")) c->slab_pdl = atoi(e) != 0;
 }
 
 // (Re)builds the TMA descriptors of both population buffers for the selected
@@ -327,8 +329,8 @@ uint64_t splitmix64(uint64_t seed, uint64_t i) {
 
 // Slabs of the pipelined step graph: the setting, or automatically 8 slabs
 // when NY is a multiple of 64 and 4 when of 32 (measured on the 128 x 64 x 128
-// droplet with 8-plane pass segments: 8 slabs 7.0 % and 4 slabs 5.3 % faster
-// than eager stepping), otherwise none.
+// droplet: 8 slabs 7-8 % and 4 slabs 5 % faster than eager stepping),
+// otherwise none.
 int slab_count(const vefd_ctx* c) {
     if (c->slabs >= 0) return c->slabs;
     return c->cfg.ny % 64 == 0 ? 8 : (c->cfg.ny % 32 == 0 ? 4 : 0);
@@ -690,7 +692,10 @@ static vefd_status slab_capture(vefd_ctx* c, int64_t chunk) {
     cudaError_t ce = cudaEventRecord(c->slab_fork, c->cap);
     for (int k = 0; k < K && ce == cudaSuccess; ++k) ce = cudaStreamWaitEvent(c->slab_s[k], c->slab_fork, 0);
     StepParams p0 = params_of(c);
-    p0.pdl = 0;  // ordering comes from the graph edges
+    // a slab's kernels follow each other on its stream; with programmatic
+    // launch the next one may start its prologue while the previous drains
+    // (the cross-slab edges stay full dependencies)
+    p0.pdl = c->pdl && c->slab_pdl ? 1 : 0;
     p0.post_zs = c->slab_zs;
     for (int64_t t = 0; t < chunk && ce == cudaSuccess; ++t) {
         const int par = (int)(t & 1);
