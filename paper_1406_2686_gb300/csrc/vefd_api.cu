@@ -78,7 +78,7 @@ struct vefd_ctx {
     // lattice kernel and densities/FENE-P pass a node that waits only for the
     // neighbouring slabs; `slab_chunk` steps per replayed graph
     int slabs = -1;  // -1 automatic (slab_count), 0 off
-    int slab_chunk = 64;
+    int slab_chunk = 128;
     int slab_zs = 12;                      // z-segment of the slab passes (planes marched per block)
     bool slab_pdl = false;                 // programmatic launch between a slab's consecutive kernels
     cudaStream_t cap = nullptr;            // capture origin
