@@ -259,10 +259,12 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * step, so results are bit-identical.
  * The graph is used when: the lattice is D3Q19; the kernel configuration is
  * a staged tile 0-2 with post mode 2; NY is a multiple of 8 * slabs; kernel
- * timing is off; and the context stream is not being captured.  The Euler
- * start, steps with pending densities, and the remainder of nsteps after
- * whole chunks run eagerly.  The graph is re-captured when the parameters,
- * kernel choice or buffer parity change.  slabs = 0 turns it off;
+ * timing is off; and the context stream is not being captured.  Some steps
+ * run eagerly: the Euler start, steps with pending densities, the remainder
+ * of nsteps after whole chunks, and one step that brings the ping-pong buffers
+ * back to the parity the graph was captured at (rather than capturing the
+ * other parity).  The graph is re-captured when the parameters or kernel
+ * choice change.  slabs = 0 turns it off;
  * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64,
  * 4 when of 32, otherwise none (on the 128 x 64 x 128 droplet, against eager
  * stepping: 8 slabs +7 to +8 %, 4 slabs +5 %).

@@ -87,6 +87,7 @@ struct vefd_ctx {
     cudaEvent_t slab_fork = nullptr;
     cudaGraphExec_t slab_exec = nullptr;
     std::vector<double> slab_key;          // state the graph was captured for
+    int slab_parity = -1;                  // population buffer parity (cur) the graph starts from
     // optional per-kernel timing of vefd_step (events on the context stream)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -746,6 +747,7 @@ static vefd_status slab_capture(vefd_ctx* c, int64_t chunk) {
         return fail(c, VEFD_ERR_CUDA, "step graph instantiation failed");
     }
     c->slab_key = state_key(c);
+    c->slab_parity = c->cur;
     return VEFD_OK;
 }
 
@@ -757,6 +759,13 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
     if (nsteps < 0) return fail(c, VEFD_ERR_ARG, "nsteps must be >= 0");
     if (nsteps > 0 && slab_usable(c)) {
         if (!steady_state(c)) {
+            st = step_eager(c, 1);
+            if (st != VEFD_OK) return st;
+            nsteps -= 1;
+        }
+        // a captured graph replays from one ping-pong parity: one eager step
+        // brings the state back to it instead of capturing the other parity
+        if (c->slab_exec && nsteps > c->slab_chunk && c->cur != c->slab_parity) {
             st = step_eager(c, 1);
             if (st != VEFD_OK) return st;
             nsteps -= 1;
