@@ -426,6 +426,62 @@ PREC_TOL = {  # relative L2 after 3 steps from a random state
 }
 
 
+@pytest.mark.slow
+def test_precision_full_geometry_report(capsys):
+    """The 16-bit storage geometry, 256 x 128 x 256 (R = 32, 2R/H = 0.5, the
+    benchmark's parameters scaled): every storage type against the FP64
+    oracle after 20 steps (the oracle needs about 1 s per step here), and the
+    FP16 and BF16 runs against the FP32 run after 5000 steps (relative L2 of
+    rho_A, u and C, and the mid-plane droplet deformation D).  Bounds follow
+    the storage precision; every run keeps the component masses."""
+    from paper_1406_2686_gb300 import vefd, warmstart
+    nx, ny, nz, R = 256, 128, 256, 32.0
+    P = _droplet_pair(nx, ny, nz, R)
+    P.o.step(20)
+    fields = (("rhoA", vefd.RHO_A, oracle.F_RHO_A), ("u", vefd.U, oracle.F_U), ("C", vefd.C, oracle.F_C))
+    ref20 = {k: P.o.read(of) for k, _, of in fields}
+    del P.o
+    P.g.close()
+    rA, rB = inputs.droplet_fields(nx, ny, nz, R=R, seed=1, noise=1e-3)
+    rA, rB = inputs.to_f32_exact(rA), inputs.to_f32_exact(rB)
+    p = P.p
+    vs_oracle, at5000, D, mass = {}, {}, {}, {}
+    for prec in (0, 1, 2):
+        g = vefd.Lattice(lattice=1, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=p["G"], eta_A=p["eta_A"],
+                         eta_B=p["eta_B"], delta=p["delta"], precision=prec)
+        g.set_wall_shear(p["u_wall"])
+        g.set_fenep(p["tau_p"], p["eta_p"], p["L2"], p["kappa"], p["phase"], 1)
+        g.init_fields(rA, rB)
+        m0 = g.diagnostics()[:2]
+        g.step(20)
+        vs_oracle[prec] = {k: rel_l2(g.read(gf).astype(np.float64), ref20[k]) for k, gf, _ in fields}
+        g.step(4980)
+        at5000[prec] = {k: g.read(gf).astype(np.float64) for k, gf, _ in fields}
+        D[prec] = warmstart.deformation(g.read(vefd.PHI)[nz // 2].astype(np.float64))
+        mass[prec] = float(np.max(np.abs(g.diagnostics()[:2] / m0 - 1)))
+        assert g.status() == 0
+        g.close()
+    oracle_bound = {0: 1e-5, 1: 5e-3, 2: 5e-2}
+    fp32_bound = {1: dict(rhoA=5e-2, u=2e-2, C=1e-2), 2: dict(rhoA=3e-1, u=2e-1, C=1e-1)}
+    d_bound = {1: 0.06, 2: 0.15}
+    rows = []
+    for prec in (0, 1, 2):
+        for k, v in vs_oracle[prec].items():
+            assert v < oracle_bound[prec], (prec, k, v)
+        vs32 = {k: rel_l2(at5000[prec][k], at5000[0][k]) for k in at5000[prec]}
+        if prec:
+            for k, v in vs32.items():
+                assert v < fp32_bound[prec][k], (prec, k, v)
+            assert abs(D[prec] - D[0]) / D[0] < d_bound[prec]
+        assert mass[prec] < 1e-6
+        rows.append((("fp32", "fp16", "bf16")[prec], vs_oracle[prec], vs32, D[prec], mass[prec]))
+    with capsys.disabled():
+        print("\nstorage  vs oracle @20: rhoA / u / C        vs FP32 @5000: rhoA / u / C      D @5000   mass")
+        for name, vo, v32, d, m in rows:
+            print("%-8s %8.1e %8.1e %8.1e      %8.1e %8.1e %8.1e   %.4f   %.1e" % (
+                name, vo["rhoA"], vo["u"], vo["C"], v32["rhoA"], v32["u"], v32["C"], d, m))
+
+
 class PrecPair(Pair):
     def __init__(self, precision, **kw):
         from paper_1406_2686_gb300 import vefd
