@@ -197,6 +197,28 @@ def test_config1_couette_2000_steps():
     assert abs(P.g.diagnostics()[0] / m0 - 1) < 1e-6
 
 
+def test_config1_couette_20000_steps():
+    """The same Couette set-up over the full 20000 steps (20 relaxation times
+    of the polymer, close to the steady state): u and C stay within 1e-5 of
+    the oracle, the mass within 1e-6, and the velocity profile is the linear
+    Couette profile between the walls (halfway bounce-back, walls at y = -1/2
+    and NY - 1/2)."""
+    eta_s = 1.0 / 6.0
+    P = Pair(lattice=0, nx=64, ny=32, ncomp=1, walls=1, eta_A=eta_s, eta_B=eta_s, u_wall=0.01, tau_p=1000.0,
+             eta_p=eta_s * 0.4 / 0.6, L2=100.0, kappa=0.0)
+    P.init(np.ones((1, 32, 64)))
+    m0 = P.g.diagnostics()[0]
+    P.step(20000)
+    for fld in ("u", "C"):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    assert abs(P.g.diagnostics()[0] / m0 - 1) < 1e-6
+    ux = P.both("u")[0][0].mean(axis=-1).ravel()  # x-averaged u_x(y)
+    y = np.arange(32) + 0.5
+    lin = 0.01 - 2 * 0.01 * y / 32.0            # +u_wall at y = -1/2, -u_wall at y = NY - 1/2
+    assert np.max(np.abs(ux - lin)) < 1e-6
+
+
 def _droplet_pair(nx, ny, nz, R, seed=1, **kw):
     """Confined droplet set-up (D3Q19, 2 components, G = 1.5, rho 2.0 / 0.1,
     width 5, phi noise 1e-3, viscoelastic droplet, L^2 = 100) scaled to the
