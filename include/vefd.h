@@ -271,7 +271,7 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * Each slab's densities/FENE-P pass marches z-segments of 12 planes (shorter
  * blocks than the whole-lattice pass, so a slab's pass, which the next lattice
  * kernels of its neighbours wait for, finishes sooner).  VEFD_ERR_ARG for
- * slabs 1, below -1 or above 64, or a bad chunk (default 128). */
+ * slabs 1, below -1 or above 64, or a bad chunk (default 256). */
 vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
 /* The slab count in effect (0: none), the chunk, and active = 1 when the next
  * vefd_step would use the graph. */

@@ -216,7 +216,7 @@ def vefd_get_status(ctx):
     return int(bits.value)
 
 
-def vefd_set_step_graph(ctx, slabs, chunk=128):
+def vefd_set_step_graph(ctx, slabs, chunk=256):
     return _check(ctx, load().vefd_set_step_graph(ctx, int(slabs), int(chunk)))
 
 
@@ -473,7 +473,7 @@ class Lattice:
     def status(self):
         return vefd_get_status(self.ctx)
 
-    def set_step_graph(self, slabs, chunk=128):
+    def set_step_graph(self, slabs, chunk=256):
         """Pipelined y-slab step graph (slabs >= 2; 0 off; -1 automatic)."""
         vefd_set_step_graph(self.ctx, slabs, chunk)
 

@@ -381,8 +381,8 @@ def test_step_graph_bit_identical(case):
         R.step(8)
         assert same(G, R)
     # the automatic choice: 8 slabs for NY a multiple of 64, 4 for 32, else none
-    assert make(dict(box, ny=64), seed=1).step_graph == (8, 128, True)
-    assert make(dict(box, ny=32), seed=1).step_graph == (4, 128, True)
+    assert make(dict(box, ny=64), seed=1).step_graph == (8, 256, True)
+    assert make(dict(box, ny=32), seed=1).step_graph == (4, 256, True)
     assert make(dict(box, ny=16), seed=1).step_graph[0] == 0
     # shapes or choices the graph cannot take step eagerly
     H = make(box, seed=72)

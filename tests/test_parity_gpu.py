@@ -279,14 +279,14 @@ def test_droplet_2000_steps_variants(variant):
 
 def test_full_size_droplet_sampled_step():
     """Full 128 x 64 x 128 confined droplet in the benchmark's launch
-    configuration (the pipelined 8-slab step graph, 128-step chunks): after
-    300 GPU steps (two graph replays among them) the state is loaded into the
+    configuration (the pipelined 8-slab step graph, 256-step chunks): after
+    600 GPU steps (two graph replays among them) the state is loaded into the
     oracle and both take one more step; every node agrees (one FP32 step),
     mass is conserved over the run, and the diagnostics agree."""
     P = _droplet_pair(128, 64, 128, 16.0)
-    assert P.g.step_graph == (8, 128, True)
+    assert P.g.step_graph == (8, 256, True)
     m0 = P.g.diagnostics()[:2]
-    P.g.step(300)
+    P.g.step(600)
     m1 = P.g.diagnostics()[:2]
     assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
     from paper_1406_2686_gb300 import vefd
