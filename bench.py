@@ -295,6 +295,7 @@ def time_variant(S, steps, warmup, model=None):
     import torch
     lat = make_lattice(S, model)
     lat.step(warmup)
+    lat.prepare_step_graph()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(lat.stream)
@@ -384,6 +385,7 @@ def time_ensemble(steps, warmup, chunk=32, setups=None, label=None):
     lats = build()
     for L in lats:
         L.step(warmup)
+        L.prepare_step_graph()
     torch.cuda.synchronize()
     e0.record(stream)
     for L in lats:
@@ -452,6 +454,7 @@ def run_ours(args):
     timed_config = list(lat.kernel_config())
     with torch.cuda.stream(stream):
         lat.step(W)
+        lat.prepare_step_graph()  # capture outside the timed region (no step is taken)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()

@@ -273,6 +273,13 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * kernels of its neighbours wait for, finishes sooner).  VEFD_ERR_ARG for
  * slabs 1, below -1 or above 64, or a bad chunk (default 256). */
 vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
+/* Captures and instantiates the step graph for the current state now, so the
+ * next vefd_step call of at least one chunk replays it without capturing
+ * first (capture records 2 x slabs x chunk launches).  Takes no step.  A no-op
+ * when the graph does not apply or the state is not steady yet (the Euler
+ * start or densities pending: take a step first).  VEFD_ERR_STATE before
+ * initialisation, VEFD_ERR_CUDA on capture errors. */
+vefd_status vefd_prepare_step_graph(vefd_ctx *ctx);
 /* The slab count in effect (0: none), the chunk, and active = 1 when the next
  * vefd_step would use the graph. */
 vefd_status vefd_get_step_graph(vefd_ctx *ctx, int *slabs, int *chunk, int *active);

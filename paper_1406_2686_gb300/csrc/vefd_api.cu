@@ -1000,6 +1000,19 @@ vefd_status vefd_set_step_graph(vefd_ctx* c, int slabs, int chunk) {
     return VEFD_OK;
 }
 
+vefd_status vefd_prepare_step_graph(vefd_ctx* c) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (!slab_usable(c) || !steady_state(c)) return VEFD_OK;
+    if (c->slab_exec && c->slab_key == state_key(c)) return VEFD_OK;
+    if (c->slab_exec) {
+        cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(c->slab_exec);
+        c->slab_exec = nullptr;
+    }
+    return slab_capture(c, c->slab_chunk);
+}
+
 vefd_status vefd_get_step_graph(vefd_ctx* c, int* slabs, int* chunk, int* active) {
     if (!c || !slabs || !chunk || !active) return VEFD_ERR_ARG;
     *slabs = slab_count(c);

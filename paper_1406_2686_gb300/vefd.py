@@ -44,7 +44,8 @@ EXPORTS = [
     "vefd_diagnostics_noalloc", "vefd_set_polymer_coupling", "vefd_set_kernel_config", "vefd_get_kernel_config",
     "vefd_autotune", "vefd_ensemble_create", "vefd_ensemble_step", "vefd_ensemble_last_error",
     "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_set_config",
-    "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_set_step_graph", "vefd_get_step_graph", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
+    "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_set_step_graph", "vefd_get_step_graph",
+    "vefd_prepare_step_graph", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
 ]
 
 _lib = None
@@ -105,6 +106,7 @@ def load(build_if_missing=True):
         "vefd_ensemble_get_config": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint)],
         "vefd_ensemble_autotune": [vp, i64, i64, ctypes.POINTER(dbl)],
         "vefd_set_step_graph": [vp, cint, cint],
+        "vefd_prepare_step_graph": [vp],
         "vefd_get_step_graph": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)],
     }
     for name, args in sigs.items():
@@ -218,6 +220,10 @@ def vefd_get_status(ctx):
 
 def vefd_set_step_graph(ctx, slabs, chunk=256):
     return _check(ctx, load().vefd_set_step_graph(ctx, int(slabs), int(chunk)))
+
+
+def vefd_prepare_step_graph(ctx):
+    return _check(ctx, load().vefd_prepare_step_graph(ctx))
 
 
 def vefd_get_step_graph(ctx):
@@ -476,6 +482,11 @@ class Lattice:
     def set_step_graph(self, slabs, chunk=256):
         """Pipelined y-slab step graph (slabs >= 2; 0 off; -1 automatic)."""
         vefd_set_step_graph(self.ctx, slabs, chunk)
+
+    def prepare_step_graph(self):
+        """Capture the step graph now (no step taken) so that the next long
+        step call only replays it."""
+        vefd_prepare_step_graph(self.ctx)
 
     @property
     def step_graph(self):

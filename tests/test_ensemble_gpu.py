@@ -374,6 +374,8 @@ def test_step_graph_bit_identical(case):
             G.step(n)
             R.step(n)
             assert same(G, R), (slabs, n)
+            G.prepare_step_graph()         # captures (or keeps) the graph, takes no step
+            assert same(G, R)
         assert G.status() == 0 and G.steps_done == 34
         G.set_wall_shear(0.005)            # a parameter change re-captures
         R.set_wall_shear(0.005)
