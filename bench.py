@@ -312,6 +312,59 @@ def time_variant(S, steps, warmup, model=None):
     return out
 
 
+def time_d2q9_couette(big_steps=1000, warmup=100):
+    """The single-component D2Q9 FENE-P Couette set-up (tau = 1, walls +-0.01,
+    tau_P = 1000, eta_P / (eta_s + eta_P) = 0.4, L^2 = 100, C = I): the wall
+    time of its 20000 steps on the 64 x 32 lattice (2048 nodes, so launch-
+    latency bound), and MLUPS on a scaled 4096 x 2048 lattice, where the
+    algorithmic bytes are 136 per node update (18 populations, 4 C
+    components and 4 history components, each read and written once)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2686_gb300 import vefd
+    eta_s = 1.0 / 6.0
+    peak, _ = measured_peak()
+
+    def lattice(nx, ny):
+        L = vefd.Lattice(lattice=vefd.D2Q9, nx=nx, ny=ny, nz=1, ncomp=1, walls=1, eta_A=eta_s, eta_B=eta_s)
+        L.set_wall_shear(0.01)
+        L.set_fenep(1000.0, eta_s * 0.4 / 0.6, 100.0, 0.0, 0, 1)
+        L.init_fields(np.ones((1, ny, nx), np.float32))
+        return L
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    small = lattice(64, 32)
+    small.step(1)
+    small.prepare_step_graph()  # the whole-lattice graph, captured outside the timed region
+    torch.cuda.synchronize()
+    e0.record(small.stream)
+    small.step(20000)
+    e1.record(small.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["64x32_20000_steps"] = {"ms": round(ms, 2), "us_per_step": round(ms / 20000 * 1e3, 2),
+                                "step_graph": list(small.step_graph), "status_bits": small.status()}
+    small.close()
+    big = lattice(4096, 2048)
+    big.step(warmup)
+    big.prepare_step_graph()
+    torch.cuda.synchronize()
+    e0.record(big.stream)
+    big.step(big_steps)
+    e1.record(big.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = 4096 * 2048
+    bw = 136 * n / (ms / big_steps / 1e3) / 1e9
+    out["4096x2048"] = {"value": round(n * big_steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "steps": big_steps,
+                        "step_roofline": {"achieved": round(bw, 1), "frac": round(bw / peak, 4),
+                                          "algorithmic_bytes_per_node": 136}, "status_bits": big.status()}
+    big.close()
+    return out
+
+
 def ensemble_setups(n=64, seed=7, umax=0.08, screen=100):
     """n uneven sheared-droplet boxes sweeping the set-up: NX in {32, 64, 96},
     NY and NZ in {32, 40, ..., 96}; Ca in [0.05, 0.3], De in [0.1, 4]
@@ -531,10 +584,12 @@ def run_ours(args):
         line["variants"] = {pn: time_variant(Setup(S.name, pn), vsteps, min(W, 50)) for pn in ("fp16", "bf16")}
         for name, model in (("mrt", dict(collision=1)), ("cholesky", dict(chol=1)), ("paper_sec2", PAPER_MODEL)):
             line["variants"][name] = time_variant(S, vsteps, min(W, 50), model)
+        line["variants"]["d2q9_couette"] = time_d2q9_couette()
         line["variants"]["note"] = ("fp16/bf16: 16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
                                     "and C; mrt: moment-space collision with the paper's relaxation times; cholesky: "
                                     "log-Cholesky conformation update; paper_sec2: both plus the polymer stress in the "
-                                    "equilibrium; %d steps each" % vsteps)
+                                    "equilibrium; %d steps each; d2q9_couette: the one-component D2Q9 Couette "
+                                    "set-up, 20000 steps at 64 x 32 (time) and MLUPS at 4096 x 2048" % vsteps)
     if not args.no_ensemble and S.prec == 0:
         line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
         line["ensemble_small"] = time_ensemble(max(100, K // 20), min(W, 20), setups=small_setups(),

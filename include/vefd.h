@@ -246,32 +246,36 @@ vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *
  * frees the scratch lattice's device memory and synchronises the context
  * stream.  VEFD_ERR_UNSTABLE when the scratch run trips a guard. */
 vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
-/* Pipelined step graph (implementation detail; the paper steps the whole
- * lattice).  With slabs >= 2, vefd_step runs whole chunks of `chunk` steps
- * (even, >= 2) as a replayed CUDA graph in which the lattice is split into
- * `slabs` slabs of NY / slabs rows.  Each slab's lattice kernel and
- * densities/FENE-P pass is a graph node that waits only for the nodes of the
- * neighbouring slabs it exchanges data with: its lattice kernel of step n+1
- * waits for the passes of step n on slabs k-1, k, k+1, and its pass of step n
- * waits for the lattice kernels of step n on those slabs.  Work on different
- * slabs then overlaps, and a slab's new populations can be re-read while
- * still in L2.  The kernels and their per-node arithmetic are those of the eager
- * step, so results are bit-identical.
- * The graph is used when: the lattice is D3Q19; the kernel configuration is
- * a staged tile 0-2 with post mode 2; NY is a multiple of 8 * slabs; kernel
- * timing is off; and the context stream is not being captured.  Some steps
- * run eagerly: the Euler start, steps with pending densities, the remainder
- * of nsteps after whole chunks, and one step that brings the ping-pong buffers
- * back to the parity the graph was captured at (rather than capturing the
- * other parity).  The graph is re-captured when the parameters or kernel
- * choice change.  slabs = 0 turns it off;
- * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64,
- * 4 when of 32, otherwise none (on the 128 x 64 x 128 droplet, against eager
- * stepping: 8 slabs +7 to +8 %, 4 slabs +5 %).
- * Each slab's densities/FENE-P pass marches z-segments of 12 planes (shorter
- * blocks than the whole-lattice pass, so a slab's pass, which the next lattice
- * kernels of its neighbours wait for, finishes sooner).  VEFD_ERR_ARG for
- * slabs 1, below -1 or above 64, or a bad chunk (default 256). */
+/* Step graph (implementation detail; the paper steps the whole lattice).
+ * vefd_step runs whole chunks of `chunk` steps (even, >= 2) as a replayed
+ * CUDA graph, in one of two forms.
+ * - Pipelined slabs (slabs >= 2): the lattice is split into `slabs` slabs of
+ *   NY / slabs rows.  Each slab's lattice kernel and densities/FENE-P pass is
+ *   a graph node that waits only for the nodes of the neighbouring slabs it
+ *   exchanges data with: its lattice kernel of step n+1 waits for the passes
+ *   of step n on slabs k-1, k, k+1, and its pass of step n waits for the
+ *   lattice kernels of step n on those slabs.  Work on different slabs then
+ *   overlaps, and a slab's new populations can be re-read while still in L2.
+ *   Each slab's pass marches z-segments of 12 planes (shorter blocks than
+ *   the whole-lattice pass, so the pass its neighbours wait for finishes
+ *   sooner).  This form needs: D3Q19; a staged tile 0-2 with post mode 2;
+ *   NY a multiple of 8 * slabs.  An explicit slab count the lattice does not
+ *   admit means eager stepping.
+ * - Whole-lattice (slabs = 1): the eager launch pairs of `chunk` steps,
+ *   replayed as one graph; any lattice and kernel choice.  It saves the
+ *   host-side launch cost, which bounds small lattices.
+ * In both forms the kernels and their per-node arithmetic are those of the
+ * eager step, so results are bit-identical.  slabs = 0 turns the graph off;
+ * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64, 4 when
+ * of 32, where the split applies, otherwise the whole-lattice form (on the
+ * 128 x 64 x 128 droplet, against eager stepping: 8 slabs +7 to +8 %,
+ * 4 slabs +5 %).  The graph is used when kernel timing is off and the
+ * context stream is not being captured.  Some steps run eagerly: the Euler
+ * start, steps with pending densities, the remainder of nsteps after whole
+ * chunks, and one step that brings the ping-pong buffers back to the parity
+ * the graph was captured at (rather than capturing the other parity).  The
+ * graph is re-captured when the parameters or kernel choice change.
+ * VEFD_ERR_ARG for slabs below -1 or above 64, or a bad chunk (default 256). */
 vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
 /* Captures and instantiates the step graph for the current state now, so the
  * next vefd_step call of at least one chunk replays it without capturing
@@ -280,8 +284,8 @@ vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
  * start or densities pending: take a step first).  VEFD_ERR_STATE before
  * initialisation, VEFD_ERR_CUDA on capture errors. */
 vefd_status vefd_prepare_step_graph(vefd_ctx *ctx);
-/* The slab count in effect (0: none), the chunk, and active = 1 when the next
- * vefd_step would use the graph. */
+/* The slab count in effect (0: no graph, 1: the whole-lattice form), the
+ * chunk, and active = 1 when the next vefd_step would use the graph. */
 vefd_status vefd_get_step_graph(vefd_ctx *ctx, int *slabs, int *chunk, int *active);
 
 /* ---- ensembles of independent lattices (implementation detail: the paper

@@ -328,13 +328,25 @@ uint64_t splitmix64(uint64_t seed, uint64_t i) {
     return z ^ (z >> 31);
 }
 
-// Slabs of the pipelined step graph: the setting, or automatically 8 slabs
-// when NY is a multiple of 64 and 4 when of 32 (measured on the 128 x 64 x 128
-// droplet: 8 slabs 7-8 % and 4 slabs 5 % faster than eager stepping),
-// otherwise none.
+// The pipelined y-slab split applies for K slabs: staged lattice tiles (not
+// the persistent forms) with the separate z-marching pass, D3Q19, and rows
+// that split into K slabs of whole 32 x 8 columns.
+bool slabs_fit(const vefd_ctx* c, int K) {
+    return K >= 2 && c->cfg.lattice == VEFD_D3Q19 && c->tma_ok && c->zm_ok && !c->fused_ok && c->lat_tile <= 2 &&
+           c->cfg.ny % (8 * K) == 0;
+}
+
+// Slabs of the step graph for this lattice and kernel choice (0: no graph,
+// 1: whole-lattice launch pairs replayed as a graph): the setting, or
+// automatically 8 slabs when NY is a multiple of 64 and 4 when of 32 where
+// the split applies (measured on the 128 x 64 x 128 droplet: 8 slabs 7-8 %
+// and 4 slabs 5 % faster than eager stepping), otherwise 1.  An explicit slab
+// count the lattice does not admit means no graph.
 int slab_count(const vefd_ctx* c) {
+    if (c->slabs >= 2) return slabs_fit(c, c->slabs) ? c->slabs : 0;
     if (c->slabs >= 0) return c->slabs;
-    return c->cfg.ny % 64 == 0 ? 8 : (c->cfg.ny % 32 == 0 ? 4 : 0);
+    const int K = c->cfg.ny % 64 == 0 ? 8 : (c->cfg.ny % 32 == 0 ? 4 : 0);
+    return slabs_fit(c, K) ? K : 1;
 }
 
 // Everything a captured step bakes into its launches: parameters, kernel
@@ -352,15 +364,10 @@ std::vector<double> state_key(const vefd_ctx* m) {
 // start or the densities-on-demand pass).
 bool steady_state(const vefd_ctx* m) { return m->drho_valid && (m->have_prev || !m->fd_on); }
 
-// The pipelined step graph applies: staged lattice tiles (not the persistent
-// forms) with the separate z-marching pass, D3Q19, rows that split into
-// `slabs` slabs of whole 32 x 8 columns, no kernel timing, and a stream that
-// is not itself being captured.
+// The step graph applies: a slab count (or the whole-lattice graph), no
+// kernel timing, and a stream that is not itself being captured.
 bool slab_usable(vefd_ctx* c) {
-    const int K = slab_count(c);
-    if (K < 2 || c->cfg.lattice != VEFD_D3Q19 || !c->tma_ok || !c->zm_ok || c->fused_ok || c->lat_tile > 2 ||
-        c->prof_on || c->cfg.ny % (8 * K) != 0)
-        return false;
+    if (slab_count(c) < 1 || c->prof_on) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
     return true;
@@ -662,6 +669,51 @@ vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, siz
 // t waits for the lattice kernels of step t on slabs k - 1, k, k + 1 (their
 // pushes and velocities reach its rows).  With walls the outer slabs have one
 // neighbour, otherwise the slabs wrap.  Same-slab order is its stream's order.
+static vefd_status step_eager(vefd_ctx* c, int64_t nsteps);
+
+// Captures `chunk` eager steps (whole-lattice launch pairs) into c->slab_exec:
+// the graph form for lattices and kernel choices the slab split does not
+// take; it saves the host-side launch cost of small lattices.  Capture only
+// records the launches, so the host state they advanced is put back.
+static vefd_status plain_capture(vefd_ctx* c, int64_t chunk) {
+    if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(c, VEFD_ERR_CUDA, "cannot create the capture stream");
+    const int cur = c->cur, ccur = c->ccur, hp = c->have_prev;
+    const int64_t steps = c->steps;
+    float* const dr = c->drho;
+    float* const dra = c->drho_alt;
+    const bool dv = c->drho_valid;
+    cudaStream_t own = c->stream;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(c, VEFD_ERR_CUDA, "cannot begin capture");
+    c->stream = c->cap;
+    const vefd_status st = step_eager(c, chunk);
+    c->stream = own;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce2 = cudaStreamEndCapture(c->cap, &graph);
+    c->cur = cur;
+    c->ccur = ccur;
+    c->have_prev = hp;
+    c->steps = steps;
+    c->drho = dr;
+    c->drho_alt = dra;
+    c->drho_valid = dv;
+    if (st != VEFD_OK || ce2 != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st != VEFD_OK ? st : fail(c, VEFD_ERR_CUDA, "step graph capture failed: %s", cudaGetErrorString(ce2));
+    }
+    const cudaError_t ce = cudaGraphInstantiate(&c->slab_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        c->slab_exec = nullptr;
+        return fail(c, VEFD_ERR_CUDA, "step graph instantiation failed");
+    }
+    c->slab_key = state_key(c);
+    c->slab_parity = c->cur;
+    return VEFD_OK;
+}
+
 static vefd_status slab_capture(vefd_ctx* c, int64_t chunk) {
     const int K = slab_count(c);
     if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
@@ -755,7 +807,11 @@ static vefd_status slab_capture(vefd_ctx* c, int64_t chunk) {
     return VEFD_OK;
 }
 
-static vefd_status step_eager(vefd_ctx* c, int64_t nsteps);
+// The step graph for the current setting: the slab pipeline or the
+// whole-lattice form.
+static vefd_status graph_capture(vefd_ctx* c, int64_t chunk) {
+    return slab_count(c) >= 2 ? slab_capture(c, chunk) : plain_capture(c, chunk);
+}
 
 vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
     vefd_status st = need_ready(c);
@@ -782,7 +838,7 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
                     cudaGraphExecDestroy(c->slab_exec);
                     c->slab_exec = nullptr;
                 }
-                st = slab_capture(c, chunk);
+                st = graph_capture(c, chunk);
                 if (st != VEFD_OK) return st;
             }
             for (int64_t r = 0; r < full; ++r) VEFD_CUDA(c, cudaGraphLaunch(c->slab_exec, c->stream));
@@ -987,7 +1043,7 @@ vefd_status vefd_clear_status(vefd_ctx* c) {
 }
 
 vefd_status vefd_set_step_graph(vefd_ctx* c, int slabs, int chunk) {
-    if (!c || slabs < -1 || slabs > 64 || slabs == 1 || chunk < 2 || (chunk & 1)) return VEFD_ERR_ARG;
+    if (!c || slabs < -1 || slabs > 64 || chunk < 2 || (chunk & 1)) return VEFD_ERR_ARG;
     if (c->slabs != slabs || c->slab_chunk != chunk) {
         if (c->slab_exec) {
             cudaStreamSynchronize(c->stream);
@@ -1010,7 +1066,7 @@ vefd_status vefd_prepare_step_graph(vefd_ctx* c) {
         cudaGraphExecDestroy(c->slab_exec);
         c->slab_exec = nullptr;
     }
-    return slab_capture(c, c->slab_chunk);
+    return graph_capture(c, c->slab_chunk);
 }
 
 vefd_status vefd_get_step_graph(vefd_ctx* c, int* slabs, int* chunk, int* active) {

@@ -385,7 +385,7 @@ def test_step_graph_bit_identical(case):
     # the automatic choice: 8 slabs for NY a multiple of 64, 4 for 32, else none
     assert make(dict(box, ny=64), seed=1).step_graph == (8, 256, True)
     assert make(dict(box, ny=32), seed=1).step_graph == (4, 256, True)
-    assert make(dict(box, ny=16), seed=1).step_graph[0] == 0
+    assert make(dict(box, ny=16), seed=1).step_graph == (1, 256, True)  # the whole-lattice form
     # shapes or choices the graph cannot take step eagerly
     H = make(box, seed=72)
     H.set_step_graph(3, 4)                 # NY not a multiple of 8 * 3
@@ -393,7 +393,32 @@ def test_step_graph_bit_identical(case):
     H.set_step_graph(2, 4)
     H.set_kernel_config(3, 2)              # persistent tile
     assert H.step_graph[2] is False
-    for bad in ((1, 4), (2, 3), (-2, 4)):
+    for bad in ((65, 4), (2, 3), (-2, 4)):
         with pytest.raises(vefd.VefdError) as ei:
             H.set_step_graph(*bad)
         assert ei.value.status == vefd.ERR_ARG
+
+
+@pytest.mark.parametrize("k", [0, 3, 4])
+@pytest.mark.parametrize("config", [None, (0, 0), (3, 1)])
+def test_whole_lattice_graph_bit_identical(k, config):
+    """The whole-lattice step graph (eager launch pairs replayed as one graph)
+    for lattices and kernel choices the slab split does not take (D2Q9, a
+    coupling variant, the column march with fused densities, a persistent
+    tile with the tiled pass) gives the eager step's bits across the Euler
+    start, replays, parity realignment and eager remainders."""
+    box = BOXES[k]
+    G = make(box, seed=81)
+    R = make(box, seed=81)
+    if config is not None:
+        G.set_kernel_config(*config)
+        R.set_kernel_config(*config)
+    R.set_step_graph(0)
+    G.set_step_graph(1, 4)
+    assert G.step_graph == (1, 4, True)
+    for n in (11, 1, 8, 5, 9):
+        G.step(n)
+        R.step(n)
+        assert same(G, R), (n, G.kernel_config())
+    assert G.status() == 0 and G.steps_done == 34
+
