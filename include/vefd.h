@@ -321,9 +321,12 @@ vefd_status vefd_ensemble_step(vefd_ensemble *ens, int64_t nsteps, int64_t chunk
  * component count, storage type, collision operator, FENE-P switch and
  * programmatic-launch setting, and each takes the staged lattice kernel and
  * the separate z-marching densities/FENE-P pass (NX % 32 == 0, NY % 8 == 0,
- * kernel config post mode 2), a replayed step is ONE lattice-kernel launch
- * over the 32 x 4 x 2 tiles of all members and ONE densities/FENE-P launch
- * over their 32 x 8 columns.  Each block finds its member by binary search
+ * kernel config post mode 2), the members are split into up to 4 groups of
+ * about equal node count (contiguous in member order), and a replayed step
+ * is, per group, ONE lattice-kernel launch over the 32 x 4 x 2 tiles of its
+ * members and ONE densities/FENE-P launch over their 32 x 8 columns; each
+ * group's launches are one graph branch, so the groups overlap.  Each block
+ * finds its member by binary search
  * over a device table holding the member's parameters, the buffers and
  * tensor maps of both ping-pong parities, and its tile counts; the table is
  * rebuilt with every re-capture.  Per node the arithmetic is the member's own

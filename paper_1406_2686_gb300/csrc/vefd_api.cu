@@ -1356,7 +1356,12 @@ struct vefd_ensemble {
     EnsMember* d_table = nullptr;
     int* d_start = nullptr;
     size_t d_cap = 0;           // members the device table holds
-    int lat_items = 0, post_items = 0;
+    // members split into contiguous groups of about equal node count; each
+    // group's launches form one graph branch, so groups overlap like the
+    // per-member branches do (start[] is relative to the group's first member)
+    int groups = 0;             // 0: automatic
+    std::vector<int> gbeg;      // first member of each group, then the member count
+    std::vector<int> glat, gpost;  // lattice tiles and z-march columns of each group
 };
 
 namespace {
@@ -1418,8 +1423,33 @@ vefd_status ens_build_table(vefd_ensemble* e) {
     const int zs = e->post_seg > 0 ? e->post_seg : ens_post_segment(e, sms);
     e->table.assign(n, EnsMember{});
     e->start.assign(2 * n, 0);
-    long long lat = 0, post = 0;
+    // groups: contiguous members, split at equal shares of the total nodes
+    int G = e->groups > 0 ? e->groups : 4;
+    if (const char* env = getenv("VEFD_ENS_GROUPS")) G = atoi(env) > 0 ? atoi(env) : G;
+    G = std::max(1, std::min(G, (int)n));
+    long long total = 0;
+    for (const vefd_ctx* m : e->members) total += m->N;
+    e->gbeg.assign(1, 0);
+    {
+        long long acc = 0;
+        for (size_t k = 0; k < n; ++k) {
+            acc += e->members[k]->N;
+            const int g = (int)e->gbeg.size();  // groups opened so far
+            if (k + 1 < n && g < G && acc * G >= total * g) e->gbeg.push_back((int)k + 1);
+        }
+        e->gbeg.push_back((int)n);
+    }
+    const int ng = (int)e->gbeg.size() - 1;
+    e->glat.assign(ng, 0);
+    e->gpost.assign(ng, 0);
+    long long lat = 0, post = 0, lat_max = 0, post_max = 0;
+    int grp = 0;
     for (size_t k = 0; k < n; ++k) {
+        if ((int)k == e->gbeg[grp + 1]) {
+            ++grp;
+            lat = 0;
+            post = 0;
+        }
         vefd_ctx* m = e->members[k];
         EnsMember& M = e->table[k];
         M.p = params_of(m);
@@ -1448,10 +1478,13 @@ vefd_status ens_build_table(vefd_ensemble* e) {
         e->start[n + k] = (int)post;
         lat += (long long)M.ntx * M.nty * M.ntz;
         post += (long long)M.ncx * M.ncy * M.nseg;
+        lat_max = std::max(lat_max, lat);
+        post_max = std::max(post_max, post);
+        e->glat[grp] = (int)std::min(lat, 0x7fffffffLL);
+        e->gpost[grp] = (int)std::min(post, 0x7fffffffLL);
     }
-    if (lat > 0x7fffffffLL || post > 0x7fffffffLL) return ens_fail(e, VEFD_ERR_ARG, "ensemble too large for one launch");
-    e->lat_items = (int)lat;
-    e->post_items = (int)post;
+    if (lat_max > 0x7fffffffLL || post_max > 0x7fffffffLL)
+        return ens_fail(e, VEFD_ERR_ARG, "ensemble too large for one launch");
     if (e->d_cap < n) {
         if (e->main) cudaStreamSynchronize(e->main);
         if (e->d_table) cudaFree(e->d_table);
@@ -1483,12 +1516,22 @@ vefd_status ens_capture_batched(vefd_ensemble* e, int64_t chunk) {
     const bool fd = a->fd_on != 0, pdl = a->pdl;
     if (cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return ens_fail(e, VEFD_ERR_CUDA, "cannot begin capture");
-    cudaError_t ce = cudaSuccess;
-    for (int64_t k = 0; k < chunk && ce == cudaSuccess; ++k) {
-        const int par = (int)(k & 1);
-        ce = launch_lattice_batch(nc, prec, a->collision, e->d_table, e->d_start, nm, e->lat_items, par, pdl, e->main);
-        if (ce == cudaSuccess)
-            ce = launch_post_batch(nc, prec, fd, e->d_table, e->d_start + nm, nm, e->post_items, par, pdl, e->main);
+    cudaError_t ce = cudaEventRecord(e->fork, e->main);
+    const int ng = (int)e->gbeg.size() - 1;
+    for (int g = 0; g < ng && ce == cudaSuccess; ++g) {
+        const int m0 = e->gbeg[g], gm = e->gbeg[g + 1] - m0;
+        cudaStream_t s = e->branch[g];
+        ce = cudaStreamWaitEvent(s, e->fork, 0);
+        for (int64_t k = 0; k < chunk && ce == cudaSuccess; ++k) {
+            const int par = (int)(k & 1);
+            ce = launch_lattice_batch(nc, prec, a->collision, e->d_table + m0, e->d_start + m0, gm, e->glat[g], par,
+                                      pdl, s);
+            if (ce == cudaSuccess)
+                ce = launch_post_batch(nc, prec, fd, e->d_table + m0, e->d_start + nm + m0, gm, e->gpost[g], par, pdl,
+                                       s);
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(e->join[g], s);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(e->main, e->join[g], 0);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t ce2 = cudaStreamEndCapture(e->main, &graph);
