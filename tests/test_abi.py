@@ -106,6 +106,31 @@ def test_parameter_validation_on_host(lib):
         vefd.vefd_destroy(ctx)
 
 
+def test_step_graph_and_ensemble_argument_checks(lib):
+    """The step-graph, wait self-test and ensemble configuration calls check
+    their arguments on the host before touching the device."""
+    cfg = _cfg()
+    ctx = vefd.vefd_create(cfg, 0)
+    try:
+        for slabs, chunk in ((-2, 256), (65, 256), (8, 3), (8, 0)):
+            assert lib.vefd_set_step_graph(ctx, slabs, chunk) == vefd.ERR_ARG
+        for slabs in (-1, 0, 1, 2, 8):
+            assert lib.vefd_set_step_graph(ctx, slabs, 64) == vefd.OK
+        assert lib.vefd_prepare_step_graph(ctx) == vefd.ERR_STATE  # nothing bound
+        assert lib.vefd_wait_selftest(ctx, 2) == vefd.ERR_ARG
+        assert lib.vefd_wait_selftest(ctx, 0) == vefd.ERR_STATE
+    finally:
+        vefd.vefd_destroy(ctx)
+    assert lib.vefd_set_step_graph(None, 8, 64) == vefd.ERR_ARG
+    assert lib.vefd_prepare_step_graph(None) == vefd.ERR_ARG
+    assert lib.vefd_ensemble_set_batched(None, 1) == vefd.ERR_ARG
+    assert lib.vefd_ensemble_set_config(None, 1, 0) == vefd.ERR_ARG
+    assert lib.vefd_ensemble_autotune(None, 64, 32, None) == vefd.ERR_ARG
+    assert lib.vefd_ensemble_is_batched(None) == 0
+    b, z = ctypes.c_int(), ctypes.c_int()
+    assert lib.vefd_ensemble_get_config(None, ctypes.byref(b), ctypes.byref(z)) == vefd.ERR_ARG
+
+
 def test_d2q9_field_sizes(lib):
     cfg = _cfg(lattice=vefd.D2Q9, nz=1, ncomp=1)
     ctx = vefd.vefd_create(cfg, 0)
