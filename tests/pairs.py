@@ -74,3 +74,19 @@ def rel_l2(a, b):
 
 def max_abs(a, b):
     return float(np.max(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))))
+
+
+def identity_rows(nc):
+    """1 on the diagonal components of a stored tensor (xx xy xz yy yz zz, or
+    xx xy yy zz for D2Q9), 0 elsewhere."""
+    return np.array([1, 0, 0, 1, 0, 1.0]) if nc == 6 else np.array([1, 0, 1, 1.0])
+
+
+def dev_rel_l2(a, b):
+    """Relative L2 of the departure from the identity of two tensor fields
+    shaped (nc, ...): ||(a - I) - (b - I)|| / ||b - I||.  The identity
+    dominates ||C||, so this is the measure of the polymer deformation."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    eye = identity_rows(a.shape[0]).reshape((-1,) + (1,) * (a.ndim - 1))
+    return rel_l2(a - eye, b - eye)

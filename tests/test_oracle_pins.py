@@ -416,6 +416,57 @@ def test_couette_fenep_closed_form():
         assert np.max(np.abs(C[k] - Cex[kk])) < 1e-6 * max(1, abs(Cex[kk]))
     u = o.read(oracle.F_U)[0]
     assert np.max(np.abs(u - cf.couette_profile(ny, U)[None, :, None])) < 1e-9
+    # the diagnostics of that steady state (Sec. 3.1, Eqs. lindner, lindner2 and N2S)
+    _check_couette_diagnostics(o.diagnostics(), 4, ny, U)
+
+
+def _check_couette_diagnostics(d, nx, ny, U):
+    """Diagnostics of a one-component steady FENE-P Couette flow at
+    Lambda = tau_P gamma_dot = -0.625, L^2 = 100 (the lower wall moves at +U):
+      5  <sigma_P,xy> = -S(0.625, 100)           (shear stress, sign of gamma_dot)
+      6  <sigma_P,xx - sigma_P,yy> = N(0.625, 100) (first normal stress difference)
+      15 <tr sigma_P> - 3 = N                      (sigma_yy = sigma_zz = 1)
+      7  max tr C / L^2 = tr C of the closed form / L^2
+      8  max |u| = U (NY - 1) / NY                 (the rows next to the walls)
+      0  mass = NX NY; 2-4 momentum = 0 (antisymmetric profile)
+      one component, phi = 1 everywhere: the indicator fills the NX x NY
+      rectangle, so area 9 = volume 14 = NX NY, the centroid 12, 13 is
+      ((NX - 1)/2, (NY - 1)/2), the second moments are (n^2 - 1)/12 and
+      theta 11 is pi/2 for the taller side along y, D 10 = (a - b)/(a + b)
+      with a, b the square roots of those moments."""
+    S, N = cf.shear_S(0.625, 100.0), cf.shear_N(0.625, 100.0)
+    Cex, _ = cf.shear_conformation(-0.625, 100.0)
+    assert abs(d[5] - (-S)) < 1e-6 * S
+    assert abs(d[6] - N) < 1e-6 * N
+    assert abs(d[15] - N) < 1e-6 * N
+    assert abs(d[7] - (Cex[0] + Cex[3] + Cex[5]) / 100.0) < 1e-8
+    assert abs(d[8] - U * (ny - 1) / ny) < 1e-9
+    assert abs(d[0] - nx * ny) < 1e-9 and abs(d[1]) == 0.0
+    assert np.max(np.abs(d[2:5])) < 1e-10
+    assert d[9] == nx * ny and d[14] == nx * ny
+    assert abs(d[12] - (nx - 1) / 2) < 1e-12 and abs(d[13] - (ny - 1) / 2) < 1e-12
+    ia, ib = math.sqrt((ny * ny - 1) / 12.0), math.sqrt((nx * nx - 1) / 12.0)
+    assert abs(d[10] - (ia - ib) / (ia + ib)) < 1e-12
+    assert abs(d[11] - math.pi / 2) < 1e-12
+
+
+def test_couette_diagnostics_signs():
+    """The diagnostic pins above catch a transposed or sign-flipped stress
+    average: the same Couette flow with the walls reversed (Lambda = +0.625)
+    flips <sigma_P,xy> and keeps <N_1> (Eq. N2S: N = 2 S^2 is even in S)."""
+    ny, U = 8, 0.02
+    gdot = 2 * U / ny
+    taup = 0.625 / gdot
+    for sign in (+1, -1):
+        o = oracle.Oracle(lattice=oracle.D2Q9, nx=2, ny=ny, eta_A=1 / 6, eta_B=1 / 6, u_wall=sign * U, tau_p=taup,
+                          eta_p=1 / 9, L2=100.0)
+        o.init_fields(np.ones((1, ny, 2)))
+        o.step(int(25 * taup))
+        d = o.diagnostics()
+        S, N = cf.shear_S(0.625, 100.0), cf.shear_N(0.625, 100.0)
+        assert abs(d[5] + sign * S) < 1e-6 * S
+        assert abs(d[6] - N) < 1e-6 * N and abs(d[15] - N) < 1e-6 * N
+        assert abs(d[8] - U * (ny - 1) / ny) < 1e-9
 
 
 def test_fenep_at_rest_and_symmetry():
@@ -477,6 +528,43 @@ def test_deformation_diagnostic_ellipse():
     assert abs(d[10] - (a - b) / (a + b)) < 0.01
     assert abs(d[11] - th) < 0.01
     assert abs(d[9] - math.pi * a * b) / (math.pi * a * b) < 0.02
+    # centroid of the ellipse and, for D2Q9, volume = area of the one plane
+    assert abs(d[12] - 47.5) < 0.05 and abs(d[13] - 39.5) < 0.05
+    assert d[14] == d[9] == np.count_nonzero(inside)
+    # at rest with C = I: no stress, no motion
+    assert d[5] == 0.0 and d[6] == 0.0 and d[15] == 0.0 and d[8] == 0.0
+    assert abs(d[7] - 3.0 / o.cfg["L2"]) < 1e-15
+
+
+def test_deformation_diagnostic_sphere_and_angle_range():
+    """3-D indicator: a sphere of radius r at an off-centre point gives the
+    volume (4/3) pi r^3 (14), the disc of its mid-plane z = NZ/2 (9, the
+    plane of Sec. 4.1's D), D = 0 and the centroid of the sphere.  An
+    ellipse rotated by -pi/5 returns theta = -pi/5 (11 lies in (-pi/2, pi/2])."""
+    nx, ny, nz, r = 40, 36, 32, 9.0
+    c = (21.3, 17.0, 16.0)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    inside = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 < r * r
+    rA = np.where(inside, 2.0, 0.1)
+    o = oracle.Oracle(lattice=oracle.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, G=0.0)
+    o.init_fields(rA, 2.1 - rA)
+    d = o.diagnostics()
+    assert abs(d[14] - 4.0 / 3.0 * math.pi * r ** 3) / d[14] < 0.02
+    assert d[14] == np.count_nonzero(inside) and d[9] == np.count_nonzero(inside[nz // 2])
+    assert abs(d[9] - math.pi * r * r) / d[9] < 0.03
+    assert d[10] < 0.02
+    assert abs(d[12] - c[0]) < 0.1 and abs(d[13] - c[1]) < 1e-9
+    nx, ny = 96, 80
+    a, b, th = 22.0, 14.0, -math.pi / 5
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    xc, yc = x - 47.5, y - 39.5
+    xr = xc * math.cos(th) + yc * math.sin(th)
+    yr = -xc * math.sin(th) + yc * math.cos(th)
+    rA = np.where((xr / a) ** 2 + (yr / b) ** 2 < 1, 2.0, 0.1)[None]
+    o = oracle.Oracle(lattice=oracle.D2Q9, nx=nx, ny=ny, ncomp=2, G=0.0)
+    o.init_fields(rA, 2.1 - rA)
+    d = o.diagnostics()
+    assert abs(d[11] - th) < 0.01 and abs(d[10] - (a - b) / (a + b)) < 0.01
 
 
 def _golden():
