@@ -219,11 +219,21 @@ __device__ __forceinline__ unsigned fenep_compute(V v, float hy1, float hy2, con
     if (p.chol) {
         chol_step<NC>(c, Rc, Rprev, p.have_prev, p.L2m3, cnew, Rnew);
     } else {
+        // Compensated AB2: the sum c + inc is rounded to FP32, and its exact
+        // rounding error e (Knuth's TwoSum) is carried into the next step's
+        // increment through the stored history, R~ = R - 2e, so that
+        // 3/2 R' - 1/2 R~ = 3/2 R' - 1/2 R + e.  Near steady state the increment
+        // falls below half an ulp of C - I; without the carry it would be lost
+        // and C would stall up to (tau_P / f) ulp short of the fixed point.
+        // The history then stays within FP32 rounding of max(|R|, |e|).
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float inc = p.have_prev ? 1.5f * Rc[k] - 0.5f * Rprev[k] : Rc[k];
-            cnew[k] = c[k] + inc;
-            Rnew[k] = Rc[k];
+            const float sum = c[k] + inc;
+            const float inc_kept = sum - c[k];
+            const float err = (c[k] - (sum - inc_kept)) + (inc - inc_kept);
+            cnew[k] = sum;
+            Rnew[k] = fmaf(-2.0f, err, Rc[k]);
         }
     }
     float trn = 0.0f;

@@ -16,7 +16,7 @@ import oracle
 from oracle import closed_forms as cf
 from paper_1406_2686_gb300 import inputs
 
-from pairs import Pair, max_abs, rel_l2
+from pairs import Pair, dev_rel_l2, max_abs, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -87,6 +87,65 @@ VARIANTS = {
 @pytest.fixture(scope="module", autouse=True)
 def _threads():
     oracle.set_threads(0)
+
+
+# Deformation tolerances after many steps.  C and sigma_P are compared both
+# whole (the contract) and as departures from the identity, which is the
+# polymer deformation itself: ||C - I|| is 5-50 times smaller than ||C|| in
+# these set-ups, so the same absolute FP32 error weighs that much more.
+DEV_TOL = 1e-4
+
+
+def check_deformation(P, label=""):
+    """Relative L2 of C - I and sigma_P - I against the oracle; returns both."""
+    eC = dev_rel_l2(*P.both("C"))
+    eS = dev_rel_l2(*P.both("sigma"))
+    print("%s C: %.2e  C - I: %.2e  sigma_P - I: %.2e" % (label, rel_l2(*P.both("C")), eC, eS))
+    assert eC < DEV_TOL, ("C - I", eC)
+    assert eS < DEV_TOL, ("sigma_P - I", eS)
+    return eC, eS
+
+
+def check_diagnostics(P, dg=None, do=None, rtol=1e-5):
+    """All 16 diagnostics of the library (vefd_diagnostics) against the
+    oracle's on the same state (Sec. 4.1 measures and conservation sums):
+      0-1 masses to 1e-6 relative; 2-4 momentum to rtol of M max|u|;
+      5, 6, 15 (<sigma_xy>, <N_1>, <tr sigma_P> - 3) to rtol of the mean
+      magnitude of the summed quantity; 7, 8 (max tr C / L^2, max |u|) to
+      rtol and 10 rtol; the indicator phi > 0 (area 9, D 10, theta 11,
+      centroid 12-13, volume 14) exactly when no node has |phi| below 1e-4,
+      else within what the ambiguous nodes can change."""
+    dg = P.g.diagnostics() if dg is None else dg
+    do = P.o.diagnostics() if do is None else do
+    assert abs(dg[0] / do[0] - 1) < 1e-6
+    if P.p["ncomp"] == 2:
+        assert abs(dg[1] / do[1] - 1) < 1e-6
+    mass = do[0] + do[1]
+    for k in (2, 3, 4):
+        assert abs(dg[k] - do[k]) <= rtol * mass * do[8] + 1e-12, (k, dg[k], do[k])
+    sig = P.o.read(oracle.F_SIGMA_P)
+    nc = sig.shape[0]
+    yy = 3 if nc == 6 else 2
+    tr = sig[0] + sig[yy] + sig[nc - 1]
+    scale = {5: np.mean(np.abs(sig[1])), 6: np.mean(np.abs(sig[0] - sig[yy])), 15: np.mean(np.abs(tr - 3.0))}
+    for k, sc in scale.items():
+        assert abs(dg[k] - do[k]) <= rtol * max(sc, abs(do[k])) + 1e-12, (k, dg[k], do[k], sc)
+    assert abs(dg[7] / do[7] - 1) < rtol, (7, dg[7], do[7])
+    if do[8] > 0:
+        assert abs(dg[8] / do[8] - 1) < 10 * rtol, (8, dg[8], do[8])
+    else:
+        assert dg[8] == 0.0
+    phi = P.o.read(oracle.F_PHI) if P.p["ncomp"] == 2 else np.ones((P.o.nz, P.o.ny, P.o.nx))
+    amb = np.abs(phi) < 1e-4
+    n_plane = int(np.count_nonzero(amb[P.o.nz // 2]))
+    n_all = int(np.count_nonzero(amb))
+    assert abs(dg[9] - do[9]) <= n_plane and abs(dg[14] - do[14]) <= n_all, (dg[9], do[9], dg[14], do[14])
+    if n_plane == 0:
+        assert np.allclose(dg[10:14], do[10:14], rtol=1e-9, atol=1e-9), (dg[10:14], do[10:14])
+    else:
+        area = max(do[9], 1.0)
+        assert abs(dg[10] - do[10]) <= 4.0 * n_plane / area
+        assert abs(dg[12] - do[12]) <= P.o.nx * n_plane / area and abs(dg[13] - do[13]) <= P.o.ny * n_plane / area
 
 
 @pytest.mark.parametrize("name", sorted(VARIANTS))
@@ -194,33 +253,35 @@ def test_config1_couette_2000_steps():
     for fld in ("u", "C"):
         g, o = P.both(fld)
         assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    eC, eS = check_deformation(P, "couette 2000")
+    assert eC < 1e-5 and eS < 1e-5
     assert abs(P.g.diagnostics()[0] / m0 - 1) < 1e-6
+    check_diagnostics(P)
 
 
 def test_config1_couette_20000_steps():
     """The same Couette set-up over the full 20000 steps (20 relaxation times
-    of the polymer, close to the steady state): u stays within 1e-5 of the
-    oracle and the mass within 1e-6; the velocity profile is the linear
-    Couette profile between the walls (halfway bounce-back, walls at y = -1/2
-    and NY - 1/2).  Near steady state the FP32 AB2 update loses increments
-    below half an ulp of C - I, so the GPU's C may stop short of the FP64
-    oracle's by up to (tau_P / f) ulp per component (the bound of the
-    closed-form test below), which at 20000 steps exceeds 1e-5 relative."""
+    of the polymer, close to the steady state): u and C within 1e-5 relative
+    L2 of the oracle, C - I and sigma_P - I too, the mass within 1e-6, all 16
+    diagnostics as the oracle's, and the velocity profile the linear Couette
+    profile between the walls (halfway bounce-back, walls at y = -1/2 and
+    NY - 1/2).  Near steady state the AB2 increment of C falls below half an
+    ulp of C - I; the library carries that rounding error into the next
+    increment (compensated update), so C keeps converging."""
     eta_s = 1.0 / 6.0
     P = Pair(lattice=0, nx=64, ny=32, ncomp=1, walls=1, eta_A=eta_s, eta_B=eta_s, u_wall=0.01, tau_p=1000.0,
              eta_p=eta_s * 0.4 / 0.6, L2=100.0, kappa=0.0)
     P.init(np.ones((1, 32, 64)))
     m0 = P.g.diagnostics()[0]
     P.step(20000)
-    g, o = P.both("u")
-    assert rel_l2(g, o) < 1e-5, rel_l2(g, o)
-    g, o = P.both("C")
-    _, Z = cf.shear_conformation(-0.625, 100.0)
-    for k in range(g.shape[0]):
-        dev = float(np.max(np.abs(o[k] - (1.0 if k in (0, 2, 3) else 0.0))))
-        tol = 1000.0 / Z * float(np.spacing(np.float32(max(dev, 1e-3)))) + 1e-6
-        assert np.max(np.abs(g[k] - o[k])) < tol, (k, np.max(np.abs(g[k] - o[k])), tol)
+    for fld in ("u", "C"):
+        g, o = P.both(fld)
+        print("couette 20000 %s: %.2e" % (fld, rel_l2(g, o)))
+        assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    eC, eS = check_deformation(P, "couette 20000")
+    assert eC < 1e-5 and eS < 1e-5
     assert abs(P.g.diagnostics()[0] / m0 - 1) < 1e-6
+    check_diagnostics(P)
     ux = P.both("u")[0][0].mean(axis=-1).ravel()  # x-averaged u_x(y)
     y = np.arange(32) + 0.5
     lin = 0.01 - 2 * 0.01 * y / 32.0            # +u_wall at y = -1/2, -u_wall at y = NY - 1/2
@@ -255,8 +316,10 @@ def test_droplet_2000_steps():
     for fld in ("u", "C"):
         g, o = P.both(fld)
         assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    check_deformation(P, "droplet 2000")
     m1 = P.g.diagnostics()[:2]
     assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
+    check_diagnostics(P)
     assert P.g.status() == 0
 
 
@@ -272,8 +335,15 @@ def test_droplet_2000_steps_variants(variant):
     for fld in ("u", "C"):
         g, o = P.both(fld)
         assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    check_deformation(P, "droplet 2000 %r" % (variant,))
     m1 = P.g.diagnostics()[:2]
     assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
+    # The Cholesky scheme (Sec. 2) advances the factor of sigma_P and rebuilds
+    # C from it every step; the state is the stored C, rounded to FP32 each
+    # step with no carry of the rounding error (the direct scheme carries it in
+    # the AB2 history), so C - I is about ten times less accurate (1.4e-5 at
+    # 2000 steps) and the stress averages are held to 3e-5.
+    check_diagnostics(P, rtol=3e-5 if variant.get("chol") else 1e-5)
     assert P.g.status() == 0
 
 
@@ -293,22 +363,22 @@ def test_full_size_droplet_sampled_step():
     P.o.write(oracle.F_POPS, P.g.read(vefd.POPS).astype(np.float64))
     P.o.write(oracle.F_C, P.g.read(vefd.C).astype(np.float64))
     P.o.write(oracle.F_RPREV, P.g.read(vefd.RPREV).astype(np.float64))
-    dg, do = P.g.diagnostics(), P.o.diagnostics()
-    assert abs(dg[0] / do[0] - 1) < 1e-6 and abs(dg[1] / do[1] - 1) < 1e-6
-    assert np.allclose(dg[2:5], do[2:5], rtol=1e-4, atol=1e-6 * abs(do[0]) * 1e-3)
-    assert abs(dg[10] - do[10]) < 2e-3 and abs(dg[9] - do[9]) <= 4
+    # the oracle's diagnostics of the library's own state: every value agrees
+    check_diagnostics(P)
     P.step(1)
     for fld, tol in (("pops", 1e-6), ("u", 1e-5), ("C", 1e-6)):
         g, o = P.both(fld)
         assert rel_l2(g, o) < tol, (fld, rel_l2(g, o))
+    assert dev_rel_l2(*P.both("C")) < 1e-5 and dev_rel_l2(*P.both("sigma")) < 1e-5
+    check_diagnostics(P)
 
 
 def test_config1_closed_form_20000_steps():
     """The GPU path alone reaches the steady-shear closed form of Sec. 3.1
-    (Lambda = -0.625, L^2 = 100) after 20000 steps = 20 tau_P.  The bound is
-    the FP32 stagnation limit of the AB2 update: increments below half an
-    ulp of C - I are lost, so C can stop within (tau_P / f) * ulp of steady
-    state; the profile stays the exact Couette line."""
+    (Eqs. lindner and lindner2, Lambda = -0.625, L^2 = 100) after 20000 steps
+    = 20 tau_P: every component of C within 1e-5 relative of the closed form
+    at every node (C - I within 1e-5 relative L2), <sigma_P,xy> = -S and
+    <N_1> = N within 1e-5 relative, and the profile the exact Couette line."""
     from paper_1406_2686_gb300 import vefd
     eta_s = 1.0 / 6.0
     g = vefd.Lattice(lattice=0, nx=64, ny=32, nz=1, ncomp=1, walls=1, eta_A=eta_s, eta_B=eta_s)
@@ -318,16 +388,19 @@ def test_config1_closed_form_20000_steps():
     g.step(20000)
     C = g.read(vefd.C).astype(np.float64)
     Cex, Z = cf.shear_conformation(-0.625, 100.0)
-    for k, kk in enumerate((0, 1, 3, 5)):
-        dev = abs(Cex[kk] - (1.0 if kk in (0, 3, 5) else 0.0))
-        ulp = np.spacing(np.float32(max(dev, 1e-3)))
-        tol = 1000.0 / Z * float(ulp) + 1e-6
-        assert np.max(np.abs(C[k] - Cex[kk])) < tol, (k, np.max(np.abs(C[k] - Cex[kk])), tol)
+    ex = np.array([Cex[kk] for kk in (0, 1, 3, 5)])
+    for k in range(4):
+        err = np.max(np.abs(C[k] - ex[k]))
+        print("closed form C[%d]: max rel %.2e" % (k, err / abs(ex[k])))
+        assert err <= 1e-5 * abs(ex[k]), (k, err)
+    full = np.broadcast_to(ex[:, None, None, None], C.shape)
+    assert dev_rel_l2(C, full) < 1e-5
     u = g.read(vefd.U)[0].astype(np.float64)
     assert np.max(np.abs(u - cf.couette_profile(32, 0.01)[None, :, None])) < 2e-7
-    sig = g.read(vefd.SIGMA_P).astype(np.float64)
-    assert abs(np.mean(sig[1]) - (-cf.shear_S(0.625, 100.0))) < 1e-4
-    assert abs(np.mean(sig[0] - sig[2]) - cf.shear_N(0.625, 100.0)) < 2e-4
+    d = g.diagnostics()
+    S, N = cf.shear_S(0.625, 100.0), cf.shear_N(0.625, 100.0)
+    assert abs(d[5] + S) < 1e-5 * S and abs(d[6] - N) < 1e-5 * N and abs(d[15] - N) < 1e-5 * N
+    assert abs(d[7] - (ex[0] + ex[2] + ex[3]) / 100.0) < 1e-5 * d[7]
 
 
 def test_guards_flag_instability():
@@ -448,6 +521,20 @@ def test_empty_step_and_errors():
         P.g.step(-1)
     with pytest.raises(ValueError):
         P.g.write(vefd.C, np.zeros(3, np.float32))
+    # densities that are not finite or are negative are refused on the
+    # device-side check, and the context must be initialised again
+    for bad in (np.nan, -0.5, np.inf):
+        rho = np.ones((1, 5, 8), np.float32)
+        rho[0, 2, 3] = bad
+        with pytest.raises(vefd.VefdError) as ei:
+            P.g.init_fields(rho)
+        assert ei.value.status == vefd.ERR_ARG
+        with pytest.raises(vefd.VefdError) as ei:
+            P.g.step(1)
+        assert ei.value.status == vefd.ERR_STATE
+    P.g.init_fields(np.ones((1, 5, 8), np.float32))
+    P.g.step(2)
+    assert P.g.status() == 0
 
 
 # --- 16-bit population storage (FP16 / BF16 deviations, FP32 arithmetic) -----
