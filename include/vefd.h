@@ -142,7 +142,11 @@ vefd_status vefd_set_conformation_update(vefd_ctx *ctx, int scheme);
  * when C0 is NULL), AB2 history cleared (the next step is forward Euler).
  * rho_A (N), rho_B (N, ignored for one component), u (dim*N or NULL for
  * rest), C0 (nc*N or NULL); host or device FP32 per on_device.
- * Also resets the step counter and the status word. */
+ * Also resets the step counter and the status word.  Each component's
+ * domain-mean density (the reference of the stored deviations) is an FP64
+ * sum on the device in a fixed order.  Densities that are not finite or are
+ * negative give VEFD_ERR_ARG and leave the context uninitialised (VEFD_ERR_STATE
+ * for stepping and reads until a valid call).  Synchronises the stream. */
 vefd_status vefd_init_fields(vefd_ctx *ctx, const float *rho_A, const float *rho_B, const float *u,
                              const float *C0, int on_device);
 /* Convenience droplet initialisation computed on the host: rho_A = rho_out +
@@ -248,7 +252,11 @@ vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *
 vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
 /* Step graph (implementation detail; the paper steps the whole lattice).
  * vefd_step runs whole chunks of `chunk` steps (even, >= 2) as a replayed
- * CUDA graph, in one of two forms.
+ * CUDA graph, and the even remainder of the call (nsteps mod chunk, rounded
+ * down to even) as one replay of a graph of that many steps, so calls of any
+ * length replay graphs.  A context keeps up to four graph sizes (the chunk
+ * and the remainders of recent calls, least recently used dropped first),
+ * each captured on first use.  The graphs take one of two forms.
  * - Pipelined slabs (slabs >= 2): the lattice is split into `slabs` slabs of
  *   NY / slabs rows.  Each slab's lattice kernel and densities/FENE-P pass is
  *   a graph node that waits only for the nodes of the neighbouring slabs it
@@ -271,10 +279,11 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * 128 x 64 x 128 droplet, against eager stepping: 8 slabs +7 to +8 %,
  * 4 slabs +5 %).  The graph is used when kernel timing is off and the
  * context stream is not being captured.  Some steps run eagerly: the Euler
- * start, steps with pending densities, the remainder of nsteps after whole
- * chunks, and one step that brings the ping-pong buffers back to the parity
- * the graph was captured at (rather than capturing the other parity).  The
- * graph is re-captured when the parameters or kernel choice change.
+ * start, steps with pending densities, the last step of an odd count, and
+ * one step that brings the ping-pong buffers back to the parity the graphs
+ * were captured at (rather than capturing the other parity; a call of fewer
+ * than three steps at the other parity steps eagerly).  The graphs are
+ * re-captured when the parameters or kernel choice change.
  * VEFD_ERR_ARG for slabs below -1 or above 64, or a bad chunk (default 256). */
 vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
 /* Captures and instantiates the step graph for the current state now, so the
@@ -284,6 +293,14 @@ vefd_status vefd_set_step_graph(vefd_ctx *ctx, int slabs, int chunk);
  * start or densities pending: take a step first).  VEFD_ERR_STATE before
  * initialisation, VEFD_ERR_CUDA on capture errors. */
 vefd_status vefd_prepare_step_graph(vefd_ctx *ctx);
+/* As vefd_prepare_step_graph, for a call of nsteps steps: captures now every
+ * graph that vefd_step(ctx, nsteps) would replay from the current state (the
+ * chunk when nsteps >= chunk, and the even remainder), so that call only
+ * replays.  Graphs held for the other ping-pong parity are dropped first.
+ * Takes no step; a no-op where the graph does not apply or the state is not
+ * steady yet.  VEFD_ERR_ARG for nsteps < 0, VEFD_ERR_STATE before
+ * initialisation, VEFD_ERR_CUDA on capture errors. */
+vefd_status vefd_prepare_steps(vefd_ctx *ctx, int64_t nsteps);
 /* The slab count in effect (0: no graph, 1: the whole-lattice form), the
  * chunk, and active = 1 when the next vefd_step would use the graph. */
 vefd_status vefd_get_step_graph(vefd_ctx *ctx, int *slabs, int *chunk, int *active);
@@ -322,7 +339,8 @@ vefd_status vefd_ensemble_step(vefd_ensemble *ens, int64_t nsteps, int64_t chunk
  * programmatic-launch setting, and each takes the staged lattice kernel and
  * the separate z-marching densities/FENE-P pass (NX % 32 == 0, NY % 8 == 0,
  * kernel config post mode 2), the members are split into up to 4 groups of
- * about equal node count (contiguous in member order), and a replayed step
+ * about equal node count (contiguous in member order; the count is set by
+ * vefd_ensemble_set_groups), and a replayed step
  * is, per group, ONE lattice-kernel launch over the 32 x 4 x 2 tiles of its
  * members and ONE densities/FENE-P launch over their 32 x 8 columns; each
  * group's launches are one graph branch, so the groups overlap.  Each block
@@ -347,6 +365,16 @@ int vefd_ensemble_is_batched(const vefd_ensemble *ens);
  * a negative segment. */
 vefd_status vefd_ensemble_set_config(vefd_ensemble *ens, int batched, int post_segment);
 vefd_status vefd_ensemble_get_config(const vefd_ensemble *ens, int *batched, int *post_segment);
+/* Group count of the batched launches (no counterpart in the paper; a
+ * launch-layout choice): 0 (the default) means 4; otherwise 1..64, clamped to
+ * the member count.  Members are split into that many contiguous groups of
+ * about equal node count, each group one graph branch of two launches per
+ * step.  Results do not depend on the group count (bit-identical).  Takes
+ * effect at the next replay (after waiting for earlier replays).
+ * VEFD_ERR_ARG for a NULL ensemble or groups outside 0..64. */
+vefd_status vefd_ensemble_set_groups(vefd_ensemble *ens, int groups);
+/* The group-count setting (0: automatic). */
+vefd_status vefd_ensemble_get_groups(const vefd_ensemble *ens, int *groups);
 /* The ensemble's own autotuner.  It times four configurations: graph branches,
  * and batched launches with the automatic z-segment, twice it and half of it.
  * Each is timed as `steps` replayed steps (after one untimed replay that
@@ -377,8 +405,10 @@ void vefd_ensemble_destroy(vefd_ensemble *ens);
  * values listed for vefd_diagnostics.  Work runs on `stream` and the call
  * synchronises it.  Lattices above 8,388,608 nodes exceed the scratch array
  * and are rejected with VEFD_ERR_ARG, as are bad sizes and NULL inputs.
- * The first call on each device looks up the scratch address with that
- * device current, so make that first call before any stream capture.  Every
+ * The first call in each CUDA context (on each device, and again after a
+ * device reset replaced the context) looks up the scratch address with that
+ * context current and caches it under the context's unique ID, so make that
+ * first call before any stream capture.  Every
  * call shares the one scratch array and rewrites every row it reads, so
  * nothing needs clearing between calls, but calls that overlap on the GPU
  * race on it. */

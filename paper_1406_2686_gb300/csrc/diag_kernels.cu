@@ -158,7 +158,56 @@ __global__ void k_diag_final(const double* __restrict__ partial, int nrows, doub
     out[k] = v;
 }
 
+// Initial densities: FP64 sums of rho_A and rho_B and the count of values
+// that are not finite or are negative, per block over a grid-stride share,
+// then summed over the rows in index order (one thread per value).
+__global__ void __launch_bounds__(256) k_density_sums(const float* __restrict__ a, const float* __restrict__ b,
+                                                      long long N, double* __restrict__ partial) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float va = a[i];
+        acc[0] += va;
+        acc[2] += (isfinite(va) && va >= 0.0f) ? 0.0 : 1.0;
+        if (b) {
+            const float vb = b[i];
+            acc[1] += vb;
+            acc[2] += (isfinite(vb) && vb >= 0.0f) ? 0.0 : 1.0;
+        }
+    }
+    __shared__ double sh[3][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = sh[threadIdx.x][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+        partial[blockIdx.x * 3 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_density_final(const double* __restrict__ partial, int nrows, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= 3) return;
+    double v = partial[k];
+    for (int r = 1; r < nrows; ++r) v += partial[r * 3 + k];
+    out[k] = v;
+}
+
 }  // namespace
+
+cudaError_t launch_density_sums(const float* rho_A, const float* rho_B, long long N, double* partial, double* out,
+                                cudaStream_t s) {
+    long long blocks = (N + 255) / 256;
+    if (blocks > kDiagBlocks) blocks = kDiagBlocks;
+    if (blocks < 1) blocks = 1;
+    k_density_sums<<<(int)blocks, 256, 0, s>>>(rho_A, rho_B, N, partial);
+    k_density_final<<<1, 32, 0, s>>>(partial, (int)blocks, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_derived(int lattice, int ncomp, int which, const StepParams& p, const float* drho,
                            const float* Ct, float* dst, cudaStream_t s) {

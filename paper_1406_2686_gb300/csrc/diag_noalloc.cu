@@ -19,6 +19,9 @@
 // threads) race on it.
 #include <cmath>
 #include <mutex>
+#include <vector>
+
+#include <cuda.h>
 
 #include "vefd.h"
 #include "vefd_internal.cuh"
@@ -29,7 +32,6 @@ namespace {
 constexpr int kNoallocRows = 4096;
 constexpr int kNodesPerBlock = 2048;
 constexpr int kThreads = 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[(kNoallocRows + 1) * kDiagVals];
 
@@ -129,24 +131,73 @@ __global__ void k_diag_rows_final(double* __restrict__ rows, int nrows) {
 }
 
 std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  The array's
-// name in host code is only a handle, so the address is looked up once per
-// device (with that device current) and cached.
+// Scratch addresses by CUDA context.  A context's ID is unique for the life
+// of the process, so a device reset (which destroys the context and, with it,
+// the module holding the array) leads to a fresh lookup in the new context
+// instead of a stale address.
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double* addr;
+};
+std::vector<ScratchEntry> g_scratch;
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+cudaError_t driver_entry_points() {
+    if (g_ctx_get_current && g_ctx_get_id) return cudaSuccess;
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || !a)
+        return cudaErrorNotSupported;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qb != cudaDriverEntryPointSuccess || !b)
+        return cudaErrorNotSupported;
+    g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(a);
+    g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(b);
+    return cudaSuccess;
+}
+
+// ID of the calling thread's current context (0 when there is none).
+unsigned long long current_ctx_id() {
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current context.  In host code
+// the array's name is only a handle, so the address is looked up with
+// cudaGetSymbolAddress, once per context (which also makes the device's
+// primary context current if no context is yet), and cached under the
+// context's ID.
 cudaError_t scratch_on_current_device(double** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    e = driver_entry_points();
+    if (e != cudaSuccess) return e;
+    unsigned long long id = current_ctx_id();
+    if (id != 0)
+        for (const ScratchEntry& s : g_scratch)
+            if (s.ctx_id == id) {
+                *out = s.addr;
+                return cudaSuccess;
+            }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    id = current_ctx_id();
+    if (id == 0) return cudaErrorInvalidValue;
+    g_scratch.push_back(ScratchEntry{id, static_cast<double*>(p)});
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 

@@ -85,9 +85,13 @@ struct vefd_ctx {
     std::vector<cudaStream_t> slab_s;      // one capture stream per slab
     std::vector<cudaEvent_t> slab_evL, slab_evP;
     cudaEvent_t slab_fork = nullptr;
-    cudaGraphExec_t slab_exec = nullptr;
-    std::vector<double> slab_key;          // state the graph was captured for
-    int slab_parity = -1;                  // population buffer parity (cur) the graph starts from
+    // replayed step graphs, keyed by their (even) step count: the main chunk of
+    // slab_chunk steps and up to kGraphSizes - 1 other sizes (the even
+    // remainders of recent calls), most recently used first.  All of them are
+    // captured from one state (slab_key) and ping-pong parity (slab_parity).
+    std::vector<std::pair<int64_t, cudaGraphExec_t>> graphs;
+    std::vector<double> slab_key;          // state the graphs were captured for
+    int slab_parity = -1;                  // population buffer parity (cur) the graphs start from
     // optional per-kernel timing of vefd_step (events on the context stream)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -459,7 +463,7 @@ vefd_status vefd_bind_device_memory(vefd_ctx* c, void* dev_ptr, size_t bytes) {
 void vefd_destroy(vefd_ctx* c) {
     if (!c) return;
     if (c->stream || c->mem) cudaStreamSynchronize(c->stream);
-    if (c->slab_exec) cudaGraphExecDestroy(c->slab_exec);
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
     for (cudaStream_t s : c->slab_s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->slab_evL) cudaEventDestroy(e);
     for (cudaEvent_t e : c->slab_evP) cudaEventDestroy(e);
@@ -546,26 +550,7 @@ vefd_status vefd_init_fields(vefd_ctx* c, const float* rho_A, const float* rho_B
     if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
     const long long N = c->N;
     const size_t plane = sizeof(float) * (size_t)N;
-    // reference densities: domain means, so that the stored deviations are small
-    std::vector<float> host;
-    for (int s = 0; s < c->cfg.ncomp; ++s) {
-        const float* src = s == 0 ? rho_A : rho_B;
-        const float* h = src;
-        if (on_device) {
-            host.resize((size_t)N);
-            VEFD_CUDA(c, cudaMemcpyAsync(host.data(), src, plane, cudaMemcpyDeviceToHost, c->stream));
-            VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
-            h = host.data();
-        }
-        double sum = 0.0;
-        for (long long i = 0; i < N; ++i) {
-            if (!std::isfinite(h[i]) || h[i] < 0.0f) return fail(c, VEFD_ERR_ARG, "densities must be finite and >= 0");
-            sum += h[i];
-        }
-        c->rho_ref[s] = (double)(float)(sum / (double)N);
-    }
-    if (c->cfg.ncomp == 1) c->rho_ref[1] = 0.0;
-    // stage the inputs in the second population buffer
+    // stage the inputs in the staging planes
     c->cur = 0;
     c->ccur = 0;
     float* st = c->dbg;
@@ -578,6 +563,19 @@ vefd_status vefd_init_fields(vefd_ctx* c, const float* rho_A, const float* rho_B
     if (c->cfg.ncomp == 2) VEFD_CUDA(c, cudaMemcpyAsync(sB, rho_B, plane, kind, c->stream));
     if (u) VEFD_CUDA(c, cudaMemcpyAsync(sU, u, plane * c->D, kind, c->stream));
     if (C0) VEFD_CUDA(c, cudaMemcpyAsync(sC, C0, plane * c->NC, kind, c->stream));
+    // reference densities: domain means (FP64 sums in a fixed order on the
+    // device), so that the stored deviations are small; the densities must be
+    // finite and non-negative
+    double sums[3];
+    VEFD_CUDA(c, launch_density_sums(sA, c->cfg.ncomp == 2 ? sB : nullptr, N, c->diag_part, c->diag_out, c->stream));
+    VEFD_CUDA(c, cudaMemcpyAsync(sums, c->diag_out, sizeof sums, cudaMemcpyDeviceToHost, c->stream));
+    VEFD_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sums[2] != 0.0) {
+        c->initialised = 0;
+        return fail(c, VEFD_ERR_ARG, "densities must be finite and >= 0");
+    }
+    c->rho_ref[0] = (double)(float)(sums[0] / (double)N);
+    c->rho_ref[1] = c->cfg.ncomp == 2 ? (double)(float)(sums[1] / (double)N) : 0.0;
     StepParams p = params_of(c);
     VEFD_CUDA(c, launch_init_equilibrium(c->cfg.lattice, c->cfg.ncomp, p, sA, sB, u ? sU : nullptr, c->f[0],
                                          c->frest, c->stream));
@@ -662,7 +660,7 @@ vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, siz
     return VEFD_OK;
 }
 
-// Captures `chunk` steps as the pipelined y-slab graph into c->slab_exec.
+// Captures `chunk` steps as the pipelined y-slab graph into *out.
 // Slab k's lattice kernel of step t waits for the densities/FENE-P passes of
 // step t - 1 on slabs k - 1, k, k + 1 (their densities, stress and velocity
 // reads border its rows, and its pushes reach theirs); slab k's pass of step
@@ -671,11 +669,11 @@ vefd_status vefd_write_field(vefd_ctx* c, vefd_field field, const void* src, siz
 // neighbour, otherwise the slabs wrap.  Same-slab order is its stream's order.
 static vefd_status step_eager(vefd_ctx* c, int64_t nsteps);
 
-// Captures `chunk` eager steps (whole-lattice launch pairs) into c->slab_exec:
+// Captures `chunk` eager steps (whole-lattice launch pairs) into *out:
 // the graph form for lattices and kernel choices the slab split does not
 // take; it saves the host-side launch cost of small lattices.  Capture only
 // records the launches, so the host state they advanced is put back.
-static vefd_status plain_capture(vefd_ctx* c, int64_t chunk) {
+static vefd_status plain_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* out) {
     if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(c, VEFD_ERR_CUDA, "cannot create the capture stream");
     const int cur = c->cur, ccur = c->ccur, hp = c->have_prev;
@@ -703,18 +701,16 @@ static vefd_status plain_capture(vefd_ctx* c, int64_t chunk) {
         cudaGetLastError();
         return st != VEFD_OK ? st : fail(c, VEFD_ERR_CUDA, "step graph capture failed: %s", cudaGetErrorString(ce2));
     }
-    const cudaError_t ce = cudaGraphInstantiate(&c->slab_exec, graph, 0);
+    const cudaError_t ce = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
-        c->slab_exec = nullptr;
+        *out = nullptr;
         return fail(c, VEFD_ERR_CUDA, "step graph instantiation failed");
     }
-    c->slab_key = state_key(c);
-    c->slab_parity = c->cur;
     return VEFD_OK;
 }
 
-static vefd_status slab_capture(vefd_ctx* c, int64_t chunk) {
+static vefd_status slab_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* out) {
     const int K = slab_count(c);
     if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(c, VEFD_ERR_CUDA, "cannot create the capture stream");
@@ -796,21 +792,78 @@ static vefd_status slab_capture(vefd_ctx* c, int64_t chunk) {
         cudaGetLastError();
         return fail(c, VEFD_ERR_CUDA, "step graph capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
     }
-    ce = cudaGraphInstantiate(&c->slab_exec, graph, 0);
+    ce = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
-        c->slab_exec = nullptr;
+        *out = nullptr;
         return fail(c, VEFD_ERR_CUDA, "step graph instantiation failed");
     }
-    c->slab_key = state_key(c);
-    c->slab_parity = c->cur;
     return VEFD_OK;
 }
 
-// The step graph for the current setting: the slab pipeline or the
-// whole-lattice form.
-static vefd_status graph_capture(vefd_ctx* c, int64_t chunk) {
-    return slab_count(c) >= 2 ? slab_capture(c, chunk) : plain_capture(c, chunk);
+// Graph sizes kept per context (the main chunk and recent remainders).
+constexpr size_t kGraphSizes = 4;
+
+// Destroys every captured step graph (after the replays in flight).
+static void drop_graphs(vefd_ctx* c) {
+    if (c->graphs.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+    c->graphs.clear();
+}
+
+// The step graph of `n` steps (n even) for the current setting and state: the
+// slab pipeline or the whole-lattice form, captured on first use.  Graphs of a
+// stale state are dropped first; beyond kGraphSizes sizes the least recently
+// used one goes.
+static vefd_status graph_get(vefd_ctx* c, int64_t n, cudaGraphExec_t* exec) {
+    const std::vector<double> key = state_key(c);
+    if (!c->graphs.empty() && (c->slab_key != key || c->slab_parity != c->cur)) drop_graphs(c);
+    for (size_t k = 0; k < c->graphs.size(); ++k)
+        if (c->graphs[k].first == n) {
+            std::rotate(c->graphs.begin(), c->graphs.begin() + k, c->graphs.begin() + k + 1);
+            *exec = c->graphs[0].second;
+            return VEFD_OK;
+        }
+    cudaGraphExec_t e = nullptr;
+    const vefd_status st = slab_count(c) >= 2 ? slab_capture(c, n, &e) : plain_capture(c, n, &e);
+    if (st != VEFD_OK) return st;
+    if (c->graphs.size() >= kGraphSizes) {
+        cudaStreamSynchronize(c->stream);  // its replays may still be in flight
+        cudaGraphExecDestroy(c->graphs.back().second);
+        c->graphs.pop_back();
+    }
+    c->graphs.insert(c->graphs.begin(), std::make_pair(n, e));
+    c->slab_key = key;
+    c->slab_parity = c->cur;
+    *exec = e;
+    // upload now (in stream order), so that the first replay only launches
+    VEFD_CUDA(c, cudaGraphUpload(e, c->stream));
+    return VEFD_OK;
+}
+
+// How vefd_step replays `nsteps` steps from the current state: `pre` eager
+// steps (the Euler start or densities pass, and one step that brings the
+// ping-pong parity back to the captured graphs'), `full` replays of the main
+// chunk, one replay of the even remainder `part`, then eager steps for the
+// rest (none or one).  Graphs are used only where the step graph applies.
+static void step_plan(const vefd_ctx* c, int64_t nsteps, int64_t* pre, int64_t* full, int64_t* part) {
+    *pre = *full = *part = 0;
+    if (nsteps <= 0) return;
+    if (!steady_state(c)) {
+        *pre = 1;
+        --nsteps;
+    }
+    // graphs replay from one parity; realign with one eager step when that
+    // still leaves a graph's worth of steps, otherwise step eagerly
+    const int parity = c->cur ^ (int)(*pre & 1);
+    if (!c->graphs.empty() && parity != c->slab_parity) {
+        if (nsteps < 3) return;
+        ++*pre;
+        --nsteps;
+    }
+    *full = nsteps / c->slab_chunk;
+    *part = (nsteps % c->slab_chunk) & ~(int64_t)1;
 }
 
 vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
@@ -818,34 +871,27 @@ vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
     if (st != VEFD_OK) return st;
     if (nsteps < 0) return fail(c, VEFD_ERR_ARG, "nsteps must be >= 0");
     if (nsteps > 0 && slab_usable(c)) {
-        if (!steady_state(c)) {
-            st = step_eager(c, 1);
+        int64_t pre, full, part;
+        step_plan(c, nsteps, &pre, &full, &part);
+        if (pre > 0) {
+            st = step_eager(c, pre);
             if (st != VEFD_OK) return st;
-            nsteps -= 1;
+            nsteps -= pre;
         }
-        // a captured graph replays from one ping-pong parity: one eager step
-        // brings the state back to it instead of capturing the other parity
-        if (c->slab_exec && nsteps > c->slab_chunk && c->cur != c->slab_parity) {
-            st = step_eager(c, 1);
-            if (st != VEFD_OK) return st;
-            nsteps -= 1;
-        }
-        const int64_t chunk = c->slab_chunk, full = nsteps / chunk;
+        cudaGraphExec_t exec = nullptr;
         if (full > 0) {
-            if (!c->slab_exec || c->slab_key != state_key(c)) {
-                if (c->slab_exec) {
-                    cudaStreamSynchronize(c->stream);  // earlier replays may still be in flight
-                    cudaGraphExecDestroy(c->slab_exec);
-                    c->slab_exec = nullptr;
-                }
-                st = graph_capture(c, chunk);
-                if (st != VEFD_OK) return st;
-            }
-            for (int64_t r = 0; r < full; ++r) VEFD_CUDA(c, cudaGraphLaunch(c->slab_exec, c->stream));
-            // an even chunk leaves every ping-pong parity where it was
-            c->steps += full * chunk;
-            nsteps -= full * chunk;
+            st = graph_get(c, c->slab_chunk, &exec);
+            if (st != VEFD_OK) return st;
+            for (int64_t r = 0; r < full; ++r) VEFD_CUDA(c, cudaGraphLaunch(exec, c->stream));
         }
+        if (part > 0) {
+            st = graph_get(c, part, &exec);
+            if (st != VEFD_OK) return st;
+            VEFD_CUDA(c, cudaGraphLaunch(exec, c->stream));
+        }
+        // even step counts leave every ping-pong parity where it was
+        c->steps += full * c->slab_chunk + part;
+        nsteps -= full * c->slab_chunk + part;
     }
     return step_eager(c, nsteps);
 }
@@ -1045,11 +1091,7 @@ vefd_status vefd_clear_status(vefd_ctx* c) {
 vefd_status vefd_set_step_graph(vefd_ctx* c, int slabs, int chunk) {
     if (!c || slabs < -1 || slabs > 64 || chunk < 2 || (chunk & 1)) return VEFD_ERR_ARG;
     if (c->slabs != slabs || c->slab_chunk != chunk) {
-        if (c->slab_exec) {
-            cudaStreamSynchronize(c->stream);
-            cudaGraphExecDestroy(c->slab_exec);
-            c->slab_exec = nullptr;
-        }
+        drop_graphs(c);
         c->slabs = slabs;
         c->slab_chunk = chunk;
     }
@@ -1060,13 +1102,24 @@ vefd_status vefd_prepare_step_graph(vefd_ctx* c) {
     vefd_status st = need_ready(c);
     if (st != VEFD_OK) return st;
     if (!slab_usable(c) || !steady_state(c)) return VEFD_OK;
-    if (c->slab_exec && c->slab_key == state_key(c)) return VEFD_OK;
-    if (c->slab_exec) {
-        cudaStreamSynchronize(c->stream);
-        cudaGraphExecDestroy(c->slab_exec);
-        c->slab_exec = nullptr;
-    }
-    return graph_capture(c, c->slab_chunk);
+    cudaGraphExec_t exec = nullptr;
+    return graph_get(c, c->slab_chunk, &exec);
+}
+
+vefd_status vefd_prepare_steps(vefd_ctx* c, int64_t nsteps) {
+    vefd_status st = need_ready(c);
+    if (st != VEFD_OK) return st;
+    if (nsteps < 0) return fail(c, VEFD_ERR_ARG, "nsteps must be >= 0");
+    if (!slab_usable(c) || !steady_state(c)) return VEFD_OK;
+    // graphs of the other ping-pong parity would cost the call an eager
+    // realigning step: capture at this parity instead
+    if (!c->graphs.empty() && c->slab_parity != c->cur) drop_graphs(c);
+    int64_t pre, full, part;
+    step_plan(c, nsteps, &pre, &full, &part);
+    cudaGraphExec_t exec = nullptr;
+    if (full > 0) st = graph_get(c, c->slab_chunk, &exec);
+    if (st == VEFD_OK && part > 0) st = graph_get(c, part, &exec);
+    return st;
 }
 
 vefd_status vefd_get_step_graph(vefd_ctx* c, int* slabs, int* chunk, int* active) {
@@ -1425,7 +1478,6 @@ vefd_status ens_build_table(vefd_ensemble* e) {
     e->start.assign(2 * n, 0);
     // groups: contiguous members, split at equal shares of the total nodes
     int G = e->groups > 0 ? e->groups : 4;
-    if (const char* env = getenv("VEFD_ENS_GROUPS")) G = atoi(env) > 0 ? atoi(env) : G;
     G = std::max(1, std::min(G, (int)n));
     long long total = 0;
     for (const vefd_ctx* m : e->members) total += m->N;
@@ -1548,6 +1600,8 @@ vefd_status ens_capture_batched(vefd_ensemble* e, int64_t chunk) {
         return ens_fail(e, VEFD_ERR_CUDA, "graph instantiation failed");
     }
     e->batched = true;
+    // upload now (in stream order), so that the first replay only launches
+    if (cudaGraphUpload(e->exec, e->main) != cudaSuccess) return ens_fail(e, VEFD_ERR_CUDA, "graph upload failed");
     return VEFD_OK;
 }
 
@@ -1660,6 +1714,8 @@ vefd_status ens_capture(vefd_ensemble* e, int64_t chunk) {
         return ens_fail(e, VEFD_ERR_CUDA, "graph instantiation failed");
     }
     e->batched = false;
+    // upload now (in stream order), so that the first replay only launches
+    if (cudaGraphUpload(e->exec, e->main) != cudaSuccess) return ens_fail(e, VEFD_ERR_CUDA, "graph upload failed");
     return VEFD_OK;
 }
 
@@ -1773,6 +1829,26 @@ vefd_status vefd_ensemble_get_config(const vefd_ensemble* e, int* batched, int* 
     if (!e || !batched || !post_segment) return VEFD_ERR_ARG;
     *batched = e->batched_pref;
     *post_segment = e->post_seg;
+    return VEFD_OK;
+}
+
+vefd_status vefd_ensemble_set_groups(vefd_ensemble* e, int groups) {
+    if (!e || groups < 0 || groups > 64) return VEFD_ERR_ARG;
+    if (e->groups != groups) {
+        // the next replay re-captures; earlier replays may still be in flight
+        if (e->exec) {
+            cudaStreamSynchronize(e->main);
+            cudaGraphExecDestroy(e->exec);
+        }
+        e->exec = nullptr;
+        e->groups = groups;
+    }
+    return VEFD_OK;
+}
+
+vefd_status vefd_ensemble_get_groups(const vefd_ensemble* e, int* groups) {
+    if (!e || !groups) return VEFD_ERR_ARG;
+    *groups = e->groups;
     return VEFD_OK;
 }
 

@@ -421,6 +421,10 @@ cudaError_t launch_derived(int lattice, int ncomp, int which, const StepParams& 
 
 // Diagnostics: per-block FP64 partials then a fixed-order final reduction.
 constexpr int kDiagSums = 15, kDiagMax = 2, kDiagVals = kDiagSums + kDiagMax;
+// out[0..2] = FP64 sums of rho_A and rho_B (rho_B may be NULL) and the count of
+// values that are not finite or negative; partial holds kDiagBlocks x 3 doubles.
+cudaError_t launch_density_sums(const float* rho_A, const float* rho_B, long long N, double* partial, double* out,
+                                cudaStream_t s);
 constexpr int kDiagBlocks = 608;  // 4 x 152 SMs
 cudaError_t launch_diagnostics(int lattice, int ncomp, const StepParams& p, const float* drho, const float* u,
                                const float* Ct, double* partial, double* out, cudaStream_t s);

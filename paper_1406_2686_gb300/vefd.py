@@ -46,6 +46,7 @@ EXPORTS = [
     "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_set_config",
     "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_set_step_graph", "vefd_get_step_graph",
     "vefd_prepare_step_graph", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
+    "vefd_prepare_steps", "vefd_ensemble_set_groups", "vefd_ensemble_get_groups"
 ]
 
 _lib = None
@@ -107,6 +108,9 @@ def load(build_if_missing=True):
         "vefd_ensemble_autotune": [vp, i64, i64, ctypes.POINTER(dbl)],
         "vefd_set_step_graph": [vp, cint, cint],
         "vefd_prepare_step_graph": [vp],
+        "vefd_prepare_steps": [vp, i64],
+        "vefd_ensemble_set_groups": [vp, cint],
+        "vefd_ensemble_get_groups": [vp, ctypes.POINTER(cint)],
         "vefd_get_step_graph": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)],
     }
     for name, args in sigs.items():
@@ -226,6 +230,10 @@ def vefd_prepare_step_graph(ctx):
     return _check(ctx, load().vefd_prepare_step_graph(ctx))
 
 
+def vefd_prepare_steps(ctx, nsteps):
+    return _check(ctx, load().vefd_prepare_steps(ctx, int(nsteps)))
+
+
 def vefd_get_step_graph(ctx):
     s, c, a = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(ctx, load().vefd_get_step_graph(ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(a)))
@@ -343,6 +351,16 @@ def vefd_ensemble_get_config(ens):
     b, z = ctypes.c_int(), ctypes.c_int()
     _ens_check(ens, load().vefd_ensemble_get_config(ens, ctypes.byref(b), ctypes.byref(z)))
     return b.value, z.value
+
+
+def vefd_ensemble_set_groups(ens, groups):
+    return _ens_check(ens, load().vefd_ensemble_set_groups(ens, int(groups)))
+
+
+def vefd_ensemble_get_groups(ens):
+    g = ctypes.c_int()
+    _ens_check(ens, load().vefd_ensemble_get_groups(ens, ctypes.byref(g)))
+    return g.value
 
 
 def vefd_ensemble_autotune(ens, steps=64, chunk=32):
@@ -488,6 +506,10 @@ class Lattice:
         step call only replays it."""
         vefd_prepare_step_graph(self.ctx)
 
+    def prepare_steps(self, nsteps):
+        """Capture every graph a later step(nsteps) call replays (no step taken)."""
+        vefd_prepare_steps(self.ctx, nsteps)
+
     @property
     def step_graph(self):
         """(slabs, chunk, active)."""
@@ -561,6 +583,14 @@ class Ensemble:
     def config(self):
         """(batched, post z-segment) requested for the replays."""
         return vefd_ensemble_get_config(self.ens)
+
+    def set_groups(self, groups):
+        """Group count of the batched launches (0: automatic, 4)."""
+        vefd_ensemble_set_groups(self.ens, groups)
+
+    @property
+    def groups(self):
+        return vefd_ensemble_get_groups(self.ens)
 
     def autotune(self, steps=64, chunk=32):
         """Times graph branches and batched launches with three z-segments,

@@ -117,16 +117,21 @@ def test_step_graph_and_ensemble_argument_checks(lib):
         for slabs in (-1, 0, 1, 2, 8):
             assert lib.vefd_set_step_graph(ctx, slabs, 64) == vefd.OK
         assert lib.vefd_prepare_step_graph(ctx) == vefd.ERR_STATE  # nothing bound
+        assert lib.vefd_prepare_steps(ctx, 20) == vefd.ERR_STATE
         assert lib.vefd_wait_selftest(ctx, 2) == vefd.ERR_ARG
         assert lib.vefd_wait_selftest(ctx, 0) == vefd.ERR_STATE
     finally:
         vefd.vefd_destroy(ctx)
     assert lib.vefd_set_step_graph(None, 8, 64) == vefd.ERR_ARG
     assert lib.vefd_prepare_step_graph(None) == vefd.ERR_ARG
+    assert lib.vefd_prepare_steps(None, 20) == vefd.ERR_ARG
     assert lib.vefd_ensemble_set_batched(None, 1) == vefd.ERR_ARG
     assert lib.vefd_ensemble_set_config(None, 1, 0) == vefd.ERR_ARG
     assert lib.vefd_ensemble_autotune(None, 64, 32, None) == vefd.ERR_ARG
     assert lib.vefd_ensemble_is_batched(None) == 0
+    assert lib.vefd_ensemble_set_groups(None, 2) == vefd.ERR_ARG
+    g = ctypes.c_int()
+    assert lib.vefd_ensemble_get_groups(None, ctypes.byref(g)) == vefd.ERR_ARG
     b, z = ctypes.c_int(), ctypes.c_int()
     assert lib.vefd_ensemble_get_config(None, ctypes.byref(b), ctypes.byref(z)) == vefd.ERR_ARG
 
@@ -140,3 +145,43 @@ def test_d2q9_field_sizes(lib):
         assert vefd.vefd_field_bytes(ctx, vefd.C) == 4 * 4 * 48
     finally:
         vefd.vefd_destroy(ctx)
+
+
+_NOALLOC_ARGS = r"""
+import ctypes, sys
+sys.path.insert(0, %r)
+from paper_1406_2686_gb300 import vefd
+lib = vefd.load(build_if_missing=False)
+out = (ctypes.c_double * 16)()
+p = ctypes.c_void_p(256)  # never dereferenced: every case is refused on the host
+cases = [
+    (1, 257, 128, 256, 2, 100.0, p, p, p, p),  # one x-row beyond the 8,388,608-node scratch capacity
+    (1, 4096, 4096, 4096, 2, 100.0, p, p, p, p),
+    (0, 8, 8, 2, 1, 100.0, p, None, p, p),     # D2Q9 needs nz == 1
+    (1, 8, 8, 8, 2, 100.0, p, None, p, p),     # two components need rho_B
+    (1, 8, 8, 8, 1, 2.0, p, None, p, p),       # L^2 must exceed 3
+    (2, 8, 8, 8, 1, 100.0, p, None, p, p),     # unknown lattice
+    (1, 0, 8, 8, 1, 100.0, p, None, p, p),     # empty lattice
+    (1, 8, 8, 8, 3, 100.0, p, p, p, p),        # three components
+    (1, 8, 8, 8, 1, 100.0, None, None, p, p),  # NULL input
+]
+print(",".join(str(lib.vefd_diagnostics_noalloc(*c, None, out)) for c in cases))
+print(lib.vefd_diagnostics_noalloc(1, 8, 8, 8, 1, 100.0, p, None, p, p, None, None))
+"""
+
+
+def test_noalloc_argument_checks_without_a_device(lib):
+    """The allocation-free diagnostics refuse bad sizes, the oversize lattice
+    and NULL inputs on the host, before any CUDA call: run with no visible
+    device, so that a check that let a case through would answer
+    VEFD_ERR_CUDA (no device) rather than launch on placeholder pointers."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", _NOALLOC_ARGS % root], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    codes, null_out = r.stdout.split()
+    assert codes.split(",") == [str(vefd.ERR_ARG)] * 9, codes
+    assert int(null_out) == vefd.ERR_ARG

@@ -234,6 +234,36 @@ def test_batched_ensemble_matches_single_lattices():
         assert a.status() == 0
 
 
+@pytest.mark.parametrize("groups", [1, 2, 4, 9])
+def test_batched_ensemble_group_counts_bit_identical(groups):
+    """The group count only changes which graph branch a member's tiles are
+    launched in: 1, 2, 4 and more groups than members (clamped to one member
+    per group) give the default count's bits, and the same state as each box
+    stepped alone to FP32 rounding."""
+    from paper_1406_2686_gb300 import vefd
+    ref = [make(b, seed=60 + i) for i, b in enumerate(BATCH_BOXES)]
+    got = [make(b, seed=60 + i) for i, b in enumerate(BATCH_BOXES)]
+    alone = [make(b, seed=60 + i) for i, b in enumerate(BATCH_BOXES)]
+    R, G = vefd.Ensemble(ref), vefd.Ensemble(got)
+    assert R.groups == 0
+    G.set_groups(groups)
+    assert G.groups == groups
+    for n in (23, 1, 16):
+        R.step(n, chunk=4)
+        G.step(n, chunk=4)
+        for L in alone:
+            L.step(n)
+    assert G.batched and R.batched
+    for a, b, c in zip(got, ref, alone):
+        assert same(a, b)
+        assert close_state(a, c)
+    with pytest.raises(vefd.VefdError) as ei:
+        G.set_groups(65)
+    assert ei.value.status == vefd.ERR_ARG
+    R.close()
+    G.close()
+
+
 @pytest.mark.parametrize("variant", ["fp16", "mrt_chol", "one_component"])
 def test_batched_ensemble_variants(variant):
     """The batched kernels for 16-bit storage, the moment-space collision with
@@ -357,7 +387,8 @@ def test_step_graph_bit_identical(case):
     """The pipelined y-slab step graph (each slab's lattice kernel and
     densities/FENE-P pass a node waiting only for its neighbouring slabs) runs
     the eager step's kernels on row ranges: bit-identical results, across the
-    Euler start, replays of both parities and eager remainders."""
+    Euler start, replays of both parities, remainder graphs of many sizes
+    (more than the four a context keeps) and odd last steps."""
     from paper_1406_2686_gb300 import vefd
     box = {"walls": dict(BATCH_BOXES[0], ny=32),
            "periodic": dict(BATCH_BOXES[1], ny=16, nz=6),
@@ -368,15 +399,19 @@ def test_step_graph_bit_identical(case):
         R = make(box, seed=71)
         R.set_step_graph(0)                # eager launch pairs
         assert R.step_graph[2] is False
-        G.set_step_graph(slabs, 4)
-        assert G.step_graph == (slabs, 4, True)
-        for n in (11, 1, 8, 5, 9):
+        G.set_step_graph(slabs, 8)
+        assert G.step_graph == (slabs, 8, True)
+        calls = (11, 1, 8, 5, 9, 20, 2, 3, 6, 14, 7, 22)
+        for k, n in enumerate(calls):
             G.step(n)
             R.step(n)
             assert same(G, R), (slabs, n)
-            G.prepare_step_graph()         # captures (or keeps) the graph, takes no step
+            if k % 2:
+                G.prepare_step_graph()     # captures (or keeps) the graph, takes no step
+            else:
+                G.prepare_steps(calls[(k + 1) % len(calls)])
             assert same(G, R)
-        assert G.status() == 0 and G.steps_done == 34
+        assert G.status() == 0 and G.steps_done == sum(calls)
         G.set_wall_shear(0.005)            # a parameter change re-captures
         R.set_wall_shear(0.005)
         G.step(8)
@@ -416,9 +451,9 @@ def test_whole_lattice_graph_bit_identical(k, config):
     R.set_step_graph(0)
     G.set_step_graph(1, 4)
     assert G.step_graph == (1, 4, True)
-    for n in (11, 1, 8, 5, 9):
+    for n in (11, 1, 8, 5, 9, 2, 6, 3):
         G.step(n)
         R.step(n)
         assert same(G, R), (n, G.kernel_config())
-    assert G.status() == 0 and G.steps_done == 34
+    assert G.status() == 0 and G.steps_done == 45
 

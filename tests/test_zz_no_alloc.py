@@ -59,18 +59,30 @@ def test_noalloc_diagnostics_match_context(lattice):
     lat.close()
 
 
-def test_noalloc_rejects_oversize_and_bad_args():
+@pytest.mark.slow
+def test_noalloc_at_capacity():
+    """Exactly at the documented capacity, 256 x 128 x 256 = 8,388,608 nodes
+    (4096 reduction blocks: every partial row of the scratch array is used
+    and the result row follows the last one), two calls in a row agree with
+    the context's own diagnostics of the same state."""
+    import torch
+
     from paper_1406_2686_gb300 import vefd
 
-    lib = vefd.load()
-    out = (vefd.ctypes.c_double * 16)()
-    dummy = vefd.ctypes.c_void_p(256)
-    # 8,388,608 nodes is the scratch capacity; one more row of x is refused before any launch
-    st = lib.vefd_diagnostics_noalloc(1, 257, 128, 256, 2, 100.0, dummy, dummy, dummy, dummy, None, out)
-    assert st == vefd.ERR_ARG
-    st = lib.vefd_diagnostics_noalloc(0, 8, 8, 2, 1, 100.0, dummy, None, dummy, dummy, None, out)
-    assert st == vefd.ERR_ARG
-    st = lib.vefd_diagnostics_noalloc(1, 8, 8, 8, 2, 100.0, dummy, None, dummy, dummy, None, out)
-    assert st == vefd.ERR_ARG
-    st = lib.vefd_diagnostics_noalloc(1, 8, 8, 8, 1, 2.0, dummy, None, dummy, dummy, None, out)
-    assert st == vefd.ERR_ARG
+    nx, ny, nz = 256, 128, 256
+    L2 = 100.0
+    lat = vefd.Lattice(lattice=vefd.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=0.21, eta_B=0.35)
+    lat.set_wall_shear(0.02)
+    lat.set_fenep(100.0, 0.14, L2, 1e-3, 1, 1)
+    lat.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, 32.0, 2.0, 0.1, 5.0, 5, 1e-3)
+    stream = lat.stream.cuda_stream
+    for call in range(2):
+        lat.step(4)
+        ref = lat.diagnostics()
+        f = _fields(lat, vefd)
+        torch.cuda.synchronize()
+        got = vefd.vefd_diagnostics_noalloc(1, nx, ny, nz, 2, L2, f[vefd.RHO_A].data_ptr(), f[vefd.RHO_B].data_ptr(),
+                                            f[vefd.U].data_ptr(), f[vefd.C].data_ptr(), stream)
+        _compare(ref, got)
+        del f
+    lat.close()
