@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel tiles")
     ap.add_argument("--step-graph", type=int, default=-1,
                     help="slabs of the pipelined step graph (-1 automatic, 0 eager launch pairs)")
+    ap.add_argument("--kernel-config", default="",
+                    help="lattice_tile,post_mode kernel choice for the timed lattice (default: the library default)")
     ap.add_argument("--profile-region", action="store_true",
                     help="only run --warmup steps, prepare the graphs of --steps steps and bracket that one call "
                          "with cudaProfilerStart/Stop (for ncu --profile-from-start off); prints no JSON line")
@@ -293,10 +295,12 @@ def replica_throughput(elapsed_ms, nodes_per_rank, steps, device="cpu"):
     return ms, nodes_per_rank * steps * world / (ms / 1e3) / 1e6
 
 
-def time_variant(S, steps, warmup, model=None):
-    """MLUPS of one storage or model variant on the same workload (events on the library stream)."""
+def time_variant(S, steps, warmup, model=None, kernel_config=None):
+    """MLUPS of one storage, model or kernel-choice variant on the same workload (events on the library stream)."""
     import torch
     lat = make_lattice(S, model)
+    if kernel_config is not None:
+        lat.set_kernel_config(*kernel_config)
     lat.step(warmup)
     lat.prepare_steps(steps)
     torch.cuda.synchronize()
@@ -310,7 +314,8 @@ def time_variant(S, steps, warmup, model=None):
     bw = S.step_bytes * S.N / (ms / steps / 1e3) / 1e9
     out = {"value": round(S.N * steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "ms_per_step": round(ms / steps, 5),
            "step_roofline": {"achieved": round(bw, 1), "frac": round(bw / peak, 4),
-                             "algorithmic_bytes_per_node": S.step_bytes}, "status_bits": lat.status()}
+                             "algorithmic_bytes_per_node": S.step_bytes}, "status_bits": lat.status(),
+           "kernel_config": list(lat.kernel_config()), "step_graph": list(lat.step_graph)}
     lat.close()
     return out
 
@@ -494,6 +499,8 @@ def run_ours(args):
     NX, NY, NZ = S.NX, S.NY, S.NZ
     lat = make_lattice(S)
     lat.set_step_graph(args.step_graph)
+    if args.kernel_config:
+        lat.set_kernel_config(*[int(v) for v in args.kernel_config.split(",")])
     stream = lat.stream
     K, W = args.steps, args.warmup
     tune = None
@@ -591,6 +598,8 @@ def run_ours(args):
         line["variants"] = {pn: time_variant(Setup(S.name, pn), vsteps, min(W, 50)) for pn in ("fp16", "bf16")}
         for name, model in (("mrt", dict(collision=1)), ("cholesky", dict(chol=1)), ("paper_sec2", PAPER_MODEL)):
             line["variants"][name] = time_variant(S, vsteps, min(W, 50), model)
+        # the column-marching lattice kernel with partial densities (post mode 0)
+        line["variants"]["fused_densities"] = time_variant(S, vsteps, min(W, 50), kernel_config=(0, 0))
         line["variants"]["d2q9_couette"] = time_d2q9_couette()
         line["variants"]["note"] = ("fp16/bf16: 16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
                                     "and C; mrt: moment-space collision with the paper's relaxation times; cholesky: "

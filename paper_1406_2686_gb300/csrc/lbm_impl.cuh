@@ -804,68 +804,81 @@ cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const St
 }
 
 // Column-marching form (D3Q19, NX % 32 == 0, NY % 8 == 0) that also yields
-// the densities of the new populations, so the densities pass does not read
-// them again.  A block owns a 32 x 8 column and walks the planes [z0, z1) of
-// its z-segment; per plane:
-//   1. one TMA copy stages the plane's moving populations f^n (box 32 x 8 x 1
-//      x P) while the threads gather neighbour densities and feedback stress;
-//   2. each thread collides its node and writes the values leaving the node
-//      back into its own staging slots (bounced ones with the wall term);
-//      values bound for another column or segment are stored straight to
-//      their destination nodes in global memory;
-//   3. after a barrier each thread pulls, for its own (x, y), the values
-//      arriving from inside the column: at (x, y, z + c_z) from
-//      (x - c_x, y - c_y, z), and bounce-backs at (x, y, z); it stores them
-//      (aligned, coalesced rows) and adds them, with the rest population, to
-//      partial densities of planes z - 1, z, z + 1 in a fixed order;
-//   4. plane z - 1 has then received everything from inside the segment and
-//      its partial density is written to b.drho_next.
-template <class PT, int NCOMP, int COLL>
-__global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
-    k_lattice_zm(const __grid_constant__ CUtensorMap tm_fin, StepBufs b, StepParams p, int zs, int rev) {
+// partial densities of the new populations, so that the densities pass reads
+// back only the populations that crossed a column side or a segment end.  A
+// block owns a 32 x 8 column and walks the planes [z0, z1) of its z-segment;
+// per plane:
+//   1. the plane's moving populations f^n arrive by one bulk tensor copy (box
+//      32 x 8 x 1 x P) into one of two staging buffers; the copy of the next
+//      plane is issued at the start of the iteration, so it overlaps this
+//      plane's work;
+//   2. each thread gathers neighbour densities and feedback stress, collides
+//      its node and pushes every value to its destination in global memory
+//      exactly as the tiled kernel does (bounced ones to its own node), and
+//      also writes each value into its own staging slot, whose pre-collision
+//      content it has consumed;
+//   3. after a barrier each thread adds, in a fixed direction order, the
+//      values arriving at its (x, y) from inside the column (from the slots of
+//      their source threads; bounced ones from its own slots) to partial
+//      densities of planes z - 1, z, z + 1 when that plane lies in the segment;
+//   4. plane z - 1 has then received everything from inside the column and
+//      segment, and its partial density goes to b.drho_next.
+// The densities pass adds the populations that crossed a column side or a
+// segment end, reading them from the new population buffer.
+template <class PT, int NCOMP, int COLL, bool EDGE>
+__device__ __forceinline__ void lattice_column(const CUtensorMap* tm_fin, const StepBufs& b, const StepParams& p,
+                                               int x0, int y0, int z0, int z1) {
     using L = D3Q19;
     constexpr int P = NCOMP * (L::Q - 1);
     constexpr int T = 256;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
     extern __shared__ __align__(128) unsigned char sraw[];
-    PT* sP = reinterpret_cast<PT*>(sraw);  // [P][8][32]: f^n of the plane, then the values leaving each node
-    __shared__ __align__(8) unsigned long long bar;
+    PT* sbuf = reinterpret_cast<PT*>(sraw);  // two buffers of [P][8][32]
+    __shared__ __align__(8) unsigned long long bars[2];
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-    const int nx = p.nx, ny = p.ny, nz = p.nz, N = (int)p.N;
-    const int x0 = tile_index(blockIdx.x, gridDim.x, rev) * 32;
-    const int y0 = tile_index(blockIdx.y, gridDim.y, rev) * 8;
-    const int z0 = tile_index(blockIdx.z, gridDim.z, rev) * zs;
-    const int z1 = min(z0 + zs, nz);
+    const int nx = p.nx, ny = p.ny, nz = p.nz, N = (int)p.N, plane = nx * ny;
     const int x = x0 + tx, y = y0 + ty;
     const bool leader = t == 0;
-    const unsigned bar_a = smem_u32(&bar);
-    if (leader) mbar_init(bar_a);
+    const unsigned bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+    if (leader) {
+        mbar_init(bar0);
+        mbar_init(bar1);
+    }
     __syncthreads();
+    const int nplanes = z1 - z0;
+    if (leader && nplanes > 0) tma_load_4d(smem_u32(sbuf), tm_fin, x0, y0, z0, 0, bar0, kBytes);
     const ColumnTopo topo{nx == 32, ny == 8 && !p.walls, nz == 1};
-    const bool wall_lo = p.walls && y == 0, wall_hi = p.walls && y == ny - 1;
-    PT* fout = static_cast<PT*>(b.fout);
+    const bool wall_lo = EDGE && p.walls && y == 0, wall_hi = EDGE && p.walls && y == ny - 1;
+    // streaming offsets in y are periodic (walls are handled by bounce-back)
+    int oy[3];
+    oy[0] = (EDGE && y == 0 ? ny - 1 : -1) * nx;
+    oy[1] = 0;
+    oy[2] = (EDGE && y == ny - 1 ? 1 - ny : 1) * nx;
+    PT* const fout = static_cast<PT*>(b.fout);
     float pm[NCOMP], pc[NCOMP], pn[NCOMP];  // partial densities of planes z - 1, z, z + 1
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) pm[s] = pc[s] = pn[s] = 0.0f;
-    for (int k = 0; k < z1 - z0; ++k) {
-        const int z = z0 + k;
-        if (leader) {
-            // every thread released the buffer at the barrier ending the previous plane
+    for (int k = 0; k < nplanes; ++k) {
+        const int z = z0 + k, slot = k & 1;
+        PT* const sP = sbuf + slot * P * T;
+        if (leader && k + 1 < nplanes) {
+            // the other buffer was released by every thread at the barrier ending the previous plane
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_load_4d(smem_u32(sP), &tm_fin, x0, y0, z, 0, bar_a, kBytes);
+            tma_load_4d(smem_u32(sbuf + (slot ^ 1) * P * T), tm_fin, x0, y0, z + 1, 0, slot ? bar0 : bar1, kBytes);
         }
         NodeGather<L, NCOMP> g;
         node_gather<L, NCOMP>(b, p, x, y, z, true, g);
-        const bool ok = mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));
+        const bool ok = mbar_wait_bounded_parity(slot ? bar1 : bar0, (unsigned)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (leader) {
                 atomicOr(b.status, kStTimeout);
-                mbar_wait_bounded_parity(bar_a, (unsigned)(k & 1));  // bounded: let the copy land before leaving
+                // let the copies this block still has in flight land (bounded) before leaving
+                mbar_wait_bounded_parity(slot ? bar1 : bar0, (unsigned)((k >> 1) & 1));
+                if (k + 1 < nplanes) mbar_wait_bounded_parity(slot ? bar0 : bar1, (unsigned)(((k + 1) >> 1) & 1));
             }
             return;
         }
         const int node = g.nb.i;
-        // moments of the staged populations (second moments for the moment-space collision)
         float jx = 0.0f, jy = 0.0f, jz = 0.0f;
         float pif[NCOMP][6];
 #pragma unroll
@@ -886,24 +899,23 @@ __global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
         b.u[node] = st.ux;
         b.u[N + node] = st.uy;
         b.u[2 * N + node] = st.uz;
+        const int* ox = g.nb.ox;
+        const int* oz = g.nb.oz;
         float rest[NCOMP];
         collide_emit<PT, L, NCOMP, COLL>(
             p, st, g.qloc, pif, wall_lo, wall_hi,
             [&](int s, int a) { return pop_smem(sP, (s * (L::Q - 1) + a - 1) * T + t); },
             [&](int s, int a, PT va, PT vb, bool ba, bool bb) {
+                PT* out = fout + (long long)s * (L::Q - 1) * N - N;
                 const int ab = a + 1;
                 const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+                if (ba) out[ab * N + node] = va;
+                else out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = va;
+                if (bb) out[a * N + node] = vb;
+                else out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
                 // this thread's own slots: its reads of them are done
                 sP[(s * (L::Q - 1) + a - 1) * T + t] = va;
                 sP[(s * (L::Q - 1) + ab - 1) * T + t] = vb;
-                if (!ba && !zm_inner(tx + cx, ty + cy, z + cz, z0, z1, topo)) {
-                    const int xd = wrap1(x + cx, nx), yd = wrap1(y + cy, ny), zd = wrap1(z + cz, nz);
-                    fout[(long long)(s * (L::Q - 1) + a - 1) * N + (zd * ny + yd) * nx + xd] = va;
-                }
-                if (!bb && !zm_inner(tx - cx, ty - cy, z - cz, z0, z1, topo)) {
-                    const int xd = wrap1(x - cx, nx), yd = wrap1(y - cy, ny), zd = wrap1(z - cz, nz);
-                    fout[(long long)(s * (L::Q - 1) + ab - 1) * N + (zd * ny + yd) * nx + xd] = vb;
-                }
             },
             rest);
         // the rest population stays at the node, in FP32, updated in place
@@ -913,45 +925,51 @@ __global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
             pc[s] += rest[s];
         }
         __syncthreads();
-        // values arriving at this (x, y) from inside the column and segment
+        // values arriving at this (x, y) from inside the column, in direction order
 #pragma unroll
         for (int s = 0; s < NCOMP; ++s) {
 #pragma unroll
             for (int a = 1; a < L::Q; ++a) {
                 const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
-                const long long plane_a = (long long)(s * (L::Q - 1) + a - 1) * N;
-                if ((cy > 0 && wall_lo) || (cy < 0 && wall_hi)) {
+                if (EDGE && ((cy > 0 && wall_lo) || (cy < 0 && wall_hi))) {
                     // the opposite population left through the wall and came back
-                    const PT v = sP[(s * (L::Q - 1) + opposite(a) - 1) * T + t];
-                    fout[plane_a + node] = v;
-                    pc[s] += pop_get(v);
+                    pc[s] += pop_get(sP[(s * (L::Q - 1) + opposite(a) - 1) * T + t]);
                 } else if (zm_inner(tx - cx, ty - cy, z + cz, z0, z1, topo)) {
                     const int src = ((ty - cy) & 7) * 32 + ((tx - cx) & 31);
-                    const PT v = sP[(s * (L::Q - 1) + a - 1) * T + src];
-                    const int zd = topo.nz1 ? z : z + cz;
-                    fout[plane_a + (zd * ny + y) * nx + x] = v;
-                    const float fv = pop_get(v);
+                    const float fv = pop_get(sP[(s * (L::Q - 1) + a - 1) * T + src]);
                     if (cz == 0 || topo.nz1) pc[s] += fv;
                     else if (cz < 0) pm[s] += fv;
                     else pn[s] += fv;
                 }
             }
         }
-        // plane z - 1 is complete within the segment
-        if (k > 0) dens_store<NCOMP>(b.drho_next, node - nx * ny, pm);
+        // plane z - 1 is complete within the column and segment
+        if (k > 0) dens_store<NCOMP>(b.drho_next, node - plane, pm);
 #pragma unroll
         for (int s = 0; s < NCOMP; ++s) {
             pm[s] = pc[s];
             pc[s] = pn[s];
             pn[s] = 0.0f;
         }
-        __syncthreads();  // the pulls are done before the next copy overwrites the buffer
+        __syncthreads();  // the pulls are done before this buffer takes the copy after next
     }
     // the segment's last plane: what arrives from the next segment comes through memory
-    if (z1 > z0) {
-        const int node = ((z1 - 1) * ny + y) * nx + x;
-        dens_store<NCOMP>(b.drho_next, node, pm);
-    }
+    if (nplanes > 0) dens_store<NCOMP>(b.drho_next, ((z1 - 1) * ny + y) * nx + x, pm);
+}
+
+template <class PT, int NCOMP, int COLL>
+__global__ void __launch_bounds__(256, 3)
+    k_lattice_zm(const __grid_constant__ CUtensorMap tm_fin, StepBufs b, StepParams p, int zs, int rev) {
+    const int x0 = tile_index(blockIdx.x, gridDim.x, rev) * 32;
+    const int y0 = p.ylo + tile_index(blockIdx.y, gridDim.y, rev) * 8;
+    const int z0 = tile_index(blockIdx.z, gridDim.z, rev) * zs;
+    const int z1 = min(z0 + zs, p.nz);
+    // columns whose rows all have both y-neighbours inside the lattice take the
+    // path without bounce-back and y-wrap logic (block-uniform branch)
+    if (y0 > 0 && y0 + 8 < p.ny)
+        lattice_column<PT, NCOMP, COLL, false>(&tm_fin, b, p, x0, y0, z0, z1);
+    else
+        lattice_column<PT, NCOMP, COLL, true>(&tm_fin, b, p, x0, y0, z0, z1);
 }
 
 inline int lattice_sm_count() {
@@ -991,7 +1009,7 @@ cudaError_t launch_pers_tile(const CUtensorMap* tm, const StepParams& p, const S
 // (SMs x resident blocks) blocks over the columns and z-segments.
 inline int zm_segment_length(const StepParams& p) {
     const int cols = (p.nx / 32) * (p.ny / 8);
-    int nseg = (VEFD_LATTICE_THREADS_PER_SM / 256) * lattice_sm_count() / (cols > 0 ? cols : 1);
+    int nseg = 3 * lattice_sm_count() / (cols > 0 ? cols : 1);  // three resident blocks per SM
     if (nseg < 1) nseg = 1;
     if (nseg > p.nz) nseg = p.nz;
     return (p.nz + nseg - 1) / nseg;
@@ -999,9 +1017,15 @@ inline int zm_segment_length(const StepParams& p) {
 
 template <class PT, int NCOMP, int COLL>
 cudaError_t launch_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int zs, int rev, cudaStream_t s) {
-    constexpr int smem = NCOMP * 18 * 256 * (int)sizeof(PT);
-    static_assert(smem <= 48 * 1024, "the staged plane must fit the default shared-memory limit");
-    dim3 blk(32, 8, 1), grd(p.nx / 32, p.ny / 8, (p.nz + zs - 1) / zs);
+    constexpr int smem = 2 * NCOMP * 18 * 256 * (int)sizeof(PT);  // two staged planes
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_lattice_zm<PT, NCOMP, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 blk(32, 8, 1), grd(p.nx / 32, (p.yhi - p.ylo) / 8, (p.nz + zs - 1) / zs);
     k_lattice_zm<PT, NCOMP, COLL><<<grd, blk, smem, s>>>(*tm, b, p, zs, rev);
     return cudaGetLastError();
 }
