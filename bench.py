@@ -320,6 +320,54 @@ def time_variant(S, steps, warmup, model=None, kernel_config=None):
     return out
 
 
+def measured_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def time_nn_gemm(reps=20):
+    """TFLOP/s of the warm-start network's tensor-core GEMM (vefd_nn_gemm_bf16:
+    TMA-fed 4-stage ring, tcgen05 BF16 MMAs with FP32 accumulation in tensor
+    memory): a square 8192^3 product, and the shape of a 16 -> 32 channel
+    3x3x3 convolution on the 64^3 input (im2col: M = 262144 voxels, N = 32,
+    K = 27 * 16 = 432 padded to 432) whose operands stream from HBM.
+    Events on the current stream around `reps` back-to-back launches."""
+    import torch
+
+    from paper_1406_2686_gb300 import nn
+    peak, src = measured_bf16_peak()
+    out = {"peak_tflops": peak, "peak_source": src}
+    for name, (M, N, K) in (("square_8192", (8192, 8192, 8192)), ("conv_64cube_16to32", (262144, 32, 432))):
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            nn.gemm(A, B, C=C, status=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            nn.gemm(A, B, C=C, status=st)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
+        # spot check against a plain torch matmul of the same BF16 operands
+        rows = torch.arange(0, M, max(1, M // 64), device="cuda")
+        ref = (A[rows].float() @ B.float().T)
+        err = float((C[rows] - ref).abs().max() / ref.abs().max().clamp_min(1e-30))
+        out[name] = {"M": M, "N": N, "K": K, "ms": round(ms, 4), "tflops": round(tf, 1), "frac": round(tf / peak, 4),
+                     "hbm_gbs": round((M * K * 2 + N * K * 2 + M * N * 4) / (ms / 1e3) / 1e9, 1),
+                     "max_rel_err_vs_fp32_matmul": err, "status": int(st.item())}
+        del A, B, C
+    return out
+
+
 def time_d2q9_couette(big_steps=1000, warmup=100):
     """The single-component D2Q9 FENE-P Couette set-up (tau = 1, walls +-0.01,
     tau_P = 1000, eta_P / (eta_s + eta_P) = 0.4, L^2 = 100, C = I): the wall
@@ -601,6 +649,7 @@ def run_ours(args):
         # the column-marching lattice kernel with partial densities (post mode 0)
         line["variants"]["fused_densities"] = time_variant(S, vsteps, min(W, 50), kernel_config=(0, 0))
         line["variants"]["d2q9_couette"] = time_d2q9_couette()
+        line["nn_gemm"] = time_nn_gemm()
         line["variants"]["note"] = ("fp16/bf16: 16-bit moving-population deviations, FP32 rest population, FP32 arithmetic "
                                     "and C; mrt: moment-space collision with the paper's relaxation times; cholesky: "
                                     "log-Cholesky conformation update; paper_sec2: both plus the polymer stress in the "

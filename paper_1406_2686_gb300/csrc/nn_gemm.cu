@@ -1,14 +1,24 @@
 // Tensor-core GEMM for the convolution layers of the warm-start network:
 //   C[M x N] (FP32) = A[M x K] (BF16) * B[N x K]^T (BF16)  (+ C when accumulate)
-// A and B are K-major (row-major with K contiguous).  Every CTA owns one
-// 128 x BN tile of C; K advances in chunks of 64.  Per chunk the 128 threads
-// copy the two operand tiles into shared memory in the canonical
-// no-swizzle K-major layout (8-row x 16-byte core matrices), one elected
-// thread issues four tcgen05.mma (M = 128, N = BN, K = 16, BF16 inputs, FP32
-// accumulator in tensor memory) and commits them to an mbarrier, which every
-// thread waits on (bounded) before the tiles are overwritten.  At the end the
-// four warps read their 32 accumulator lanes with tcgen05.ld and store C.
-// Tensor memory is allocated by warp 0 and freed on every exit path.
+// A and B are K-major (row-major with K contiguous).
+//
+// k_gemm_tma (vefd_nn_gemm_bf16 and its split-K form): every CTA owns one
+// 128 x BN tile of C (BN = 32, 64, 128 or 256) and walks K in chunks of 64
+// through a ring of kStages shared-memory stages.  One thread issues the bulk
+// tensor copies of both operand chunks (TMA, 128-byte swizzle, zero fill
+// beyond the matrices) into a free stage; another issues the four
+// tcgen05.mma (M = 128, N = BN, K = 16 each, BF16 inputs, FP32 accumulator in
+// tensor memory) of each loaded stage and commits them to the stage's "empty"
+// barrier, which frees the stage for the copy kStages chunks later.  Copies
+// and matrix operations thus overlap.  After the last commit the four warps
+// read their 32 accumulator lanes with tcgen05.ld and store C.
+//
+// k_gemm_bf16 (vefd_nn_gemm_bf16_layout only): the threads copy both tiles into
+// the no-swizzle K-major core-matrix layout with plain loads, one chunk at a
+// time; it exists to test the descriptor's byte offsets of that layout.
+//
+// Tensor memory is allocated by warp 0 and freed on every exit path; every
+// wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -182,6 +192,159 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+constexpr int kStages = 4;
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzled layout (rows of 64 BF16 = 128 bytes, 8-row atoms of 1024 bytes,
+// atom-aligned): start address, leading byte offset unused (16), stride byte
+// offset 1024 between 8-row groups, descriptor version 1, layout 2 (128-byte
+// swizzle).  Along K the start address advances 32 bytes per 16 elements.
+__device__ __forceinline__ uint64_t smem_desc_sw128(unsigned addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* tm, int c0, int c1, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               float* __restrict__ C, int ldc, int M, int N, int K, int accumulate, int k_split,
+               long long c_split_stride, unsigned* __restrict__ status) {
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "tcgen05 M = 128 needs N in [16, 256], a multiple of 16");
+    constexpr unsigned kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    constexpr unsigned kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2, kStageBytes = kABytes + kBBytes;
+    extern __shared__ unsigned char dsm[];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+    __shared__ unsigned tmem_base;
+    __shared__ int abort_flag;
+    // stages [A | B] at 1024-byte boundaries (the swizzle atom)
+    const unsigned base = (smem_addr(dsm) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    // split K: block z reduces K range [kb, ke) into its own slice of C
+    const int kb = blockIdx.z * k_split, ke = min(K, kb + k_split);
+    C += blockIdx.z * c_split_stride;
+    const int nk = (ke - kb + kBK - 1) / kBK;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init1(smem_addr(&full[s]));
+            mbar_init1(smem_addr(&empty[s]));
+        }
+        mbar_init1(smem_addr(&done));
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
+    if (threadIdx.x == 0) {
+        // producer: chunk kt into stage kt % kStages once the matrix operations
+        // of chunk kt - kStages have released it
+        int issued = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kStages;
+            if (kt >= kStages && !mbar_wait(smem_addr(&empty[s]), (unsigned)((kt / kStages - 1) & 1))) {
+                abort_flag = 1;
+                break;
+            }
+            if (*(volatile int*)&abort_flag) break;
+            const unsigned fb = smem_addr(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStageBytes)
+                         : "memory");
+            const unsigned sa = base + (unsigned)s * kStageBytes;
+            tma_load_2d(sa, &tmA, kb + kt * kBK, m0, fb);
+            tma_load_2d(sa + kABytes, &tmB, kb + kt * kBK, n0, fb);
+            issued = kt + 1;
+        }
+        // bounded: the copies in flight land before the block can leave
+        for (int kt = issued - kStages > 0 ? issued - kStages : 0; kt < issued; ++kt)
+            mbar_wait(smem_addr(&full[kt % kStages]), (unsigned)((kt / kStages) & 1));
+    } else if (threadIdx.x == 32) {
+        // matrix operations of each loaded chunk, committed to its stage's empty barrier
+        constexpr uint32_t idesc = instr_desc(kBM, BN);
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kStages;
+            if (!mbar_wait(smem_addr(&full[s]), (unsigned)((kt / kStages) & 1))) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned sa = base + (unsigned)s * kStageBytes;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+                const uint64_t bd = smem_desc_sw128(sa + kABytes + kk * 32);
+                const unsigned acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&empty[s]))
+                         : "memory");
+        }
+        // arrives once every matrix operation issued above has completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(&done))
+                     : "memory");
+    }
+    const bool finished = nk == 0 || mbar_wait(smem_addr(&done), 0u);
+    const bool ok = !__syncthreads_or(!finished || abort_flag != 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && nk > 0) {
+        // accumulator row 32 * warp + lane, 16 columns per load
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t v[16];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+                float* c = C + (size_t)row * ldc + n0 + c0;
+                if (n0 + c0 + 16 <= N && !accumulate && ((reinterpret_cast<uintptr_t>(c) & 15u) == 0)) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(c + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                                        __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + c0 + j < N) c[j] = accumulate ? c[j] + __uint_as_float(v[j]) : __uint_as_float(v[j]);
+                }
+            }
+        }
+    } else if (!ok && threadIdx.x == 0) {
+        atomicOr(status, kStatusTimeout);
+    }
+    if (!ok && threadIdx.x == 32 && nk > 0) mbar_wait(smem_addr(&done), 0u);  // bounded: matrix operations first
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
 }  // namespace
 }  // namespace vefd_nn
 
@@ -221,18 +384,83 @@ int launch_gemm(const void* A, int lda, const void* B, int ldb, float* C, int ld
 }
 }  // namespace
 
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map of a K-major BF16 matrix [rows][K] (leading dimension ld
+// elements): boxes of 64 K x box_rows rows, 128-byte swizzle, zero fill.
+bool kmajor_map(CUtensorMap* out, const void* base, int rows, int K, int ld, int box_rows) {
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_tma_bn(const CUtensorMap& ta, const CUtensorMap& tb, float* C, int ldc, int M, int N, int K,
+                          int accumulate, int k_split, long long c_split_stride, unsigned* status, cudaStream_t s) {
+    constexpr int smem = kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;  // + alignment slack
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_gemm_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int splits = (K + k_split - 1) / k_split;
+    dim3 grd((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
+    k_gemm_tma<BN><<<grd, kThreads, smem, s>>>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride, status);
+    return cudaGetLastError();
+}
+
+int launch_gemm_tma(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N, int K,
+                    int accumulate, int k_split, long long c_split_stride, unsigned* status, void* stream) {
+    if (!A || !B || !C || !status || M < 1 || N < 1 || K < 8) return VEFD_NN_ERR_ARG;
+    if (K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N) return VEFD_NN_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) return VEFD_NN_ERR_ARG;
+    if (k_split < kBK || k_split % kBK != 0) return VEFD_NN_ERR_ARG;
+    if ((K + k_split - 1) / k_split > 65535) return VEFD_NN_ERR_ARG;
+    const int bn = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    CUtensorMap ta, tb;
+    if (!kmajor_map(&ta, A, M, K, lda, kBM) || !kmajor_map(&tb, B, N, K, ldb, bn)) return VEFD_NN_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    switch (bn) {
+    case 32: e = launch_tma_bn<32>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride, status, s); break;
+    case 64: e = launch_tma_bn<64>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride, status, s); break;
+    case 128: e = launch_tma_bn<128>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride, status, s); break;
+    default: e = launch_tma_bn<256>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride, status, s); break;
+    }
+    return e == cudaSuccess ? VEFD_NN_OK : VEFD_NN_ERR_CUDA;
+}
+}  // namespace
+
 extern "C" int vefd_nn_gemm_bf16(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M, int N,
                                  int K, int accumulate, unsigned* status, void* stream) {
     const int ks = ((K + kBK - 1) / kBK) * kBK;
-    return launch_gemm(A, lda, B, ldb, C, ldc, M, N, K, accumulate, 128u, 1024u, 0, ks < kBK ? kBK : ks, 0, status,
-                       stream);
+    return launch_gemm_tma(A, lda, B, ldb, C, ldc, M, N, K, accumulate, ks < kBK ? kBK : ks, 0, status, stream);
 }
 
 extern "C" int vefd_nn_gemm_bf16_splitk(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M,
                                         int N, int K, int k_split, long long c_split_stride, unsigned* status,
                                         void* stream) {
     if (c_split_stride < (long long)M * ldc) return VEFD_NN_ERR_ARG;
-    return launch_gemm(A, lda, B, ldb, C, ldc, M, N, K, 0, 128u, 1024u, 0, k_split, c_split_stride, status, stream);
+    return launch_gemm_tma(A, lda, B, ldb, C, ldc, M, N, K, 0, k_split, c_split_stride, status, stream);
 }
 
 extern "C" int vefd_nn_gemm_bf16_layout(const void* A, int lda, const void* B, int ldb, float* C, int ldc, int M,

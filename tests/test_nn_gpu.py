@@ -42,7 +42,8 @@ def test_gemm_layout_fields():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 32, 64), (256, 64, 128), (300, 48, 200), (1000, 128, 4096),
-                                   (129, 16, 8), (4096, 100, 432)])
+                                   (129, 16, 8), (4096, 100, 432), (384, 256, 320), (700, 200, 1000),
+                                   (512, 640, 264), (130, 129, 72)])
 def test_gemm_matches_fp64(M, N, K):
     import torch
     from paper_1406_2686_gb300 import nn
@@ -53,6 +54,32 @@ def test_gemm_matches_fp64(M, N, K):
     assert int(st.item()) == 0
     err = float((C.double().cpu() - ref).abs().max())
     assert err < _tol(ref, K), err
+
+
+@pytest.mark.parametrize("K,k_split", [(1000, 256), (4096, 1024), (200, 64)])
+def test_gemm_splitk_slices_sum_to_product(K, k_split):
+    """The split-K form: slice z reduces K in [z k_split, (z + 1) k_split) into
+    its own C slice (the last slice ragged, zero-filled beyond K); the slices
+    sum to A B^T, and each slice equals the product of its K range."""
+    import torch
+    from paper_1406_2686_gb300 import nn
+    M, N = 260, 96
+    A, B, ref = _bf16_pair(M, N, K, K + k_split)
+    splits = (K + k_split - 1) // k_split
+    parts = torch.full((splits, M, N), 7.0, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lb = nn.L()
+    Ad, Bd = A.cuda(), B.cuda()  # kept alive until the kernel has run
+    nn._check(lb.vefd_nn_gemm_bf16_splitk(Ad.data_ptr(), K, Bd.data_ptr(), K, parts.data_ptr(), N, M, N, K, k_split,
+                                          M * N, st.data_ptr(), nn._stream()), "splitk")
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    got = parts.double().cpu()
+    assert float((got.sum(0) - ref).abs().max()) < _tol(ref, K)
+    for z in range(splits):
+        k0, k1 = z * k_split, min(K, (z + 1) * k_split)
+        sub = A[:, k0:k1].double() @ B[:, k0:k1].double().T
+        assert float((got[z] - sub).abs().max()) < _tol(sub, k1 - k0), z
 
 
 def test_gemm_accumulate_and_strides():
