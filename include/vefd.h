@@ -375,13 +375,21 @@ vefd_status vefd_ensemble_get_config(const vefd_ensemble *ens, int *batched, int
 vefd_status vefd_ensemble_set_groups(vefd_ensemble *ens, int groups);
 /* The group-count setting (0: automatic). */
 vefd_status vefd_ensemble_get_groups(const vefd_ensemble *ens, int *groups);
-/* The ensemble's own autotuner.  It times four configurations: graph branches,
- * and batched launches with the automatic z-segment, twice it and half of it.
+/* Lattice tiles of the batched launches (no counterpart in the paper; a launch
+ * shape): 0 (default) 32 x 4 x 2 nodes, 1 32 x 8 x 1.  Results agree with
+ * vefd_step to FP32 rounding for both.  Takes effect at the next replay (after
+ * waiting for earlier replays).  VEFD_ERR_ARG for a NULL ensemble or another
+ * value. */
+vefd_status vefd_ensemble_set_tile(vefd_ensemble *ens, int tile);
+vefd_status vefd_ensemble_get_tile(const vefd_ensemble *ens, int *tile);
+/* The ensemble's own autotuner.  It times seven configurations: graph
+ * branches; and batched launches with each lattice tile (0, 1), each with the
+ * automatic z-segment of the densities pass, twice it and half of it.
  * Each is timed as `steps` replayed steps (after one untimed replay that
  * captures it), and the fastest is kept.  The timed steps are real steps:
- * every member advances by 4 (steps + chunk) steps (plus one eager step if its
+ * every member advances by 7 (steps + chunk) steps (plus one eager step if its
  * Euler start is pending), its results those of vefd_step to FP32 rounding.
- * times_ms (4 slots, or NULL) receives each configuration's milliseconds, -1
+ * times_ms (7 slots, or NULL) receives each configuration's milliseconds, -1
  * where the members do not allow batched launches.  Synchronises.
  * VEFD_ERR_ARG unless steps is a positive multiple of an even chunk;
  * otherwise as vefd_ensemble_step. */

@@ -670,17 +670,20 @@ __global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (B
 }
 
 // Batched ensemble form: block i runs tile i - start[m] of member m with that
-// member's parameters, buffers and tensor map (parity selects the ping-pong state).
-template <class PT, int NCOMP, int COLL>
+// member's parameters, buffers and tensor map (parity selects the ping-pong
+// state).  Tiles are 32 x BY x BZ (32 x 4 x 2 or 32 x 8 x 1, the ensemble's
+// tile choice; the member table's tile counts and tensor maps follow it).
+template <class PT, int NCOMP, int COLL, int BY, int BZ>
 __global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
     k_lattice_batch(const EnsMember* __restrict__ members, const int* __restrict__ start, int nm, int parity) {
+    static_assert(BY * BZ == 8, "256-thread tiles");
     const int m = batch_member(start, nm, (int)blockIdx.x);
     const EnsMember& M = members[m];
     const int t = (int)blockIdx.x - start[m];
     // the member's parameters and buffers, read from shared memory by the node code
     __shared__ StepParams sp;
     __shared__ StepBufs sb;
-    const int lt = (threadIdx.z * 4 + threadIdx.y) * 32 + threadIdx.x;
+    const int lt = (threadIdx.z * BY + threadIdx.y) * 32 + threadIdx.x;
     static_assert(sizeof(StepParams) % 4 == 0 && sizeof(StepBufs) % 4 == 0, "word copies");
     if (lt < (int)(sizeof(StepParams) / 4))
         reinterpret_cast<int*>(&sp)[lt] = reinterpret_cast<const int*>(&M.p)[lt];
@@ -688,27 +691,35 @@ __global__ void __launch_bounds__(256, VEFD_LATTICE_THREADS_PER_SM / 256)
         reinterpret_cast<int*>(&sb)[lt - sizeof(StepParams) / 4] =
             reinterpret_cast<const int*>(&M.b[parity])[lt - sizeof(StepParams) / 4];
     const int r = t / M.ntx;
-    const int x0 = (t % M.ntx) * 32, y0 = (r % M.nty) * 4, z0 = (r / M.nty) * 2;
+    const int x0 = (t % M.ntx) * 32, y0 = (r % M.nty) * BY, z0 = (r / M.nty) * BZ;
     const CUtensorMap* tm = &M.tm_lat[M.cur0 ^ parity];  // the populations read
     if (lt == 0) tensormap_acquire(tm);                   // the thread that issues the copy
     __syncthreads();
-    lattice_tile<PT, D3Q19, NCOMP, 32, 4, 2, COLL>(tm, sb, sp, x0, y0, z0);
+    lattice_tile<PT, D3Q19, NCOMP, 32, BY, BZ, COLL>(tm, sb, sp, x0, y0, z0);
 }
 
-template <int COLL>
-cudaError_t launch_lattice_batch_coll(int ncomp, int prec, const EnsMember* members, const int* start, int nm,
+template <int COLL, int BY, int BZ>
+cudaError_t launch_lattice_batch_tile(int ncomp, int prec, const EnsMember* members, const int* start, int nm,
                                       int items, int parity, bool pdl, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     VEFD_WITH_PT(prec, {
         constexpr int smem_unit = 18 * 256 * (int)sizeof(PT);
         if (ncomp == 2)
-            e = launch_pdl(pdl, k_lattice_batch<PT, 2, COLL>, dim3(items), dim3(32, 4, 2), 2 * smem_unit, s,
+            e = launch_pdl(pdl, k_lattice_batch<PT, 2, COLL, BY, BZ>, dim3(items), dim3(32, BY, BZ), 2 * smem_unit, s,
                            members, start, nm, parity);
         else
-            e = launch_pdl(pdl, k_lattice_batch<PT, 1, COLL>, dim3(items), dim3(32, 4, 2), smem_unit, s, members,
-                           start, nm, parity);
+            e = launch_pdl(pdl, k_lattice_batch<PT, 1, COLL, BY, BZ>, dim3(items), dim3(32, BY, BZ), smem_unit, s,
+                           members, start, nm, parity);
     });
     return e;
+}
+
+// tile 0: 32 x 4 x 2, tile 1: 32 x 8 x 1
+template <int COLL>
+cudaError_t launch_lattice_batch_coll(int ncomp, int prec, int tile, const EnsMember* members, const int* start,
+                                      int nm, int items, int parity, bool pdl, cudaStream_t s) {
+    return tile == 1 ? launch_lattice_batch_tile<COLL, 8, 1>(ncomp, prec, members, start, nm, items, parity, pdl, s)
+                     : launch_lattice_batch_tile<COLL, 4, 2>(ncomp, prec, members, start, nm, items, parity, pdl, s);
 }
 
 // Persistent form (single-relaxation-time collision): a grid of (SMs x

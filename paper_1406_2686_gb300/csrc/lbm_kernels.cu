@@ -176,10 +176,10 @@ cudaError_t launch_wait_selftest(unsigned* status, int arrive, long long cycles,
     return cudaGetLastError();
 }
 
-cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, const EnsMember* members, const int* start, int nm,
-                                 int items, int parity, bool pdl, cudaStream_t s) {
-    if (coll == 1) return launch_lattice_batch_mrt(ncomp, prec, members, start, nm, items, parity, pdl, s);
-    return launch_lattice_batch_coll<0>(ncomp, prec, members, start, nm, items, parity, pdl, s);
+cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, int tile, const EnsMember* members, const int* start,
+                                 int nm, int items, int parity, bool pdl, cudaStream_t s) {
+    if (coll == 1) return launch_lattice_batch_mrt(ncomp, prec, tile, members, start, nm, items, parity, pdl, s);
+    return launch_lattice_batch_coll<0>(ncomp, prec, tile, members, start, nm, items, parity, pdl, s);
 }
 
 cudaError_t launch_init_equilibrium(int lattice, int ncomp, const StepParams& p, const float* rhoA,

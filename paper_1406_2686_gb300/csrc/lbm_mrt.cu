@@ -15,9 +15,9 @@ cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs
     return launch_zm_coll<1>(ncomp, p, b, s, tensor_map, zs, rev);
 }
 
-cudaError_t launch_lattice_batch_mrt(int ncomp, int prec, const EnsMember* members, const int* start, int nm,
-                                     int items, int parity, bool pdl, cudaStream_t s) {
-    return launch_lattice_batch_coll<1>(ncomp, prec, members, start, nm, items, parity, pdl, s);
+cudaError_t launch_lattice_batch_mrt(int ncomp, int prec, int tile, const EnsMember* members, const int* start,
+                                     int nm, int items, int parity, bool pdl, cudaStream_t s) {
+    return launch_lattice_batch_coll<1>(ncomp, prec, tile, members, start, nm, items, parity, pdl, s);
 }
 
 }  // namespace vefd

@@ -1403,6 +1403,7 @@ struct vefd_ensemble {
     // step over the tiles of all members, from a device table of members
     int batched_pref = 1;       // use them when the members allow
     int post_seg = 0;           // z-segment of the batched densities pass: 0 automatic, else planes
+    int tile = 0;               // batched lattice tiles: 0 32 x 4 x 2, 1 32 x 8 x 1
     bool batched = false;       // the captured graph uses them
     std::vector<EnsMember> table;
     std::vector<int> start;     // lattice tiles then z-march columns: first item of each member
@@ -1440,7 +1441,7 @@ bool ens_batchable(const vefd_ensemble* e) {
     return true;
 }
 
-constexpr int kEnsTuneSlots = 4;  // configurations vefd_ensemble_autotune times
+constexpr int kEnsTuneSlots = 7;  // configurations vefd_ensemble_autotune times
 
 // z-segment length of the batched z-march pass: fewest (waves x planes per
 // block), counting two planes of ring prologue per block.
@@ -1507,8 +1508,8 @@ vefd_status ens_build_table(vefd_ensemble* e) {
         M.p = params_of(m);
         M.cur0 = m->cur;
         for (int j = 0; j < 2; ++j) {
-            M.tm_lat[j] = m->tmap_post[j];  // box 32 x 4 x 2
-            M.tm_post[j] = m->tmap_zm[j];   // box 32 x 8 x 1
+            M.tm_lat[j] = e->tile == 1 ? m->tmap_zm[j] : m->tmap_post[j];  // box of the lattice tile
+            M.tm_post[j] = m->tmap_zm[j];                                    // box 32 x 8 x 1
         }
         for (int par = 0; par < 2; ++par) {
             const int cur = m->cur ^ par, ccur = m->ccur ^ (m->fd_on ? par : 0);
@@ -1519,9 +1520,10 @@ vefd_status ens_build_table(vefd_ensemble* e) {
             b.Cout = m->C[1 - ccur];
             M.b[par] = b;
         }
+        const int tby = e->tile == 1 ? 8 : 4, tbz = e->tile == 1 ? 1 : 2;
         M.ntx = (m->cfg.nx + 31) / 32;
-        M.nty = (m->cfg.ny + 3) / 4;
-        M.ntz = (m->cfg.nz + 1) / 2;
+        M.nty = (m->cfg.ny + tby - 1) / tby;
+        M.ntz = (m->cfg.nz + tbz - 1) / tbz;
         M.ncx = m->cfg.nx / 32;
         M.ncy = m->cfg.ny / 8;
         M.zs = std::min(zs, m->cfg.nz);
@@ -1576,8 +1578,8 @@ vefd_status ens_capture_batched(vefd_ensemble* e, int64_t chunk) {
         ce = cudaStreamWaitEvent(s, e->fork, 0);
         for (int64_t k = 0; k < chunk && ce == cudaSuccess; ++k) {
             const int par = (int)(k & 1);
-            ce = launch_lattice_batch(nc, prec, a->collision, e->d_table + m0, e->d_start + m0, gm, e->glat[g], par,
-                                      pdl, s);
+            ce = launch_lattice_batch(nc, prec, a->collision, e->tile, e->d_table + m0, e->d_start + m0, gm,
+                                      e->glat[g], par, pdl, s);
             if (ce == cudaSuccess)
                 ce = launch_post_batch(nc, prec, fd, e->d_table + m0, e->d_start + nm + m0, gm, e->gpost[g], par, pdl,
                                        s);
@@ -1832,6 +1834,26 @@ vefd_status vefd_ensemble_get_config(const vefd_ensemble* e, int* batched, int* 
     return VEFD_OK;
 }
 
+vefd_status vefd_ensemble_set_tile(vefd_ensemble* e, int tile) {
+    if (!e || (tile != 0 && tile != 1)) return VEFD_ERR_ARG;
+    if (e->tile != tile) {
+        // the next replay re-captures; earlier replays may still be in flight
+        if (e->exec) {
+            cudaStreamSynchronize(e->main);
+            cudaGraphExecDestroy(e->exec);
+        }
+        e->exec = nullptr;
+        e->tile = tile;
+    }
+    return VEFD_OK;
+}
+
+vefd_status vefd_ensemble_get_tile(const vefd_ensemble* e, int* tile) {
+    if (!e || !tile) return VEFD_ERR_ARG;
+    *tile = e->tile;
+    return VEFD_OK;
+}
+
 vefd_status vefd_ensemble_set_groups(vefd_ensemble* e, int groups) {
     if (!e || groups < 0 || groups > 64) return VEFD_ERR_ARG;
     if (e->groups != groups) {
@@ -1874,20 +1896,24 @@ vefd_status vefd_ensemble_autotune(vefd_ensemble* e, int64_t steps, int64_t chun
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
     const int auto_zs = ens_post_segment(e, sms);
-    // graph branches; batched with the automatic z-segment, twice and half as long
-    const int cand[kEnsTuneSlots][2] = {{0, 0}, {1, 0}, {1, 2 * auto_zs}, {1, std::max(1, auto_zs / 2)}};
+    // graph branches; batched with lattice tiles 32 x 4 x 2 and 32 x 8 x 1, each
+    // with the automatic z-segment of the pass, twice and half as long
+    const int half = std::max(1, auto_zs / 2);
+    const int cand[kEnsTuneSlots][3] = {{0, 0, 0},        {1, 0, 0}, {1, 2 * auto_zs, 0}, {1, half, 0},
+                                        {1, 0, 1},        {1, 2 * auto_zs, 1}, {1, half, 1}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
         return ens_fail(e, VEFD_ERR_CUDA, "cannot create timing events");
     }
-    const int keep_b = e->batched_pref, keep_s = e->post_seg;
+    const int keep_b = e->batched_pref, keep_s = e->post_seg, keep_t = e->tile;
     vefd_status st = VEFD_OK;
     double best = 1e300;
     int best_k = -1;
     for (int k = 0; k < kEnsTuneSlots && st == VEFD_OK; ++k) {
         if (times_ms) times_ms[k] = -1.0;
         st = vefd_ensemble_set_config(e, cand[k][0], cand[k][1]);
+        if (st == VEFD_OK) st = vefd_ensemble_set_tile(e, cand[k][2]);
         // one untimed replay, which captures the graph
         if (st == VEFD_OK) st = vefd_ensemble_step(e, chunk, chunk);
         if (st != VEFD_OK) break;
@@ -1909,9 +1935,11 @@ vefd_status vefd_ensemble_autotune(vefd_ensemble* e, int64_t steps, int64_t chun
     cudaEventDestroy(e1);
     if (st != VEFD_OK || best_k < 0) {
         vefd_ensemble_set_config(e, keep_b, keep_s);
+        vefd_ensemble_set_tile(e, keep_t);
         return st != VEFD_OK ? st : ens_fail(e, VEFD_ERR_CUDA, "no configuration was timed");
     }
-    return vefd_ensemble_set_config(e, cand[best_k][0], cand[best_k][1]);
+    st = vefd_ensemble_set_config(e, cand[best_k][0], cand[best_k][1]);
+    return st != VEFD_OK ? st : vefd_ensemble_set_tile(e, cand[best_k][2]);
 }
 
 int vefd_ensemble_is_batched(const vefd_ensemble* e) { return e && e->exec && e->batched ? 1 : 0; }

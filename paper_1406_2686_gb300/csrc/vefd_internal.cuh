@@ -363,10 +363,12 @@ cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs
 // One bounded wait on an mbarrier that one thread completes (arrive != 0) or
 // that nothing completes; on running out of `cycles` it sets kStTimeout.
 cudaError_t launch_wait_selftest(unsigned* status, int arrive, long long cycles, cudaStream_t s);
-cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, const EnsMember* members, const int* start, int nm,
-                                 int items, int parity, bool pdl, cudaStream_t s);
-cudaError_t launch_lattice_batch_mrt(int ncomp, int prec, const EnsMember* members, const int* start, int nm,
-                                     int items, int parity, bool pdl, cudaStream_t s);
+// `tile` 0: 32 x 4 x 2 tiles, 1: 32 x 8 x 1 (the member table's tile counts and
+// lattice tensor maps must be built for the same tile).
+cudaError_t launch_lattice_batch(int ncomp, int prec, int coll, int tile, const EnsMember* members, const int* start,
+                                 int nm, int items, int parity, bool pdl, cudaStream_t s);
+cudaError_t launch_lattice_batch_mrt(int ncomp, int prec, int tile, const EnsMember* members, const int* start,
+                                     int nm, int items, int parity, bool pdl, cudaStream_t s);
 cudaError_t launch_post_batch(int ncomp, int prec, bool fd, const EnsMember* members, const int* start, int nm,
                               int items, int parity, bool pdl, cudaStream_t s);
 // Staged tile shapes of the lattice kernel: tile 0..2 ->

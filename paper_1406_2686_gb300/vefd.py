@@ -46,7 +46,8 @@ EXPORTS = [
     "vefd_ensemble_destroy", "vefd_wait_selftest", "vefd_ensemble_set_batched", "vefd_ensemble_set_config",
     "vefd_ensemble_get_config", "vefd_ensemble_autotune", "vefd_set_step_graph", "vefd_get_step_graph",
     "vefd_prepare_step_graph", "vefd_ensemble_is_batched", "vefd_set_collision", "vefd_set_conformation_update",
-    "vefd_prepare_steps", "vefd_ensemble_set_groups", "vefd_ensemble_get_groups"
+    "vefd_prepare_steps", "vefd_ensemble_set_groups", "vefd_ensemble_get_groups", "vefd_ensemble_set_tile",
+    "vefd_ensemble_get_tile",
 ]
 
 _lib = None
@@ -110,6 +111,8 @@ def load(build_if_missing=True):
         "vefd_prepare_step_graph": [vp],
         "vefd_prepare_steps": [vp, i64],
         "vefd_ensemble_set_groups": [vp, cint],
+        "vefd_ensemble_set_tile": [vp, cint],
+        "vefd_ensemble_get_tile": [vp, ctypes.POINTER(cint)],
         "vefd_ensemble_get_groups": [vp, ctypes.POINTER(cint)],
         "vefd_get_step_graph": [vp, ctypes.POINTER(cint), ctypes.POINTER(cint), ctypes.POINTER(cint)],
     }
@@ -353,6 +356,16 @@ def vefd_ensemble_get_config(ens):
     return b.value, z.value
 
 
+def vefd_ensemble_set_tile(ens, tile):
+    return _ens_check(ens, load().vefd_ensemble_set_tile(ens, int(tile)))
+
+
+def vefd_ensemble_get_tile(ens):
+    t = ctypes.c_int()
+    _ens_check(ens, load().vefd_ensemble_get_tile(ens, ctypes.byref(t)))
+    return t.value
+
+
 def vefd_ensemble_set_groups(ens, groups):
     return _ens_check(ens, load().vefd_ensemble_set_groups(ens, int(groups)))
 
@@ -364,7 +377,7 @@ def vefd_ensemble_get_groups(ens):
 
 
 def vefd_ensemble_autotune(ens, steps=64, chunk=32):
-    t = (ctypes.c_double * 4)()
+    t = (ctypes.c_double * 7)()
     _ens_check(ens, load().vefd_ensemble_autotune(ens, int(steps), int(chunk), t))
     return [float(v) for v in t]
 
@@ -583,6 +596,14 @@ class Ensemble:
     def config(self):
         """(batched, post z-segment) requested for the replays."""
         return vefd_ensemble_get_config(self.ens)
+
+    def set_tile(self, tile):
+        """Lattice tiles of the batched launches: 0 32 x 4 x 2, 1 32 x 8 x 1."""
+        vefd_ensemble_set_tile(self.ens, tile)
+
+    @property
+    def tile(self):
+        return vefd_ensemble_get_tile(self.ens)
 
     def set_groups(self, groups):
         """Group count of the batched launches (0: automatic, 4)."""

@@ -130,6 +130,8 @@ def test_step_graph_and_ensemble_argument_checks(lib):
     assert lib.vefd_ensemble_autotune(None, 64, 32, None) == vefd.ERR_ARG
     assert lib.vefd_ensemble_is_batched(None) == 0
     assert lib.vefd_ensemble_set_groups(None, 2) == vefd.ERR_ARG
+    assert lib.vefd_ensemble_set_tile(None, 1) == vefd.ERR_ARG
+    assert lib.vefd_ensemble_get_tile(None, ctypes.byref(ctypes.c_int())) == vefd.ERR_ARG
     g = ctypes.c_int()
     assert lib.vefd_ensemble_get_groups(None, ctypes.byref(g)) == vefd.ERR_ARG
     b, z = ctypes.c_int(), ctypes.c_int()

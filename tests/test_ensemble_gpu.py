@@ -234,6 +234,46 @@ def test_batched_ensemble_matches_single_lattices():
         assert a.status() == 0
 
 
+@pytest.mark.parametrize("variant", ["fp32", "fp16", "mrt_chol"])
+def test_batched_ensemble_tile_32x8x1(variant):
+    """Batched launches with 32 x 8 x 1 lattice tiles give each box's own step
+    (FP32 rounding), across the Euler start, replays of both parities and an
+    odd remainder, and agree with the 32 x 4 x 2 tiles to the same rounding."""
+    from paper_1406_2686_gb300 import vefd
+    boxes = [dict(b) for b in BATCH_BOXES]
+    prep = lambda L: None
+    if variant == "fp16":
+        for b in boxes:
+            b["precision"] = 1
+    elif variant == "mrt_chol":
+        def prep(L):
+            L.set_collision(1)
+            L.set_conformation_update(1)
+    rel = 1e-3 if variant == "fp16" else 1e-6
+    ens = [make(b, seed=80 + i) for i, b in enumerate(boxes)]
+    ref = [make(b, seed=80 + i) for i, b in enumerate(boxes)]
+    alone = [make(b, seed=80 + i) for i, b in enumerate(boxes)]
+    for L in ens + ref + alone:
+        prep(L)
+    E, R = vefd.Ensemble(ens), vefd.Ensemble(ref)
+    E.set_tile(1)
+    assert E.tile == 1 and R.tile == 0
+    for n in (23, 1, 16):
+        E.step(n, chunk=4)
+        R.step(n, chunk=4)
+        for L in alone:
+            L.step(n)
+    assert E.batched and R.batched
+    for a, r, c in zip(ens, ref, alone):
+        assert close_state(a, c, rel) and close_state(a, r, rel)
+        assert a.status() == 0
+    with pytest.raises(vefd.VefdError) as ei:
+        E.set_tile(2)
+    assert ei.value.status == vefd.ERR_ARG
+    E.close()
+    R.close()
+
+
 @pytest.mark.parametrize("groups", [1, 2, 4, 9])
 def test_batched_ensemble_group_counts_bit_identical(groups):
     """The group count only changes which graph branch a member's tiles are
@@ -340,9 +380,10 @@ def test_batched_ensemble_many_members():
 
 def test_ensemble_config_and_autotune():
     """The ensemble's own autotuner times graph branches and batched launches
-    with three z-segment lengths of the densities pass, keeps the fastest, and
-    its timed steps are ordinary steps (results as stepping alone); an
-    ensemble the batched kernels cannot take only times the branches."""
+    with two lattice tiles and three z-segment lengths of the densities pass,
+    keeps the fastest, and its timed steps are ordinary steps (results as
+    stepping alone); an ensemble the batched kernels cannot take only times
+    the branches."""
     from paper_1406_2686_gb300 import vefd
     boxes = BATCH_BOXES[:3]
     ens = [make(b, seed=60 + i) for i, b in enumerate(boxes)]
@@ -353,13 +394,15 @@ def test_ensemble_config_and_autotune():
     assert E.config == (1, 3)
     E.step(9, chunk=4)                      # 1 eager start, 2 replays with 3-plane segments
     assert E.batched
-    times = E.autotune(steps=8, chunk=4)    # 4 x (8 + 4) steps
-    assert len(times) == 4 and all(t > 0 for t in times)
+    times = E.autotune(steps=8, chunk=4)    # 7 x (8 + 4) steps
+    assert len(times) == 7 and all(t > 0 for t in times)
     best = int(np.argmin(times))
     b, z = E.config
     assert b == (0 if best == 0 else 1)
+    if best > 0:
+        assert E.tile == (0 if best < 4 else 1)
     E.step(8, chunk=4)
-    total = 9 + 4 * 12 + 8
+    total = 9 + 7 * 12 + 8
     for L in alone:
         L.step(total)
     for a, r in zip(ens, alone):
@@ -377,7 +420,7 @@ def test_ensemble_config_and_autotune():
     # a D2Q9 member: no batched launches, only the branches are timed
     F = vefd.Ensemble([make(BOXES[3], seed=5), make(BATCH_BOXES[0], seed=6)])
     times = F.autotune(steps=4, chunk=2)
-    assert times[0] > 0 and times[1:] == [-1.0, -1.0, -1.0]
+    assert times[0] > 0 and times[1:] == [-1.0] * 6
     assert F.config[0] == 0
     F.close()
 
