@@ -109,7 +109,9 @@ def parse():
     ap.add_argument("--ws-train", type=int, default=128, help="training set-ups for --warmstart")
     ap.add_argument("--ws-eval", type=int, default=12, help="held-out set-ups for --warmstart")
     ap.add_argument("--ws-epochs", type=int, default=60)
-    ap.add_argument("--ws-lr", type=float, default=1e-3)
+    ap.add_argument("--ws-lr", type=float, default=5e-4)
+    ap.add_argument("--ws-channels", default="16,32,80,152",
+                    help="U-Net channels per level (multiples of 8; 16,32,80,152 = 2.07 M parameters)")
     ap.add_argument("--ws-tol", type=float, default=2e-6)
     return ap.parse_args()
 
@@ -659,7 +661,8 @@ def run_ours(args):
                                     "set-up, 20000 steps at 64 x 32 (time) and MLUPS at 4096 x 2048" % vsteps)
     if not args.no_warmstart and S.prec == 0:
         # bounded form of --warmstart: 48 training set-ups, 40 epochs, 8 held out
-        line["warmstart"] = warmstart_measure(48, 8, 40, args.ws_lr, args.ws_tol)
+        line["warmstart"] = warmstart_measure(48, 8, 40, args.ws_lr, args.ws_tol,
+                                              tuple(int(v) for v in args.ws_channels.split(",")))
     if not args.no_ensemble and S.prec == 0:
         line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
         line["ensemble_small"] = time_ensemble(max(100, K // 20), min(W, 20), setups=small_setups(),
@@ -672,7 +675,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def warmstart_measure(n_train, n_eval, epochs, lr, tol, log=None):
+def warmstart_measure(n_train, n_eval, epochs, lr, tol, channels=(16, 32, 80, 152), log=None):
     """Time to steady deformation of held-out droplet set-ups, cold start
     versus a start from the trained network's prediction: data from the
     method's own steady states, training and prediction on this package's
@@ -686,7 +689,7 @@ def warmstart_measure(n_train, n_eval, epochs, lr, tol, log=None):
     eval_setups = ws.sample_setups(n_eval, seed=29)
     X, Y, rec = ws.make_dataset(train_setups, tol=tol, log=log)
     t_data = time.perf_counter() - t0
-    net = nn.UNet(ws.N_IN, ws.N_OUT, c=16, seed=0)
+    net = nn.UNet(ws.N_IN, ws.N_OUT, seed=0, channels=tuple(channels))
     t1 = time.perf_counter()
     losses = ws.train(net, X, Y, epochs=epochs, lr=lr, log=log)
     torch.cuda.synchronize()
@@ -704,7 +707,8 @@ def warmstart_measure(n_train, n_eval, epochs, lr, tol, log=None):
         "config": {"box": "64^3 D3Q19 two-component droplet, walls in y", "train_setups": len(train_setups),
                    "eval_setups": len(eval_setups), "steady_rule": "|dD| < %g per tau_em over 5 consecutive tau_em "
                    "(mid-plane, smooth indicator)" % tol, "network": "3-D U-Net, %d parameters, BF16 tcgen05 GEMMs, "
-                   "FP32 accumulate" % net.n_params(), "epochs": epochs, "lr": lr},
+                   "FP32 accumulate" % net.n_params(), "channels": list(channels), "epochs": epochs, "lr": lr,
+                   "lr_schedule": "linear ramp from lr/10 over the first epoch, then geometric decay to lr/10"},
         "steps": {"cold_median": int(np.median([r["cold_steps"] for r in res])),
                   "warm_median": int(np.median([r["warm_steps"] for r in res]))},
         "seconds": {"cold_median": round(float(np.median(cold)), 4), "warm_median": round(float(np.median(warm)), 4),
@@ -723,7 +727,8 @@ def run_warmstart(args):
     import torch
     torch.cuda.set_device(0)
     log = (lambda m: print(m, file=sys.stderr, flush=True))
-    line = warmstart_measure(args.ws_train, args.ws_eval, args.ws_epochs, args.ws_lr, args.ws_tol, log=log)
+    chans = tuple(int(v) for v in args.ws_channels.split(","))
+    line = warmstart_measure(args.ws_train, args.ws_eval, args.ws_epochs, args.ws_lr, args.ws_tol, chans, log=log)
     line.update({"n_gpus": 1, "data": "synthetic (steady states generated by the lattice-Boltzmann/FENE-P step)"})
     print(json.dumps(line), flush=True)
 

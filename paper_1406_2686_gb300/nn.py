@@ -248,15 +248,16 @@ def mse(pred, target):
 
 
 class UNet:
-    """3-D convolutional U-Net: four resolution levels (channels c, 2c, 4c, 8c),
-    two convolutions per level, stride-2 convolutions down, nearest-neighbour
-    upsampling and skip concatenation up, a linear 3x3x3 output layer.  Input
-    and output are channels-last FP32 [B, D, H, W, C] with D, H, W divisible by 8."""
+    """3-D convolutional U-Net: four resolution levels (channels c, 2c, 4c, 8c,
+    or the per-level plan `channels`, each a multiple of 8), two convolutions
+    per level, stride-2 convolutions down, nearest-neighbour upsampling and
+    skip concatenation up, a linear 3x3x3 output layer.  Input and output are
+    channels-last FP32 [B, D, H, W, C] with D, H, W divisible by 8."""
 
-    def __init__(self, cin, cout, c=16, seed=0):
+    def __init__(self, cin, cout, c=16, seed=0, channels=None):
         import torch
         g = torch.Generator().manual_seed(seed)
-        c0, c1, c2, c3 = c, 2 * c, 4 * c, 8 * c
+        c0, c1, c2, c3 = channels if channels is not None else (c, 2 * c, 4 * c, 8 * c)
         self.cout = cout
         self.e0 = [Conv3d(cin, c0, gen=g), Conv3d(c0, c0, gen=g)]
         self.e1 = [Conv3d(c0, c1, 2, gen=g), Conv3d(c1, c1, gen=g)]

@@ -193,23 +193,28 @@ def make_dataset(setups, tol=1e-5, max_steps=80000, log=None):
     return np.stack(X), np.stack(Y), rec
 
 
-def train(net, X, Y, epochs=30, lr=1e-3, seed=0, log=None):
+def train(net, X, Y, epochs=30, lr=1e-3, seed=0, log=None, warmup=1):
     """Adam on the mean squared error of the normalised targets, one sample per
-    step, the learning rate decaying geometrically to lr / 10 over the epochs."""
+    step, the learning rate decaying geometrically to lr / 10 over the epochs;
+    over the first `warmup` epochs it also ramps linearly from lr / 10, so that
+    the first steps at full rate cannot switch off whole layers of units."""
     import torch
     n = X.shape[0]
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     rng = np.random.default_rng(seed)
     losses = []
+    k = 0
     for ep in range(epochs):
         tot = torch.zeros(8, device="cuda")
         lr_ep = lr * 0.1 ** (ep / max(1, epochs - 1))
         for i in rng.permutation(n):
+            ramp = min(1.0, 0.1 + 0.9 * k / max(1, warmup * n)) if warmup > 0 else 1.0
+            k += 1
             out = net.forward(Xd[i:i + 1].contiguous())
             parts, grad = nn.mse(out, Yd[i:i + 1].contiguous())
             net.backward(grad)
-            net.adam_step(lr=lr_ep)
+            net.adam_step(lr=lr_ep * ramp)
             tot += parts
         losses.append(float(tot.sum()) / (n * Y[0].size))
         if log and (ep % 5 == 4 or ep == epochs - 1):

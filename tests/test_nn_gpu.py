@@ -159,13 +159,15 @@ def test_conv_layer_matches_torch(cin, cout, stride, relu, shape):
     assert int(lay.status.item()) == 0
 
 
-def test_unet_gradients_match_torch():
+@pytest.mark.parametrize("channels", [(8, 16, 32, 64), (8, 16, 24, 40)])
+def test_unet_gradients_match_torch(channels):
     """The whole U-Net (forward, MSE loss, backward through every layer, skip
-    and upsampling) against FP64 autograd of the same weights."""
+    and upsampling) against FP64 autograd of the same weights, for the
+    doubling channel plan and an uneven one."""
     import torch
     import torch.nn.functional as F
     from paper_1406_2686_gb300 import nn
-    net = nn.UNet(5, 8, c=8, seed=3)
+    net = nn.UNet(5, 8, seed=3, channels=channels)
     g = torch.Generator().manual_seed(5)
     for lay in net.layers:
         lay.b.copy_(torch.randn(lay.cout, generator=g).cuda() * 0.05)
