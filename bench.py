@@ -69,6 +69,9 @@ class Setup:
         pbytes = 2 * 18 * (4 if self.prec == 0 else 2) * 2 + 2 * 4 * 2
         self.pop_bytes = pbytes
         self.step_bytes = pbytes + 6 * 4 * 2 + 6 * 4 * 2   # 400 for FP32, 256 for 16-bit
+        # the same count with every population (the rest one too) in the storage
+        # type: 400 for FP32, 248 for 16-bit storage
+        self.step_bytes_all_stored = 2 * 19 * (4 if self.prec == 0 else 2) * 2 + 6 * 4 * 2 * 2
 KERNEL_NAMES = ["moments", "lattice_collide_stream", "densities_fenep_fd"]
 
 
@@ -316,9 +319,13 @@ def time_variant(S, steps, warmup, model=None, kernel_config=None):
     ms = e0.elapsed_time(e1)
     peak, _ = measured_peak()
     bw = S.step_bytes * S.N / (ms / steps / 1e3) / 1e9
+    bw_all = S.step_bytes_all_stored * S.N / (ms / steps / 1e3) / 1e9
     out = {"value": round(S.N * steps / (ms / 1e3) / 1e6, 1), "unit": MLUPS, "ms_per_step": round(ms / steps, 5),
            "step_roofline": {"achieved": round(bw, 1), "frac": round(bw / peak, 4),
-                             "algorithmic_bytes_per_node": S.step_bytes}, "status_bits": lat.status(),
+                             "algorithmic_bytes_per_node": S.step_bytes,
+                             "frac_all_populations_stored": round(bw_all / peak, 4),
+                             "bytes_per_node_all_populations_stored": S.step_bytes_all_stored},
+           "status_bits": lat.status(),
            "kernel_config": list(lat.kernel_config()), "step_graph": list(lat.step_graph)}
     lat.close()
     return out

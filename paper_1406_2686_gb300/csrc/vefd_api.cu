@@ -995,9 +995,12 @@ vefd_status vefd_read_field(vefd_ctx* c, vefd_field field, void* dst, size_t byt
     case VEFD_RHO_A:
     case VEFD_RHO_B:
     case VEFD_PHI: {
-        StepBufs b = bufs_of(c);
-        VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
-        c->drho_valid = true;
+        // the densities of the current state: kept by the step, else computed from the populations
+        if (!c->drho_valid) {
+            StepBufs b = bufs_of(c);
+            VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+            c->drho_valid = true;
+        }
         VEFD_CUDA(c, launch_derived(c->cfg.lattice, c->cfg.ncomp, (int)field, p, c->drho, c->C[c->ccur], stg,
                                     c->stream));
         return copy_out(c, dst, stg, bytes, dst_on_device);

@@ -565,60 +565,84 @@ PREC_TOL = {  # relative L2 after 3 steps from a random state
 }
 
 
+REF256 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "droplet256_fp64_5000.npz")
+
+# Per-field bounds against the FP64 oracle after 5000 steps of the
+# 256 x 128 x 256 droplet (relative L2 over the stored planes).  FP32 carries
+# the 1e-5 contract of u and C (rho_A, dominated by the interface, 1e-4, as in
+# the 64 x 32 x 64 report).  The 16-bit bounds follow from the storage
+# precision: FP16 (11-bit significand) keeps u and C within a few 1e-3;
+# BF16 (8-bit significand) moves the interface, so its bounds only say that
+# the run stays a droplet of the same size and shape class.
+REF256_BOUNDS = {0: dict(rhoA=1e-4, rhoB=1e-4, u=1e-5, C=1e-5, CmI=1e-4, D=1e-4),
+                 1: dict(rhoA=5e-2, rhoB=5e-2, u=1e-2, C=5e-3, CmI=5e-2, D=5e-2),
+                 2: dict(rhoA=6e-1, rhoB=6e-1, u=2e-1, C=5e-2, CmI=5e-1, D=3e-1)}
+
+
 @pytest.mark.slow
-def test_precision_full_geometry_report(capsys):
-    """The 16-bit storage geometry, 256 x 128 x 256 (R = 32, 2R/H = 0.5, the
-    benchmark's parameters scaled): every storage type against the FP64
-    oracle after 20 steps (the oracle needs about 1 s per step here), and the
-    FP16 and BF16 runs against the FP32 run after 5000 steps (relative L2 of
-    rho_A, u and C, and the mid-plane droplet deformation D).  Bounds follow
-    the storage precision; every run keeps the component masses."""
-    from paper_1406_2686_gb300 import vefd, warmstart
+@pytest.mark.skipif(not os.path.exists(REF256), reason="FP64 reference sample not generated")
+def test_precision_full_geometry_vs_oracle(capsys):
+    """The storage-precision geometry, 256 x 128 x 256 (R = 32, 2R/H = 0.5,
+    the benchmark droplet scaled), FP32, FP16 and BF16 population storage,
+    each after 5000 steps against the FP64 oracle's run of the same seeded
+    state (stored by oracle/make_droplet256_reference.py: the planes z = NZ/2
+    and y = NY/2 of rho_A, rho_B, u and C, and the oracle's diagnostics):
+    relative L2 per field, of C - I, the deformation D of the shear plane,
+    and the component masses."""
+    import json
+
+    from paper_1406_2686_gb300 import vefd
+    ref = np.load(REF256)
+    meta = json.loads(str(ref["meta"]))
     nx, ny, nz, R = 256, 128, 256, 32.0
-    P = _droplet_pair(nx, ny, nz, R)
-    P.o.step(20)
-    fields = (("rhoA", vefd.RHO_A, oracle.F_RHO_A), ("u", vefd.U, oracle.F_U), ("C", vefd.C, oracle.F_C))
-    ref20 = {k: P.o.read(of) for k, _, of in fields}
-    del P.o
-    P.g.close()
-    rA, rB = inputs.droplet_fields(nx, ny, nz, R=R, seed=1, noise=1e-3)
+    etaB = 2.1 / 3.0 * 0.5
+    p = dict(lattice=1, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=0.6 * etaB, eta_B=etaB,
+             u_wall=0.1 * 0.09 / (R * etaB) * ny / 2, tau_p=R * etaB / 0.09 * etaB / (0.4 * etaB), eta_p=0.4 * etaB,
+             L2=100.0, kappa=1e-3, phase=1)
+    for k, v in p.items():
+        assert abs(meta["params"][k] - v) <= 1e-12 * max(1.0, abs(v)), (k, meta["params"][k], v)
+    assert meta["steps"] == 5000
+    rA, rB = inputs.droplet_fields(nx, ny, nz, R=R, seed=meta["seed"], noise=1e-3)
     rA, rB = inputs.to_f32_exact(rA), inputs.to_f32_exact(rB)
-    p = P.p
-    vs_oracle, at5000, D, mass = {}, {}, {}, {}
+    zref, yref = ref["zplane"], ref["yplane"]
+    rows = {"rhoA": slice(0, 1), "rhoB": slice(1, 2), "u": slice(2, 5), "C": slice(5, 11)}
+    eye = np.array([1, 0, 0, 1, 0, 1.0])[:, None, None]
+    table = []
     for prec in (0, 1, 2):
         g = vefd.Lattice(lattice=1, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=p["G"], eta_A=p["eta_A"],
-                         eta_B=p["eta_B"], delta=p["delta"], precision=prec)
+                         eta_B=p["eta_B"], delta=0.1, precision=prec)
         g.set_wall_shear(p["u_wall"])
         g.set_fenep(p["tau_p"], p["eta_p"], p["L2"], p["kappa"], p["phase"], 1)
         g.init_fields(rA, rB)
         m0 = g.diagnostics()[:2]
-        g.step(20)
-        vs_oracle[prec] = {k: rel_l2(g.read(gf).astype(np.float64), ref20[k]) for k, gf, _ in fields}
-        g.step(4980)
-        at5000[prec] = {k: g.read(gf).astype(np.float64) for k, gf, _ in fields}
-        D[prec] = warmstart.deformation(g.read(vefd.PHI)[nz // 2].astype(np.float64))
-        mass[prec] = float(np.max(np.abs(g.diagnostics()[:2] / m0 - 1)))
+        g.step(5000)
+        full = np.concatenate([g.read(vefd.RHO_A)[None], g.read(vefd.RHO_B)[None], g.read(vefd.U),
+                               g.read(vefd.C)]).astype(np.float64)
+        d = g.diagnostics()
         assert g.status() == 0
         g.close()
-    oracle_bound = {0: 1e-5, 1: 5e-3, 2: 5e-2}
-    fp32_bound = {1: dict(rhoA=5e-2, u=2e-2, C=1e-2), 2: dict(rhoA=3e-1, u=2e-1, C=1e-1)}
-    d_bound = {1: 0.06, 2: 0.15}
-    rows = []
-    for prec in (0, 1, 2):
-        for k, v in vs_oracle[prec].items():
-            assert v < oracle_bound[prec], (prec, k, v)
-        vs32 = {k: rel_l2(at5000[prec][k], at5000[0][k]) for k in at5000[prec]}
-        if prec:
-            for k, v in vs32.items():
-                assert v < fp32_bound[prec][k], (prec, k, v)
-            assert abs(D[prec] - D[0]) / D[0] < d_bound[prec]
-        assert mass[prec] < 1e-6
-        rows.append((("fp32", "fp16", "bf16")[prec], vs_oracle[prec], vs32, D[prec], mass[prec]))
+        zg, yg = full[:, nz // 2], full[:, :, ny // 2]
+        err = {}
+        for name, sl in rows.items():
+            a = np.concatenate([zg[sl].ravel(), yg[sl].ravel()])
+            b = np.concatenate([zref[sl].ravel(), yref[sl].ravel()])
+            err[name] = rel_l2(a, b)
+        cg = np.concatenate([(zg[5:11] - eye).ravel(), (yg[5:11] - eye).ravel()])
+        co = np.concatenate([(zref[5:11] - eye).ravel(), (yref[5:11] - eye).ravel()])
+        err["CmI"] = rel_l2(cg, co)
+        err["D"] = abs(d[10] - ref["diag"][10]) / ref["diag"][10]
+        err["mass"] = float(np.max(np.abs(d[:2] / m0 - 1)))
+        table.append((("fp32", "fp16", "bf16")[prec], err, d[10]))
     with capsys.disabled():
-        print("\nstorage  vs oracle @20: rhoA / u / C        vs FP32 @5000: rhoA / u / C      D @5000   mass")
-        for name, vo, v32, d, m in rows:
-            print("%-8s %8.1e %8.1e %8.1e      %8.1e %8.1e %8.1e   %.4f   %.1e" % (
-                name, vo["rhoA"], vo["u"], vo["C"], v32["rhoA"], v32["u"], v32["C"], d, m))
+        print("\nvs FP64 oracle after 5000 steps, 256x128x256 (oracle D = %.5f)" % ref["diag"][10])
+        print("storage  " + "  ".join("%8s" % k for k in ("rhoA", "rhoB", "u", "C", "C-I", "D", "mass")) + "   D")
+        for name, e, dval in table:
+            print("%-8s " % name + "  ".join("%8.2e" % e[k] for k in ("rhoA", "rhoB", "u", "C", "CmI", "D", "mass"))
+                  + "   %.5f" % dval)
+    for prec, (name, e, _) in enumerate(table):
+        for k, bound in REF256_BOUNDS[prec].items():
+            assert e[k] < bound, (name, k, e[k])
+        assert e["mass"] < 1e-6, (name, e["mass"])
 
 
 class PrecPair(Pair):
