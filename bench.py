@@ -113,6 +113,8 @@ def parse():
     ap.add_argument("--ws-eval", type=int, default=12, help="held-out set-ups for --warmstart")
     ap.add_argument("--ws-epochs", type=int, default=60)
     ap.add_argument("--ws-lr", type=float, default=5e-4)
+    ap.add_argument("--ws-blend", type=float, default=0.5,
+                    help="scale of the predicted increments over the cold start (1: the prediction as it is)")
     ap.add_argument("--ws-channels", default="16,32,80,152",
                     help="U-Net channels per level (multiples of 8; 16,32,80,152 = 2.07 M parameters)")
     ap.add_argument("--ws-tol", type=float, default=2e-6)
@@ -669,7 +671,7 @@ def run_ours(args):
     if not args.no_warmstart and S.prec == 0:
         # bounded form of --warmstart: 48 training set-ups, 40 epochs, 8 held out
         line["warmstart"] = warmstart_measure(48, 8, 40, args.ws_lr, args.ws_tol,
-                                              tuple(int(v) for v in args.ws_channels.split(",")))
+                                              tuple(int(v) for v in args.ws_channels.split(",")), args.ws_blend)
     if not args.no_ensemble and S.prec == 0:
         line["ensemble"] = time_ensemble(max(100, K // 20), min(W, 20))
         line["ensemble_small"] = time_ensemble(max(100, K // 20), min(W, 20), setups=small_setups(),
@@ -682,7 +684,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def warmstart_measure(n_train, n_eval, epochs, lr, tol, channels=(16, 32, 80, 152), log=None):
+def warmstart_measure(n_train, n_eval, epochs, lr, tol, channels=(16, 32, 80, 152), blend=0.5, log=None):
     """Time to steady deformation of held-out droplet set-ups, cold start
     versus a start from the trained network's prediction: data from the
     method's own steady states, training and prediction on this package's
@@ -701,7 +703,7 @@ def warmstart_measure(n_train, n_eval, epochs, lr, tol, channels=(16, 32, 80, 15
     losses = ws.train(net, X, Y, epochs=epochs, lr=lr, log=log)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    res = ws.evaluate(net, eval_setups, tol=tol, log=log)
+    res = ws.evaluate(net, eval_setups, tol=tol, log=log, blend=blend)
     cold = np.array([r["cold_seconds"] for r in res])
     warm = np.array([r["warm_seconds"] for r in res])
     derr = np.array([r["D_rel_err"] for r in res])
@@ -715,6 +717,7 @@ def warmstart_measure(n_train, n_eval, epochs, lr, tol, channels=(16, 32, 80, 15
                    "eval_setups": len(eval_setups), "steady_rule": "|dD| < %g per tau_em over 5 consecutive tau_em "
                    "(mid-plane, smooth indicator)" % tol, "network": "3-D U-Net, %d parameters, BF16 tcgen05 GEMMs, "
                    "FP32 accumulate" % net.n_params(), "channels": list(channels), "epochs": epochs, "lr": lr,
+                   "blend": blend,
                    "lr_schedule": "linear ramp from lr/10 over the first epoch, then geometric decay to lr/10"},
         "steps": {"cold_median": int(np.median([r["cold_steps"] for r in res])),
                   "warm_median": int(np.median([r["warm_steps"] for r in res]))},
@@ -735,7 +738,8 @@ def run_warmstart(args):
     torch.cuda.set_device(0)
     log = (lambda m: print(m, file=sys.stderr, flush=True))
     chans = tuple(int(v) for v in args.ws_channels.split(","))
-    line = warmstart_measure(args.ws_train, args.ws_eval, args.ws_epochs, args.ws_lr, args.ws_tol, chans, log=log)
+    line = warmstart_measure(args.ws_train, args.ws_eval, args.ws_epochs, args.ws_lr, args.ws_tol, chans,
+                             args.ws_blend, log=log)
     line.update({"n_gpus": 1, "data": "synthetic (steady states generated by the lattice-Boltzmann/FENE-P step)"})
     print(json.dumps(line), flush=True)
 

@@ -222,16 +222,20 @@ def train(net, X, Y, epochs=30, lr=1e-3, seed=0, log=None, warmup=1):
     return losses
 
 
-def warm_lattice(net, setup, phi0_dev):
+def warm_lattice(net, setup, phi0_dev, blend=1.0):
     """A lattice started from the network's prediction, built on the device:
     input assembly (host, cheap), network, field conversion, init_fields.
-    Each component's density field is rescaled to the set-up's mass (that of
-    the initial droplet): the step conserves the masses, so they, not the
+    The predicted increments over the cold start (phi - phi0, u, C - I) are
+    scaled by `blend` (1: the prediction, 0: the cold start).  Each
+    component's density field is rescaled to the set-up's mass (that of the
+    initial droplet): the step conserves the masses, so they, not the
     prediction, decide the droplet size."""
     import torch
     phi0 = phi0_dev.cpu().numpy()
     x = torch.from_numpy(net_input(setup, phi0)[None]).cuda().contiguous()
     out = net.forward(x)[0]
+    if blend != 1.0:
+        nn.scale(out, blend)
     rA, rB, u, C = nn.to_fields(out, phi0_dev, setup.u_wall, C_SCALE, RHO_TOT, L2)
     mA = 0.5 * RHO_TOT * float(np.sum(1.0 + phi0.astype(np.float64)))
     mB = 0.5 * RHO_TOT * float(np.sum(1.0 - phi0.astype(np.float64)))
@@ -242,9 +246,10 @@ def warm_lattice(net, setup, phi0_dev):
     return lat
 
 
-def evaluate(net, setups, tol=1e-5, max_steps=80000, log=None):
+def evaluate(net, setups, tol=1e-5, max_steps=80000, log=None, blend=1.0):
     """Cold and warm runs of every set-up to steady state; per set-up the
-    steps, seconds (warm: including the network prediction) and D of both."""
+    steps, seconds (warm: including the network prediction) and D of both
+    (`blend` as in warm_lattice)."""
     import torch
     res = []
     for i, s in enumerate(setups):
@@ -254,7 +259,7 @@ def evaluate(net, setups, tol=1e-5, max_steps=80000, log=None):
         cold.close()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        warm = warm_lattice(net, s, phi0)
+        warm = warm_lattice(net, s, phi0, blend)
         torch.cuda.synchronize()
         t_pred = time.perf_counter() - t0
         w_steps, w_d, w_sec, w_conv = run_to_steady(s, warm, tol, max_steps)
