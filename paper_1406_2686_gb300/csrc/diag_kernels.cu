@@ -8,6 +8,8 @@
 // sigma_P,xy, sigma_P,xx - sigma_P,yy, tr sigma_P - 3, droplet volume, and the
 // zeroth to second moments of the indicator phi > 0 in the plane z = NZ/2
 // (semi-axes and orientation follow on the host); maxima: tr C / L^2 and |u|.
+#include <cmath>
+
 #include "vefd_internal.cuh"
 
 namespace vefd {
@@ -146,16 +148,20 @@ __global__ void __launch_bounds__(256) k_diag_partial(const float* __restrict__ 
     }
 }
 
+// One warp per value: lane l combines rows l, l + 32, l + 64, ... in index
+// order, then the lanes are combined by a fixed shuffle tree, so the result
+// does not depend on scheduling.
 __global__ void k_diag_final(const double* __restrict__ partial, int nrows, double* __restrict__ out) {
-    // one thread per value, rows summed in index order
-    const int k = threadIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= kDiagVals) return;
-    double v = partial[k];
-    for (int r = 1; r < nrows; ++r) {
+    const bool sum = k < kDiagSums;
+    double v = sum ? 0.0 : -INFINITY;
+    for (int r = lane; r < nrows; r += 32) {
         const double t = partial[r * kDiagVals + k];
-        v = k < kDiagSums ? v + t : fmax(v, t);
+        v = sum ? v + t : fmax(v, t);
     }
-    out[k] = v;
+    v = sum ? warp_sum(v) : warp_max(v);
+    if (lane == 0) out[k] = v;
 }
 
 // Initial densities: FP64 sums of rho_A and rho_B and the count of values
@@ -189,12 +195,14 @@ __global__ void __launch_bounds__(256) k_density_sums(const float* __restrict__ 
     }
 }
 
+// One warp per value, as k_diag_final.
 __global__ void k_density_final(const double* __restrict__ partial, int nrows, double* __restrict__ out) {
-    const int k = threadIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= 3) return;
-    double v = partial[k];
-    for (int r = 1; r < nrows; ++r) v += partial[r * 3 + k];
-    out[k] = v;
+    double v = 0.0;
+    for (int r = lane; r < nrows; r += 32) v += partial[r * 3 + k];
+    v = warp_sum(v);
+    if (lane == 0) out[k] = v;
 }
 
 }  // namespace
@@ -205,7 +213,7 @@ cudaError_t launch_density_sums(const float* rho_A, const float* rho_B, long lon
     if (blocks > kDiagBlocks) blocks = kDiagBlocks;
     if (blocks < 1) blocks = 1;
     k_density_sums<<<(int)blocks, 256, 0, s>>>(rho_A, rho_B, N, partial);
-    k_density_final<<<1, 32, 0, s>>>(partial, (int)blocks, out);
+    k_density_final<<<1, 3 * 32, 0, s>>>(partial, (int)blocks, out);
     return cudaGetLastError();
 }
 
@@ -231,7 +239,7 @@ cudaError_t launch_diagnostics(int lattice, int ncomp, const StepParams& p, cons
     if (blocks < 1) blocks = 1;
     if (lattice == 1) k_diag_partial<3, 6><<<(int)blocks, 256, 0, s>>>(drho, u, Ct, ncomp, partial, p);
     else k_diag_partial<2, 4><<<(int)blocks, 256, 0, s>>>(drho, u, Ct, ncomp, partial, p);
-    k_diag_final<<<1, 32, 0, s>>>(partial, (int)blocks, out);
+    k_diag_final<<<1, kDiagVals * 32, 0, s>>>(partial, (int)blocks, out);
     return cudaGetLastError();
 }
 

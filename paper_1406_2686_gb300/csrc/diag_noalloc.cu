@@ -118,16 +118,19 @@ __global__ void __launch_bounds__(kThreads) k_diag_rows_abs(const float* __restr
     }
 }
 
-// Sums the rows in index order into the result row kNoallocRows.
+// Combines the rows into the result row kNoallocRows: one warp per value,
+// lane l taking rows l, l + 32, ... in index order, then a fixed shuffle tree.
 __global__ void k_diag_rows_final(double* __restrict__ rows, int nrows) {
-    const int k = threadIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= kDiagVals) return;
-    double v = rows[k];
-    for (int r = 1; r < nrows; ++r) {
+    const bool sum = k < kDiagSums;
+    double v = sum ? 0.0 : -INFINITY;
+    for (int r = lane; r < nrows; r += 32) {
         const double t = rows[(long long)r * kDiagVals + k];
-        v = k < kDiagSums ? v + t : fmax(v, t);
+        v = sum ? v + t : fmax(v, t);
     }
-    rows[(long long)kNoallocRows * kDiagVals + k] = v;
+    v = sum ? wsum(v) : wmax(v);
+    if (lane == 0) rows[(long long)kNoallocRows * kDiagVals + k] = v;
 }
 
 std::mutex g_setup_mutex;
@@ -227,7 +230,7 @@ extern "C" vefd_status vefd_diagnostics_noalloc(int lattice, int nx, int ny, int
         k_diag_rows_abs<3, 6><<<nblocks, kThreads, 0, s>>>(rho_A, rB, u, C, nx, ny, nz, L2, rows);
     else
         k_diag_rows_abs<2, 4><<<nblocks, kThreads, 0, s>>>(rho_A, rB, u, C, nx, ny, nz, L2, rows);
-    k_diag_rows_final<<<1, 32, 0, s>>>(rows, nblocks);
+    k_diag_rows_final<<<1, kDiagVals * 32, 0, s>>>(rows, nblocks);
     if (cudaGetLastError() != cudaSuccess) return VEFD_ERR_CUDA;
     double v[kDiagVals];
     if (cudaMemcpyAsync(v, rows + (size_t)kNoallocRows * kDiagVals, sizeof v, cudaMemcpyDeviceToHost, s) !=

@@ -311,7 +311,8 @@ vefd_status macro_pass(vefd_ctx* c, bool with_dbg) {
     StepParams p = params_of(c);
     StepBufs b = bufs_of(c);
     b.dbg = with_dbg ? c->dbg : nullptr;
-    VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
+    // densities and feedback stress of the current state (kept by the step when current)
+    if (!c->drho_valid) VEFD_CUDA(c, launch_pre(c->cfg.lattice, c->cfg.ncomp, p, b, c->stream));
     VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, false, p, b, c->stream, nullptr, 0, 0));
     c->drho_valid = true;
     return VEFD_OK;
