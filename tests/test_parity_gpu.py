@@ -737,3 +737,76 @@ def test_precision_error_report(capsys):
         print("\nstorage  " + "  ".join("%8s" % k for k in ("rhoA", "rhoB", "phi", "u", "C", "mass")))
         for name, e in rows:
             print("%-8s " % name + "  ".join("%8.2e" % e[k] for k in ("rhoA", "rhoB", "phi", "u", "C", "mass")))
+
+
+@pytest.mark.slow
+def test_newtonian_droplet_deformation_shapira_haber(capsys):
+    """Physics check of the whole GPU path (not parity): a Newtonian droplet
+    of viscosity ratio 1 in the confined shear flow of Sec. 4.1 (the benchmark
+    geometry, R = 16, 2R/H = 0.5).  The droplet first relaxes at rest; its
+    surface tension follows from the Laplace law, sigma = R (P_in - P_out) / 2
+    with the bulk pressure of Eq. PTexpanded and R from the droplet volume.
+    The sheared run starts from that relaxed state with the Couette profile
+    imposed (the channel's own spin-up, H^2 / nu = 24576 steps, would let the
+    droplet dissolve noticeably into the matrix meanwhile), at the wall speed
+    that sets Ca = 0.1 for the measured sigma.  After 100 emulsion times the
+    steady deformation of the shear plane exceeds Taylor's unconfined value
+    and lies within 30 % of the confined prediction of Shapira and Haber
+    quoted in Sec. 4.1 (D = 0.1264 at Ca = 0.1, lambda = 1, R/H = 0.25),
+    evaluated at the droplet's size then.  Measured: D = 0.150 against 0.120
+    (sigma = 0.099 from the Laplace law, 10 % above the 0.09 of Sec. 4.1; the
+    interface is about 5 nodes wide at R = 16, so both sigma and the moment
+    measure of D carry errors of this order).  The bound catches a wrong
+    shear direction, a missing or doubled force term or a wrong viscosity,
+    not the last ten per cent."""
+    from paper_1406_2686_gb300 import vefd
+    nx, ny, nz, R = 128, 64, 128, 16.0
+    eta = 2.1 / 3.0 * 0.5
+
+    def lattice():
+        g = vefd.Lattice(lattice=1, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=eta, eta_B=eta)
+        g.set_fenep(100.0, 0.0, 100.0, 0.0, 0, 0)
+        return g
+
+    rest = lattice()
+    rest.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, R, 2.0, 0.1, 5.0, 3, 0.0)
+    rest.step(3000)
+    rA, rB = rest.read(vefd.RHO_A), rest.read(vefd.RHO_B)
+    d = rest.diagnostics()
+    rest.close()
+    p = cf.bulk_pressure(rA.astype(np.float64), rB.astype(np.float64), 1.5)
+    c = (nz // 2, ny // 2, nx // 2)
+    p_in = float(np.mean(p[c[0] - 2:c[0] + 2, c[1] - 2:c[1] + 2, c[2] - 2:c[2] + 2]))
+    p_out = float(np.mean(p[:6, ny // 2 - 2:ny // 2 + 2, :6]))
+    R_eff = (3.0 * d[14] / (4.0 * math.pi)) ** (1.0 / 3.0)
+    sigma = 0.5 * R_eff * (p_in - p_out)
+    gdot = 0.1 * sigma / (R_eff * eta)
+    tau_em = R_eff * eta / sigma
+    g = lattice()
+    u_wall = gdot * ny / 2
+    u = np.zeros((3, nz, ny, nx), np.float32)
+    u[0] = cf.couette_profile(ny, u_wall)[None, :, None]
+    g.set_wall_shear(u_wall)
+    g.init_fields(rA, rB, u)
+    nsamp, every = 20, int(5 * tau_em)
+    hist, vol = [], []
+    for _ in range(nsamp):
+        g.step(every)
+        dg = g.diagnostics()
+        hist.append(dg[10])
+        vol.append(dg[14])
+    assert g.status() == 0
+    g.close()
+    last = np.array(hist[-8:])
+    D = float(last.mean())
+    R_end = (3.0 * float(np.mean(vol[-8:])) / (4.0 * math.pi)) ** (1.0 / 3.0)
+    Ca_end = gdot * R_end * eta / sigma
+    D_sh = cf.shapira_haber_D(Ca_end, 1.0, R_end / ny)
+    with capsys.disabled():
+        print("\nLaplace: sigma %.4f (R %.2f, tau_em %.0f steps); D every %d steps %s; D %.4f +- %.4f; R_end %.2f, "
+              "Ca_end %.4f; Shapira-Haber %.4f, Taylor %.4f"
+              % (sigma, R_eff, tau_em, every, " ".join("%.4f" % v for v in hist), D, last.std(), R_end, Ca_end, D_sh,
+                 cf.taylor_D(Ca_end, 1.0)))
+    assert last.std() < 0.03 * D                         # steady up to the pixel noise
+    assert abs(D / D_sh - 1) < 0.30, (D, D_sh)
+    assert D > cf.taylor_D(Ca_end, 1.0)
