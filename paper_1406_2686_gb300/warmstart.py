@@ -120,12 +120,40 @@ def deformation(phi_plane):
     return (a - b) / (a + b)
 
 
-def run_to_steady(setup, lat, tol=1e-5, max_steps=80000, hold=5):
-    """Steps `lat` in chunks of one emulsion time until D has changed by less
-    than tol in each of `hold` consecutive chunks (a single quiet chunk can be
-    the turning point of an overshoot).  Returns (steps, D, seconds, converged)."""
+STEP_QUANTUM = 50  # the check interval of the steady rule is a multiple of this
+
+
+def check_interval(setup):
+    """Steps between two checks of the steady rule: the emulsion time, rounded
+    to a multiple of STEP_QUANTUM (at least one quantum)."""
+    return STEP_QUANTUM * max(1, int(round(setup.tau_em / STEP_QUANTUM)))
+
+
+def deformation_device(phi_plane):
+    """deformation() of a device tensor [ny, nx] (FP64 moments on the device)."""
     import torch
-    chunk = max(50, int(round(setup.tau_em)))
+    w = torch.clamp(0.5 * (1.0 + phi_plane.double() / 0.9), 0.0, 1.0)
+    ny, nx = w.shape
+    y = torch.arange(ny, device=w.device, dtype=torch.float64)[:, None]
+    x = torch.arange(nx, device=w.device, dtype=torch.float64)[None, :]
+    m = w.sum()
+    cx, cy = (w * x).sum() / m, (w * y).sum() / m
+    ixx = (w * (x - cx) ** 2).sum() / m
+    iyy = (w * (y - cy) ** 2).sum() / m
+    ixy = (w * (x - cx) * (y - cy)).sum() / m
+    tr, det = ixx + iyy, ixx * iyy - ixy * ixy
+    disc = torch.sqrt(torch.clamp(0.25 * tr * tr - det, min=0.0))
+    a, b = torch.sqrt(0.5 * tr + disc), torch.sqrt(torch.clamp(0.5 * tr - disc, min=0.0))
+    return float((a - b) / (a + b))
+
+
+def run_to_steady(setup, lat, tol=1e-5, max_steps=80000, hold=5):
+    """Steps `lat` in chunks of about one emulsion time (check_interval) until
+    D has changed by less than tol in each of `hold` consecutive chunks (a
+    single quiet chunk can be the turning point of an overshoot).  Returns
+    (steps, D, seconds, converged)."""
+    import torch
+    chunk = check_interval(setup)
     zc = setup.N // 2
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -190,6 +218,66 @@ def make_dataset(setups, tol=1e-5, max_steps=80000, log=None):
             log("sample %d: Ca %.3f De %.2f 2R/H %.2f lambda %.2f phase %+d -> %d steps, D %.4f%s" %
                 (i, s.Ca, s.De, s.conf, s.lam, s.phase, steps, d, "" if conv else " (cap)"))
         lat.close()
+    return np.stack(X), np.stack(Y), rec
+
+
+def make_dataset_ensemble(setups, tol=1e-5, max_steps=80000, group=32, hold=5, seed0=100, log=None):
+    """make_dataset with the set-ups stepped together as ensembles of up to
+    `group` lattices (vefd.Ensemble: one replayed graph per STEP_QUANTUM steps
+    for all of them).  Each member follows the steady rule of run_to_steady on
+    its own check interval; converged members (and those at max_steps) leave,
+    and the next set-ups join.  Same seeds and the same fields as
+    make_dataset up to the floating-point order of the ensemble kernels."""
+    import torch
+    n = len(setups)
+    X, Y = [None] * n, [None] * n
+    rec = [None] * n
+    pending = list(range(n))
+    active = []  # [index, lattice, phi0, steps, d_prev, quiet]
+    t0 = time.perf_counter()
+    E = None
+    while pending or active:
+        changed = False
+        while pending and len(active) < group:
+            i = pending.pop(0)
+            lat = setups[i].cold(seed=seed0 + i)
+            active.append([i, lat, lat.read(vefd.PHI), 0, None, 0])
+            changed = True
+        if changed or E is None:
+            if E is not None:
+                E.close()
+            E = vefd.Ensemble([a[1] for a in active])
+        E.step(STEP_QUANTUM, chunk=STEP_QUANTUM)
+        done = []
+        for a in active:
+            i, lat = a[0], a[1]
+            s = setups[i]
+            a[3] += STEP_QUANTUM
+            if a[3] % check_interval(s):
+                continue
+            d = deformation_device(lat.read(vefd.PHI, device=True)[s.dims[2] // 2])
+            a[5] = a[5] + 1 if (a[4] is not None and abs(d - a[4]) < tol) else 0
+            a[4] = d
+            if a[5] >= hold or a[3] >= max_steps:
+                phi, u, C = fields(lat)
+                X[i] = net_input(s, a[2])
+                Y[i] = net_target(s, a[2], phi, u, C)
+                rec[i] = dict(steps=a[3], D=d, seconds=None, converged=a[5] >= hold)
+                done.append(a)
+                if log:
+                    log("sample %d: Ca %.3f De %.2f 2R/H %.2f lambda %.2f phase %+d -> %d steps, D %.4f%s" %
+                        (i, s.Ca, s.De, s.conf, s.lam, s.phase, a[3], d, "" if a[5] >= hold else " (cap)"))
+        if done:
+            E.close()
+            E = None
+            for a in done:
+                active.remove(a)
+                a[1].close()
+    if E is not None:
+        E.close()
+    torch.cuda.synchronize()
+    if log:
+        log("ensemble dataset: %d set-ups in %.1f s" % (n, time.perf_counter() - t0))
     return np.stack(X), np.stack(Y), rec
 
 
