@@ -2,16 +2,17 @@
 //   C[M x N] (FP32) = A[M x K] (BF16) * B[N x K]^T (BF16)  (+ C when accumulate)
 // A and B are K-major (row-major with K contiguous).
 //
-// k_gemm_tma (vefd_nn_gemm_bf16 and its split-K form): every CTA owns one
-// 128 x BN tile of C (BN = 32, 64, 128 or 256) and walks K in chunks of 64
-// through a ring of kStages shared-memory stages.  One thread issues the bulk
-// tensor copies of both operand chunks (TMA, 128-byte swizzle, zero fill
-// beyond the matrices) into a free stage; another issues the four
-// tcgen05.mma (M = 128, N = BN, K = 16 each, BF16 inputs, FP32 accumulator in
-// tensor memory) of each loaded stage and commits them to the stage's "empty"
-// barrier, which frees the stage for the copy kStages chunks later.  Copies
-// and matrix operations thus overlap.  After the last commit the four warps
-// read their 32 accumulator lanes with tcgen05.ld and store C.
+// k_gemm_tma (vefd_nn_gemm_bf16 and its split-K form): a persistent grid of at
+// most one CTA per SM walks the 128 x BN tiles of C (BN = 32, 64, 128 or 256;
+// split-K slices are further tiles), K in chunks of 64 through a ring of
+// kStages shared-memory stages.  One thread issues the bulk tensor copies of
+// both operand chunks (TMA, 128-byte swizzle, zero fill beyond the matrices)
+// into a free stage; another issues the four tcgen05.mma (M = 128, N = BN,
+// K = 16 each, BF16 inputs, FP32 accumulator in tensor memory) of each loaded
+// stage and commits them to the stage's "empty" barrier, which frees the
+// stage for the copy kStages chunks later.  Two accumulators alternate
+// between tiles, so four epilogue warps read one tile's accumulator with
+// tcgen05.ld and store C while the next tile's matrix operations run.
 //
 // k_gemm_bf16 (vefd_nn_gemm_bf16_layout only): the threads copy both tiles into
 // the no-swizzle K-major core-matrix layout with plain loads, one chunk at a
@@ -212,32 +213,53 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* tm,
         : "memory");
 }
 
+// Persistent form: a grid of at most one CTA per SM walks the output tiles
+// (tile = blockIdx.x + j * gridDim.x; split-K slices are further tiles) with
+// two tensor-memory accumulators, so that the epilogue of tile j overlaps the
+// main loop of tile j + 1.  Warp roles (192 threads):
+//   warp 0, one thread: bulk tensor copies of both operand chunks into the
+//     ring of kStages stages, each stage reused once the matrix operations of
+//     the chunk kStages earlier have released it (barrier "empty");
+//   warp 1, one thread: waits for each loaded stage ("full"), issues its four
+//     tcgen05.mma into accumulator j % 2, commits them to the stage's "empty"
+//     barrier, and after the tile's last chunk commits to "acc_full[j % 2]";
+//     before the first chunk of tile j (j >= 2) it waits for "acc_empty",
+//     which the epilogue arrives on once it has read that accumulator;
+//   warps 2-5: the epilogue; warp w reads tensor-memory lanes 32 (w % 4) ...
+//     (its lane quarter), i.e. rows 32 (w % 4) + lane of the tile.
+// Every wait is bounded; a timeout sets the status bit and an abort flag that
+// the other roles see at their next wait; the block then waits (bounded) for
+// its copies and matrix operations in flight before freeing tensor memory.
+constexpr int kPersistThreads = 192;
+
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kPersistThreads, 1)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                float* __restrict__ C, int ldc, int M, int N, int K, int accumulate, int k_split,
                long long c_split_stride, unsigned* __restrict__ status) {
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "tcgen05 M = 128 needs N in [16, 256], a multiple of 16");
-    constexpr unsigned kTmemCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    constexpr unsigned kAccCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    constexpr unsigned kTmemCols = 2 * kAccCols;  // two accumulators
     constexpr unsigned kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2, kStageBytes = kABytes + kBBytes;
     extern __shared__ unsigned char dsm[];
-    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2];
     __shared__ unsigned tmem_base;
     __shared__ int abort_flag;
-    // stages [A | B] at 1024-byte boundaries (the swizzle atom)
-    const unsigned base = (smem_addr(dsm) + 1023u) & ~1023u;
+    const unsigned base = (smem_addr(dsm) + 1023u) & ~1023u;  // stages at the 1024-byte swizzle atom
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    // split K: block z reduces K range [kb, ke) into its own slice of C
-    const int kb = blockIdx.z * k_split, ke = min(K, kb + k_split);
-    C += blockIdx.z * c_split_stride;
-    const int nk = (ke - kb + kBK - 1) / kBK;
+    const int tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + BN - 1) / BN;
+    const int splits = (K + k_split - 1) / k_split;
+    const int ntiles = tiles_m * tiles_n * splits;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init1(smem_addr(&full[s]));
             mbar_init1(smem_addr(&empty[s]));
         }
-        mbar_init1(smem_addr(&done));
+        for (int a = 0; a < 2; ++a) {
+            mbar_init1(smem_addr(&acc_full[a]));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_addr(&acc_empty[a])) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
     if (warp == 0) {
@@ -250,95 +272,151 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
+    volatile int* abortp = &abort_flag;
+    auto tile_coords = [&](int t, int& m0, int& n0, int& kb, int& ke) {
+        const int mt = t % tiles_m, r = t / tiles_m;
+        m0 = mt * kBM;
+        n0 = (r % tiles_n) * BN;
+        kb = (r / tiles_n) * k_split;
+        ke = min(K, kb + k_split);
+    };
+    bool failed = false;
     if (threadIdx.x == 0) {
-        // producer: chunk kt into stage kt % kStages once the matrix operations
-        // of chunk kt - kStages have released it
-        int issued = 0;
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % kStages;
-            if (kt >= kStages && !mbar_wait(smem_addr(&empty[s]), (unsigned)((kt / kStages - 1) & 1))) {
-                abort_flag = 1;
-                break;
+        // producer
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+            int m0, n0, kb, ke;
+            tile_coords(t, m0, n0, kb, ke);
+            const int nk = (ke - kb + kBK - 1) / kBK;
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                const int s = it % kStages;
+                if (it >= kStages && !mbar_wait(smem_addr(&empty[s]), (unsigned)((it / kStages - 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                if (*abortp) {
+                    failed = true;
+                    break;
+                }
+                const unsigned fb = smem_addr(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStageBytes)
+                             : "memory");
+                const unsigned sa = base + (unsigned)s * kStageBytes;
+                tma_load_2d(sa, &tmA, kb + kt * kBK, m0, fb);
+                tma_load_2d(sa + kABytes, &tmB, kb + kt * kBK, n0, fb);
             }
-            if (*(volatile int*)&abort_flag) break;
-            const unsigned fb = smem_addr(&full[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStageBytes)
-                         : "memory");
-            const unsigned sa = base + (unsigned)s * kStageBytes;
-            tma_load_2d(sa, &tmA, kb + kt * kBK, m0, fb);
-            tma_load_2d(sa + kABytes, &tmB, kb + kt * kBK, n0, fb);
-            issued = kt + 1;
         }
-        // bounded: the copies in flight land before the block can leave
-        for (int kt = issued - kStages > 0 ? issued - kStages : 0; kt < issued; ++kt)
-            mbar_wait(smem_addr(&full[kt % kStages]), (unsigned)((kt / kStages) & 1));
+        if (failed) *abortp = 1;
+        // bounded: the copies in flight (the last kStages issued) land before the block leaves
+        for (int q = it > kStages ? it - kStages : 0; q < it; ++q)
+            mbar_wait(smem_addr(&full[q % kStages]), (unsigned)((q / kStages) & 1));
     } else if (threadIdx.x == 32) {
-        // matrix operations of each loaded chunk, committed to its stage's empty barrier
+        // matrix operations
         constexpr uint32_t idesc = instr_desc(kBM, BN);
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % kStages;
-            if (!mbar_wait(smem_addr(&full[s]), (unsigned)((kt / kStages) & 1))) {
-                abort_flag = 1;
+        int it = 0, j = 0;
+        for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x, ++j) {
+            int m0, n0, kb, ke;
+            tile_coords(t, m0, n0, kb, ke);
+            const int nk = (ke - kb + kBK - 1) / kBK;
+            const int acc = j & 1;
+            // the epilogue has read this accumulator's previous tile
+            if (j >= 2 && !mbar_wait(smem_addr(&acc_empty[acc]), (unsigned)((j / 2 - 1) & 1))) {
+                failed = true;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned sa = base + (unsigned)s * kStageBytes;
+            const unsigned dcol = tmem + (unsigned)acc * kAccCols;
+            for (int kt = 0; kt < nk; ++kt, ++it) {
+                const int s = it % kStages;
+                if (!mbar_wait(smem_addr(&full[s]), (unsigned)((it / kStages) & 1)) || *abortp) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned sa = base + (unsigned)s * kStageBytes;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(sa + kk * 32);
-                const uint64_t bd = smem_desc_sw128(sa + kABytes + kk * 32);
-                const unsigned acc = (kt > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+                    const uint64_t bd = smem_desc_sw128(sa + kABytes + kk * 32);
+                    const unsigned accum = (kt > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_addr(&empty[s]))
+                             : "memory");
             }
+            if (failed) break;
+            // arrives once the tile's matrix operations have completed
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&empty[s]))
+                             smem_addr(&acc_full[acc]))
                          : "memory");
         }
-        // arrives once every matrix operation issued above has completed
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_addr(&done))
-                     : "memory");
-    }
-    const bool finished = nk == 0 || mbar_wait(smem_addr(&done), 0u);
-    const bool ok = !__syncthreads_or(!finished || abort_flag != 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && nk > 0) {
-        // accumulator row 32 * warp + lane, 16 columns per load
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t v[16];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(taddr)
-                : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
-                float* c = C + (size_t)row * ldc + n0 + c0;
-                if (n0 + c0 + 16 <= N && !accumulate && ((reinterpret_cast<uintptr_t>(c) & 15u) == 0)) {
+        if (failed) {
+            *abortp = 1;
+            // bounded: every matrix operation issued has completed before tensor memory is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&acc_full[j & 1]))
+                         : "memory");
+            mbar_wait(smem_addr(&acc_full[j & 1]), (unsigned)((j / 2) & 1));
+        }
+    } else if (warp >= 2) {
+        // epilogue: lane quarter of this warp
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int acc = j & 1;
+            // warp-uniform decision: the tensor-memory loads below need all 32 lanes
+            const bool ready = mbar_wait(smem_addr(&acc_full[acc]), (unsigned)((j / 2) & 1)) && !*abortp;
+            if (!__all_sync(0xffffffffu, ready)) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int m0, n0, kb, ke;
+            tile_coords(t, m0, n0, kb, ke);
+            float* Ct = C + (long long)(kb / k_split) * c_split_stride;
+            const int row = m0 + q * 32 + lane;
+            const unsigned tbase = tmem + ((unsigned)(q * 32) << 16) + (unsigned)acc * kAccCols;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(tbase + (unsigned)c0)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < M) {
+                    float* c = Ct + (size_t)row * ldc + n0 + c0;
+                    if (n0 + c0 + 16 <= N && !accumulate && ((reinterpret_cast<uintptr_t>(c) & 15u) == 0)) {
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4*>(c + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                                                        __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-                } else {
+                        for (int jj = 0; jj < 16; jj += 4)
+                            *reinterpret_cast<float4*>(c + jj) =
+                                make_float4(__uint_as_float(v[jj]), __uint_as_float(v[jj + 1]),
+                                            __uint_as_float(v[jj + 2]), __uint_as_float(v[jj + 3]));
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (n0 + c0 + j < N) c[j] = accumulate ? c[j] + __uint_as_float(v[j]) : __uint_as_float(v[j]);
+                        for (int jj = 0; jj < 16; ++jj)
+                            if (n0 + c0 + jj < N)
+                                c[jj] = accumulate ? c[jj] + __uint_as_float(v[jj]) : __uint_as_float(v[jj]);
+                    }
                 }
             }
+            // this warp has read its lanes of the accumulator
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&acc_empty[acc])) : "memory");
         }
-    } else if (!ok && threadIdx.x == 0) {
-        atomicOr(status, kStatusTimeout);
+        if (failed) *abortp = 1;
     }
-    if (!ok && threadIdx.x == 32 && nk > 0) mbar_wait(smem_addr(&done), 0u);  // bounded: matrix operations first
+    __syncwarp();
+    if (failed && lane == 0) atomicOr(status, kStatusTimeout);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -422,9 +500,17 @@ cudaError_t launch_tma_bn(const CUtensorMap& ta, const CUtensorMap& tb, float* C
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int splits = (K + k_split - 1) / k_split;
-    dim3 grd((M + kBM - 1) / kBM, (N + BN - 1) / BN, splits);
-    k_gemm_tma<BN><<<grd, kThreads, smem, s>>>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride, status);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+    }
+    const long long tiles = (long long)((M + kBM - 1) / kBM) * ((N + BN - 1) / BN) * ((K + k_split - 1) / k_split);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    k_gemm_tma<BN><<<grid, kPersistThreads, smem, s>>>(ta, tb, C, ldc, M, N, K, accumulate, k_split, c_split_stride,
+                                                        status);
     return cudaGetLastError();
 }
 
