@@ -205,7 +205,10 @@ const char *vefd_last_error(const vefd_ctx *ctx);
 vefd_status vefd_kernels_per_step(const vefd_ctx *ctx, int *n);
 /* Per-kernel timing of vefd_step: when on, every launch of a step is
  * bracketed by CUDA events on the context stream (turning it on clears the
- * record).  Tracing aid, not a hot-path requirement. */
+ * record).  Tracing aid, not a hot-path requirement.  (Independently, the
+ * library marks vefd_step, graph captures, diagnostics, checkpoints,
+ * autotuning and ensemble steps as NVTX ranges, visible to a profiler such as
+ * Nsight Systems and free otherwise.) */
 vefd_status vefd_profile_kernels(vefd_ctx *ctx, int on);
 /* Synchronises and returns, per kernel class (0 densities of the initial
  * populations, 1 lattice collide-stream, 2 densities of the new populations

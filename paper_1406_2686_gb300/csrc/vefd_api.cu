@@ -13,6 +13,7 @@
 #include <vector>
 
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "vefd.h"
 #include "vefd_internal.cuh"
@@ -100,6 +101,13 @@ struct vefd_ctx {
 };
 
 namespace {
+
+// NVTX range for the duration of a scope (header-only NVTX3: a no-op unless a
+// profiler such as Nsight Systems is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 vefd_status fail(vefd_ctx* c, vefd_status st, const char* fmt, ...) {
     if (c) {
@@ -675,6 +683,7 @@ static vefd_status step_eager(vefd_ctx* c, int64_t nsteps);
 // take; it saves the host-side launch cost of small lattices.  Capture only
 // records the launches, so the host state they advanced is put back.
 static vefd_status plain_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* out) {
+    Range range("vefd capture step graph (whole lattice)");
     if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(c, VEFD_ERR_CUDA, "cannot create the capture stream");
     const int cur = c->cur, ccur = c->ccur, hp = c->have_prev;
@@ -712,6 +721,7 @@ static vefd_status plain_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* ou
 }
 
 static vefd_status slab_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* out) {
+    Range range("vefd capture step graph (y-slabs)");
     const int K = slab_count(c);
     if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(c, VEFD_ERR_CUDA, "cannot create the capture stream");
@@ -868,6 +878,7 @@ static void step_plan(const vefd_ctx* c, int64_t nsteps, int64_t* pre, int64_t* 
 }
 
 vefd_status vefd_step(vefd_ctx* c, int64_t nsteps) {
+    Range range("vefd_step");
     vefd_status st = need_ready(c);
     if (st != VEFD_OK) return st;
     if (nsteps < 0) return fail(c, VEFD_ERR_ARG, "nsteps must be >= 0");
@@ -1025,6 +1036,7 @@ vefd_status vefd_read_field(vefd_ctx* c, vefd_field field, void* dst, size_t byt
 }
 
 vefd_status vefd_diagnostics(vefd_ctx* c, double out[16]) {
+    Range range("vefd_diagnostics");
     vefd_status st = need_ready(c);
     if (st != VEFD_OK) return st;
     if (!out) return fail(c, VEFD_ERR_ARG, "NULL output");
@@ -1196,6 +1208,7 @@ struct CkptHeader {
 }  // namespace
 
 vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
+    Range range("vefd_checkpoint");
     vefd_status st = need_ready(c);
     if (st != VEFD_OK) return st;
     if (!path) return fail(c, VEFD_ERR_ARG, "NULL path");
@@ -1246,6 +1259,7 @@ vefd_status vefd_checkpoint(vefd_ctx* c, const char* path) {
 }
 
 vefd_status vefd_restore(vefd_ctx* c, const char* path) {
+    Range range("vefd_restore");
     if (!c || !path) return fail(c, VEFD_ERR_ARG, "NULL argument");
     if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
     FILE* fh = fopen(path, "rb");
@@ -1314,6 +1328,7 @@ vefd_status vefd_get_kernel_config(const vefd_ctx* c, int* lattice_tile, int* po
 }
 
 vefd_status vefd_autotune(vefd_ctx* c, int steps, double* times_ms) {
+    Range range("vefd_autotune");
     if (!c || steps < 1) return fail(c, VEFD_ERR_ARG, "steps must be >= 1");
     if (!c->mem) return fail(c, VEFD_ERR_STATE, "device memory is not bound");
     if (times_ms)
@@ -1777,6 +1792,7 @@ void vefd_ensemble_destroy(vefd_ensemble* e) {
 }
 
 vefd_status vefd_ensemble_step(vefd_ensemble* e, int64_t nsteps, int64_t chunk) {
+    Range range("vefd_ensemble_step");
     if (!e) return VEFD_ERR_ARG;
     if (nsteps < 0) return ens_fail(e, VEFD_ERR_ARG, "nsteps must be >= 0");
     if (chunk < 2 || (chunk & 1)) return ens_fail(e, VEFD_ERR_ARG, "chunk must be even and >= 2");

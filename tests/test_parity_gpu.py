@@ -810,3 +810,33 @@ def test_newtonian_droplet_deformation_shapira_haber(capsys):
     assert last.std() < 0.03 * D                         # steady up to the pixel noise
     assert abs(D / D_sh - 1) < 0.30, (D, D_sh)
     assert D > cf.taylor_D(Ca_end, 1.0)
+
+
+def test_diagnostics_log_csv(tmp_path):
+    """The diagnostics log: rows before the first step and every `every`
+    steps, the 16 values of vefd_diagnostics and the mass drift per row, as
+    CSV; a guard bit set during the run stops it with ERR_UNSTABLE after
+    writing the rows so far."""
+    import csv
+
+    from paper_1406_2686_gb300 import monitor, vefd
+    P = _droplet_pair(24, 16, 20, 4.0)
+    path = str(tmp_path / "diag.csv")
+    rows = monitor.run_logged(P.g, 45, 10, path)
+    assert [r[0] for r in rows] == [0, 10, 20, 30, 40, 45]
+    with open(path) as fh:
+        got = list(csv.reader(fh))
+    assert got[0] == monitor.COLUMNS and len(got) == 7
+    P.o.step(45)
+    do = P.o.diagnostics()
+    last = np.array([float(v) for v in got[-1][1:17]])
+    assert abs(last[0] / do[0] - 1) < 1e-6 and abs(last[10] - do[10]) < 1e-3
+    assert max(float(r[-1]) for r in got[1:]) < 1e-6
+    C = P.g.read(vefd.C)
+    C[0, 3, 4, 5] = np.nan
+    P.g.write(vefd.C, C)
+    with pytest.raises(vefd.VefdError) as ei:
+        monitor.run_logged(P.g, 30, 10, path)
+    assert ei.value.status == vefd.ERR_UNSTABLE
+    with open(path) as fh:
+        assert len(list(csv.reader(fh))) == 3  # header, the starting row and the row that saw the bit
