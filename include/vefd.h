@@ -69,7 +69,9 @@ typedef enum {
 } vefd_field;
 
 /* Guard bits of the device status word (sticky until vefd_clear_status). */
-enum { VEFD_ST_NAN = 1, VEFD_ST_TRACE = 2, VEFD_ST_MACH = 4, VEFD_ST_RHO = 8, VEFD_ST_TIMEOUT = 16 };
+enum { VEFD_ST_NAN = 1, VEFD_ST_TRACE = 2, VEFD_ST_MACH = 4, VEFD_ST_RHO = 8, VEFD_ST_TIMEOUT = 16,
+       VEFD_ST_BOUNDS = 32 /* debug library only (built with VEFD_BOUNDS_CHECK): a neighbour index of a
+                              step kernel left the lattice; the access was skipped */ };
 
 /* Lattice and two-component fluid (Sec. 2). */
 typedef struct {

@@ -284,7 +284,7 @@ __device__ __forceinline__ void fenep_node(const float* __restrict__ Ct, float* 
     }
     auto v = [&](int k, int d) -> float {
         const float* base = k < NC ? Ct + k * N : u + (k - NC) * N;
-        return __ldg(base + idx[d]);
+        return idx_ok(idx[d], N, status) ? __ldg(base + idx[d]) : 0.0f;
     };
     float Rprev[NC], Rnew[NC];
 #pragma unroll
@@ -506,10 +506,11 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
         const int gi = zz * plane + y * nx + x;
         const int gh = zz * plane + hyg * nx + hx;
 #pragma unroll
+        const bool ok_i = idx_ok(gi, N, status), ok_h = hvalid && idx_ok(gh, N, status);
         for (int k = 0; k < kZmNF; ++k) {
             const float* base = k < 6 ? Ct + k * N : u + (k - 6) * N;
-            v_in[k] = __ldg(base + gi);
-            if (hvalid) v_h[k] = __ldg(base + gh);
+            v_in[k] = ok_i ? __ldg(base + gi) : 0.0f;
+            if (hvalid) v_h[k] = ok_h ? __ldg(base + gh) : 0.0f;
         }
     };
     auto store_plane = [&](int slot, const float v_in[kZmNF], const float v_h[kZmNF]) {

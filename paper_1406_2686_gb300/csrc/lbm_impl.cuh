@@ -130,8 +130,8 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
         for (int a = 1; a < L::Q; ++a) {
             const int j = nb.at(L::cx(a), L::cy(a), L::cz(a));
             const bool axis = L::w(a) == L::w(1);
-            float dj[2];
-            dens_ldg<2>(b.drho, j, dj);
+            float dj[2] = {0.0f, 0.0f};
+            if (idx_ok(j, N, b.status)) dens_ldg<2>(b.drho, j, dj);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const float t = dj[s];
@@ -158,12 +158,13 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
         return;
     }
     float div[3] = {0.f, 0.f, 0.f};
+    auto qget = [&](int k, int j) -> float { return idx_ok(j, N, b.status) ? __ldg(Q + k * N + j) : 0.0f; };
     {
         const int jm = nb.at(-1, 0, 0), jp = nb.at(1, 0, 0);
 #pragma unroll
         for (int jj = 0; jj < L::D; ++jj) {
             const int k = qidx<L>(0, jj);
-            div[jj] += 0.5f * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
+            div[jj] += 0.5f * (qget(k, jp) - qget(k, jm));
         }
     }
     {
@@ -179,7 +180,7 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
 #pragma unroll
         for (int jj = 0; jj < L::D; ++jj) {
             const int k = qidx<L>(1, jj);
-            div[jj] += h * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
+            div[jj] += h * (qget(k, jp) - qget(k, jm));
         }
     }
     if (L::D == 3) {
@@ -187,7 +188,7 @@ __device__ __forceinline__ void neighbour_forces(const StepBufs& b, const StepPa
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             const int k = qidx<L>(2, jj);
-            div[jj] += 0.5f * (__ldg(Q + k * N + jp) - __ldg(Q + k * N + jm));
+            div[jj] += 0.5f * (qget(k, jp) - qget(k, jm));
         }
     }
 #pragma unroll
@@ -489,9 +490,11 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
             const int ab = a + 1;
             const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
             if (ba) out[ab * N + node] = va;
-            else out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = va;
+            else if (idx_ok(node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1], N, b.status))
+                out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = va;
             if (bb) out[a * N + node] = vb;
-            else out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
+            else if (idx_ok(node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz], N, b.status))
+                out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
         },
         rest);
     // the rest population stays at the node, in FP32, and is updated in place
@@ -921,9 +924,11 @@ __device__ __forceinline__ void lattice_column(const CUtensorMap* tm_fin, const 
                 const int ab = a + 1;
                 const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
                 if (ba) out[ab * N + node] = va;
-                else out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = va;
+                else if (idx_ok(node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1], N, b.status))
+                    out[a * N + node + ox[cx + 1] + oy[cy + 1] + oz[cz + 1]] = va;
                 if (bb) out[a * N + node] = vb;
-                else out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
+                else if (idx_ok(node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz], N, b.status))
+                    out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
                 // this thread's own slots: its reads of them are done
                 sP[(s * (L::Q - 1) + a - 1) * T + t] = va;
                 sP[(s * (L::Q - 1) + ab - 1) * T + t] = vb;

@@ -297,7 +297,22 @@ __device__ __forceinline__ bool zm_inner(int lane, int row, int zp, int z0, int 
 }
 
 // Device guard bits (mirror VEFD_ST_*).
-constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTimeout = 16u;
+constexpr unsigned kStNan = 1u, kStTrace = 2u, kStMach = 4u, kStRho = 8u, kStTimeout = 16u, kStBounds = 32u;
+
+// Debug builds (-DVEFD_BOUNDS_CHECK, a separate library): every neighbour
+// index the step kernels compute (pushes, density and stress gathers, the
+// FENE-P stencil) is checked against the lattice; an index outside [0, N)
+// sets kStBounds and the access is skipped (a skipped load reads 0).  In the
+// regular build the check is compiled out.
+#ifdef VEFD_BOUNDS_CHECK
+__device__ __forceinline__ bool idx_ok(long long j, long long N, unsigned* status) {
+    if (j >= 0 && j < N) return true;
+    atomicOr(status, kStBounds);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool idx_ok(long long, long long, unsigned*) { return true; }
+#endif
 
 // Pointers of one step.
 struct StepBufs {

@@ -17,7 +17,7 @@ D2Q9, D3Q19 = 0, 1
 FP32, FP16, BF16 = 0, 1, 2
 RHO_A, RHO_B, PHI, U, C, SIGMA_P, POPS, RPREV, G_A, G_B, F_P, TAU = range(12)
 OK, ERR_ARG, ERR_CUDA, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5
-ST_NAN, ST_TRACE, ST_MACH, ST_RHO, ST_TIMEOUT = 1, 2, 4, 8, 16
+ST_NAN, ST_TRACE, ST_MACH, ST_RHO, ST_TIMEOUT, ST_BOUNDS = 1, 2, 4, 8, 16, 32
 
 
 class VefdError(RuntimeError):
@@ -58,15 +58,18 @@ def library_path():
 
 
 def load(build_if_missing=True):
-    """Load libvefd.so (building it in-tree when absent and nvcc is present)."""
+    """Load libvefd.so (building it in-tree when absent and nvcc is present).
+    With VEFD_DEBUG_LIB=1 in the environment the bounds-checked debug library
+    is loaded instead (guard bit ST_BOUNDS)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = build_lib.LIB
-    if not os.path.exists(path) or not build_lib.up_to_date():
+    debug = os.environ.get("VEFD_DEBUG_LIB") == "1"
+    path = build_lib.LIB_DEBUG if debug else build_lib.LIB
+    if not os.path.exists(path) or not build_lib.up_to_date(debug):
         if not build_if_missing:
             raise OSError("libvefd.so is not built: run __graft_entry__.build()")
-        build_lib.build()
+        build_lib.build(debug=debug)
     L = ctypes.CDLL(path)
     vp, sz, i64, dbl, cint = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_double, ctypes.c_int
     pcfg = ctypes.POINTER(vefd_config)
