@@ -125,14 +125,30 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
-def source_hash():
+def _hash_sources(names):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1406_2686_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(f.encode())
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(names):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def source_hash():
+    """Hash of every CUDA source of the library."""
+    csrc = os.path.join(ROOT, "paper_1406_2686_gb300", "csrc")
+    return _hash_sources([f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh"))])
+
+
+# the translation units and headers the two step kernels (and their launch
+# shapes) are built from
+STEP_KERNEL_SOURCES = ("vefd_internal.cuh", "lbm_impl.cuh", "lbm_kernels.cu", "fd_kernels.cu")
+
+
+def kernel_source_hash():
+    """Hash of the step kernels' sources: a recorded ncu traffic figure holds
+    while these are unchanged, whatever else in the library changes."""
+    return _hash_sources(STEP_KERNEL_SOURCES)
 
 
 def measured_peak():
@@ -144,16 +160,19 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, kernel_config=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current step-kernel sources (and, when given, the same kernel
+    choice)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get(kernel)
-    if not e or e.get("source_sha") != source_hash():
+    if not e or e.get("kernel_sha") != kernel_source_hash():
+        return None
+    if kernel_config is not None and list(e.get("kernel_config", [])) != list(kernel_config):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -620,7 +639,7 @@ def run_ours(args):
     avg_s = kms[dom] / max(klaunch[dom], 1) / 1e3
     algo = kernel_algo_bytes(S, dname) * N
     achieved = algo / avg_s / 1e9
-    traffic = recorded_traffic(dname) if (S.name, S.prec) == ("droplet128", 0) else None
+    traffic = recorded_traffic(dname, timed_config) if (S.name, S.prec) == ("droplet128", 0) else None
     roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes_per_launch": algo,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
@@ -657,7 +676,7 @@ def run_ours(args):
                           "algorithmic_bytes_per_node": S.step_bytes},
         "kernels": kernels, "gpu_launches": launches, "step_graph": step_graph, "clocks": clk, "e2e": e2e,
         "autotune": tune, "kernel_config": timed_config,
-        "status_bits": status, "source_sha": source_hash(),
+        "status_bits": status, "source_sha": source_hash(), "kernel_sha": kernel_source_hash(),
     }
     lat.close()
     if not args.no_variants and S.prec == 0:

@@ -423,8 +423,9 @@ void vefd_ensemble_destroy(vefd_ensemble *ens);
  * context current and caches it under the context's unique ID, so make that
  * first call before any stream capture.  Every
  * call shares the one scratch array and rewrites every row it reads, so
- * nothing needs clearing between calls, but calls that overlap on the GPU
- * race on it. */
+ * nothing needs clearing between calls; a lock held from the first launch to
+ * the synchronisation makes host threads that call at the same time take
+ * turns on it. */
 vefd_status vefd_diagnostics_noalloc(int lattice, int nx, int ny, int nz, int ncomp, double L2,
                                      const float *rho_A, const float *rho_B, const float *u, const float *C,
                                      void *stream, double out[16]);

@@ -134,6 +134,9 @@ __global__ void k_diag_rows_final(double* __restrict__ rows, int nrows) {
 }
 
 std::mutex g_setup_mutex;
+// Held from the first launch to the synchronisation, so that host threads
+// calling at the same time take turns on the one scratch array.
+std::mutex g_run_mutex;
 
 // Scratch addresses by CUDA context.  A context's ID is unique for the life
 // of the process, so a device reset (which destroys the context and, with it,
@@ -226,17 +229,19 @@ extern "C" vefd_status vefd_diagnostics_noalloc(int lattice, int nx, int ny, int
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nblocks = (int)((N + kNodesPerBlock - 1) / kNodesPerBlock);
     const float* rB = ncomp == 2 ? rho_B : nullptr;
+    double v[kDiagVals];
+    std::unique_lock<std::mutex> run(g_run_mutex);
     if (lattice == VEFD_D3Q19)
         k_diag_rows_abs<3, 6><<<nblocks, kThreads, 0, s>>>(rho_A, rB, u, C, nx, ny, nz, L2, rows);
     else
         k_diag_rows_abs<2, 4><<<nblocks, kThreads, 0, s>>>(rho_A, rB, u, C, nx, ny, nz, L2, rows);
     k_diag_rows_final<<<1, kDiagVals * 32, 0, s>>>(rows, nblocks);
     if (cudaGetLastError() != cudaSuccess) return VEFD_ERR_CUDA;
-    double v[kDiagVals];
     if (cudaMemcpyAsync(v, rows + (size_t)kNoallocRows * kDiagVals, sizeof v, cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
         return VEFD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return VEFD_ERR_CUDA;
+    run.unlock();
     const double n = (double)N;
     for (int k = 0; k < 16; ++k) out[k] = 0.0;
     out[0] = v[0];

@@ -45,12 +45,29 @@ def test_small_ensemble_and_headline_setup():
 
 @pytest.mark.parametrize("name", ["lattice_collide_stream", "densities_fenep_fd"])
 def test_recorded_traffic_matches_sources_or_is_null(name):
-    """The committed DRAM traffic is reported only for the sources it was
-    captured on."""
+    """The committed DRAM traffic is reported only for the step-kernel
+    sources and the kernel choice it was captured on."""
     import json
     rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[name]
     got = bench.recorded_traffic(name)
-    if rec["source_sha"] == bench.source_hash():
+    if rec["kernel_sha"] == bench.kernel_source_hash():
         assert got == rec["dram_bytes_read"] + rec["dram_bytes_write"] == rec["dram_bytes_per_launch"]
+        assert bench.recorded_traffic(name, rec["kernel_config"]) == got
+        assert bench.recorded_traffic(name, [rec["kernel_config"][0] + 1, rec["kernel_config"][1]]) is None
     else:
         assert got is None
+
+
+def test_kernel_source_hash_covers_the_step_kernels():
+    """Every local include of the step kernels' translation units is in the
+    hashed set, so a change to any of them invalidates the traffic record."""
+    import re
+    csrc = os.path.join(ROOT, "paper_1406_2686_gb300", "csrc")
+    todo, seen = ["lbm_kernels.cu", "fd_kernels.cu"], set()
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        todo += re.findall(r'#include "([^"]+)"', open(os.path.join(csrc, f)).read())
+    assert seen == set(bench.STEP_KERNEL_SOURCES)

@@ -86,3 +86,61 @@ def test_noalloc_at_capacity():
         _compare(ref, got)
         del f
     lat.close()
+
+
+def test_noalloc_concurrent_host_threads():
+    """Eight host threads call the entry point at the same time, each on its
+    own stream, over four different lattices.  The calls share the one
+    scratch array, so the library serialises them; every call returns exactly
+    (bit for bit) what a lone call on the same fields returned."""
+    import threading
+
+    import torch
+
+    from paper_1406_2686_gb300 import vefd
+
+    L2 = 100.0
+    cases = []
+    for i, (nx, ny, nz) in enumerate([(48, 32, 40), (64, 32, 32), (40, 24, 56), (96, 64, 48)]):
+        lat = vefd.Lattice(lattice=vefd.D3Q19, nx=nx, ny=ny, nz=nz, ncomp=2, walls=1, G=1.5, eta_A=0.21,
+                           eta_B=0.35)
+        lat.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, 6.0 + 2 * i, 2.0, 0.1, 5.0, 3, 1e-3)
+        lat.set_wall_shear(0.02 + 0.01 * i)
+        lat.set_fenep(50.0, 0.14, L2, 1e-3, 1, 1)
+        lat.step(30 + 10 * i)
+        f = _fields(lat, vefd)
+        torch.cuda.synchronize()
+        cases.append(((nx, ny, nz), f, lat))
+    s0 = torch.cuda.Stream()
+
+    def call(case, stream):
+        (nx, ny, nz), f, _ = case
+        return vefd.vefd_diagnostics_noalloc(vefd.D3Q19, nx, ny, nz, 2, L2, f[vefd.RHO_A].data_ptr(),
+                                             f[vefd.RHO_B].data_ptr(), f[vefd.U].data_ptr(), f[vefd.C].data_ptr(),
+                                             stream.cuda_stream)
+
+    alone = [np.array(call(c, s0)) for c in cases]
+    results, errors = {}, []
+    start = threading.Barrier(8)
+
+    def worker(t):
+        try:
+            stream = torch.cuda.Stream()
+            start.wait()
+            got = [np.array(call(cases[(t + r) % 4], stream)) for r in range(24)]
+            results[t] = got
+        except Exception as e:  # reported below, on the main thread
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(8)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=120)
+    assert not errors, errors
+    assert len(results) == 8
+    for t, got in results.items():
+        for r, v in enumerate(got):
+            assert np.array_equal(v, alone[(t + r) % 4]), (t, r)
+    for _, _, lat in cases:
+        lat.close()
