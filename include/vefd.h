@@ -90,7 +90,10 @@ typedef struct {
 
 /* Creates a context on the current CUDA device; `stream` is a cudaStream_t
  * (NULL = legacy default stream).  Validates cfg; allocates device buffers
- * unless cfg->external_memory.  Errors: VEFD_ERR_ARG, VEFD_ERR_CUDA. */
+ * unless cfg->external_memory.  The kernels index a population plane by
+ * 32-bit offsets, so one lattice holds at most 2^31 / 40 = 53,687,091 nodes
+ * (about 23 GB of state with FP32 storage); larger ones are refused with
+ * VEFD_ERR_ARG.  Errors: VEFD_ERR_ARG, VEFD_ERR_CUDA. */
 vefd_status vefd_create(const vefd_config *cfg, void *stream, vefd_ctx **out);
 /* Bytes of device memory a context with this config needs. */
 vefd_status vefd_required_bytes(const vefd_config *cfg, size_t *bytes);

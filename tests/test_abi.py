@@ -187,3 +187,18 @@ def test_noalloc_argument_checks_without_a_device(lib):
     codes, null_out = r.stdout.split()
     assert codes.split(",") == [str(vefd.ERR_ARG)] * 9, codes
     assert int(null_out) == vefd.ERR_ARG
+
+
+def test_lattice_size_limit(lib):
+    """One lattice holds at most 2^31 / 40 nodes (32-bit plane offsets): the
+    largest admitted size is sized, one node more is refused, with and
+    without walls (the check needs no device)."""
+    limit = (1 << 31) // 40
+    assert limit == 53687091
+    assert vefd.vefd_required_bytes(_cfg(nx=limit, ny=1, nz=1, lattice=vefd.D2Q9, walls=0)) > 0
+    with pytest.raises(vefd.VefdError):
+        vefd.vefd_required_bytes(_cfg(nx=limit + 1, ny=1, nz=1, lattice=vefd.D2Q9, walls=0))
+    # 512 x 256 x 409 = 53,608,448 nodes fit; 512 x 256 x 410 = 53,739,520 do not
+    assert vefd.vefd_required_bytes(_cfg(nx=512, ny=256, nz=409)) > 0
+    with pytest.raises(vefd.VefdError):
+        vefd.vefd_required_bytes(_cfg(nx=512, ny=256, nz=410))
