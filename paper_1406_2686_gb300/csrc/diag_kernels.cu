@@ -72,6 +72,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Exactly (n / d > 0) without the division, for the doubles the indicator
+// compares (differences of FP32 values, so the quotient never underflows):
+// a finite nonzero d keeps or flips the sign of n; d = +-0 gives +-inf of the
+// sign n and d share (NaN for n = 0 or NaN); an infinite or NaN d gives a
+// zero or NaN quotient.
+__device__ __forceinline__ bool ratio_positive(double n, double d) {
+    if (d != 0.0 && isfinite(d)) return d > 0.0 ? n > 0.0 : n < 0.0;
+    if (d == 0.0) return n != 0.0 && !isnan(n) && signbit(n) == signbit(d);
+    return false;
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -87,12 +98,17 @@ __global__ void __launch_bounds__(256) k_diag_partial(const float* __restrict__ 
     double acc[kDiagVals];
 #pragma unroll
     for (int k = 0; k < kDiagVals; ++k) acc[k] = 0.0;
-    const double L2 = (double)p.L2m3 + 3.0;
+    // the maxima are kept of tr(C - I) and |u|^2; the host maps them to
+    // max tr C / L^2 and max |u| (both maps are monotone, so the result is the
+    // same as mapping every node)
+    acc[15] = -INFINITY;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % p.nx);
-        const long long r = i / p.nx;
-        const int y = (int)(r % p.ny);
-        const int z = (int)(r / p.ny);
+        // a lattice has fewer than 2^31 nodes (checked at creation)
+        const int ii = (int)i;
+        const int x = ii % p.nx;
+        const int r = ii / p.nx;
+        const int y = r % p.ny;
+        const int z = r / p.ny;
         const double dA = drho[i * ncomp];
         const double dB = ncomp == 2 ? (double)drho[2 * i + 1] : 0.0;
         const double rA = (double)p.rho_ref[0] + dA;
@@ -117,7 +133,7 @@ __global__ void __launch_bounds__(256) k_diag_partial(const float* __restrict__ 
         acc[5] += f * cxy;
         acc[6] += f * (cxx - cyy);
         acc[7] += f * trt + 3.0 * fm1;
-        const bool ind = ncomp == 2 ? (rA - rB) / rho > 0.0 : true;
+        const bool ind = ncomp == 2 ? ratio_positive(rA - rB, rho) : true;
         if (ind) {
             acc[8] += 1.0;
             if (z == zc) {
@@ -129,8 +145,8 @@ __global__ void __launch_bounds__(256) k_diag_partial(const float* __restrict__ 
                 acc[14] += (double)y * y;
             }
         }
-        acc[15] = fmax(acc[15], (trt + 3.0) / L2);
-        acc[16] = fmax(acc[16], sqrt(u2));
+        acc[15] = fmax(acc[15], trt);
+        acc[16] = fmax(acc[16], u2);
     }
     __shared__ double sh[kDiagVals][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

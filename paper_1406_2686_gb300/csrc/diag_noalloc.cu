@@ -47,8 +47,20 @@ __device__ __forceinline__ double wmax(double v) {
     return v;
 }
 
+// Exactly (n / d > 0) without the division, for differences and sums of FP32
+// values (the quotient never underflows): a finite nonzero d keeps or flips
+// the sign of n; d = +-0 gives +-inf of the sign n and d share (NaN for n = 0
+// or NaN); an infinite or NaN d gives a zero or NaN quotient.
+__device__ __forceinline__ bool ratio_positive(double n, double d) {
+    if (d != 0.0 && isfinite(d)) return d > 0.0 ? n > 0.0 : n < 0.0;
+    if (d == 0.0) return n != 0.0 && !isnan(n) && signbit(n) == signbit(d);
+    return false;
+}
+
 // Same sums and maxima as the context's diagnostics kernel, from absolute
-// densities: one row of partials per block of kNodesPerBlock nodes.
+// densities: one row of partials per block of kNodesPerBlock nodes.  The
+// maxima are kept of tr C and |u|^2; the host maps them to max tr C / L^2 and
+// max |u| (monotone maps, so the same as mapping every node).
 template <int D, int NC>
 __global__ void __launch_bounds__(kThreads) k_diag_rows_abs(const float* __restrict__ rA, const float* __restrict__ rB,
                                                             const float* __restrict__ u, const float* __restrict__ Ct,
@@ -58,14 +70,17 @@ __global__ void __launch_bounds__(kThreads) k_diag_rows_abs(const float* __restr
     double acc[kDiagVals];
 #pragma unroll
     for (int k = 0; k < kDiagVals; ++k) acc[k] = 0.0;
+    acc[15] = -INFINITY;
     const long long first = (long long)blockIdx.x * kNodesPerBlock;
     for (int t = threadIdx.x; t < kNodesPerBlock; t += kThreads) {
         const long long i = first + t;
         if (i >= N) break;
-        const int x = (int)(i % nx);
-        const long long r = i / nx;
-        const int y = (int)(r % ny);
-        const int z = (int)(r / ny);
+        // N is at most the scratch capacity (8,388,608 nodes)
+        const int ii = (int)i;
+        const int x = ii % nx;
+        const int r = ii / nx;
+        const int y = r % ny;
+        const int z = r / ny;
         const double a = rA[i];
         const double b = rB ? (double)rB[i] : 0.0;
         const double rho = a + b;
@@ -87,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_rows_abs(const float* __restr
         acc[5] += f * c[1];
         acc[6] += f * (c[0] - cyy);
         acc[7] += f * tr - 3.0;
-        const bool ind = rB ? (a - b) / rho > 0.0 : true;
+        const bool ind = rB ? ratio_positive(a - b, rho) : true;
         if (ind) {
             acc[8] += 1.0;
             if (z == zc) {
@@ -99,8 +114,8 @@ __global__ void __launch_bounds__(kThreads) k_diag_rows_abs(const float* __restr
                 acc[14] += (double)y * y;
             }
         }
-        acc[15] = fmax(acc[15], tr / L2);
-        acc[16] = fmax(acc[16], sqrt(u2));
+        acc[15] = fmax(acc[15], tr);
+        acc[16] = fmax(acc[16], u2);
     }
     __shared__ double sh[kDiagVals][kThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -251,8 +266,9 @@ extern "C" vefd_status vefd_diagnostics_noalloc(int lattice, int nx, int ny, int
     out[4] = lattice == VEFD_D3Q19 ? v[4] : 0.0;
     out[5] = v[5] / n;
     out[6] = v[6] / n;
-    out[7] = v[15];
-    out[8] = v[16];
+    // the kernel keeps max tr C and max |u|^2 (empty: -inf and 0)
+    out[7] = std::fmax(0.0, v[15] / L2);
+    out[8] = std::sqrt(v[16]);
     const double m0 = v[9];
     out[9] = m0;
     if (m0 > 0.0) {

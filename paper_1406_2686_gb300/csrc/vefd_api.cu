@@ -1057,8 +1057,9 @@ vefd_status vefd_diagnostics(vefd_ctx* c, double out[16]) {
     out[4] = c->D == 3 ? v[4] : 0.0;
     out[5] = v[5] / N;
     out[6] = v[6] / N;
-    out[7] = v[15];
-    out[8] = v[16];
+    // the kernel keeps max tr(C - I) and max |u|^2 (empty: -inf and 0)
+    out[7] = std::fmax(0.0, (v[15] + 3.0) / ((double)p.L2m3 + 3.0));
+    out[8] = std::sqrt(v[16]);
     const double m0 = v[9];
     out[9] = m0;
     if (m0 > 0.0) {
