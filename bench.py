@@ -828,6 +828,8 @@ def run_profile_region(args):
     S = Setup(args.workload, args.precision)
     lat = make_lattice(S)
     lat.set_step_graph(args.step_graph)
+    if args.kernel_config:
+        lat.set_kernel_config(*[int(v) for v in args.kernel_config.split(",")])
     lat.step(args.warmup)
     lat.prepare_steps(args.steps)
     torch.cuda.synchronize()
@@ -835,7 +837,8 @@ def run_profile_region(args):
     lat.step(args.steps)
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
-    print("profiled %d steps, step graph %r, status %d" % (args.steps, lat.step_graph, lat.status()), file=sys.stderr)
+    print("profiled %d steps, step graph %r, kernel choice %r, status %d"
+          % (args.steps, lat.step_graph, lat.kernel_config(), lat.status()), file=sys.stderr)
     lat.close()
 
 

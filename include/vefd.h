@@ -237,12 +237,21 @@ vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
  * NY % 8 == 0; lattice_tile is then unused; it moves fewer bytes but issues
  * about 2.7 times the lattice kernel's instructions); 1 = a 3-D tiled
  * densities/FENE-P pass; 2 (default) = the z-marching densities/FENE-P pass
- * after the tiled lattice kernel.  Post modes 1 and 2 with tiles 0-2 run the same arithmetic in the
+ * after the tiled lattice kernel; 3 = the tiled lattice kernel (D3Q19 tiles 0
+ * and 1, lattices of whole tiles) also sums, after its collision, the new
+ * populations that stay inside its tile into partial densities and writes
+ * what it pushes across each face and edge of the tile as per-node partial
+ * sums, so that the z-marching pass completes the densities from those
+ * (about 3 values per node) instead of reading the new populations back; the
+ * partial sums use the staging planes, which are free inside a step.  Post
+ * modes 1 and 2 with tiles 0-2 run the same arithmetic in the
  * same order and give bit-identical results; the persistent tiles (separately
- * compiled, multiply-adds contracted as the compiler sees fit) and post mode 0
- * (each node's new density summed in another order) agree to FP32 rounding.  A tile the lattice shape
+ * compiled, multiply-adds contracted as the compiler sees fit) and post modes 0
+ * and 3 (each node's new density summed in another order) agree to FP32
+ * rounding.  A tile the lattice shape
  * does not admit falls back to tile 0, post_mode 0 or 2 falls back to 1 where
- * the column does not fit, and shapes that admit no staged tile use the
+ * the column does not fit, post_mode 3 falls back to 2 where the tile or the
+ * lattice does not admit it, and shapes that admit no staged tile use the
  * unstaged kernels.  Returns VEFD_ERR_ARG for values outside these ranges.
  * Not to be called while steps are in flight. */
 vefd_status vefd_set_kernel_config(vefd_ctx *ctx, int lattice_tile, int post_mode);
@@ -254,7 +263,8 @@ vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *
  * state; the context's own state is untouched), then applies the fastest.
  * times_ms (host, 18 doubles or NULL) receives the times, index
  * post_mode * 6 + lattice_tile, -1 for pairs not admitted (post_mode 0 is
- * timed with lattice_tile 0 only).  Allocates and
+ * timed with lattice_tile 0 only; post_mode 3 is not timed: its lattice
+ * kernel's extra work outweighs the bytes it saves).  Allocates and
  * frees the scratch lattice's device memory and synchronises the context
  * stream.  VEFD_ERR_UNSTABLE when the scratch run trips a guard. */
 vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);

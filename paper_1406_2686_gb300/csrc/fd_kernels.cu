@@ -442,27 +442,35 @@ constexpr int zm_smem_bytes() {
     return NCOMP * 18 * kZmBX * kZmBY * (int)sizeof(PT) + 4 * kZmPlane * (int)sizeof(float);
 }
 
-// FUSED: after the column-marching lattice kernel.  drho then holds each
-// node's partial density (the rest population and every population that
+// MODE 0: the densities of the new populations, staged plane by plane.
+// MODE 1 (FUSED): after the column-marching lattice kernel.  drho then holds
+// each node's partial density (the rest population and every population that
 // arrived from inside its 32 x 8 column and lattice-kernel z-segment of
 // length zl); the pass adds, from fnew, the populations that crossed a column
 // side or a segment end, in direction order, and needs no population copy.
+// MODE 2 (PARTS): after the staged lattice kernel with partial densities
+// (tile_partials): each node's density is its slot-0 sum plus, in slot
+// order, the slots its position in its lattice tile (32 x part_by x part_bz)
+// implies; no population is read.
 // One 32 x 8 column (origin x0, y0) over the planes [z0, z0 + zs) of the
 // pass; tm_fnew is the tensor map of the new populations (box 32 x 8 x 1 x P).
-template <class PT, int NCOMP, bool FD, bool FUSED>
+template <class PT, int NCOMP, bool FD, int MODE>
 __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const float* __restrict__ frest,
                                             float* __restrict__ drho, const float* __restrict__ Ct,
                                             float* __restrict__ Cout, float* __restrict__ R,
                                             const float* __restrict__ u, float* __restrict__ Q,
                                             unsigned* __restrict__ status, const StepParams& p, int x0, int y0, int z0,
-                                            int zs, const PT* __restrict__ fnew, int zl) {
+                                            int zs, const PT* __restrict__ fnew, int zl,
+                                            const float* __restrict__ part = nullptr, int part_by = 1,
+                                            int part_bz = 1) {
+    constexpr bool FUSED = MODE == 1, PARTS = MODE == 2;
     using L = D3Q19;
     constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = kZmBX * kZmBY;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
     extern __shared__ __align__(128) unsigned char sraw[];
-    PT* sP = reinterpret_cast<PT*>(sraw);  // [P][BY][BX] populations of the current plane (not FUSED)
-    float* ring = reinterpret_cast<float*>(sraw + (FUSED ? 0 : P * T * sizeof(PT)));  // [4][NF][HY][HX]
+    PT* sP = reinterpret_cast<PT*>(sraw);  // [P][BY][BX] populations of the current plane (MODE 0)
+    float* ring = reinterpret_cast<float*>(sraw + (MODE != 0 ? 0 : P * T * sizeof(PT)));  // [4][NF][HY][HX]
     __shared__ __align__(8) unsigned long long bar;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -543,7 +551,7 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
         if (k == z1 - z0 - 1) pdl_trigger();
         // new populations of this plane: one bulk copy (the buffer was released
         // by every thread at the barrier ending the previous iteration)
-        if (!FUSED && leader) {
+        if (MODE == 0 && leader) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tma_load_4d(smem_u32(sP), tm_fnew, x0, y0, z, 0, bar_a, kBytes);
         }
@@ -572,6 +580,23 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
                     d += pop_get(fnew[(s * (L::Q - 1) + a - 1) * N + i]);
                 }
                 rest[s] = d;
+            }
+        } else if (PARTS) {
+            // slot 0, then the neighbouring tiles' pushes (x, y, z, xy, xz, yz)
+            const int ly = y % part_by, lz = z % part_bz;
+            const bool xe = tx == 0 || tx == kZmBX - 1;
+            const bool ye = (ly == 0 && (y > 0 || !p.walls)) || (ly == part_by - 1 && (y < ny - 1 || !p.walls));
+            const bool ze = lz == 0 || lz == part_bz - 1;
+            const bool use[7] = {true, xe, ye, ze, xe && ye, xe && ze, ye && ze};
+#pragma unroll
+            for (int s = 0; s < NCOMP; ++s) rest[s] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                if (!use[q]) continue;
+                float w[NCOMP] = {};
+                if (idx_ok(i, N, status)) dens_ldg<NCOMP>(part + (long long)q * N * NCOMP, i, w);
+#pragma unroll
+                for (int s = 0; s < NCOMP; ++s) rest[s] = q == 0 ? w[s] : rest[s] + w[s];
             }
         } else {
 #pragma unroll
@@ -611,7 +636,7 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
         }
         // densities of the new populations (same summation order as elsewhere)
         float d[NCOMP];
-        if (FUSED) {
+        if (FUSED || PARTS) {
 #pragma unroll
             for (int s = 0; s < NCOMP; ++s) d[s] = rest[s];
             dens_store<NCOMP>(drho, i, d);
@@ -638,18 +663,21 @@ __device__ __forceinline__ void post_column(const CUtensorMap* tm_fnew, const fl
     }
 }
 
-template <class PT, int NCOMP, bool FD, bool FUSED>
+template <class PT, int NCOMP, bool FD, int MODE>
 __global__ void __launch_bounds__(kZmBX * kZmBY, 2) k_post_zm(const __grid_constant__ CUtensorMap tm_fnew,
                                                                const float* __restrict__ frest,
                                                                float* __restrict__ drho, const float* __restrict__ Ct,
                                                                float* __restrict__ Cout, float* __restrict__ R,
                                                                const float* __restrict__ u, float* __restrict__ Q,
                                                                unsigned* __restrict__ status, StepParams p, int zs,
-                                                               int rev, const PT* __restrict__ fnew, int zl) {
+                                                               int rev, const PT* __restrict__ fnew, int zl,
+                                                               const float* __restrict__ part, int part_by,
+                                                               int part_bz) {
     const int x0 = (rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x) * kZmBX;
     const int y0 = p.ylo + (rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y) * kZmBY;
     const int z0 = (rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z) * zs;
-    post_column<PT, NCOMP, FD, FUSED>(&tm_fnew, frest, drho, Ct, Cout, R, u, Q, status, p, x0, y0, z0, zs, fnew, zl);
+    post_column<PT, NCOMP, FD, MODE>(&tm_fnew, frest, drho, Ct, Cout, R, u, Q, status, p, x0, y0, z0, zs, fnew, zl,
+                                     part, part_by, part_bz);
 }
 
 // Batched ensemble form: block i (taken in reverse order, so the pass starts on
@@ -667,7 +695,7 @@ __global__ void __launch_bounds__(kZmBX * kZmBY, 2)
     const int r = t / M.ncx;
     const CUtensorMap* tm = &M.tm_post[1 - (M.cur0 ^ parity)];      // the populations just written
     if ((threadIdx.x | threadIdx.y) == 0) tensormap_acquire(tm);  // the thread that issues the copies
-    post_column<PT, NCOMP, FD, false>(tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p,
+    post_column<PT, NCOMP, FD, 0>(tm, b.frest, b.drho, b.Cin, b.Cout, b.R, b.u, b.Q, b.status, p,
                                       (t % M.ncx) * kZmBX, (r % M.ncy) * kZmBY, (r / M.ncy) * M.zs, M.zs,
                                       static_cast<const PT*>(b.fout), 1);
 }
@@ -760,13 +788,15 @@ bool post_zm_eligible(int lattice, int nx, int ny) { return lattice == 1 && nx %
 namespace {
 int g_sm_count = 0;
 
-template <class PT, int NCOMP, bool FD, bool FUSED>
-cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev, int zl) {
-    constexpr int smem = FUSED ? 4 * kZmPlane * (int)sizeof(float) : zm_smem_bytes<PT, NCOMP>();
+template <class PT, int NCOMP, bool FD, int MODE>
+cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, cudaStream_t s, int rev, int zl,
+                    Parts parts = Parts{}) {
+    constexpr bool FUSED = MODE == 1;
+    constexpr int smem = MODE != 0 ? 4 * kZmPlane * (int)sizeof(float) : zm_smem_bytes<PT, NCOMP>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_post_zm<PT, NCOMP, FD, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(k_post_zm<PT, NCOMP, FD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -786,21 +816,30 @@ cudaError_t post_zm(const CUtensorMap* tm, const StepParams& p, const StepBufs& 
     // FUSED reads the partial densities of the new time level and completes them in place
     float* dens = FUSED ? b.drho_next : b.drho;
     const CUtensorMap dummy{};
-    return launch_pdl(p.pdl != 0, k_post_zm<PT, NCOMP, FD, FUSED>, grd, blk, smem, s, FUSED ? dummy : *tm,
+    return launch_pdl(p.pdl != 0, k_post_zm<PT, NCOMP, FD, MODE>, grd, blk, smem, s, MODE != 0 ? dummy : *tm,
                       (const float*)b.frest, dens, (const float*)b.Cin, b.Cout, b.R, (const float*)b.u, b.Q, b.status,
-                      p, zs, rev, static_cast<const PT*>(b.fout), zl);
+                      p, zs, rev, static_cast<const PT*>(b.fout), zl, (const float*)parts.part, parts.by, parts.bz);
 }
 }  // namespace
 
 cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBufs& b, const void* tensor_map_fnew,
-                           cudaStream_t s, int rev) {
+                           cudaStream_t s, int rev, Parts parts) {
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map_fnew);
     cudaError_t e = cudaSuccess;
+    if (parts.part && (parts.by < 2 || parts.bz < 2)) return cudaErrorInvalidValue;
     VEFD_WITH_PT(p.prec, {
-        if (ncomp == 2)
-            e = fd ? post_zm<PT, 2, true, false>(tm, p, b, s, rev, 1) : post_zm<PT, 2, false, false>(tm, p, b, s, rev, 1);
-        else
-            e = fd ? post_zm<PT, 1, true, false>(tm, p, b, s, rev, 1) : post_zm<PT, 1, false, false>(tm, p, b, s, rev, 1);
+        if (parts.part) {
+            if (ncomp == 2)
+                e = fd ? post_zm<PT, 2, true, 2>(tm, p, b, s, rev, 1, parts)
+                       : post_zm<PT, 2, false, 2>(tm, p, b, s, rev, 1, parts);
+            else
+                e = fd ? post_zm<PT, 1, true, 2>(tm, p, b, s, rev, 1, parts)
+                       : post_zm<PT, 1, false, 2>(tm, p, b, s, rev, 1, parts);
+        } else if (ncomp == 2) {
+            e = fd ? post_zm<PT, 2, true, 0>(tm, p, b, s, rev, 1) : post_zm<PT, 2, false, 0>(tm, p, b, s, rev, 1);
+        } else {
+            e = fd ? post_zm<PT, 1, true, 0>(tm, p, b, s, rev, 1) : post_zm<PT, 1, false, 0>(tm, p, b, s, rev, 1);
+        }
     });
     return e;
 }
@@ -810,9 +849,9 @@ cudaError_t launch_post_zm_fused(int ncomp, bool fd, const StepParams& p, const 
     cudaError_t e = cudaSuccess;
     VEFD_WITH_PT(p.prec, {
         if (ncomp == 2)
-            e = fd ? post_zm<PT, 2, true, true>(nullptr, p, b, s, rev, zs) : post_zm<PT, 2, false, true>(nullptr, p, b, s, rev, zs);
+            e = fd ? post_zm<PT, 2, true, 1>(nullptr, p, b, s, rev, zs) : post_zm<PT, 2, false, 1>(nullptr, p, b, s, rev, zs);
         else
-            e = fd ? post_zm<PT, 1, true, true>(nullptr, p, b, s, rev, zs) : post_zm<PT, 1, false, true>(nullptr, p, b, s, rev, zs);
+            e = fd ? post_zm<PT, 1, true, 1>(nullptr, p, b, s, rev, zs) : post_zm<PT, 1, false, 1>(nullptr, p, b, s, rev, zs);
     });
     return e;
 }

@@ -465,11 +465,16 @@ __device__ __forceinline__ void collide_emit(const StepParams& p, const Local<NC
 // node (periodic offsets in x, y, z), a bounced one to this node's opposite
 // direction; the rest population is updated in place.  EDGE = false is for
 // nodes known to have y-neighbours inside the lattice (no wall row, no
-// periodic wrap in y), which skips the bounce-back and wrap logic.
-template <class PT, class L, int NCOMP, int COLL, bool EDGE = true, class FGet>
+// periodic wrap in y), which skips the bounce-back and wrap logic.  PARTS:
+// every value this node emits in direction a (as stored, bounced or not) is
+// also written to its staging slot a (own[(s (Q-1) + a - 1) T]), whose
+// pre-collision content has just been read, and the new rest populations are
+// returned in rest_out.
+template <class PT, class L, int NCOMP, int COLL, bool EDGE = true, bool PARTS = false, class FGet>
 __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepParams& p, const Nbr& nb,
                                                const Local<NCOMP>& st, const float qloc[L::NQ],
-                                               const float (*pif)[6], FGet fget) {
+                                               const float (*pif)[6], FGet fget, PT* own = nullptr, int T = 0,
+                                               float* rest_out = nullptr) {
     const int N = (int)p.N;
     const int node = nb.i;
     const int* ox = nb.ox;
@@ -495,11 +500,19 @@ __device__ __forceinline__ void collide_stream(const StepBufs& b, const StepPara
             if (bb) out[a * N + node] = vb;
             else if (idx_ok(node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz], N, b.status))
                 out[ab * N + node + ox[1 - cx] + oy[1 - cy] + oz[1 - cz]] = vb;
+            if constexpr (PARTS) {
+                own[(s * (L::Q - 1) + a - 1) * T] = va;
+                own[(s * (L::Q - 1) + ab - 1) * T] = vb;
+            }
         },
         rest);
     // the rest population stays at the node, in FP32, and is updated in place
 #pragma unroll
     for (int s = 0; s < NCOMP; ++s) b.frest[s * N + node] = rest[s];
+    if constexpr (PARTS) {
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) rest_out[s] = rest[s];
+    }
 }
 
 template <class PT, class L, int NCOMP, bool STREAM, int COLL>
@@ -584,16 +597,16 @@ __device__ __forceinline__ void node_gather(const StepBufs& b, const StepParams&
                                             NodeGather<L, NCOMP>& g) {
     g.nb = make_nbr(active ? x : 0, active ? y : 0, active ? z : 0, p);
     if (!active) return;
-    const long long N = p.N;
     // the node's own deviations come from the density buffer (bit-identical to
     // the sum of the staged populations)
     dens_ldg<NCOMP>(b.drho, g.nb.i, g.dr);
     neighbour_forces<L, NCOMP>(b, p, g.nb, g.acc, g.Fp, g.qloc);
 }
 
-template <class PT, class L, int NCOMP, int T, int COLL, bool EDGE = true>
+template <class PT, class L, int NCOMP, int T, int COLL, bool EDGE = true, bool PARTS = false>
 __device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams& p, const PT* sf, int t,
-                                             const NodeGather<L, NCOMP>& g) {
+                                             const NodeGather<L, NCOMP>& g, PT* own = nullptr,
+                                             float* rest_out = nullptr) {
     const long long N = p.N;
     const int i = g.nb.i;
     float jx = 0.0f, jy = 0.0f, jz = 0.0f;
@@ -617,15 +630,123 @@ __device__ __forceinline__ void node_collide(const StepBufs& b, const StepParams
     b.u[N + i] = st.uy;
     if (L::D == 3) b.u[2 * N + i] = st.uz;
     // volatile reads keep the populations in shared memory instead of registers
-    collide_stream<PT, L, NCOMP, COLL, EDGE>(b, p, g.nb, st, g.qloc, pif,
-                                 [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); });
+    collide_stream<PT, L, NCOMP, COLL, EDGE, PARTS>(
+        b, p, g.nb, st, g.qloc, pif, [&](int s, int a) { return pop_smem(sf, (s * (L::Q - 1) + a - 1) * T + t); },
+        own, T, rest_out);
+}
+
+// Partial densities of time n+1 from one staged D3Q19 tile (BX, BY, BZ >= 2),
+// after every thread has written what its node emitted into its own slots
+// of sf.  Slot 0 of b.part gets, for each node d of the tile, its new rest
+// population plus, in direction order, each population that reached d from
+// inside the tile or came back to d from a wall.  Slots 1-6 get, for each node
+// e just outside the tile (in the neighbouring tile across x, y, z, xy, xz or
+// yz), the sum in direction order of the populations this tile pushed into e.
+// A node lies on at most one face of its tile per axis, so for every node and
+// slot at most one tile writes, and the densities pass reads exactly the
+// slots its node's position in its tile implies (slot 0 always; a slot across
+// y only when that side is not a wall).  Positions beyond a wall receive
+// nothing (those populations bounced back into slot 0 of their source).
+template <class PT, int NCOMP, int BX, int BY, int BZ>
+__device__ __forceinline__ void tile_partials(const PT* sf, const StepBufs& b, const StepParams& p, float* part,
+                                              int x0, int y0, int z0, int t, const float rest[NCOMP], bool active) {
+    using L = D3Q19;
+    static_assert(BX >= 2 && BY >= 2 && BZ >= 2, "a node must lie on at most one face per axis");
+    constexpr int T = BX * BY * BZ;
+    const int N = (int)p.N, nx = p.nx, ny = p.ny, nz = p.nz;
+    const int tx = t % BX, ty = (t / BX) % BY, tz = t / (BX * BY);
+    auto val = [&](int s, int a, int src) -> float { return pop_get(sf[(s * (L::Q - 1) + a - 1) * T + src]); };
+    if (active) {
+        const int y = y0 + ty;
+        float v[NCOMP];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) v[s] = rest[s];
+#pragma unroll
+        for (int a = 1; a < L::Q; ++a) {
+            const int cx = L::cx(a), cy = L::cy(a), cz = L::cz(a);
+            const int gy = y - cy;
+            if (p.walls && (gy < 0 || gy >= ny)) {
+                // from beyond a wall: this node's own value in the opposite direction, bounced
+                const int ao = (a & 1) ? a + 1 : a - 1;
+#pragma unroll
+                for (int s = 0; s < NCOMP; ++s) v[s] += val(s, ao, t);
+            } else if ((unsigned)(tx - cx) < (unsigned)BX && (unsigned)(ty - cy) < (unsigned)BY &&
+                       (unsigned)(tz - cz) < (unsigned)BZ) {
+                const int src = t - ((cz * BY + cy) * BX + cx);
+#pragma unroll
+                for (int s = 0; s < NCOMP; ++s) v[s] += val(s, a, src);
+            }
+        }
+        const int i = ((z0 + tz) * ny + y) * nx + x0 + tx;
+        if (idx_ok(i, N, b.status)) dens_store<NCOMP>(part, i, v);
+    }
+    // the shell: z faces, y faces, yz edges, x faces, xy edges, xz edges
+    constexpr int nZ = 2 * BX * BY, nY = 2 * BX * BZ, nYZ = 4 * BX, nX = 2 * BY * BZ, nXY = 4 * BZ, nXZ = 4 * BY;
+    constexpr int total = nZ + nY + nYZ + nX + nXY + nXZ;
+    for (int w = t; w < total; w += T) {
+        int ex, ey, ez, slot, q = w;
+        if (q < nZ) {
+            slot = 3;
+            ez = q >= BX * BY ? BZ : -1;
+            q %= BX * BY;
+            ex = q % BX;
+            ey = q / BX;
+        } else if ((q -= nZ) < nY) {
+            slot = 2;
+            ey = q >= BX * BZ ? BY : -1;
+            q %= BX * BZ;
+            ex = q % BX;
+            ez = q / BX;
+        } else if ((q -= nY) < nYZ) {
+            slot = 6;
+            ey = (q & 1) ? BY : -1;
+            ez = (q & 2) ? BZ : -1;
+            ex = q >> 2;
+        } else if ((q -= nYZ) < nX) {
+            slot = 1;
+            ex = q >= BY * BZ ? BX : -1;
+            q %= BY * BZ;
+            ey = q % BY;
+            ez = q / BY;
+        } else if ((q -= nX) < nXY) {
+            slot = 4;
+            ex = (q & 1) ? BX : -1;
+            ey = (q & 2) ? BY : -1;
+            ez = q >> 2;
+        } else {
+            q -= nXY;
+            slot = 5;
+            ex = (q & 1) ? BX : -1;
+            ez = (q & 2) ? BZ : -1;
+            ey = q >> 2;
+        }
+        const int gy = y0 + ey;
+        if (p.walls && (gy < 0 || gy >= ny)) continue;
+        float v[NCOMP];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) v[s] = 0.0f;
+#pragma unroll
+        for (int a = 1; a < L::Q; ++a) {
+            const int sx = ex - L::cx(a), sy = ey - L::cy(a), sz = ez - L::cz(a);
+            if ((unsigned)sx < (unsigned)BX && (unsigned)sy < (unsigned)BY && (unsigned)sz < (unsigned)BZ) {
+                const int src = (sz * BY + sy) * BX + sx;
+#pragma unroll
+                for (int s = 0; s < NCOMP; ++s) v[s] += val(s, a, src);
+            }
+        }
+        const int gx = wrap1(x0 + ex, nx), gz = wrap1(z0 + ez, nz), gyy = p.walls ? gy : wrap1(gy, ny);
+        const int i = (gz * ny + gyy) * nx + gx;
+        if (idx_ok(i, N, b.status)) dens_store<NCOMP>(part + (long long)slot * N * NCOMP, i, v);
+    }
 }
 
 // One staged tile (origin x0, y0, z0) of the lattice kernel; tm_fin is the
-// tensor map of b.fin with box BX x BY x BZ x P.
-template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL>
+// tensor map of b.fin with box BX x BY x BZ x P.  PARTS (D3Q19): the
+// post-collision values also stay in the staging slots, and the tile writes
+// the partial densities of time n+1 to `part` (tile_partials).
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL, bool PARTS = false>
 __device__ __forceinline__ void lattice_tile(const CUtensorMap* tm_fin, const StepBufs& b, const StepParams& p, int x0,
-                                             int y0, int z0) {
+                                             int y0, int z0, float* part = nullptr) {
     constexpr int P = NCOMP * (L::Q - 1);  // moving populations
     constexpr int T = BX * BY * BZ;
     constexpr unsigned kBytes = (unsigned)(P * T * sizeof(PT));
@@ -646,6 +767,32 @@ __device__ __forceinline__ void lattice_tile(const CUtensorMap* tm_fin, const St
     pdl_wait();
     NodeGather<L, NCOMP> g;
     node_gather<L, NCOMP>(b, p, x, y, z, active, g);
+    if constexpr (PARTS) {
+        const int t = (tz * BY + ty) * BX + tx;
+        // the tile's threads meet at a barrier below: take the timeout
+        // decision together
+        const bool ok = mbar_wait_bounded(bar_a);
+        if (__syncthreads_or(!ok)) {
+            if (leader) {
+                atomicOr(b.status, kStTimeout);
+                mbar_wait_bounded(bar_a);  // bounded: let the copy land before leaving
+            }
+            return;
+        }
+        pdl_trigger();
+        float rest[NCOMP];
+#pragma unroll
+        for (int s = 0; s < NCOMP; ++s) rest[s] = 0.0f;
+        if (active) {
+            if (y0 > 0 && y0 + BY < p.ny)
+                node_collide<PT, L, NCOMP, T, COLL, false, true>(b, p, sf, t, g, sf + t, rest);
+            else
+                node_collide<PT, L, NCOMP, T, COLL, true, true>(b, p, sf, t, g, sf + t, rest);
+        }
+        __syncthreads();
+        tile_partials<PT, NCOMP, BX, BY, BZ>(sf, b, p, part, x0, y0, z0, t, rest, active);
+        return;
+    }
     // bounded wait for the staged populations; on timeout report and leave
     if (!mbar_wait_bounded(bar_a)) {
         if (leader) {
@@ -670,6 +817,15 @@ __global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (B
     lattice_tile<PT, L, NCOMP, BX, BY, BZ, COLL>(&tm_fin, b, p, tile_index(blockIdx.x, gridDim.x, rev) * BX,
                                                  p.ylo + tile_index(blockIdx.y, gridDim.y, rev) * BY,
                                                  tile_index(blockIdx.z, gridDim.z, rev) * BZ);
+}
+
+// The same tile that also writes the partial densities of time n+1 (post mode 3).
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL>
+__global__ void __launch_bounds__(BX * BY * BZ, VEFD_LATTICE_THREADS_PER_SM / (BX * BY * BZ))
+    k_lattice_tma_parts(const __grid_constant__ CUtensorMap tm_fin, StepBufs b, StepParams p, int rev, float* part) {
+    lattice_tile<PT, L, NCOMP, BX, BY, BZ, COLL, true>(&tm_fin, b, p, tile_index(blockIdx.x, gridDim.x, rev) * BX,
+                                                       p.ylo + tile_index(blockIdx.y, gridDim.y, rev) * BY,
+                                                       tile_index(blockIdx.z, gridDim.z, rev) * BZ, part);
 }
 
 // Batched ensemble form: block i runs tile i - start[m] of member m with that
@@ -815,6 +971,16 @@ cudaError_t launch_tma_tile(const CUtensorMap* tm, const StepParams& p, const St
     static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
     dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.yhi - p.ylo + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
     return launch_pdl(p.pdl != 0, k_lattice_tma<PT, L, NCOMP, BX, BY, BZ, COLL>, grd, blk, smem, s, *tm, b, p, rev);
+}
+
+template <class PT, class L, int NCOMP, int BX, int BY, int BZ, int COLL>
+cudaError_t launch_tma_tile_parts(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev,
+                                  cudaStream_t s, float* part) {
+    constexpr int smem = NCOMP * (L::Q - 1) * BX * BY * BZ * (int)sizeof(PT);
+    static_assert(smem <= 48 * 1024, "staged tile must fit the default shared-memory limit");
+    dim3 blk(BX, BY, BZ), grd((p.nx + BX - 1) / BX, (p.yhi - p.ylo + BY - 1) / BY, (p.nz + BZ - 1) / BZ);
+    return launch_pdl(p.pdl != 0, k_lattice_tma_parts<PT, L, NCOMP, BX, BY, BZ, COLL>, grd, blk, smem, s, *tm, b, p,
+                      rev, part);
 }
 
 // Column-marching form (D3Q19, NX % 32 == 0, NY % 8 == 0) that also yields
@@ -1061,9 +1227,17 @@ cudaError_t launch_zm_coll(int ncomp, const StepParams& p, const StepBufs& b, cu
 // time only: the moment-space collision takes the staged form of the tile).
 template <class PT, class L, int NCOMP, int COLL>
 cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBufs& b, int rev, cudaStream_t s,
-                       int tile) {
+                       int tile, Parts parts) {
     if (COLL != 0 && tile >= 3) tile -= 3;
     if constexpr (L::D == 3) {
+        if (parts.part) {
+            // partial densities: the 32 x 4 x 2 and 32 x 2 x 4 tiles (the host admits no other)
+            if (tile == 1 && parts.by == 2 && parts.bz == 4)
+                return launch_tma_tile_parts<PT, L, NCOMP, 32, 2, 4, COLL>(tm, p, b, rev, s, parts.part);
+            if (tile == 0 && parts.by == 4 && parts.bz == 2)
+                return launch_tma_tile_parts<PT, L, NCOMP, 32, 4, 2, COLL>(tm, p, b, rev, s, parts.part);
+            return cudaErrorInvalidValue;
+        }
         switch (tile) {
         case 1: return launch_tma_tile<PT, L, NCOMP, 32, 2, 4, COLL>(tm, p, b, rev, s);
         case 2: return launch_tma_tile<PT, L, NCOMP, 32, 8, 1, COLL>(tm, p, b, rev, s);
@@ -1088,20 +1262,21 @@ cudaError_t launch_tma(const CUtensorMap* tm, const StepParams& p, const StepBuf
 // is given, else the register kernel).
 template <int COLL>
 cudaError_t launch_lattice_coll(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
-                                const void* tensor_map, int rev, int tile) {
+                                const void* tensor_map, int rev, int tile, Parts parts) {
     if (tensor_map) {
         const CUtensorMap* tm = static_cast<const CUtensorMap*>(tensor_map);
         cudaError_t e = cudaSuccess;
         VEFD_WITH_PT(p.prec, {
             if (lattice == 1)
-                e = ncomp == 2 ? launch_tma<PT, D3Q19, 2, COLL>(tm, p, b, rev, s, tile)
-                               : launch_tma<PT, D3Q19, 1, COLL>(tm, p, b, rev, s, tile);
+                e = ncomp == 2 ? launch_tma<PT, D3Q19, 2, COLL>(tm, p, b, rev, s, tile, parts)
+                               : launch_tma<PT, D3Q19, 1, COLL>(tm, p, b, rev, s, tile, parts);
             else
-                e = ncomp == 2 ? launch_tma<PT, D2Q9, 2, COLL>(tm, p, b, rev, s, tile)
-                               : launch_tma<PT, D2Q9, 1, COLL>(tm, p, b, rev, s, tile);
+                e = ncomp == 2 ? launch_tma<PT, D2Q9, 2, COLL>(tm, p, b, rev, s, tile, parts)
+                               : launch_tma<PT, D2Q9, 1, COLL>(tm, p, b, rev, s, tile, parts);
         });
         return e;
     }
+    if (parts.part) return cudaErrorInvalidValue;  // partial densities need the staged kernel
     dim3 blk(32, 4, 1), grd = node_grid(p);
     VEFD_WITH_PT(p.prec, {
         if (lattice == 1) {

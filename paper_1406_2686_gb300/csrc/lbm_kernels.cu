@@ -132,11 +132,12 @@ cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const St
 }
 
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
-                           cudaStream_t s, const void* tensor_map, int rev, int tile) {
+                           cudaStream_t s, const void* tensor_map, int rev, int tile, Parts parts) {
     if (stream_pops) {
-        if (p.collision == 1) return launch_lattice_mrt(lattice, ncomp, p, b, s, tensor_map, rev, tile);
-        return launch_lattice_coll<0>(lattice, ncomp, p, b, s, tensor_map, rev, tile);
+        if (p.collision == 1) return launch_lattice_mrt(lattice, ncomp, p, b, s, tensor_map, rev, tile, parts);
+        return launch_lattice_coll<0>(lattice, ncomp, p, b, s, tensor_map, rev, tile, parts);
     }
+    if (parts.part) return cudaErrorInvalidValue;
     // macroscopic pass (moments, forces, velocity; no streaming)
     dim3 blk(32, 4, 1), grd = node_grid(p);
     VEFD_WITH_PT(p.prec, {

@@ -6,8 +6,8 @@
 namespace vefd {
 
 cudaError_t launch_lattice_mrt(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
-                               const void* tensor_map, int rev, int tile) {
-    return launch_lattice_coll<1>(lattice, ncomp, p, b, s, tensor_map, rev, tile);
+                               const void* tensor_map, int rev, int tile, Parts parts) {
+    return launch_lattice_coll<1>(lattice, ncomp, p, b, s, tensor_map, rev, tile, parts);
 }
 
 cudaError_t launch_lattice_zm_mrt(int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,

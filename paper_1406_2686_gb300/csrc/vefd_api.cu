@@ -67,6 +67,9 @@ struct vefd_ctx {
     bool zm_ok = false;
     // column-marching lattice kernel with the densities fused in (post_mode 0)
     bool fused_ok = false;
+    // staged lattice kernel writing partial densities that the z-marching pass
+    // completes (post_mode 3; D3Q19, 32 x 4 x 2 or 32 x 2 x 4 tiles)
+    bool parts_ok = false;
     int zm_seg_fixed = 0;  // z-segment length of the column march (0: one wave of blocks)
     bool pdl = true;       // programmatic dependent launch between the step's kernels
     // densities and feedback stress of the current state are in drho and Q
@@ -151,8 +154,9 @@ bool config_ok(const vefd_config* c, const char** why) {
 }
 
 // staging planes (FP32): the initial fields (rho_A, rho_B, 3 velocity, 6 C) and
-// the derived fields of reads and writes go through this buffer
-constexpr int kStagePlanes = 11;
+// the derived fields of reads and writes go through this buffer; inside a step
+// of post_mode 3 it holds the 7 partial-density slots (7 x 2 planes)
+constexpr int kStagePlanes = 14;
 
 struct Layout {
     size_t f0, f1, frest, drho, u, c0, c1, r, dbg, q, status, dpart, dout, total;
@@ -225,6 +229,7 @@ void build_tensor_maps(vefd_ctx* c) {
     c->tma_ok = false;
     c->zm_ok = false;
     c->fused_ok = false;
+    c->parts_ok = false;
     if (getenv("VEFD_NO_TMA") || !pop_tile_eligible(lat, prec, nx, ny, nz, 0)) return;
     // the densities/FD pass keeps the default tile
     if (!(make_pop_tensor_map(lat, nc, prec, nx, ny, nz, c->f[0], &c->tmap_post[0]) &&
@@ -244,6 +249,10 @@ void build_tensor_maps(vefd_ctx* c) {
                    make_pop_tensor_map_box(c->cfg.lattice, c->cfg.ncomp, prec, c->cfg.nx, c->cfg.ny, c->cfg.nz,
                                            c->f[1], 32, 8, 1, &c->tmap_zm[1]);
         c->fused_ok = c->zm_ok && c->post_mode == 0 && !getenv("VEFD_NO_FUSED");
+        // partial densities: every node of a whole tile (a node on at most one
+        // face per axis), tiles 32 x 4 x 2 and 32 x 2 x 4
+        c->parts_ok = c->zm_ok && c->post_mode == 3 && (tile == 0 || tile == 1) && ny % by == 0 && nz % bz == 0 &&
+                      bz >= 2 && by >= 2;
     }
 }
 
@@ -278,6 +287,17 @@ StepParams params_of(const vefd_ctx* c) {
     p.yhi = c->cfg.ny;
     p.post_zs = 0;
     return p;
+}
+
+// The partial densities of post mode 3 (off otherwise); the staging planes are
+// free inside a step.
+Parts parts_of(const vefd_ctx* c) {
+    Parts q{};
+    if (!c->parts_ok) return q;
+    int bx;
+    lattice_tile_shape(c->cfg.lattice, c->lat_tile, &bx, &q.by, &q.bz);
+    q.part = c->dbg;
+    return q;
 }
 
 StepBufs bufs_of(vefd_ctx* c) {
@@ -368,7 +388,8 @@ std::vector<double> state_key(const vefd_ctx* m) {
     return {m->u_wall, m->fext[0], m->fext[1], m->fext[2], m->tau_p, m->eta_p, m->L2, m->kappa,
             (double)m->phase, (double)m->fd_on, (double)m->coupling, (double)m->collision, (double)m->chol,
             m->rho_ref[0], m->rho_ref[1], (double)m->lat_tile, (double)m->tma_ok, (double)m->zm_ok,
-            (double)m->fused_ok, (double)(m->drho < m->drho_alt), (double)m->sched, (double)m->cur,
+            (double)m->fused_ok, (double)m->parts_ok, (double)(m->drho < m->drho_alt), (double)m->sched,
+            (double)m->cur,
             (double)m->ccur, (double)m->have_prev, (double)m->drho_valid, (double)m->pdl,
             (double)(uintptr_t)m->mem, (double)m->zm_seg_fixed, (double)slab_count(m), (double)m->slab_chunk};
 }
@@ -775,7 +796,7 @@ static vefd_status slab_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* out
             p.yhi = (k + 1) * rows;
             if (ce == cudaSuccess)
                 ce = launch_lattice(c->cfg.lattice, c->cfg.ncomp, true, p, b, c->slab_s[k], &c->tmap[cur], lat_rev,
-                                    c->lat_tile);
+                                    c->lat_tile, parts_of(c));
             if (ce == cudaSuccess) ce = cudaEventRecord(c->slab_evL[k], c->slab_s[k]);
         };
         auto pass_node = [&](int k) {
@@ -787,7 +808,8 @@ static vefd_status slab_capture(vefd_ctx* c, int64_t chunk, cudaGraphExec_t* out
             p.ylo = k * rows;
             p.yhi = (k + 1) * rows;
             if (ce == cudaSuccess)
-                ce = launch_post_zm(c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_zm[1 - cur], c->slab_s[k], post_rev);
+                ce = launch_post_zm(c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_zm[1 - cur], c->slab_s[k], post_rev,
+                                    parts_of(c));
             if (ce == cudaSuccess) ce = cudaEventRecord(c->slab_evP[k], c->slab_s[k]);
         };
         // (capturing each pass right after the lattice kernels it waits for
@@ -944,7 +966,8 @@ static vefd_status step_eager(vefd_ctx* c, int64_t nsteps) {
             // populations n -> n+1, velocity of time n
             ProfScope ps(c, 1);
             VEFD_CUDA(c, launch_lattice(c->cfg.lattice, c->cfg.ncomp, true, p, b, c->stream,
-                                        c->tma_ok ? (const void*)&c->tmap[c->cur] : nullptr, lat_rev, c->lat_tile));
+                                        c->tma_ok ? (const void*)&c->tmap[c->cur] : nullptr, lat_rev, c->lat_tile,
+                                        parts_of(c)));
         }
         {
             // densities of time n+1 (they only depend on the new populations)
@@ -952,7 +975,7 @@ static vefd_status step_eager(vefd_ctx* c, int64_t nsteps) {
             ProfScope ps(c, 2);
             if (c->zm_ok)
                 VEFD_CUDA(c, launch_post_zm(c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_zm[1 - c->cur], c->stream,
-                                            post_rev));
+                                            post_rev, parts_of(c)));
             else if (c->tma_ok)
                 VEFD_CUDA(c, launch_post_tma(c->cfg.lattice, c->cfg.ncomp, c->fd_on != 0, p, b, &c->tmap_post[1 - c->cur],
                                              c->stream, post_rev));
@@ -1314,7 +1337,7 @@ vefd_status vefd_restore(vefd_ctx* c, const char* path) {
 vefd_status vefd_set_kernel_config(vefd_ctx* c, int lattice_tile, int post_mode) {
     if (!c) return VEFD_ERR_ARG;
     if (lattice_tile < 0 || lattice_tile > 5) return fail(c, VEFD_ERR_ARG, "lattice_tile must be in 0..5");
-    if (post_mode < 0 || post_mode > 2) return fail(c, VEFD_ERR_ARG, "post_mode must be 0, 1 or 2");
+    if (post_mode < 0 || post_mode > 3) return fail(c, VEFD_ERR_ARG, "post_mode must be 0, 1, 2 or 3");
     c->lat_tile = lattice_tile;
     c->post_mode = post_mode;
     if (c->mem) build_tensor_maps(c);
@@ -1324,7 +1347,7 @@ vefd_status vefd_set_kernel_config(vefd_ctx* c, int lattice_tile, int post_mode)
 vefd_status vefd_get_kernel_config(const vefd_ctx* c, int* lattice_tile, int* post_mode) {
     if (!c || !lattice_tile || !post_mode) return VEFD_ERR_ARG;
     *lattice_tile = c->tma_ok ? c->lat_tile : -1;
-    *post_mode = c->fused_ok ? 0 : (c->zm_ok ? 2 : (c->tma_ok ? 1 : -1));
+    *post_mode = c->fused_ok ? 0 : (c->parts_ok ? 3 : (c->zm_ok ? 2 : (c->tma_ok ? 1 : -1)));
     return VEFD_OK;
 }
 

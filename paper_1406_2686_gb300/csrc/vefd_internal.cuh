@@ -331,6 +331,18 @@ struct StepBufs {
                            // densities/FD pass overwrites it with time n+1)
 };
 
+// Partial densities of time n+1 (post mode 3), passed beside StepBufs to the
+// staged lattice kernel that writes them and the z-marching pass that
+// completes them: 7 slots of N x NCOMP floats, interleaved by node like the
+// densities; slot 0 holds what reached a node from inside its lattice tile
+// (with its rest population and wall bounce-back), slots 1-6 what the
+// neighbouring tile across x, y, z, xy, xz, yz pushed into it.  by, bz: the
+// lattice tile's rows and planes (its width is 32).  part == nullptr: off.
+struct Parts {
+    float* part;
+    int by, bz;
+};
+
 // One lattice of a batched ensemble step, as the batched kernels read it from
 // device memory: parameters, the buffers of both ping-pong parities, the tensor
 // maps of the two population buffers f[0], f[1] (lattice kernel: 32 x 4 x 2
@@ -356,12 +368,14 @@ cudaError_t launch_moments(int lattice, int ncomp, const StepParams& p, const St
 // tensor_map: a CUtensorMap of b.fin for the TMA-staged kernel (streaming
 // steps only), or nullptr for the register-only kernel; `tile` selects the
 // staged tile shape (lattice_tile_shape), and the map's box must match it.
+// parts.part != nullptr (D3Q19 staged tiles 0 and 1 only): the kernel also
+// writes the partial densities of time n+1 (post mode 3).
 cudaError_t launch_lattice(int lattice, int ncomp, bool stream_pops, const StepParams& p, const StepBufs& b,
-                           cudaStream_t s, const void* tensor_map, int rev, int tile);
+                           cudaStream_t s, const void* tensor_map, int rev, int tile, Parts parts = Parts{});
 // The streaming launch with the moment-space collision (instantiated in its
 // own translation unit); same arguments as launch_lattice.
 cudaError_t launch_lattice_mrt(int lattice, int ncomp, const StepParams& p, const StepBufs& b, cudaStream_t s,
-                               const void* tensor_map, int rev, int tile);
+                               const void* tensor_map, int rev, int tile, Parts parts = Parts{});
 // Column-marching lattice kernel with fused partial densities (D3Q19,
 // NX % 32 == 0, NY % 8 == 0): reads b.fin through `tensor_map` (box 32 x 8 x 1
 // x P), writes b.fout, b.frest, b.u and the partial densities into
@@ -401,8 +415,10 @@ cudaError_t launch_post_tma(int lattice, int ncomp, bool fd, const StepParams& p
 // D3Q19 z-marching variant of the pass (needs NX % 32 == 0 and NY % 8 == 0 and a
 // tensor map of `fnew` with box 32 x 8 x 1 x P).
 bool post_zm_eligible(int lattice, int nx, int ny);
+// parts.part != nullptr: the densities are completed from the partial
+// densities of post mode 3 (no population is read).
 cudaError_t launch_post_zm(int ncomp, bool fd, const StepParams& p, const StepBufs& b, const void* tensor_map_fnew,
-                           cudaStream_t s, int rev);
+                           cudaStream_t s, int rev, Parts parts = Parts{});
 // The same pass after k_lattice_zm: completes the partial densities in
 // b.drho_next with the populations that crossed a column side or a segment
 // end (segment length zs of the lattice kernel), then the FENE-P update and

@@ -4,7 +4,8 @@ compute-sanitizer is not available on this machine; instead the library is
 built a second time with VEFD_BOUNDS_CHECK, where every neighbour index the
 step kernels compute (pushes, density and stress gathers, the FENE-P
 stencil) is checked against the lattice before the access.  Run in a child
-process on the odd and ragged shapes of the parity variants, every kernel
+process on the odd and ragged shapes of the parity variants and the lattices
+of whole tiles that admit partial densities (post mode 3), every kernel
 choice they admit, the step graph and a batched ensemble: no index leaves
 the lattice (guard bit VEFD_ST_BOUNDS stays clear), and the checked build
 still matches the oracle after three steps.
@@ -27,12 +28,13 @@ sys.path.insert(0, %(tests)r)
 import numpy as np
 from paper_1406_2686_gb300 import build_lib, vefd
 from pairs import Pair, rel_l2
-from test_parity_gpu import VARIANTS
+from test_parity_gpu import PARTS_CASES, VARIANTS
 from test_ensemble_gpu import BATCH_BOXES, make
 L = vefd.load()
 assert L._name == build_lib.LIB_DEBUG, L._name
 out = {"cases": 0, "bounds": [], "parity": []}
-for name, v in sorted(VARIANTS.items()):
+cases = sorted(VARIANTS.items()) + sorted(("parts_" + k, v) for k, v in PARTS_CASES.items())
+for name, v in cases:
     P = Pair(**v)
     P.init_random(seed=5)
     P.step(3)
@@ -44,7 +46,7 @@ for name, v in sorted(VARIANTS.items()):
     if rel_l2(g, o) > 1e-6 or bits:
         out["parity"].append([name, rel_l2(g, o), bits])
     for tile in range(6):
-        for post in range(3):
+        for post in range(4):
             Q = Pair(**v)
             try:
                 Q.g.set_kernel_config(tile, post)

@@ -99,11 +99,25 @@ def test_kernel_config_reports_and_rejects():
     assert L.kernel_config() == (2, 1)
     L.set_kernel_config(4, 2)
     assert L.kernel_config() == (4, 2)
+    # partial densities: tiles 32 x 4 x 2 and 32 x 2 x 4 only, else the z-marching pass
+    L.set_kernel_config(0, 3)
+    assert L.kernel_config() == (0, 3)
+    L.set_kernel_config(1, 3)
+    assert L.kernel_config() == (1, 2)  # NZ = 6 is no multiple of the 32 x 2 x 4 tile's 4 planes
+    W = make(dict(BOXES[0], nz=8), seed=1)
+    W.set_kernel_config(1, 3)
+    assert W.kernel_config() == (1, 3)
+    L.set_kernel_config(2, 3)
+    assert L.kernel_config() == (2, 2)
+    L.set_kernel_config(3, 3)
+    assert L.kernel_config() == (3, 2)
     T = make(BOXES[1], seed=1)  # 36 x 10 x 7: tiles fit, the column does not
+    assert T.kernel_config() == (0, 1)
+    T.set_kernel_config(0, 3)
     assert T.kernel_config() == (0, 1)
     S = make(BOXES[5], seed=1)  # 9 x 10 x 11: no staged tile fits
     assert S.kernel_config() == (-1, -1)
-    for bad in ((6, 0), (-1, 0), (0, 3)):
+    for bad in ((6, 0), (-1, 0), (0, 4)):
         with pytest.raises(vefd.VefdError) as ei:
             L.set_kernel_config(*bad)
         assert ei.value.status == vefd.ERR_ARG
@@ -423,6 +437,32 @@ def test_ensemble_config_and_autotune():
     assert times[0] > 0 and times[1:] == [-1.0] * 6
     assert F.config[0] == 0
     F.close()
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("case", ["walls", "periodic", "fp16"])
+def test_partial_densities_step_graph_bit_identical(case, tile):
+    """Post mode 3 (partial densities written by the lattice kernel, completed
+    by the z-marching pass) in the pipelined y-slab step graph: bit-identical
+    to its own eager launch pairs, over graph replays and odd remainders (a
+    slab's tiles push partial sums into the neighbouring slabs' rows, which
+    the graph edges order)."""
+    box = {"walls": dict(BATCH_BOXES[0], ny=32, nz=8),
+           "periodic": dict(BATCH_BOXES[1], ny=32, nz=8),
+           "fp16": dict(BATCH_BOXES[0], ny=32, nz=8, precision=1)}[case]
+    G = make(box, seed=81)
+    R = make(box, seed=81)
+    for L in (G, R):
+        L.set_kernel_config(tile, 3)
+        assert L.kernel_config() == (tile, 3)
+    R.set_step_graph(0)
+    G.set_step_graph(4, 8)
+    assert G.step_graph == (4, 8, True)
+    for n in (9, 8, 3, 16, 5):
+        G.step(n)
+        R.step(n)
+        assert same(G, R), n
+    assert G.status() == 0 and R.status() == 0
 
 
 @pytest.mark.parametrize("case", ["walls", "periodic", "equilibrium_coupling", "fp16"])

@@ -239,6 +239,72 @@ def test_fused_densities_agree(name, seg, monkeypatch):
     assert P.g.status() == 0
 
 
+# lattices of whole 32 x 4 x 2 (and, where NZ allows, 32 x 2 x 4) tiles for
+# the partial-density kernel choice (post mode 3)
+PARTS_CASES = {
+    "walls": dict(VARIANTS["d3q19_2c_zm_walls"], nz=8),
+    "periodic_wide": dict(VARIANTS["d3q19_2c_fused_wide"]),
+    "one_component": dict(VARIANTS["d3q19_1c_zm_periodic"], nz=8),
+    "one_tile_in_x": dict(VARIANTS["d3q19_2c_eqcoupling"], nz=8),
+    "mrt": dict(VARIANTS["d3q19_2c_mrt_zm"], nz=8),
+    "chol": dict(VARIANTS["d3q19_2c_chol_zm"], nz=8),
+    "paper": dict(VARIANTS["d3q19_2c_paper"], nz=8),
+}
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("name", sorted(PARTS_CASES))
+def test_partial_densities_agree(name, tile):
+    """Post mode 3: the tiled lattice kernel sums the new populations that stay
+    in its tile and writes what it pushes across each face and edge as partial
+    sums; the z-marching pass completes the densities from those instead of
+    reading the populations back.  Against post mode 2 (the same tile, the
+    pass summing the staged populations) only the order of each density's sum
+    differs: after one step the densities agree to a few ulps and the
+    populations to FP32 rounding, after four steps populations, C and u agree
+    to FP32 rounding."""
+    from paper_1406_2686_gb300 import vefd
+    P = Pair(**PARTS_CASES[name])
+    P.g.set_kernel_config(tile, 3)
+    P.init_random(seed=9)
+    Q = Pair(**PARTS_CASES[name])
+    Q.g.set_kernel_config(tile, 2)
+    Q.init_random(seed=9)
+    assert P.g.kernel_config() == (tile, 3), P.g.kernel_config()
+    assert Q.g.kernel_config() == (tile, 2)
+    P.g.step(1)
+    Q.g.step(1)
+    for f in (vefd.RHO_A, vefd.POPS):
+        a, r = P.g.read(f), Q.g.read(f)
+        assert np.max(np.abs(a - r)) <= 4e-7 * max(1.0, np.max(np.abs(r))), f
+    P.g.step(3)
+    Q.g.step(3)
+    for f in (vefd.POPS, vefd.C, vefd.U, vefd.RHO_A):
+        a, r = P.g.read(f), Q.g.read(f)
+        assert np.linalg.norm(a - r) <= 1e-6 * np.linalg.norm(r), f
+    assert P.g.status() == 0 and Q.g.status() == 0
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+def test_droplet_2000_steps_partial_densities(tile):
+    """Post mode 3 on the droplet (64 x 24 x 40, R = 6): the 1e-5 contract in
+    u and C after 2000 steps, mass drift within 1e-6 and the oracle's
+    diagnostics."""
+    P = _droplet_pair(64, 24, 40, 6.0)
+    P.g.set_kernel_config(tile, 3)
+    assert P.g.kernel_config() == (tile, 3)
+    m0 = P.g.diagnostics()[:2]
+    P.step(2000)
+    for fld in ("u", "C"):
+        g, o = P.both(fld)
+        assert rel_l2(g, o) < 1e-5, (fld, rel_l2(g, o))
+    check_deformation(P, "droplet 2000 partial densities")
+    m1 = P.g.diagnostics()[:2]
+    assert np.all(np.abs(m1 / m0 - 1) < 1e-6)
+    check_diagnostics(P)
+    assert P.g.status() == 0
+
+
 def test_config1_couette_2000_steps():
     """D2Q9 single-component FENE-P Couette, 64 x 32, walls +-0.01, tau = 1,
     lambda = 1000 steps, eta_P/(eta_s + eta_P) = 0.4, L^2 = 100, C = I:
