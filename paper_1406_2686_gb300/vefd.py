@@ -558,7 +558,11 @@ class Lattice:
     def kernel_times(self):
         return vefd_kernel_times(self.ctx)
 
-    def set_kernel_config(self, lattice_tile, post_mode=0):
+    def set_kernel_config(self, lattice_tile, post_mode=2):
+        """Staged tile (0-5) and densities/FENE-P pass (0 column march with fused
+        densities, 1 tiled pass, 2 z-marching pass (the default), 3 partial
+        densities from the tiled lattice kernel); shapes that do not admit a
+        choice fall back as vefd_set_kernel_config documents."""
         vefd_set_kernel_config(self.ctx, lattice_tile, post_mode)
 
     def kernel_config(self):
