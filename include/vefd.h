@@ -255,6 +255,19 @@ vefd_status vefd_kernel_times(vefd_ctx *ctx, double ms[3], int64_t launches[3]);
  * unstaged kernels.  Returns VEFD_ERR_ARG for values outside these ranges.
  * Not to be called while steps are in flight. */
 vefd_status vefd_set_kernel_config(vefd_ctx *ctx, int lattice_tile, int post_mode);
+/* Environment switches, read when memory is bound to a context (measurement
+ * and testing; the defaults are the measured fastest, and results stay
+ * within the agreements stated above):
+ *   VEFD_NO_TMA=1        unstaged kernels only;
+ *   VEFD_NO_ZMARCH=1     the 3-D tiled densities pass instead of the z-marching one;
+ *   VEFD_NO_FUSED=1      post_mode 0 runs as post_mode 2;
+ *   VEFD_NO_PDL=1        no programmatic dependent launch between a step's kernels;
+ *   VEFD_SCHEDULE=b      bit 0 walks the lattice kernel's tiles, bit 1 the pass's
+ *                        columns in reverse order (default 0);
+ *   VEFD_ZM_SEGMENT=n    z-segment length of the column march (default: one wave);
+ *   VEFD_SLAB_SEGMENT=n  z-segment of the step graph's slab passes (default 12);
+ *   VEFD_SLAB_PDL=1      programmatic launch between a slab's consecutive kernels
+ *                        inside the step graph (measured slower; off). */
 /* The configuration in effect: lattice_tile -1 and post_mode -1 mean the
  * unstaged kernels; post_mode 1 also when the column does not fit. */
 vefd_status vefd_get_kernel_config(const vefd_ctx *ctx, int *lattice_tile, int *post_mode);
