@@ -525,8 +525,8 @@ def time_ensemble(steps, warmup, chunk=32, setups=None, label=None):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lats = build()
     for L in lats:
-        L.step(warmup)
-        L.prepare_step_graph()
+        L.step(warmup + chunk)  # the same steps the ensembles take before their timed region
+        L.prepare_steps(steps)  # every graph the timed step(steps) replays
     torch.cuda.synchronize()
     e0.record(stream)
     for L in lats:
@@ -545,6 +545,7 @@ def time_ensemble(steps, warmup, chunk=32, setups=None, label=None):
         E = vefd.Ensemble(lats, stream)
         E.set_batched(batched)
         E.step(warmup, chunk)
+        E.step(chunk, chunk)  # captures the ensemble's chunk graph before the timed region
         torch.cuda.synchronize()
         e0.record(stream)
         E.step(steps, chunk)

@@ -1728,7 +1728,12 @@ vefd_status ens_capture(vefd_ensemble* e, int64_t chunk) {
         if (ce != cudaSuccess) break;
         m->stream = e->branch[k];
         m->prof_on = false;
+        // record the member's launch pairs in its branch, not a nested launch
+        // of its own step graph
+        const int slabs = m->slabs;
+        m->slabs = 0;
         st = vefd_step(m, chunk);
+        m->slabs = slabs;
         if (st != VEFD_OK) why = m->err;
         if (st == VEFD_OK) ce = cudaEventRecord(e->join[k], e->branch[k]);
         if (st == VEFD_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(e->main, e->join[k], 0);
