@@ -306,9 +306,11 @@ vefd_status vefd_autotune(vefd_ctx *ctx, int steps, double *times_ms);
  * In both forms the kernels and their per-node arithmetic are those of the
  * eager step, so results are bit-identical.  slabs = 0 turns the graph off;
  * slabs = -1 (the default) chooses 8 slabs when NY is a multiple of 64, 4 when
- * of 32, where the split applies, otherwise the whole-lattice form (on the
- * 128 x 64 x 128 droplet, against eager stepping: 8 slabs +7 to +8 %,
- * 4 slabs +5 %).  The graph is used when kernel timing is off and the
+ * of 32, where the split applies and each slab holds at least 100,000 nodes,
+ * otherwise the whole-lattice form (on the 128 x 64 x 128 droplet, against
+ * eager stepping: 8 slabs +7 to +8 %, 4 slabs +5 %; on smaller lattices the
+ * slabs' kernels cannot fill the GPU and the whole-lattice form is faster,
+ * e.g. 10042 against 6623 MLUPS on 64^3).  The graph is used when kernel timing is off and the
  * context stream is not being captured.  Some steps run eagerly: the Euler
  * start, steps with pending densities, the last step of an odd count, and
  * one step that brings the ping-pong buffers back to the parity the graphs

@@ -372,14 +372,19 @@ bool slabs_fit(const vefd_ctx* c, int K) {
 // Slabs of the step graph for this lattice and kernel choice (0: no graph,
 // 1: whole-lattice launch pairs replayed as a graph): the setting, or
 // automatically 8 slabs when NY is a multiple of 64 and 4 when of 32 where
-// the split applies (measured on the 128 x 64 x 128 droplet: 8 slabs 7-8 %
-// and 4 slabs 5 % faster than eager stepping), otherwise 1.  An explicit slab
-// count the lattice does not admit means no graph.
+// the split applies and every slab holds at least kSlabMinNodes nodes,
+// otherwise 1.  Measured on D3Q19 droplets (MLUPS, slabs / whole-lattice
+// graph): 128 x 64 x 128 10002 / 9281 and 128^3 10130 / 9629 with 8 slabs
+// of 131k and 262k nodes, but 96 x 64 x 96 8574 / 9056, 64^3 6623 / 10042
+// and 64 x 32 x 64 4654 / 8853 with slabs of 74k, 33k and 33k nodes: a
+// slab's kernels must fill the GPU beside their neighbours.  An explicit
+// slab count the lattice does not admit means no graph.
+constexpr long long kSlabMinNodes = 100000;
 int slab_count(const vefd_ctx* c) {
     if (c->slabs >= 2) return slabs_fit(c, c->slabs) ? c->slabs : 0;
     if (c->slabs >= 0) return c->slabs;
     const int K = c->cfg.ny % 64 == 0 ? 8 : (c->cfg.ny % 32 == 0 ? 4 : 0);
-    return slabs_fit(c, K) ? K : 1;
+    return slabs_fit(c, K) && c->N / K >= kSlabMinNodes ? K : 1;
 }
 
 // Everything a captured step bakes into its launches: parameters, kernel

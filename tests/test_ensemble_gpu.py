@@ -500,10 +500,13 @@ def test_step_graph_bit_identical(case):
         G.step(8)
         R.step(8)
         assert same(G, R)
-    # the automatic choice: 8 slabs for NY a multiple of 64, 4 for 32, else none
-    assert make(dict(box, ny=64), seed=1).step_graph == (8, 256, True)
-    assert make(dict(box, ny=32), seed=1).step_graph == (4, 256, True)
-    assert make(dict(box, ny=16), seed=1).step_graph == (1, 256, True)  # the whole-lattice form
+    # the automatic choice: 8 slabs for NY a multiple of 64, 4 for 32, when
+    # every slab holds at least 100,000 nodes; else the whole-lattice form
+    assert make(dict(box, nx=128, ny=64, nz=100), seed=1).step_graph == (8, 256, True)   # 102,400 per slab
+    assert make(dict(box, nx=128, ny=64, nz=96), seed=1).step_graph == (1, 256, True)    # 98,304 per slab
+    assert make(dict(box, nx=128, ny=32, nz=100), seed=1).step_graph == (4, 256, True)
+    assert make(dict(box, ny=64), seed=1).step_graph == (1, 256, True)
+    assert make(dict(box, ny=16), seed=1).step_graph == (1, 256, True)
     # shapes or choices the graph cannot take step eagerly
     H = make(box, seed=72)
     H.set_step_graph(3, 4)                 # NY not a multiple of 8 * 3
