@@ -704,13 +704,24 @@ def test_full_geometry_fp32_2000_steps_vs_oracle(capsys):
     """The parity contract on the storage-precision geometry: FP32 after 2000
     steps of the 256 x 128 x 256 droplet within 1e-5 relative L2 of the FP64
     oracle in u and C (C - I, the polymer deformation itself, within 1e-4)
-    and mass drift within 1e-6."""
-    e, dval, dref = _droplet256_vs_oracle(REF256_2000, 0, 2000)
+    and mass drift within 1e-6.  FP16 and BF16 storage are reported beside it
+    and held to mass conservation only: their error bounds belong to the
+    5000-step study, and at 2000 steps the droplet is still deforming (D is
+    0.053 against 0.134), so the relative error of D is inflated there (FP16:
+    5.4 % of 0.053, the same absolute error as 3.3 % of 0.134)."""
+    table = []
+    for prec in (0, 1, 2):
+        e, dval, dref = _droplet256_vs_oracle(REF256_2000, prec, 2000)
+        table.append((("fp32", "fp16", "bf16")[prec], e, dval))
     with capsys.disabled():
-        _print_table("vs FP64 oracle after 2000 steps, 256x128x256 (oracle D = %.5f)" % dref, [("fp32", e, dval)])
+        _print_table("vs FP64 oracle after 2000 steps, 256x128x256 (oracle D = %.5f)" % dref, table)
+    e = table[0][1]
     assert e["u"] < 1e-5 and e["C"] < 1e-5, e
     assert e["CmI"] < 1e-4 and e["rhoA"] < 1e-4 and e["rhoB"] < 1e-4, e
     assert e["D"] < 1e-4 and e["mass"] < 1e-6, e
+    for prec in (1, 2):
+        name, e, _ = table[prec]
+        assert e["mass"] < 1e-6, (name, e["mass"])
 
 
 @pytest.mark.slow
