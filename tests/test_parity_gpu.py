@@ -926,7 +926,7 @@ def test_newtonian_droplet_deformation_shapira_haber(capsys):
     R/H = 0.25), evaluated at the droplet's size then.  Measured: D = 0.150
     against 0.120.  The theory assumes Stokes flow; here the droplet Reynolds
     number rho gdot R^2 / eta is 2.7, and inertia raises D (at R = 24 and 32,
-    Re 4 and 5, D = 0.151 and 0.164).  The bound catches a wrong shear
+    Re 3.8 and 5.0, D = 0.151 and 0.164).  The bound catches a wrong shear
     direction, a missing or doubled force term or a wrong viscosity; the
     Stokes-regime test below holds D to 10 %."""
     r = _sheared_newtonian_droplet(128, 64, 128, 16.0, 2.1 / 3.0 * 0.5)
